@@ -1,0 +1,273 @@
+"""Plain FP64 CPU oracle for the periodic QM/MM-Multipole embedding (arXiv 2408.03273).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package; the CUDA library and its Python binding never do, and the
+two share no code.  The arithmetic lives in ``qmmm_oracle.c`` (Obara-Saika integrals, series /
+asymptotic Boys function, literal Ewald loops); this module only compiles it with gcc, marshals
+arrays through ctypes and composes the pieces into the energy terms of Eq. 6 / Eq. 10 and their
+gradients (Eq. 15 and the region-I integral derivatives).
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test against an independent
+result (closed forms, quadrature, limits, invariances, finite differences, direct lattice sums).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qmmm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Ewald mode bits (mirrors the C defines)
+EW_SR, EW_LR, EW_BG, EW_R1, EW_HAT = 1, 2, 4, 8, 16
+EW_ALL = EW_SR | EW_LR | EW_BG | EW_R1 | EW_HAT
+# weights of the 10 stored multipole components in a full (a,b) contraction
+W10 = np.array([1, 1, 1, 1, 1, 2, 2, 1, 2, 1], dtype=np.float64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (plain gcc, OpenMP, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            i, d = ctypes.c_int, ctypes.c_double
+            sig = {
+                "oracle_boys": (None, [i, d, dp]),
+                "oracle_norm_coeffs": (None, [i, ip, ip, ip, dp, dp, dp]),
+                "oracle_int3c_prim": (None, [i, i, d, dp, d, dp, d, dp, dp]),
+                "oracle_vpot": (None, [i, ip, ip, ip, ip, dp, dp, dp, i, dp, dp, dp, i, ip, i, dp]),
+                "oracle_vgrad": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, i, dp, dp, dp, i, dp, dp, dp, dp]),
+                "oracle_enucmm": (d, [i, dp, dp, i, dp, dp, dp, dp, dp, dp]),
+                "oracle_multipoles": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, dp, i, dp, dp]),
+                "oracle_fock_ii": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp]),
+                "oracle_pulay": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp, dp]),
+                "oracle_tensor": (None, [i, d, dp, dp]),
+                "oracle_region1": (i, [i, dp, i, dp, dp, d, i, ip, dp]),
+                "oracle_ewald_phi": (None, [i, dp, i, dp, dp, dp, dp, d, d, d, ip, i, dp]),
+                "oracle_ewald_mm": (None, [i, dp, dp, i, dp, dp, dp, dp, d, d, d, ip, i, dp, dp]),
+                "oracle_tensor_grad_qm": (None, [i, dp, dp, dp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if a is not None else None
+
+
+# ----------------------------------------------------------------------------------------------
+# elementary pieces
+# ----------------------------------------------------------------------------------------------
+
+def boys(nmax: int, T: float) -> np.ndarray:
+    out = np.zeros(nmax + 1)
+    lib().oracle_boys(nmax, float(T), _dp(out))
+    return out
+
+
+def tensor(kind: int, beta: float, d) -> np.ndarray:
+    """20 Taylor tensor components at displacement d = R_j - R_i (kind 0: 1/r, 1: erfc(beta r)/r)."""
+    dd = _d(d)
+    out = np.zeros(20)
+    lib().oracle_tensor(kind, float(beta), _dp(dd), _dp(out))
+    return out
+
+
+def int3c_prim(la, lb, a, A, b, B, kappa, C) -> np.ndarray:
+    out = np.zeros(((la + 1) * (la + 2) // 2) * ((lb + 1) * (lb + 2) // 2))
+    A, B, C = _d(A), _d(B), _d(C)
+    lib().oracle_int3c_prim(la, lb, a, _dp(A), b, _dp(B), float(kappa), _dp(C), _dp(out))
+    return out.reshape((la + 1) * (la + 2) // 2, (lb + 1) * (lb + 2) // 2)
+
+
+class _Basis:
+    def __init__(self, s):
+        self.atom, self.l = _i(s.shell_atom), _i(s.shell_l)
+        self.nprim, self.off = _i(s.shell_nprim), _i(s.shell_prim_offset)
+        self.exps = _d(s.prim_exp)
+        self.ncoef = np.zeros_like(self.exps)
+        lib().oracle_norm_coeffs(len(self.l), _ip(self.l), _ip(self.nprim), _ip(self.off), _dp(self.exps),
+                                 _dp(_d(s.prim_coeff)), _dp(self.ncoef))
+        self.n = len(self.l)
+
+    def args(self):
+        return (self.n, _ip(self.atom), _ip(self.l), _ip(self.nprim), _ip(self.off), _dp(self.exps), _dp(self.ncoef))
+
+
+def norm_coeffs(s) -> np.ndarray:
+    return _Basis(s).ncoef
+
+
+def ewald_rc(s) -> float:
+    return s.ewald_rcut if s.ewald_rcut > 0 else s.cutoff
+
+
+def region1(s):
+    """Region-I images (charge index, shift) with |R_i + L - c| < cutoff, c = QM mean."""
+    qm, mm, box = _d(s.atom_xyz), _d(s.mm_xyz), _d(s.box)
+    cap = max(16, s.nmm * 8)
+    while True:
+        idx = np.zeros(cap, dtype=np.int32)
+        sh = np.zeros((cap, 3))
+        n = lib().oracle_region1(s.natm, _dp(qm), s.nmm, _dp(mm), _dp(box), float(s.cutoff), cap, _ip(idx), _dp(sh))
+        if n <= cap:
+            return idx[:n].copy(), sh[:n].copy()
+        cap = n
+
+
+def region1_charges(s):
+    idx, sh = region1(s)
+    xyz = np.ascontiguousarray(s.mm_xyz[idx] + sh)
+    return idx, xyz, _d(s.mm_q[idx]), _d(s.mm_sigma[idx])
+
+
+def vpot(s, pairs=None, charges=None) -> np.ndarray:
+    """Region-I V (Eq. 9) over all ordered shell pairs (or the listed (A,B) pairs only)."""
+    b = _Basis(s)
+    if charges is None:
+        _, cx, cq, cs = region1_charges(s)
+    else:
+        cx, cq, cs = (_d(c) for c in charges)
+    V = np.zeros((s.nao, s.nao))
+    pr = None if pairs is None else _i(np.asarray(pairs).reshape(-1, 2))
+    npairs = 0 if pr is None else len(pr)
+    lib().oracle_vpot(*b.args(), _dp(_d(s.atom_xyz)), len(cq), _dp(cx), _dp(cq), _dp(cs), npairs, _ip(pr),
+                      s.nao, _dp(V))
+    return V
+
+
+def enucmm(s, charges=None):
+    if charges is None:
+        _, cx, cq, cs = region1_charges(s)
+    else:
+        cx, cq, cs = (_d(c) for c in charges)
+    return lib().oracle_enucmm(s.natm, _dp(_d(s.atom_xyz)), _dp(_d(s.atom_Z)), len(cq), _dp(cx), _dp(cq), _dp(cs),
+                               None, None, None)
+
+
+def multipoles(s, dm=None) -> np.ndarray:
+    b = _Basis(s)
+    dm = _d(s.dm if dm is None else dm)
+    out = np.zeros((s.natm, 10))
+    lib().oracle_multipoles(*b.args(), s.natm, _dp(_d(s.atom_xyz)), _dp(_d(s.atom_Z)), s.nao, _dp(dm), _dp(out))
+    return out
+
+
+def ewald_phi(s, mode: int = EW_ALL) -> np.ndarray:
+    """Generalised potential (20 components) at each QM atom from all MM charges."""
+    out = np.zeros((s.natm, 20))
+    km = _i(s.kmax)
+    lib().oracle_ewald_phi(s.natm, _dp(_d(s.atom_xyz)), s.nmm, _dp(_d(s.mm_xyz)), _dp(_d(s.mm_q)),
+                           _dp(_d(s.mm_sigma)), _dp(_d(s.box)), float(s.cutoff), float(ewald_rc(s)),
+                           float(s.ewald_alpha), _ip(km), mode, _dp(out))
+    return out
+
+
+def ewald_mm(s, M, mode: int = EW_ALL):
+    """MM-side potential (dE/dq) and dE/dR_MM from QM multipoles M[natm,10]."""
+    dq = np.zeros(s.nmm)
+    dR = np.zeros((s.nmm, 3))
+    km = _i(s.kmax)
+    lib().oracle_ewald_mm(s.natm, _dp(_d(s.atom_xyz)), _dp(_d(M)), s.nmm, _dp(_d(s.mm_xyz)), _dp(_d(s.mm_q)),
+                          _dp(_d(s.mm_sigma)), _dp(_d(s.box)), float(s.cutoff), float(ewald_rc(s)),
+                          float(s.ewald_alpha), _ip(km), mode, _dp(dq), _dp(dR))
+    return dq, dR
+
+
+def fock_ii(s, phi) -> np.ndarray:
+    b = _Basis(s)
+    ph = _d(phi)
+    F = np.zeros((s.nao, s.nao))
+    lib().oracle_fock_ii(*b.args(), _dp(_d(s.atom_xyz)), _dp(ph), ph.shape[1], s.nao, _dp(F))
+    return F
+
+
+def multipole_energy(M, phi) -> float:
+    """E_II = sum_j sum_c W_c M_j,c phi_j,c (first 10 components)."""
+    return float(np.sum(W10[None, :] * M * phi[:, :10]))
+
+
+# ----------------------------------------------------------------------------------------------
+# composed energy and gradient
+# ----------------------------------------------------------------------------------------------
+
+def energy(s, dm=None, mode: int = EW_ALL):
+    """Energy terms of E_QM-MM at fixed density: region-I electronic and nuclear parts and the
+    region-II multipole part (Eq. 6 QM-MM lines + Eq. 10)."""
+    dm = s.dm if dm is None else dm
+    V = vpot(s)
+    En = enucmm(s)
+    M = multipoles(s, dm)
+    phi = ewald_phi(s, mode)
+    EI = float(np.sum(dm * V))
+    EII = multipole_energy(M, phi)
+    return {"V": V, "E_I_elec": EI, "E_nuc_mm": En, "E_II": EII, "E": EI + En + EII, "M": M, "phi": phi}
+
+
+def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None):
+    """dE/dR_QM, dE/dR_MM and dE/dq of E_QM-MM at fixed density (outputs are gradients).
+
+    ``charge_subset`` restricts the region-I integral part to the listed region-I entries
+    (indices into the region-I list) -- used to sample large systems; the QM gradient is then
+    partial and only the listed charges' MM gradients are complete."""
+    dm = _d(s.dm if dm is None else dm)
+    b = _Basis(s)
+    idx, cx, cq, cs = region1_charges(s)
+    if charge_subset is not None:
+        sub = np.asarray(charge_subset)
+        idx, cx, cq, cs = idx[sub], np.ascontiguousarray(cx[sub]), cq[sub], cs[sub]
+    n = len(cq)
+    dRqm = np.zeros((s.natm, 3))
+    dC = np.zeros((n, 3))
+    dqc = np.zeros(n)
+    qm = _d(s.atom_xyz)
+    lib().oracle_vgrad(*b.args(), s.natm, _dp(qm), n, _dp(cx), _dp(cq), _dp(cs), s.nao, _dp(dm), _dp(dRqm), _dp(dC),
+                       _dp(dqc))
+    lib().oracle_enucmm(s.natm, _dp(qm), _dp(_d(s.atom_Z)), n, _dp(cx), _dp(cq), _dp(cs), _dp(dRqm), _dp(dC),
+                        _dp(dqc))
+    dRmm = np.zeros((s.nmm, 3))
+    dq = np.zeros(s.nmm)
+    np.add.at(dRmm, idx, dC)
+    np.add.at(dq, idx, dqc)
+    M = multipoles(s, dm)
+    phi = ewald_phi(s, mode)
+    lib().oracle_tensor_grad_qm(s.natm, _dp(_d(M)), _dp(phi), _dp(dRqm))
+    lib().oracle_pulay(*b.args(), _dp(qm), _dp(phi), 20, s.nao, _dp(dm), _dp(dRqm))
+    dq2, dR2 = ewald_mm(s, M, mode)
+    return {"dE_dRqm": dRqm, "dE_dRmm": dRmm + dR2, "dE_dq": dq + dq2, "M": M, "phi": phi}
