@@ -1,0 +1,362 @@
+"""Benchmark of the QM/MM-Multipole hot path on GB300.
+
+A step is one V+forces call at one geometry through the C ABI:
+    qmmm_set_positions -> qmmm_vpot -> qmmm_ewald -> qmmm_forces
+i.e. region I and the region-II potential, the region-I matrix V (Eq. 9), the multipoles and
+E_II (Eq. 6, Eq. 10), and the full gradient (region-I adjoint, tensor and Pulay terms).
+
+Metric: shell-pair x charge integrals/s = (screened shell pairs x region-I charges) per step / step
+time, plus ms per V+forces call; FP64 is the headline (the active-site workload is quoted in FP64)
+and the mixed-precision path is measured beside it with its error against FP64.
+
+Default workload: 60 QM atoms (600 shells, 1560 AOs), 59463 MM charges (TIP3P waters) in a 58 A
+box, cutoff 12 A, alpha 0.3 A^-1, kmax 16 (synthetic, seeded).  Inputs are smaller than L2 so the
+L2 is flushed (256 MiB write) before every timed step, outside the timed interval.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c1|c2|c4]
+N > 1 runs replicas (one per GPU, launched by torch.distributed.run): the path does not shard.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shell-pair x charge integrals/s; ms per V+forces call, mixed vs FP64 at 1e-6"
+UNIT = "integrals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# plain-ALU peaks at the maximum SM clock (2070 MHz, 152 SMs): FP64 2 FMA/clk/SM (the part's
+# 1.25 TFLOP/s FP64 rating), FP32 128 FMA/clk/SM
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def comb(n, k):
+    return math.comb(n, k) if n >= k >= 0 else 0
+
+
+def flops_forward(L):
+    """Algorithmic FLOPs per (primitive pair, charge) of the V sweep: Boys 25+3L, R recursion
+    2 C(L+4,4), Hermite accumulation 2 C(L+3,3), setup 15."""
+    return 25 + 3 * L + 2 * comb(L + 4, 4) + 2 * comb(L + 3, 3) + 15
+
+
+def flops_adjoint(L):
+    """Per (primitive pair, charge) of the adjoint sweep: Boys to L+1 (28+3L), R recursion to L+1
+    2 C(L+5,4), seven contractions 14 C(L+3,3), setup/accumulation/reduction 47."""
+    return 28 + 3 * L + 2 * comb(L + 5, 4) + 14 * comb(L + 3, 3) + 47
+
+
+CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la(la+1)/2 + lb
+
+
+def sweep_flops(info, adjoint):
+    f = flops_adjoint if adjoint else flops_forward
+    return sum(n * info["n_region1"] * f(CLASS_L[c]) for c, n in enumerate(info["n_prim_pairs_class"]))
+
+
+def make_system(name):
+    import workloads
+    return {"c1": workloads.config1_water, "c2": workloads.config2_active_site,
+            "c4": workloads.config4_large_site}[name]()
+
+
+def describe(s, info):
+    A = 0.52917721092
+    return (f"{s.name}: {s.natm} QM atoms, {s.nshell} shells, {s.nao} AOs, {s.nmm} MM charges (TIP3P), "
+            f"{s.box[0] * A:.1f} A box, cutoff {s.cutoff * A:.1f} A, alpha {s.ewald_alpha / A:.2f} A^-1, "
+            f"kmax {s.kmax[0]}, sigma {s.mm_sigma[0] * A:.2f} A; {info['n_shell_pairs']} screened shell pairs, "
+            f"{info['n_region1']} region-I charges")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if len(s) > 3 + k and s[3 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline(s, seconds=10.0, seed=0):
+    """The FP64 oracle on the host cores: V + adjoint for a random sample of shell pairs against
+    all region-I charges (same per-(shell pair, charge) unit as the GPU metric)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    cores = os.cpu_count()
+    idx = oracle.region1(s)[0]
+    nI = len(idx)
+    pairs_all = [(i, j) for i in range(s.nshell) for j in range(i, s.nshell)]
+    k = 2
+    elapsed, units = 0.0, 0
+    while True:
+        pick = rng.choice(len(pairs_all), k, replace=False)
+        pairs = [pairs_all[p] for p in pick]
+        # orient like the GPU planner (higher l first)
+        pairs = [(a, b) if s.shell_l[a] >= s.shell_l[b] else (b, a) for a, b in pairs]
+        t0 = time.perf_counter()
+        oracle.vpot(s, pairs=pairs)
+        oracle.vgrad_pairs(s, pairs)
+        dt = time.perf_counter() - t0
+        elapsed += dt
+        units += k * nI
+        if elapsed >= seconds or k >= len(pairs_all):
+            break
+        k = min(len(pairs_all), max(2 * k, int(k * (seconds - elapsed) / max(dt, 1e-3))))
+    return {"value": units / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{units // nI} random shell pairs x {nI} region-I charges, V + adjoint "
+                      f"(Obara-Saika, FP64, OpenMP), {elapsed:.1f} s; Ewald/multipole work not included"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle as the reference arm (host cores), bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    s = make_system(args.config)
+    per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(s, seconds=per_step, seed=i)
+        if i >= args.warmup:
+            vals.append(cb)
+    value = float(np.mean([v["value"] for v in vals]))
+    import oracle  # noqa: F401
+    nI = len(__import__("oracle").region1(s)[0])
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{s.name} ({s.natm} QM atoms, {s.nao} AOs, {s.nmm} MM charges, {nI} region-I)",
+                      "precision": "fp64", "parallelism": "replicas"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2408_03273_gb300 as q
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    args.warmup = max(3, args.warmup)
+
+    s = make_system(args.config)
+    prec = q.QMMM_MIXED if args.precision == "mixed" else q.QMMM_FP64
+    h = q.Handle(s, precision=prec)
+    stream = torch.cuda.current_stream()
+    h.set_stream(stream)
+    info = h.info
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    qm_d, mm_d, q_d, dm_d = t(s.atom_xyz), t(s.mm_xyz), t(s.mm_q), t(s.dm)
+    nao, natm, nmm = s.nao, s.natm, s.nmm
+    V_d = torch.empty((nao, nao), dtype=torch.float64, device=dev)
+    En_d, EII_d = torch.empty(1, dtype=torch.float64, device=dev), torch.empty(1, dtype=torch.float64, device=dev)
+    M_d = torch.empty((natm, 10), dtype=torch.float64, device=dev)
+    gq_d = torch.empty((natm, 3), dtype=torch.float64, device=dev)
+    gm_d = torch.empty((nmm, 3), dtype=torch.float64, device=dev)
+    gc_d = torch.empty((nmm,), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(hh, qm, mm, qq, dm, V, En, EII, M, gq, gm, gc, rec=None):
+        q.qmmm_set_positions(hh.h, qm, mm, qq)
+        q.qmmm_vpot(hh.h, V, En)
+        if rec is not None:
+            rec["vpot"].append(hh.last_timing()[0])
+        q.qmmm_ewald(hh.h, dm, EII, M, None)
+        q.qmmm_forces(hh.h, dm, gq, gm, gc)
+        if rec is not None:
+            rec["grad"].append(hh.last_timing()[0])
+
+    def timed(hh, K, W):
+        for _ in range(W):
+            step(hh, qm_d, mm_d, q_d, dm_d, V_d, En_d, EII_d, M_d, gq_d, gm_d, gc_d)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        rec = {"vpot": [], "grad": []}
+        total = 0.0
+        for _ in range(K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(hh, qm_d, mm_d, q_d, dm_d, V_d, En_d, EII_d, M_d, gq_d, gm_d, gc_d, rec)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return total / K, rec
+
+    units_per_step = info["n_shell_pairs"] * info["n_region1"]
+    with Clocks(local) as clk:
+        ms, rec = timed(h, args.steps, args.warmup)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * units_per_step / (ms * 1e-3)
+
+    # dominant kernel (region-I sweep) against the plain-ALU roofline
+    t_v, t_g = float(np.mean(rec["vpot"])), float(np.mean(rec["grad"]))
+    dom_adj = t_g >= t_v
+    fl = sweep_flops(info, dom_adj)
+    achieved = fl / ((t_g if dom_adj else t_v) * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS if prec == q.QMMM_FP64 else FP32_PEAK_TFLOPS
+    roof = {"kernel": "vgrad (region-I adjoint sweep)" if dom_adj else "vpot (region-I sweep)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel_ms": t_g if dom_adj else t_v, "other_sweep_ms": t_v if dom_adj else t_g,
+            "peak_note": ("FP64 plain-ALU peak from the unit counts at 2070 MHz (152 SMs x 2 DFMA/clk)"
+                          if prec == q.QMMM_FP64 else "FP32 plain-ALU peak at 2070 MHz (152 SMs x 128 FFMA/clk)"),
+            "flops_per_launch": fl}
+
+    # launches of our kernels per step (claim; the ncu launch list in profiles/ confirms it)
+    ncls = sum(1 for n in info["n_prim_pairs_class"] if n > 0)
+    nI = info["n_region1"]
+    ch_f = math.ceil(nI / (4096)) if nI else 0
+    ch_g = math.ceil(nI / 2560) if nI else 0
+    per_step = (11 + 1) + (ncls * ch_f + 2) + (ncls + 1) + (ncls + ncls * ch_g + 1 + 7 + 1 + 1)
+    launches = per_step * args.steps
+
+    # mixed precision beside FP64 (same GPU, same inputs), with its error against FP64
+    mixed = None
+    if not args.no_mixed and prec == q.QMMM_FP64:
+        V64, gq64, gm64, gc64 = V_d.clone(), gq_d.clone(), gm_d.clone(), gc_d.clone()
+        E64 = h.energy(dm_d).clone()
+        hm = q.Handle(s, precision=q.QMMM_MIXED)
+        hm.set_stream(stream)
+        ms_m, rec_m = timed(hm, args.steps, args.warmup)
+        Em = hm.energy(dm_d)
+        fro = float(torch.linalg.norm(V_d - V64) / torch.linalg.norm(V64))
+        gerr = max(float((gq_d - gq64).abs().max() / gq64.abs().max()),
+                   float((gm_d - gm64).abs().max() / gm64.abs().max()),
+                   float((gc_d - gc64).abs().max() / gc64.abs().max()))
+        escale = float(E64[1].abs() + E64[2].abs() + E64[3].abs())
+        t_vm, t_gm = float(np.mean(rec_m["vpot"])), float(np.mean(rec_m["grad"]))
+        flm = sweep_flops(info, t_gm >= t_vm)
+        ach_m = flm / (max(t_gm, t_vm) * 1e-3) / 1e12
+        mixed = {"value": world * units_per_step / (ms_m * 1e-3), "ms_per_step": ms_m,
+                 "speedup_vs_fp64": ms / ms_m, "vpot_sweep_ms": t_vm, "adjoint_sweep_ms": t_gm,
+                 "rel_fro_err_V": fro, "max_rel_err_forces": gerr,
+                 "rel_err_E": float(abs(Em[0] - E64[0]) / escale),
+                 "roofline": {"bound": "alu", "achieved": ach_m, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": ach_m / FP32_PEAK_TFLOPS}}
+        hm.close()
+
+    # end to end: host (pinned) inputs and outputs, copies inside the timed interval
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()  # noqa: E731
+    qm_h, mm_h, q_h, dm_h = pin(s.atom_xyz), pin(s.mm_xyz), pin(s.mm_q), pin(s.dm)
+    V_h = torch.empty((nao, nao), dtype=torch.float64).pin_memory()
+    En_h, EII_h = torch.empty(1, dtype=torch.float64).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory()
+    M_h = torch.empty((natm, 10), dtype=torch.float64).pin_memory()
+    gq_h = torch.empty((natm, 3), dtype=torch.float64).pin_memory()
+    gm_h = torch.empty((nmm, 3), dtype=torch.float64).pin_memory()
+    gc_h = torch.empty((nmm,), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        step(h, qm_h, mm_h, q_h, dm_h, V_h, En_h, EII_h, M_h, gq_h, gm_h, gc_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne = max(3, args.steps // 2)
+    for _ in range(ne):
+        step(h, qm_h, mm_h, q_h, dm_h, V_h, En_h, EII_h, M_h, gq_h, gm_h, gc_h)
+    torch.cuda.synchronize()
+    ms_e2e = (time.perf_counter() - t0) * 1e3 / ne
+    h2d = 8 * (3 * natm + 3 * nmm + nmm + 2 * nao * nao)  # positions, charges, density (ewald + forces)
+    d2h = 8 * (nao * nao + 1 + 1 + 10 * natm + 3 * natm + 3 * nmm + nmm)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == q.QMMM_FP64 else "f32+f64",
+           "data": "synthetic (seeded TIP3P water box + random active-site QM region and basis)",
+           "config": {"workload": describe(s, info), "precision": args.precision,
+                      "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "units_per_step": units_per_step},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+           "e2e": {"value": world * units_per_step / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+    if mixed:
+        out["mixed"] = mixed
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(s, seconds=12.0)
+    h.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * qmmm.h -- C ABI of the GB300 (sm_103a) implementation of the data-parallel hot path of the
+ * periodic QM/MM-Multipole electrostatic embedding (arXiv 2408.03273).
+ *
+ * The calls follow the energy partition of Eq. 1, E = E_QM + E_QM-MM + E_MM; this library owns
+ * E_QM-MM at a fixed one-body density matrix gamma and its gradient:
+ *
+ *   E_QM-MM = sum_{mu nu} gamma_{mu nu} V_{mu nu}          region-I electronic term, Eq. 9
+ *           + E_nuc_mm                                     region-I nuclear-MM term
+ *           + E_II                                         multipole terms of Eq. 6 (QM-MM
+ *                                                          lines) plus the Gaussian-charge
+ *                                                          correction of Eq. 10
+ *
+ *   V_{mu nu} = - sum_{i in I} q_i <mu nu | phi_i>,  phi_i a normalised Gaussian of exponent
+ *   1/sigma_i^2 (sigma_i <= 0: point charge, Eq. 2).
+ *   E_II = sum_j [Q_j v_j + mu_j . v_j,a + theta_j : v_j,ab] with Mulliken multipoles (SI,
+ *   "Multipolar Ewald") and the potential v of region II built from the Ewald tensors psi, minus
+ *   the point tensors T over region I, minus the screened tensors T-hat over region II.
+ *
+ * Region I (Sec. "Error Control via Charge-Octupole Estimation") is the set of MM images with
+ * |R_i + L - c| < cutoff, c the unweighted mean of the QM positions.  Ewald (SI): real-space
+ * erfc sum over images within ewald_rcut, reciprocal sum over the cube max|n_c| <= kmax_c,
+ * n != 0, G = 2 pi n / box, tin-foil boundary, neutralising background -pi/(V alpha^2).
+ *
+ * Conventions
+ *   - Atomic units (bohr, hartree, elementary charge).  Orthorhombic box.
+ *   - Cartesian Gaussian shells, l <= 3, 1..16 primitives; raw coefficients are normalised by
+ *     the library (each primitive normalises its x^l component; the contraction is
+ *     renormalised; the same factor multiplies every Cartesian component).  AO order: shells
+ *     in input order, components lexicographic (xx, xy, xz, yy, yz, zz).
+ *   - Matrices are nao x nao, row-major, FP64.  Gradients are dE/dX (not forces).
+ *   - Multipoles per atom (10): Q, mu_x, mu_y, mu_z, theta_xx, theta_xy, theta_xz, theta_yy,
+ *     theta_yz, theta_zz (theta is the non-traceless second moment).
+ *   - Pointers: every array argument may be host or device memory (detected per call with
+ *     cudaPointerGetAttributes).  Host outputs are written before the call returns; device
+ *     outputs are written on the handle's stream (the call still synchronises that stream
+ *     before returning).  Inputs are copied; the caller keeps ownership of everything it
+ *     passes.  Outputs are caller-allocated.
+ *   - Errors: every call returns QMMM_OK (0) or a negative QMMM_ERR_* code; on error, outputs
+ *     are left untouched or partially written and the handle stays usable unless the code is
+ *     QMMM_ERR_CUDA.  qmmm_strerror() gives a message, qmmm_last_error() the last detail.
+ *   - Threading: a handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef QMMM_H
+#define QMMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* QM nucleus: position (bohr) and nuclear charge (enters Q_j, SI first equation). */
+typedef struct { double xyz[3]; double Z; } qmmm_atom;
+/* Cartesian shell on atom `atom` with angular momentum l and primitives
+ * [prim_offset, prim_offset + nprim) of the primitive array. */
+typedef struct { int atom; int l; int nprim; int prim_offset; } qmmm_shell;
+/* Primitive Gaussian: exponent (bohr^-2) and raw contraction coefficient. */
+typedef struct { double exponent; double coeff; } qmmm_primitive;
+/* MM charge: position (bohr), charge (e) and Gaussian width sigma (bohr); exponent 1/sigma^2. */
+typedef struct { double xyz[3]; double q; double sigma; } qmmm_charge;
+
+enum {
+    QMMM_OK = 0,
+    QMMM_ERR_ARG = -1,           /* invalid argument (null handle, sizes, unsupported option) */
+    QMMM_ERR_ALLOC = -2,         /* device or host allocation failed */
+    QMMM_ERR_CUDA = -3,          /* a CUDA call failed; see qmmm_last_error() */
+    QMMM_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out */
+    QMMM_ERR_UNSUPPORTED_L = -5, /* a shell with l > 3 or more than 16 primitives */
+    QMMM_ERR_STATE = -6          /* call order violated (e.g. E_I requested before qmmm_vpot) */
+};
+
+enum { QMMM_FP64 = 0, QMMM_MIXED = 1 };
+
+/* Create-time options.  A NULL pointer selects the defaults in brackets. */
+typedef struct {
+    int precision;      /* QMMM_FP64 or QMMM_MIXED [QMMM_FP64]                                 */
+    double screen_tol;  /* primitive pairs with |c_a c_b| K_AB (pi/p)^{3/2} below screen_tol
+                           times the largest value are dropped; 0 disables; < 0: [1e-14]       */
+    int region_mode;    /* 0: sphere of radius cutoff about the QM centre [0]                  */
+    double ewald_rcut;  /* Ewald real-space cutoff (bohr); <= 0: equal to cutoff [cutoff]       */
+    int kmax[3];        /* reciprocal cube half-widths; 0: chosen so that exp(-G^2/4alpha^2)
+                           < 1e-8 at the edge                                                  */
+    int full_cell_test; /* reserved, must be 0                                                 */
+} qmmm_options;
+
+typedef struct qmmm_handle qmmm_handle;
+
+/* Counts describing the plan of a handle (after the last qmmm_set_positions). */
+typedef struct {
+    int nao, natm, nshell, nmm;
+    long long n_shell_pairs;    /* screened shell pairs (i <= j)                               */
+    long long n_prim_pairs;     /* screened primitive pairs                                    */
+    int n_region1;              /* region-I MM images                                          */
+    int n_gvec;                 /* reciprocal vectors in the half space (each stands for +-G) */
+    int n_sigma_classes;        /* distinct Gaussian widths                                   */
+    int precision;
+    long long n_prim_pairs_class[10]; /* screened primitive pairs per angular class (l_A >= l_B),
+                                         class index l_A (l_A + 1)/2 + l_B                        */
+    long long n_shell_pairs_class[10];
+} qmmm_info_t;
+
+/* Copies the inputs, normalises the basis, builds the angular-class-sorted, overlap-screened
+ * shell-pair list, the reciprocal vectors and the Boys tables, uploads everything to the
+ * current CUDA device and runs qmmm_set_positions with the given positions.
+ *   atoms[natm], shells[nshell], prims[nprim], charges[nmm] (host memory),
+ *   box[3] (bohr), cutoff = region-I radius R_cut (bohr), ewald_alpha (bohr^-1, the erfc
+ *   splitting parameter), opts may be NULL.  *out receives the handle. */
+int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int nshell,
+                const qmmm_primitive *prims, int nprim, const qmmm_charge *charges, int nmm,
+                const double box[3], double cutoff, double ewald_alpha,
+                const qmmm_options *opts, qmmm_handle **out);
+
+/* Stream for all later work of the handle (a cudaStream_t passed as void*; NULL = legacy). */
+int qmmm_set_stream(qmmm_handle *h, void *stream);
+
+/* Switch the V / adjoint arithmetic: QMMM_FP64, or QMMM_MIXED (FP32 Hermite recursions and
+ * charge sweeps with FP32 tile sums folded into FP64; Ewald sums and final reductions stay
+ * FP64). */
+int qmmm_set_precision(qmmm_handle *h, int precision);
+
+/* New geometry (MD step): qm_xyz[natm*3], mm_xyz[nmm*3] (bohr), mm_q[nmm] (NULL keeps the
+ * charges).  Rebuilds region I and the gamma-independent region-II potential v (20 Taylor
+ * components per QM atom, Eq. 6 QM-MM lines + Eq. 10). */
+int qmmm_set_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, const double *mm_q);
+
+/* Region-I one-electron matrix V[nao*nao] of Eq. 9 (symmetric) and, if E_nuc_mm != NULL, the
+ * region-I nuclear-MM energy sum_j sum_{i in I} Z_j q_i erf(r/sigma_i)/r.  V stays cached in
+ * the handle for qmmm_energy. */
+int qmmm_vpot(qmmm_handle *h, double *V, double *E_nuc_mm);
+
+/* Multipole part at density dm[nao*nao] (symmetric): E_II (scalar), optionally the Mulliken
+ * multipoles multipoles[natm*10] and the region-II Fock term F_II[nao*nao] of Eqs. 11-14,
+ * F_{mu nu} = -1/2 sum_j sum_c v_j,c [d_{mu in j} + d_{nu in j}] <mu|O_c(r - R_j)|nu>. */
+int qmmm_ewald(qmmm_handle *h, const double *dm, double *E_II, double *multipoles, double *F_II);
+
+/* Total E_QM-MM at dm: E[4] = {E_total, E_I_elec = sum gamma V, E_nuc_mm, E_II}.  Needs a
+ * prior qmmm_vpot at the current geometry (QMMM_ERR_STATE otherwise). */
+int qmmm_energy(qmmm_handle *h, const double *dm, double *E);
+
+/* Gradient of E_QM-MM at fixed dm (region-I integral derivatives, nuclear-MM term, tensor
+ * derivatives, and the multipole Pulay term of Eq. 15): dE_dRqm[natm*3], dE_dRmm[nmm*3],
+ * dE_dq[nmm].  Any output may be NULL. */
+int qmmm_forces(qmmm_handle *h, const double *dm, double *dE_dRqm, double *dE_dRmm, double *dE_dq);
+
+/* Plan counts. */
+int qmmm_get_info(const qmmm_handle *h, qmmm_info_t *info);
+int qmmm_nao(const qmmm_handle *h);
+
+/* Region-II potential v[natm*20] at the current geometry (components: scalar, 3 first, 6
+ * second and 10 third derivatives in the order xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz). */
+int qmmm_get_potential(qmmm_handle *h, double *v);
+
+/* Timing of the kernels launched by the last call (milliseconds, CUDA events on the handle's
+ * stream): out[0] region-I V or its adjoint sweep, out[1] everything else in the call.
+ * Returns the number of values written (2). */
+int qmmm_last_timing(const qmmm_handle *h, double *out);
+
+void qmmm_destroy(qmmm_handle *h);
+const char *qmmm_strerror(int code);
+const char *qmmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMMM_H */

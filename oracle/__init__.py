@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -56,7 +56,7 @@ def lib():
                 "oracle_norm_coeffs": (None, [i, ip, ip, ip, dp, dp, dp]),
                 "oracle_int3c_prim": (None, [i, i, d, dp, d, dp, d, dp, dp]),
                 "oracle_vpot": (None, [i, ip, ip, ip, ip, dp, dp, dp, i, dp, dp, dp, i, ip, i, dp]),
-                "oracle_vgrad": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, i, dp, dp, dp, i, dp, dp, dp, dp]),
+                "oracle_vgrad": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, i, dp, dp, dp, i, dp, i, ip, dp, dp, dp]),
                 "oracle_enucmm": (d, [i, dp, dp, i, dp, dp, dp, dp, dp, dp]),
                 "oracle_multipoles": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, dp, i, dp, dp]),
                 "oracle_fock_ii": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp]),
@@ -64,7 +64,7 @@ def lib():
                 "oracle_tensor": (None, [i, d, dp, dp]),
                 "oracle_region1": (i, [i, dp, i, dp, dp, d, i, ip, dp]),
                 "oracle_ewald_phi": (None, [i, dp, i, dp, dp, dp, dp, d, d, d, ip, i, dp]),
-                "oracle_ewald_mm": (None, [i, dp, dp, i, dp, dp, dp, dp, d, d, d, ip, i, dp, dp]),
+                "oracle_ewald_mm": (None, [i, dp, dp, i, dp, dp, dp, dp, d, d, d, ip, i, ctypes.c_void_p, dp, dp]),
                 "oracle_tensor_grad_qm": (None, [i, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
@@ -199,14 +199,20 @@ def ewald_phi(s, mode: int = EW_ALL) -> np.ndarray:
     return out
 
 
-def ewald_mm(s, M, mode: int = EW_ALL):
-    """MM-side potential (dE/dq) and dE/dR_MM from QM multipoles M[natm,10]."""
+def ewald_mm(s, M, mode: int = EW_ALL, mm_subset=None):
+    """MM-side potential (dE/dq) and dE/dR_MM from QM multipoles M[natm,10]; with ``mm_subset``
+    only the listed MM charges are evaluated (the rest stay zero)."""
     dq = np.zeros(s.nmm)
     dR = np.zeros((s.nmm, 3))
     km = _i(s.kmax)
+    only = None
+    if mm_subset is not None:
+        only = np.zeros(s.nmm, dtype=np.uint8)
+        only[np.asarray(mm_subset)] = 1
     lib().oracle_ewald_mm(s.natm, _dp(_d(s.atom_xyz)), _dp(_d(M)), s.nmm, _dp(_d(s.mm_xyz)), _dp(_d(s.mm_q)),
                           _dp(_d(s.mm_sigma)), _dp(_d(s.box)), float(s.cutoff), float(ewald_rc(s)),
-                          float(s.ewald_alpha), _ip(km), mode, _dp(dq), _dp(dR))
+                          float(s.ewald_alpha), _ip(km), mode,
+                          None if only is None else ctypes.c_void_p(only.ctypes.data), _dp(dq), _dp(dR))
     return dq, dR
 
 
@@ -240,12 +246,13 @@ def energy(s, dm=None, mode: int = EW_ALL):
     return {"V": V, "E_I_elec": EI, "E_nuc_mm": En, "E_II": EII, "E": EI + En + EII, "M": M, "phi": phi}
 
 
-def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None):
+def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None, mm_subset=None):
     """dE/dR_QM, dE/dR_MM and dE/dq of E_QM-MM at fixed density (outputs are gradients).
 
     ``charge_subset`` restricts the region-I integral part to the listed region-I entries
-    (indices into the region-I list) -- used to sample large systems; the QM gradient is then
-    partial and only the listed charges' MM gradients are complete."""
+    (indices into the region-I list) and ``mm_subset`` the Ewald MM-side sums to the listed MM
+    charges -- used to sample large systems; the QM gradient is then partial and only the listed
+    charges' MM gradients are complete."""
     dm = _d(s.dm if dm is None else dm)
     b = _Basis(s)
     idx, cx, cq, cs = region1_charges(s)
@@ -257,8 +264,8 @@ def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None):
     dC = np.zeros((n, 3))
     dqc = np.zeros(n)
     qm = _d(s.atom_xyz)
-    lib().oracle_vgrad(*b.args(), s.natm, _dp(qm), n, _dp(cx), _dp(cq), _dp(cs), s.nao, _dp(dm), _dp(dRqm), _dp(dC),
-                       _dp(dqc))
+    lib().oracle_vgrad(*b.args(), s.natm, _dp(qm), n, _dp(cx), _dp(cq), _dp(cs), s.nao, _dp(dm), 0, None, _dp(dRqm),
+                       _dp(dC), _dp(dqc))
     lib().oracle_enucmm(s.natm, _dp(qm), _dp(_d(s.atom_Z)), n, _dp(cx), _dp(cq), _dp(cs), _dp(dRqm), _dp(dC),
                         _dp(dqc))
     dRmm = np.zeros((s.nmm, 3))
@@ -269,5 +276,18 @@ def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None):
     phi = ewald_phi(s, mode)
     lib().oracle_tensor_grad_qm(s.natm, _dp(_d(M)), _dp(phi), _dp(dRqm))
     lib().oracle_pulay(*b.args(), _dp(qm), _dp(phi), 20, s.nao, _dp(dm), _dp(dRqm))
-    dq2, dR2 = ewald_mm(s, M, mode)
+    dq2, dR2 = ewald_mm(s, M, mode, mm_subset=mm_subset)
     return {"dE_dRqm": dRqm, "dE_dRmm": dRmm + dR2, "dE_dq": dq + dq2, "M": M, "phi": phi}
+
+
+def vgrad_pairs(s, pairs, dm=None):
+    """Region-I gradient pieces restricted to the listed ordered shell pairs (timing samples)."""
+    dm = _d(s.dm if dm is None else dm)
+    b = _Basis(s)
+    _, cx, cq, cs = region1_charges(s)
+    pr = _i(np.asarray(pairs).reshape(-1, 2))
+    n = len(cq)
+    dRqm, dC, dqc = np.zeros((s.natm, 3)), np.zeros((n, 3)), np.zeros(n)
+    lib().oracle_vgrad(*b.args(), s.natm, _dp(_d(s.atom_xyz)), n, _dp(cx), _dp(cq), _dp(cs), s.nao, _dp(dm), len(pr),
+                       _ip(pr), _dp(dRqm), _dp(dC), _dp(dqc))
+    return dRqm, dC, dqc

@@ -257,8 +257,11 @@ void oracle_vpot(int nshell, const int *shell_atom, const int *shell_l, const in
 void oracle_vgrad(int nshell, const int *shell_atom, const int *shell_l, const int *shell_nprim,
                   const int *shell_off, const double *exps, const double *ncoef, int natm,
                   const double *qm_xyz, int nchg, const double *c_xyz, const double *c_q,
-                  const double *c_sigma, int nao, const double *dm, double *dRqm, double *dC, double *dq)
+                  const double *c_sigma, int nao, const double *dm, int npairs, const int *pairs,
+                  double *dRqm, double *dC, double *dq)
 {
+    /* pairs != NULL: only the listed ordered shell pairs contribute (a sampling convenience;
+     * the full gradient sums every ordered pair). */
     int *aoff = (int *)malloc(sizeof(int) * nshell);
     ao_offsets(nshell, shell_l, aoff);
     int nthr = 1;
@@ -275,9 +278,11 @@ void oracle_vgrad(int nshell, const int *shell_atom, const int *shell_l, const i
 #endif
         double *myR = accR + (size_t)tid * natm * 3, *myC = accC + (size_t)tid * nchg * 4;
         os_work *w = (os_work *)malloc(sizeof(os_work));
+        long ntask = pairs ? npairs : (long)nshell * nshell;
 #pragma omp for schedule(dynamic, 1)
-        for (long t = 0; t < (long)nshell * nshell; t++) {
-            int sA = (int)(t / nshell), sB = (int)(t % nshell);
+        for (long t = 0; t < ntask; t++) {
+            int sA = pairs ? pairs[2 * t] : (int)(t / nshell);
+            int sB = pairs ? pairs[2 * t + 1] : (int)(t % nshell);
             int la = shell_l[sA], lb = shell_l[sB];
             int ca[36][3], cb[36][3];
             cart_comp(la, ca); cart_comp(lb, cb);
@@ -761,8 +766,10 @@ void oracle_ewald_phi(int natm, const double *qm_xyz, int nmm, const double *mm_
  * where Psi is the same combination of psi, T and T-hat as in oracle_ewald_phi. */
 void oracle_ewald_mm(int natm, const double *qm_xyz, const double *M, int nmm, const double *mm_xyz,
                      const double *q, const double *sigma, const double *box, double rcut, double ewald_rc,
-                     double kappa, const int *kmax, int mode, double *dq, double *dR)
+                     double kappa, const int *kmax, int mode, const unsigned char *only, double *dq, double *dR)
 {
+    /* only != NULL: evaluate the MM side for the charges with only[i] != 0 (the others are left
+     * untouched); a sampling convenience for large systems, same arithmetic. */
     double c[3], V = box[0] * box[1] * box[2];
     qm_centre(natm, qm_xyz, c);
     int mrc[3], mr1[3];
@@ -776,6 +783,7 @@ void oracle_ewald_mm(int natm, const double *qm_xyz, const double *M, int nmm, c
     static const int P2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
 #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < nmm; i++) {
+        if (only && !only[i]) continue;
         double T[20], pot = 0.0, fld[3] = {0, 0, 0};
         for (int j = 0; j < natm; j++) {
             const double *Mj = M + 10 * j;
@@ -822,7 +830,8 @@ void oracle_ewald_mm(int natm, const double *qm_xyz, const double *M, int nmm, c
     if (mode & EW_BG) {
         double Qt = 0.0;
         for (int j = 0; j < natm; j++) Qt += M[10 * j];
-        for (int i = 0; i < nmm; i++) dq[i] += -OR_PI / (V * kappa * kappa) * Qt;
+        for (int i = 0; i < nmm; i++)
+            if (!only || only[i]) dq[i] += -OR_PI / (V * kappa * kappa) * Qt;
     }
     if (mode & EW_LR) {
         /* A(G) = sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G);
@@ -851,6 +860,7 @@ void oracle_ewald_mm(int natm, const double *qm_xyz, const double *M, int nmm, c
         }
 #pragma omp parallel for schedule(dynamic, 64)
         for (int i = 0; i < nmm; i++) {
+            if (only && !only[i]) continue;
             double pot = 0.0, fr[3] = {0, 0, 0};
             for (int g = 0; g < nG; g++) {
                 if (Gv[4 * g + 3] == 0.0) continue;

@@ -1,0 +1,38 @@
+"""GB300 (sm_103a) implementation of the data-parallel hot path of the periodic QM/MM-Multipole
+electrostatic embedding (arXiv 2408.03273): the region-I one-electron matrix over
+Gaussian-smeared MM charges (Eq. 9), the multipolar Ewald coupling between QM multipoles and MM
+charges (Eq. 6 QM-MM lines, Eq. 10) and their adjoint (Eq. 15 and the region-I integral
+derivatives).
+
+The compute lives in the C-ABI library ``_build/libqmmm_gb300.so`` (include/qmmm.h).  This
+package is its thin binding: ``_lib`` exposes the C entry points under the same names,
+``Handle`` bundles a handle with a workload, and ``QMMMEnergy`` is the torch.autograd.Function
+whose backward is the hand-written adjoint kernel.
+"""
+from __future__ import annotations
+
+from . import build  # noqa: F401
+from ._lib import (  # noqa: F401
+    EXPORTS,
+    QMMM_FP64,
+    QMMM_MIXED,
+    QMMMError,
+    load,
+    library_path,
+    qmmm_create,
+    qmmm_destroy,
+    qmmm_energy,
+    qmmm_ewald,
+    qmmm_forces,
+    qmmm_get_info,
+    qmmm_get_potential,
+    qmmm_last_error,
+    qmmm_last_timing,
+    qmmm_nao,
+    qmmm_set_positions,
+    qmmm_set_precision,
+    qmmm_set_stream,
+    qmmm_strerror,
+    qmmm_vpot,
+)
+from .handle import Handle, QMMMEnergy  # noqa: F401

@@ -1,0 +1,266 @@
+"""ctypes binding of include/qmmm.h: the same entry points, argument marshalling only.
+
+Every array argument may be a numpy array (host) or a torch tensor (host or CUDA); it must be
+float64 and C-contiguous.  Outputs that the caller does not pass are allocated here (numpy on
+the host by default, or torch tensors on a given device).  The library does all arithmetic on
+the GPU; if it cannot be loaded this module raises -- there is no other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+
+QMMM_FP64, QMMM_MIXED = 0, 1
+ERRORS = {0: "QMMM_OK", -1: "QMMM_ERR_ARG", -2: "QMMM_ERR_ALLOC", -3: "QMMM_ERR_CUDA", -4: "QMMM_ERR_TIMEOUT",
+          -5: "QMMM_ERR_UNSUPPORTED_L", -6: "QMMM_ERR_STATE"}
+
+
+class QmmmAtom(ctypes.Structure):
+    _fields_ = [("xyz", c_double * 3), ("Z", c_double)]
+
+
+class QmmmShell(ctypes.Structure):
+    _fields_ = [("atom", c_int), ("l", c_int), ("nprim", c_int), ("prim_offset", c_int)]
+
+
+class QmmmPrimitive(ctypes.Structure):
+    _fields_ = [("exponent", c_double), ("coeff", c_double)]
+
+
+class QmmmCharge(ctypes.Structure):
+    _fields_ = [("xyz", c_double * 3), ("q", c_double), ("sigma", c_double)]
+
+
+class QmmmOptions(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("screen_tol", c_double), ("region_mode", c_int), ("ewald_rcut", c_double),
+                ("kmax", c_int * 3), ("full_cell_test", c_int)]
+
+
+class QmmmInfo(ctypes.Structure):
+    _fields_ = [("nao", c_int), ("natm", c_int), ("nshell", c_int), ("nmm", c_int), ("n_shell_pairs", c_ll),
+                ("n_prim_pairs", c_ll), ("n_region1", c_int), ("n_gvec", c_int), ("n_sigma_classes", c_int),
+                ("precision", c_int), ("n_prim_pairs_class", c_ll * 10), ("n_shell_pairs_class", c_ll * 10)]
+
+
+class QMMMError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        detail = _L.qmmm_last_error().decode() if _L is not None else ""
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({detail})")
+
+
+_L = None
+
+EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
+           "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
+           "qmmm_destroy", "qmmm_strerror", "qmmm_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load the sm_103a library (building it in-tree first if the sources are newer)."""
+    global _L
+    if _L is not None:
+        return _L
+    if build_if_needed and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"CUDA library {_build.LIB} is missing; run paper_2408_03273_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    sig = {
+        "qmmm_create": (c_int, [P(QmmmAtom), c_int, P(QmmmShell), c_int, P(QmmmPrimitive), c_int, P(QmmmCharge), c_int,
+                                P(c_double), c_double, c_double, P(QmmmOptions), P(c_void_p)]),
+        "qmmm_set_stream": (c_int, [c_void_p, c_void_p]),
+        "qmmm_set_precision": (c_int, [c_void_p, c_int]),
+        "qmmm_set_positions": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+        "qmmm_vpot": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "qmmm_ewald": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "qmmm_energy": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "qmmm_forces": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "qmmm_get_info": (c_int, [c_void_p, P(QmmmInfo)]),
+        "qmmm_nao": (c_int, [c_void_p]),
+        "qmmm_get_potential": (c_int, [c_void_p, c_void_p]),
+        "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
+        "qmmm_destroy": (None, [c_void_p]),
+        "qmmm_strerror": (ctypes.c_char_p, [c_int]),
+        "qmmm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _L = L
+    return L
+
+
+def _ptr(x):
+    """Address of a float64 C-contiguous numpy array or torch tensor (host or device); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be float64 and C-contiguous")
+        return c_void_p(x.ctypes.data)
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be float64 and contiguous")
+        return c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise QMMMError(rc, where)
+
+
+def _out(x, shape, like):
+    if x is not None:
+        return x
+    if like is not None and not isinstance(like, np.ndarray):
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=like.device)
+    return np.empty(shape)
+
+
+# ------------------------------------------------------------------------------------------------
+# entry points (names of the C ABI)
+# ------------------------------------------------------------------------------------------------
+
+def qmmm_create(atom_xyz, atom_Z, shell_atom, shell_l, shell_nprim, shell_prim_offset, prim_exp, prim_coeff,
+                mm_xyz, mm_q, mm_sigma, box, cutoff, ewald_alpha, precision=QMMM_FP64, screen_tol=-1.0,
+                ewald_rcut=0.0, kmax=(0, 0, 0)):
+    """Create a handle from host arrays (numpy); returns the opaque handle (int)."""
+    L = load()
+    atom_xyz = np.asarray(atom_xyz, dtype=np.float64).reshape(-1, 3)
+    natm = len(atom_xyz)
+    atoms = (QmmmAtom * natm)()
+    for j in range(natm):
+        atoms[j].xyz[:] = [float(v) for v in atom_xyz[j]]
+        atoms[j].Z = float(atom_Z[j])
+    nshell = len(shell_l)
+    shells = (QmmmShell * nshell)()
+    for s in range(nshell):
+        shells[s].atom, shells[s].l = int(shell_atom[s]), int(shell_l[s])
+        shells[s].nprim, shells[s].prim_offset = int(shell_nprim[s]), int(shell_prim_offset[s])
+    nprim = len(prim_exp)
+    prims = (QmmmPrimitive * nprim)()
+    for k in range(nprim):
+        prims[k].exponent, prims[k].coeff = float(prim_exp[k]), float(prim_coeff[k])
+    mm_xyz = np.asarray(mm_xyz, dtype=np.float64).reshape(-1, 3)
+    nmm = len(mm_xyz)
+    chg = (QmmmCharge * max(nmm, 1))()
+    for i in range(nmm):
+        chg[i].xyz[:] = [float(v) for v in mm_xyz[i]]
+        chg[i].q, chg[i].sigma = float(mm_q[i]), float(mm_sigma[i])
+    opts = QmmmOptions()
+    opts.precision, opts.screen_tol, opts.region_mode = int(precision), float(screen_tol), 0
+    opts.ewald_rcut = float(ewald_rcut)
+    opts.kmax[:] = [int(k) for k in kmax]
+    opts.full_cell_test = 0
+    bx = (c_double * 3)(*[float(b) for b in box])
+    h = c_void_p()
+    _check(L.qmmm_create(atoms, natm, shells, nshell, prims, nprim, chg, nmm, bx, float(cutoff), float(ewald_alpha),
+                         ctypes.byref(opts), ctypes.byref(h)), "qmmm_create")
+    return h.value
+
+
+def qmmm_set_stream(h, stream):
+    """stream: a torch.cuda.Stream, an integer cudaStream_t, or None (legacy stream)."""
+    s = getattr(stream, "cuda_stream", stream)
+    _check(load().qmmm_set_stream(h, c_void_p(s) if s else None), "qmmm_set_stream")
+
+
+def qmmm_set_precision(h, precision):
+    _check(load().qmmm_set_precision(h, int(precision)), "qmmm_set_precision")
+
+
+def qmmm_set_positions(h, qm_xyz, mm_xyz, mm_q=None):
+    _check(load().qmmm_set_positions(h, _ptr(qm_xyz), _ptr(mm_xyz), _ptr(mm_q)), "qmmm_set_positions")
+
+
+def qmmm_nao(h):
+    return load().qmmm_nao(h)
+
+
+def qmmm_get_info(h):
+    info = QmmmInfo()
+    _check(load().qmmm_get_info(h, ctypes.byref(info)), "qmmm_get_info")
+    out = {}
+    for f, _ in QmmmInfo._fields_:
+        v = getattr(info, f)
+        out[f] = list(v) if f.endswith("_class") else v
+    return out
+
+
+def qmmm_vpot(h, V=None, E_nuc_mm=None, like=None):
+    """Region-I V (nao x nao) and the nuclear-MM energy; returns (V, E_nuc_mm)."""
+    n = qmmm_nao(h)
+    V = _out(V, (n, n), like)
+    E = _out(E_nuc_mm, (1,), like)
+    _check(load().qmmm_vpot(h, _ptr(V), _ptr(E)), "qmmm_vpot")
+    return V, E
+
+
+def qmmm_ewald(h, dm, E_II=None, multipoles=None, F_II=None, want_F=False):
+    info = qmmm_get_info(h)
+    E = _out(E_II, (1,), dm)
+    M = _out(multipoles, (info["natm"], 10), dm)
+    F = F_II if F_II is not None else (_out(None, (info["nao"], info["nao"]), dm) if want_F else None)
+    _check(load().qmmm_ewald(h, _ptr(dm), _ptr(E), _ptr(M), _ptr(F)), "qmmm_ewald")
+    return E, M, F
+
+
+def qmmm_energy(h, dm, E=None):
+    """E = [E_total, E_I_elec, E_nuc_mm, E_II]."""
+    E = _out(E, (4,), dm)
+    _check(load().qmmm_energy(h, _ptr(dm), _ptr(E)), "qmmm_energy")
+    return E
+
+
+def qmmm_forces(h, dm, dE_dRqm=None, dE_dRmm=None, dE_dq=None):
+    info = qmmm_get_info(h)
+    gq = _out(dE_dRqm, (info["natm"], 3), dm)
+    gm = _out(dE_dRmm, (max(info["nmm"], 0), 3), dm)
+    gc = _out(dE_dq, (max(info["nmm"], 0),), dm)
+    _check(load().qmmm_forces(h, _ptr(dm), _ptr(gq), _ptr(gm), _ptr(gc)), "qmmm_forces")
+    return gq, gm, gc
+
+
+def qmmm_get_potential(h, v=None, like=None):
+    info = qmmm_get_info(h)
+    v = _out(v, (info["natm"], 20), like)
+    _check(load().qmmm_get_potential(h, _ptr(v)), "qmmm_get_potential")
+    return v
+
+
+def qmmm_last_timing(h):
+    out = (c_double * 2)()
+    load().qmmm_last_timing(h, out)
+    return float(out[0]), float(out[1])
+
+
+def qmmm_destroy(h):
+    if h:
+        load().qmmm_destroy(h)
+
+
+def qmmm_strerror(code):
+    return load().qmmm_strerror(int(code)).decode()
+
+
+def qmmm_last_error():
+    return load().qmmm_last_error().decode()

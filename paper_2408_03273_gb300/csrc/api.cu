@@ -1,0 +1,868 @@
+// api.cu -- host planner and the C ABI of include/qmmm.h.
+//
+// Planner (qmmm_create): normalise the contracted Cartesian basis, build the shell-pair list
+// (l_A >= l_B) sorted by angular class and screened at the primitive-pair level by
+// |c_a c_b| K_AB (pi/p)^{3/2}, order the MM charges by Gaussian width and spatial cell (so
+// region-I images come out grouped by width, which lets the kernels hoist
+// sqrt(kappa/(p+kappa)) out of the charge loop), tabulate the Boys function for the FP64 and
+// FP32 kernels, and write the reciprocal prefactors 2 g(G) = 2 (4 pi/V) exp(-G^2/4 alpha^2)/G^2.
+// Per geometry (qmmm_set_positions): region I by an order-preserving device compaction, then the
+// region-II potential v (20 components per QM atom).  All arithmetic on the path runs in the
+// kernels; the host only plans, copies and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "qmmm_internal.h"
+
+using namespace qmmm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t _e = (call);                                                                \
+        if (_e != cudaSuccess)                                                                  \
+            return fail(QMMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e));    \
+    } while (0)
+
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    int ensure(size_t count)
+    {
+        if (count <= n && p) return QMMM_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        size_t c = count ? count : 1;
+        if (cudaMalloc((void **)&p, c * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QMMM_ERR_ALLOC, "cudaMalloc failed");
+        }
+        n = c;
+        return QMMM_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+bool is_device_ptr(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+double dfact_odd(int n)  // (2n-1)!!
+{
+    double r = 1.0;
+    for (int k = 2 * n - 1; k > 1; k -= 2) r *= k;
+    return r;
+}
+
+// Boys table: F_m(T_k) for m = 0..nm-1 by the convergent series of the highest order (all terms
+// positive) followed by the stable downward recursion, in long double; last column e^{-T_k}.
+void boys_table(int nrow, int ncol, double step, std::vector<double> &out)
+{
+    out.assign((size_t)nrow * ncol, 0.0);
+    const int mtop = ncol - 2;
+    for (int k = 0; k < nrow; ++k) {
+        const long double T = (long double)k * step;
+        const long double eT = expl(-T);
+        long double term = 1.0L / (2 * mtop + 1), sum = term;
+        for (int i = 1; i < 4000; ++i) {
+            term *= 2.0L * T / (2 * mtop + 2 * i + 1);
+            sum += term;
+            if (term < 1e-22L * sum) break;
+        }
+        std::vector<long double> F(mtop + 1);
+        F[mtop] = eT * sum;
+        for (int m = mtop; m > 0; --m) F[m - 1] = (2.0L * T * F[m] + eT) / (2 * m - 1);
+        for (int m = 0; m <= mtop; ++m) out[(size_t)k * ncol + m] = (double)F[m];
+        out[(size_t)k * ncol + ncol - 1] = (double)eT;
+    }
+}
+
+}  // namespace
+
+struct qmmm_handle {
+    int device = 0, nsm = 152;
+    cudaStream_t stream = nullptr;
+    int natm = 0, nshell = 0, nprim = 0, nmm = 0, nao = 0;
+    int precision = QMMM_FP64;
+    double box[3] = {0, 0, 0}, cutoff = 0, alpha = 0, ewald_rc = 0;
+    int kmax[3] = {0, 0, 0};
+    double screen_tol = 1e-14;
+    double centre[3] = {0, 0, 0};
+    // host copies
+    std::vector<double> Z, qm_xyz, exps, ncoef;
+    std::vector<int> shell_atom, shell_l, shell_nprim, shell_off, shell_ao;
+    std::vector<int> perm;  // internal MM index -> user index
+    std::vector<double> cls_kappa;
+    int ncls = 0;
+    long long n_sp = 0, n_pp = 0;
+    int class_off[NCLASS + 1] = {0};
+    long long sp_class[NCLASS] = {0};
+    int nI = 0;
+    std::vector<int> cls_off_I;
+    bool V_valid = false;
+    float t_sweep = 0.f, t_other = 0.f;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    EwaldBuf ew;
+    int nblk_mm = 1;
+
+    // device buffers
+    DBuf<double> qm, Zd, dexps, dncoef, mm_xyz, mm_q, mm_beta, user_xyz, user_q;
+    DBuf<int> dshell_atom, dshell_off, dshell_ao, dperm, mm_cls, blk, cls_count, rI_idx, dcls_off;
+    DBuf<SPair> sp;
+    DBuf<uint32_t> pp;
+    DBuf<double4_32a> rI;
+    DBuf<float4> rI_hi, rI_lo;
+    DBuf<double> dcls_kappa, gfac, preal, pr1, sums, phi, boys64, V, dm, F, mult, mult_init, gqm, gchg, dq_int,
+        dR_int, dq_out, dR_out, Epart, partials, out4;
+    DBuf<float> boys32;
+    DBuf<double2> S, Spart, A;
+    DBuf<int> err;
+
+    BasisDev basis() const
+    {
+        BasisDev b;
+        b.shell_atom = dshell_atom.p;
+        b.shell_off = dshell_off.p;
+        b.shell_ao = dshell_ao.p;
+        b.exps = dexps.p;
+        b.ncoef = dncoef.p;
+        b.qm_xyz = qm.p;
+        b.sp = sp.p;
+        b.pp = pp.p;
+        b.nao = nao;
+        b.natm = natm;
+        return b;
+    }
+    RegionDev region() const
+    {
+        RegionDev r;
+        r.chg = rI.p;
+        r.chg_hi = rI_hi.p;
+        r.chg_lo = rI_lo.p;
+        r.idx = rI_idx.p;
+        r.cls_off = dcls_off.p;
+        r.cls_kappa = dcls_kappa.p;
+        r.ncls = ncls;
+        r.n = nI;
+        for (int x = 0; x < 3; ++x) r.centre[x] = centre[x];
+        return r;
+    }
+    EwaldDev ewald() const
+    {
+        EwaldDev e;
+        e.qm_xyz = qm.p;
+        e.mm_xyz = mm_xyz.p;
+        e.mm_q = mm_q.p;
+        e.mm_beta = mm_beta.p;
+        e.mm_cls = mm_cls.p;
+        e.natm = natm;
+        e.nmm = nmm;
+        for (int x = 0; x < 3; ++x) {
+            e.box[x] = box[x];
+            e.centre[x] = centre[x];
+            e.kmax[x] = kmax[x];
+            // images beyond the minimum image are needed only when a cutoff exceeds half the box
+            const double rmax = std::max(ewald_rc, 9.0 * max_sigma);
+            e.img[x] = rmax > 0.5 * box[x] ? (int)std::ceil(rmax / box[x] - 0.5) : 0;
+        }
+        e.rcut = cutoff;
+        e.ewald_rc = ewald_rc;
+        e.alpha = alpha;
+        e.G = nullptr;
+        e.nG = ewald_dense_size(e);
+        return e;
+    }
+    double max_sigma = 0.0;
+
+    ~qmmm_handle()
+    {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        qm.release(); Zd.release(); dexps.release(); dncoef.release(); mm_xyz.release(); mm_q.release();
+        mm_beta.release(); user_xyz.release(); user_q.release(); dshell_atom.release(); dshell_off.release();
+        dshell_ao.release(); dperm.release(); mm_cls.release(); blk.release(); cls_count.release();
+        rI_idx.release(); dcls_off.release(); sp.release(); pp.release(); rI.release(); rI_hi.release();
+        rI_lo.release(); dcls_kappa.release(); gfac.release(); preal.release(); pr1.release(); sums.release();
+        phi.release(); boys64.release(); V.release(); dm.release(); F.release(); mult.release();
+        mult_init.release(); gqm.release(); gchg.release(); dq_int.release(); dR_int.release();
+        dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
+        boys32.release(); S.release(); Spart.release(); A.release(); err.release();
+    }
+};
+
+namespace {
+
+constexpr int NPART = 256;
+
+int check_device_errors(qmmm_handle *h)
+{
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    CUDA_TRY(cudaGetLastError());
+    int e = 0;
+    CUDA_TRY(cudaMemcpy(&e, h->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        CUDA_TRY(cudaMemset(h->err.p, 0, sizeof(int)));
+        if (e & DEVERR_TIMEOUT) return fail(QMMM_ERR_TIMEOUT, "a bounded device wait ran out");
+        return fail(QMMM_ERR_CUDA, "device bounds check failed");
+    }
+    return QMMM_OK;
+}
+
+// copy an input array to a device buffer unless it already lives on the device
+int stage_input(qmmm_handle *h, const double *src, size_t n, DBuf<double> &buf, const double **out)
+{
+    if (is_device_ptr(src)) {
+        *out = src;
+        return QMMM_OK;
+    }
+    int rc = buf.ensure(n);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(buf.p, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    *out = buf.p;
+    return QMMM_OK;
+}
+
+int copy_out(qmmm_handle *h, double *dst, const double *src, size_t n)
+{
+    if (!dst) return QMMM_OK;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, h->stream));
+    return QMMM_OK;
+}
+
+int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, const double *mm_q)
+{
+    cudaStream_t st = h->stream;
+    // QM positions: host copy (centre) and device copy
+    if (qm_xyz) {
+        if (is_device_ptr(qm_xyz)) {
+            CUDA_TRY(cudaMemcpyAsync(h->qm.p, qm_xyz, 3 * h->natm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(h->qm_xyz.data(), qm_xyz, 3 * h->natm * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+        } else {
+            std::memcpy(h->qm_xyz.data(), qm_xyz, 3 * h->natm * sizeof(double));
+            CUDA_TRY(cudaMemcpyAsync(h->qm.p, h->qm_xyz.data(), 3 * h->natm * sizeof(double), cudaMemcpyHostToDevice, st));
+        }
+    }
+    for (int x = 0; x < 3; ++x) {
+        double c = 0.0;
+        for (int j = 0; j < h->natm; ++j) c += h->qm_xyz[3 * j + x];
+        h->centre[x] = c / h->natm;
+    }
+    // MM positions/charges: user order -> internal order
+    if (h->nmm > 0 && (mm_xyz || mm_q)) {
+        const double *ux = nullptr, *uq = nullptr;
+        int rc;
+        if (mm_xyz && (rc = stage_input(h, mm_xyz, 3 * (size_t)h->nmm, h->user_xyz, &ux))) return rc;
+        if (mm_q && (rc = stage_input(h, mm_q, (size_t)h->nmm, h->user_q, &uq))) return rc;
+        CUDA_TRY(launch_gather_mm(ux, uq, h->dperm.p, h->nmm, h->mm_xyz.p, h->mm_q.p, st));
+    }
+    EwaldDev e = h->ewald();
+    // region I: count, scan, fill (order preserving, grouped by width class)
+    h->nI = 0;
+    if (h->nmm > 0) {
+        CUDA_TRY(cudaMemsetAsync(h->cls_count.p, 0, h->ncls * sizeof(int), st));
+        CUDA_TRY(launch_region1_count(e, h->blk.p, h->cls_count.p, h->nblk_mm, st));
+        CUDA_TRY(launch_scan_blocks(h->blk.p, h->nblk_mm, st));
+        std::vector<int> cnt(h->ncls + 1);
+        CUDA_TRY(cudaMemcpyAsync(cnt.data(), h->blk.p + h->nblk_mm, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(cnt.data() + 1, h->cls_count.p, h->ncls * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        h->nI = cnt[0];
+        h->cls_off_I.assign(h->ncls + 1, 0);
+        for (int c = 0; c < h->ncls; ++c) h->cls_off_I[c + 1] = h->cls_off_I[c] + cnt[1 + c];
+        if (h->cls_off_I[h->ncls] != h->nI) return fail(QMMM_ERR_CUDA, "region-I class counts inconsistent");
+        int rc;
+        if ((rc = h->rI.ensure(h->nI)) || (rc = h->rI_hi.ensure(h->nI)) || (rc = h->rI_lo.ensure(h->nI)) ||
+            (rc = h->rI_idx.ensure(h->nI)) || (rc = h->gchg.ensure(4 * (size_t)std::max(h->nI, 1))) ||
+            (rc = h->Epart.ensure(enucmm_nblk(h->nI))))
+            return rc;
+        CUDA_TRY(cudaMemcpyAsync(h->dcls_off.p, h->cls_off_I.data(), (h->ncls + 1) * sizeof(int),
+                                 cudaMemcpyHostToDevice, st));
+        if (h->nI > 0)
+            CUDA_TRY(launch_region1_fill(e, h->blk.p, h->rI.p, h->rI_hi.p, h->rI_lo.p, h->rI_idx.p, h->nblk_mm, st));
+    } else {
+        h->cls_off_I.assign(h->ncls + 1, 0);
+    }
+    // region-II potential at the QM sites
+    CUDA_TRY(launch_ewald_phi(e, h->rI.p, h->nI, h->ew, h->phi.p, st));
+    h->V_valid = false;
+    return check_device_errors(h);
+}
+
+int chunk_size(const qmmm_handle *h, bool grad)
+{
+    if (grad) return CHUNK_GRAD;
+    return h->precision == QMMM_MIXED ? CHUNK_F32 : CHUNK_F64;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qmmm_strerror(int code)
+{
+    switch (code) {
+    case QMMM_OK: return "ok";
+    case QMMM_ERR_ARG: return "invalid argument";
+    case QMMM_ERR_ALLOC: return "allocation failed";
+    case QMMM_ERR_CUDA: return "CUDA error";
+    case QMMM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case QMMM_ERR_UNSUPPORTED_L: return "unsupported shell (l > 3 or more than 16 primitives)";
+    case QMMM_ERR_STATE: return "call order violated";
+    default: return "unknown error";
+    }
+}
+
+const char *qmmm_last_error(void) { return g_last_error.c_str(); }
+
+int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int nshell, const qmmm_primitive *prims,
+                int nprim, const qmmm_charge *charges, int nmm, const double box[3], double cutoff,
+                double ewald_alpha, const qmmm_options *opts, qmmm_handle **out)
+{
+    if (!out) return fail(QMMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!atoms || natm <= 0 || !shells || nshell <= 0 || !prims || nprim <= 0 || nmm < 0 || (nmm > 0 && !charges) ||
+        !box)
+        return fail(QMMM_ERR_ARG, "null array or non-positive size");
+    if (!(box[0] > 0 && box[1] > 0 && box[2] > 0) || !(cutoff > 0) || !(ewald_alpha > 0))
+        return fail(QMMM_ERR_ARG, "box, cutoff and ewald_alpha must be positive");
+    if (opts && opts->full_cell_test) return fail(QMMM_ERR_ARG, "full_cell_test is reserved");
+    if (opts && opts->region_mode != 0) return fail(QMMM_ERR_ARG, "only region_mode 0 (sphere) is supported");
+    if (opts && opts->precision != QMMM_FP64 && opts->precision != QMMM_MIXED)
+        return fail(QMMM_ERR_ARG, "precision must be QMMM_FP64 or QMMM_MIXED");
+
+    // host-side validation first: no CUDA call happens for invalid input
+    for (int s = 0; s < nshell; ++s) {
+        const qmmm_shell &sh = shells[s];
+        if (sh.l < 0 || sh.l > LMAX || sh.nprim < 1 || sh.nprim > MAX_NPRIM)
+            return fail(QMMM_ERR_UNSUPPORTED_L, "shell " + std::to_string(s) + ": l or nprim out of range");
+        if (sh.atom < 0 || sh.atom >= natm || sh.prim_offset < 0 || sh.prim_offset + sh.nprim > nprim)
+            return fail(QMMM_ERR_ARG, "shell " + std::to_string(s) + ": atom or primitive range invalid");
+    }
+    for (int k = 0; k < nprim; ++k)
+        if (!(prims[k].exponent > 0) || !std::isfinite(prims[k].exponent) || !std::isfinite(prims[k].coeff))
+            return fail(QMMM_ERR_ARG, "primitive " + std::to_string(k) + ": exponent must be positive and finite");
+    for (int j = 0; j < natm; ++j)
+        if (!std::isfinite(atoms[j].xyz[0]) || !std::isfinite(atoms[j].xyz[1]) || !std::isfinite(atoms[j].xyz[2]) ||
+            !std::isfinite(atoms[j].Z))
+            return fail(QMMM_ERR_ARG, "QM atom " + std::to_string(j) + ": non-finite data");
+    for (int i = 0; i < nmm; ++i)
+        if (!std::isfinite(charges[i].xyz[0]) || !std::isfinite(charges[i].xyz[1]) || !std::isfinite(charges[i].xyz[2]) ||
+            !std::isfinite(charges[i].q) || !std::isfinite(charges[i].sigma))
+            return fail(QMMM_ERR_ARG, "MM charge " + std::to_string(i) + ": non-finite data");
+    {
+        std::map<double, int> w;
+        for (int i = 0; i < nmm && (int)w.size() <= MAX_SIGMA_CLASSES; ++i)
+            w.emplace(charges[i].sigma > 0 ? charges[i].sigma : 0.0, 0);
+        if ((int)w.size() > MAX_SIGMA_CLASSES) return fail(QMMM_ERR_ARG, "more than 64 distinct Gaussian widths");
+    }
+    for (int x = 0; x < 3; ++x)
+        if (opts && opts->kmax[x] > 200) return fail(QMMM_ERR_ARG, "kmax too large (> 200)");
+
+    auto h = new qmmm_handle();
+    std::unique_ptr<qmmm_handle> guard(h);
+    CUDA_TRY(cudaGetDevice(&h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+    h->natm = natm;
+    h->nshell = nshell;
+    h->nprim = nprim;
+    h->nmm = nmm;
+    for (int x = 0; x < 3; ++x) h->box[x] = box[x];
+    h->cutoff = cutoff;
+    h->alpha = ewald_alpha;
+    h->precision = opts ? opts->precision : QMMM_FP64;
+    h->screen_tol = (opts && opts->screen_tol >= 0) ? opts->screen_tol : 1e-14;
+    h->ewald_rc = (opts && opts->ewald_rcut > 0) ? opts->ewald_rcut : cutoff;
+    for (int x = 0; x < 3; ++x) {
+        int k = opts ? opts->kmax[x] : 0;
+        if (k <= 0) {
+            // exp(-G^2 / 4 alpha^2) < 1e-8 at the cube edge
+            const double gmax = 2.0 * ewald_alpha * std::sqrt(std::log(1e8));
+            k = (int)std::ceil(gmax * box[x] / (2.0 * PI));
+        }
+        if (k > 200) return fail(QMMM_ERR_ARG, "kmax too large (> 200)");
+        h->kmax[x] = k;
+    }
+
+    // QM atoms and basis
+    h->Z.resize(natm);
+    h->qm_xyz.resize(3 * natm);
+    for (int j = 0; j < natm; ++j) {
+        h->Z[j] = atoms[j].Z;
+        for (int x = 0; x < 3; ++x) h->qm_xyz[3 * j + x] = atoms[j].xyz[x];
+    }
+    h->shell_atom.resize(nshell);
+    h->shell_l.resize(nshell);
+    h->shell_nprim.resize(nshell);
+    h->shell_off.resize(nshell);
+    h->shell_ao.resize(nshell);
+    int ao = 0;
+    for (int s = 0; s < nshell; ++s) {
+        const qmmm_shell &sh = shells[s];
+        if (sh.l < 0 || sh.l > LMAX || sh.nprim < 1 || sh.nprim > MAX_NPRIM)
+            return fail(QMMM_ERR_UNSUPPORTED_L, "shell " + std::to_string(s) + ": l or nprim out of range");
+        if (sh.atom < 0 || sh.atom >= natm || sh.prim_offset < 0 || sh.prim_offset + sh.nprim > nprim)
+            return fail(QMMM_ERR_ARG, "shell " + std::to_string(s) + ": atom or primitive range invalid");
+        h->shell_atom[s] = sh.atom;
+        h->shell_l[s] = sh.l;
+        h->shell_nprim[s] = sh.nprim;
+        h->shell_off[s] = sh.prim_offset;
+        h->shell_ao[s] = ao;
+        ao += ncart(sh.l);
+    }
+    h->nao = ao;
+    h->exps.resize(nprim);
+    h->ncoef.assign(nprim, 0.0);
+    for (int k = 0; k < nprim; ++k) {
+        if (!(prims[k].exponent > 0) || !std::isfinite(prims[k].coeff))
+            return fail(QMMM_ERR_ARG, "primitive " + std::to_string(k) + ": exponent must be positive");
+        h->exps[k] = prims[k].exponent;
+    }
+    // normalisation: x^l component of each primitive, then the contraction
+    for (int s = 0; s < nshell; ++s) {
+        const int l = h->shell_l[s], o = h->shell_off[s], n = h->shell_nprim[s];
+        for (int k = 0; k < n; ++k) {
+            const double a = h->exps[o + k];
+            h->ncoef[o + k] = prims[o + k].coeff * std::pow(2.0 * a / PI, 0.75) * std::pow(4.0 * a, 0.5 * l) /
+                              std::sqrt(dfact_odd(l));
+        }
+        double ss = 0.0;
+        for (int k = 0; k < n; ++k)
+            for (int m = 0; m < n; ++m) {
+                const double p = h->exps[o + k] + h->exps[o + m];
+                ss += h->ncoef[o + k] * h->ncoef[o + m] * dfact_odd(l) / std::pow(2.0 * p, l) * std::pow(PI / p, 1.5);
+            }
+        if (!(ss > 0)) return fail(QMMM_ERR_ARG, "shell " + std::to_string(s) + " has zero norm");
+        for (int k = 0; k < n; ++k) h->ncoef[o + k] /= std::sqrt(ss);
+    }
+
+    // shell pairs sorted by class; primitive pairs screened
+    {
+        struct Cand { int s; int code; double v; };
+        std::vector<std::vector<SPair>> sp_cls(NCLASS);
+        std::vector<std::vector<uint32_t>> pp_cls(NCLASS);
+        std::vector<double> vals;
+        double vmax = 0.0;
+        // pass 1: maximum screening value
+        for (int i = 0; i < nshell; ++i)
+            for (int j = i; j < nshell; ++j) {
+                const double *A = &h->qm_xyz[3 * h->shell_atom[i]], *B = &h->qm_xyz[3 * h->shell_atom[j]];
+                const double ab2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+                for (int ka = 0; ka < h->shell_nprim[i]; ++ka)
+                    for (int kb = 0; kb < h->shell_nprim[j]; ++kb) {
+                        const double a = h->exps[h->shell_off[i] + ka], b = h->exps[h->shell_off[j] + kb], p = a + b;
+                        const double v = std::fabs(h->ncoef[h->shell_off[i] + ka] * h->ncoef[h->shell_off[j] + kb]) *
+                                         std::exp(-a * b / p * ab2) * std::pow(PI / p, 1.5);
+                        vmax = std::max(vmax, v);
+                    }
+            }
+        const double thr = h->screen_tol * vmax;
+        long long nsp = 0;
+        for (int i = 0; i < nshell; ++i)
+            for (int j = i; j < nshell; ++j) {
+                int sA = i, sB = j;
+                if (h->shell_l[j] > h->shell_l[i]) std::swap(sA, sB);
+                const int cls = class_of(h->shell_l[sA], h->shell_l[sB]);
+                const double *A = &h->qm_xyz[3 * h->shell_atom[sA]], *B = &h->qm_xyz[3 * h->shell_atom[sB]];
+                const double ab2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+                std::vector<uint32_t> kept;
+                for (int ka = 0; ka < h->shell_nprim[sA]; ++ka)
+                    for (int kb = 0; kb < h->shell_nprim[sB]; ++kb) {
+                        const double a = h->exps[h->shell_off[sA] + ka], b = h->exps[h->shell_off[sB] + kb], p = a + b;
+                        const double v = std::fabs(h->ncoef[h->shell_off[sA] + ka] * h->ncoef[h->shell_off[sB] + kb]) *
+                                         std::exp(-a * b / p * ab2) * std::pow(PI / p, 1.5);
+                        if (h->screen_tol == 0.0 || v >= thr) kept.push_back((uint32_t)((ka << 4) | kb));
+                    }
+                if (kept.empty()) continue;
+                const int sidx = (int)sp_cls[cls].size();
+                sp_cls[cls].push_back(SPair{sA, sB, h->shell_ao[sA], h->shell_ao[sB]});
+                for (uint32_t c : kept) pp_cls[cls].push_back(((uint32_t)sidx << 8) | c);  // re-based below
+                ++nsp;
+            }
+        if (nsp >= (1LL << 24)) return fail(QMMM_ERR_ARG, "too many shell pairs (>= 2^24)");
+        std::vector<SPair> sp_all;
+        std::vector<uint32_t> pp_all;
+        h->class_off[0] = 0;
+        for (int c = 0; c < NCLASS; ++c) {
+            const uint32_t base = (uint32_t)sp_all.size();
+            for (const SPair &s : sp_cls[c]) sp_all.push_back(s);
+            for (uint32_t code : pp_cls[c]) pp_all.push_back(((((code >> 8) + base)) << 8) | (code & 0xff));
+            h->class_off[c + 1] = (int)pp_all.size();
+            h->sp_class[c] = (long long)sp_cls[c].size();
+        }
+        h->n_sp = (long long)sp_all.size();
+        h->n_pp = (long long)pp_all.size();
+        int rc;
+        if ((rc = h->sp.ensure(sp_all.size())) || (rc = h->pp.ensure(pp_all.size()))) return rc;
+        CUDA_TRY(cudaMemcpy(h->sp.p, sp_all.data(), sp_all.size() * sizeof(SPair), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->pp.p, pp_all.data(), pp_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+
+    // MM charges: width classes, internal order by (class, cell)
+    std::vector<double> sig(nmm), uq(nmm), ux(3 * (size_t)nmm);
+    for (int i = 0; i < nmm; ++i) {
+        sig[i] = charges[i].sigma > 0 ? charges[i].sigma : 0.0;
+        uq[i] = charges[i].q;
+        for (int x = 0; x < 3; ++x) ux[3 * (size_t)i + x] = charges[i].xyz[x];
+        if (!std::isfinite(sig[i]) || !std::isfinite(uq[i])) return fail(QMMM_ERR_ARG, "non-finite MM charge data");
+    }
+    std::map<double, int> wcls;
+    for (double s : sig) wcls.emplace(s, 0);
+    if ((int)wcls.size() > MAX_SIGMA_CLASSES) return fail(QMMM_ERR_ARG, "more than 64 distinct Gaussian widths");
+    {
+        int c = 0;
+        for (auto &kv : wcls) {
+            kv.second = c++;
+            h->cls_kappa.push_back(kv.first > 0 ? 1.0 / (kv.first * kv.first) : 0.0);
+            h->max_sigma = std::max(h->max_sigma, kv.first);
+        }
+        h->ncls = c > 0 ? c : 1;
+        if (h->cls_kappa.empty()) h->cls_kappa.push_back(0.0);
+    }
+    std::vector<int> cls_user(nmm);
+    std::vector<long long> key(nmm);
+    const double cell = 8.0 / 0.52917721092;  // 8 Angstrom bins
+    int ncx[3];
+    for (int x = 0; x < 3; ++x) ncx[x] = std::max(1, (int)(box[x] / cell));
+    for (int i = 0; i < nmm; ++i) {
+        cls_user[i] = wcls[sig[i]];
+        long long cid = 0;
+        for (int x = 0; x < 3; ++x) {
+            double f = ux[3 * (size_t)i + x] / box[x];
+            f -= std::floor(f);
+            int b = std::min(ncx[x] - 1, (int)(f * ncx[x]));
+            cid = cid * ncx[x] + b;
+        }
+        key[i] = (long long)cls_user[i] * (1LL << 40) + cid;
+    }
+    h->perm.resize(nmm);
+    for (int i = 0; i < nmm; ++i) h->perm[i] = i;
+    std::stable_sort(h->perm.begin(), h->perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::vector<int> cls_int(nmm);
+    std::vector<double> beta_int(nmm);
+    for (int i = 0; i < nmm; ++i) {
+        cls_int[i] = cls_user[h->perm[i]];
+        beta_int[i] = sig[h->perm[i]] > 0 ? 1.0 / sig[h->perm[i]] : 0.0;
+    }
+
+    // allocations and uploads
+    {
+        int rc;
+        const size_t nm = std::max(nmm, 1);
+        h->nblk_mm = std::max(1, (nmm + 255) / 256);
+        if ((rc = h->qm.ensure(3 * natm)) || (rc = h->Zd.ensure(natm)) || (rc = h->dexps.ensure(nprim)) ||
+            (rc = h->dncoef.ensure(nprim)) || (rc = h->dshell_atom.ensure(nshell)) || (rc = h->dshell_off.ensure(nshell)) ||
+            (rc = h->dshell_ao.ensure(nshell)) || (rc = h->mm_xyz.ensure(3 * nm)) || (rc = h->mm_q.ensure(nm)) ||
+            (rc = h->mm_beta.ensure(nm)) || (rc = h->mm_cls.ensure(nm)) || (rc = h->dperm.ensure(nm)) ||
+            (rc = h->blk.ensure(h->nblk_mm + 1)) || (rc = h->cls_count.ensure(h->ncls)) ||
+            (rc = h->dcls_off.ensure(h->ncls + 1)) || (rc = h->dcls_kappa.ensure(h->ncls)) ||
+            (rc = h->phi.ensure(20 * (size_t)natm)) || (rc = h->mult.ensure(10 * (size_t)natm)) ||
+            (rc = h->mult_init.ensure(10 * (size_t)natm)) || (rc = h->gqm.ensure(3 * (size_t)natm)) ||
+            (rc = h->dq_int.ensure(nm)) || (rc = h->dR_int.ensure(3 * nm)) || (rc = h->dq_out.ensure(nm)) ||
+            (rc = h->dR_out.ensure(3 * nm)) || (rc = h->partials.ensure(NPART)) || (rc = h->out4.ensure(8)) ||
+            (rc = h->err.ensure(1)) || (rc = h->sums.ensure(2)) || (rc = h->Epart.ensure(1)) ||
+            (rc = h->rI.ensure(1)) || (rc = h->rI_hi.ensure(1)) || (rc = h->rI_lo.ensure(1)) ||
+            (rc = h->rI_idx.ensure(1)) || (rc = h->gchg.ensure(4)))
+            return rc;
+        CUDA_TRY(cudaMemset(h->err.p, 0, sizeof(int)));
+        CUDA_TRY(cudaMemcpy(h->Zd.p, h->Z.data(), natm * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->dexps.p, h->exps.data(), nprim * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->dncoef.p, h->ncoef.data(), nprim * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->dshell_atom.p, h->shell_atom.data(), nshell * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->dshell_off.p, h->shell_off.data(), nshell * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->dshell_ao.p, h->shell_ao.data(), nshell * sizeof(int), cudaMemcpyHostToDevice));
+        if (nmm > 0) {
+            CUDA_TRY(cudaMemcpy(h->dperm.p, h->perm.data(), nmm * sizeof(int), cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(h->mm_cls.p, cls_int.data(), nmm * sizeof(int), cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(h->mm_beta.p, beta_int.data(), nmm * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        CUDA_TRY(cudaMemcpy(h->dcls_kappa.p, h->cls_kappa.data(), h->ncls * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<double> minit(10 * (size_t)natm, 0.0);
+        for (int j = 0; j < natm; ++j) minit[10 * j] = h->Z[j];
+        CUDA_TRY(cudaMemcpy(h->mult_init.p, minit.data(), minit.size() * sizeof(double), cudaMemcpyHostToDevice));
+        // Boys tables
+        std::vector<double> t64;
+        boys_table(BOYS_NROW_D, BOYS_NCOL_D, BOYS_STEP, t64);
+        if ((rc = h->boys64.ensure(t64.size()))) return rc;
+        CUDA_TRY(cudaMemcpy(h->boys64.p, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<double> t32d;
+        boys_table(BOYS_NROW_F, BOYS_NCOL_F, BOYS_STEP, t32d);
+        std::vector<float> t32((t32d.size() + 3) / 4 * 4, 0.0f);
+        for (size_t k = 0; k < t32d.size(); ++k) t32[k] = (float)t32d[k];
+        if ((rc = h->boys32.ensure(t32.size()))) return rc;
+        CUDA_TRY(cudaMemcpy(h->boys32.p, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        // Ewald buffers
+        EwaldDev e = h->ewald();
+        const int nd = ewald_dense_size(e);
+        h->ew.sf_nslice = ewald_sf_nslice(e);
+        h->ew.real_nslice = ewald_real_nslice(e, h->nsm);
+        if ((rc = h->gfac.ensure(nd)) || (rc = h->S.ensure(nd)) || (rc = h->A.ensure(nd)) ||
+            (rc = h->Spart.ensure((size_t)nd * h->ew.sf_nslice)) ||
+            (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
+            return rc;
+        h->ew.gfac = h->gfac.p;
+        h->ew.S = h->S.p;
+        h->ew.Spart = h->Spart.p;
+        h->ew.preal = h->preal.p;
+        h->ew.pr1 = h->pr1.p;
+        h->ew.A = h->A.p;
+        h->ew.sums = h->sums.p;
+        CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
+        for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
+    }
+    // initial geometry
+    std::vector<double> qm0 = h->qm_xyz;
+    int rc = run_positions(h, qm0.data(), nmm ? ux.data() : nullptr, nmm ? uq.data() : nullptr);
+    if (rc) return rc;
+    *out = guard.release();
+    return QMMM_OK;
+}
+
+int qmmm_set_stream(qmmm_handle *h, void *stream)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    h->stream = (cudaStream_t)stream;
+    return QMMM_OK;
+}
+
+int qmmm_set_precision(qmmm_handle *h, int precision)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    if (precision != QMMM_FP64 && precision != QMMM_MIXED) return fail(QMMM_ERR_ARG, "bad precision");
+    if (precision != h->precision) h->V_valid = false;
+    h->precision = precision;
+    return QMMM_OK;
+}
+
+int qmmm_set_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, const double *mm_q)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    return run_positions(h, qm_xyz, mm_xyz, mm_q);
+}
+
+int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    cudaStream_t st = h->stream;
+    int rc;
+    if ((rc = h->V.ensure((size_t)h->nao * h->nao))) return rc;
+    CUDA_TRY(cudaMemsetAsync(h->V.p, 0, (size_t)h->nao * h->nao * sizeof(double), st));
+    const BasisDev b = h->basis();
+    const RegionDev r = h->region();
+    const int ch = chunk_size(h, false);
+    CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    for (int c0 = 0; c0 < h->nI; c0 += ch) {
+        const int c1 = std::min(h->nI, c0 + ch);
+        for (int cls = 0; cls < NCLASS; ++cls) {
+            const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
+            if (p1 <= p0) continue;
+            if (h->precision == QMMM_MIXED)
+                CUDA_TRY(launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, h->V.p, h->err.p, h->nsm, st));
+            else
+                CUDA_TRY(launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, h->V.p, h->err.p, h->nsm, st));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(h->ev[1], st));
+    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
+                           nullptr, 0, st));
+    CUDA_TRY(launch_sum(h->Epart.p, enucmm_nblk(h->nI), h->out4.p + 4, st));
+    if ((rc = copy_out(h, Vout, h->V.p, (size_t)h->nao * h->nao))) return rc;
+    if ((rc = copy_out(h, E_nuc_mm, h->out4.p + 4, 1))) return rc;
+    CUDA_TRY(cudaEventRecord(h->ev[2], st));
+    if ((rc = check_device_errors(h))) return rc;
+    cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+    h->V_valid = true;
+    return QMMM_OK;
+}
+
+static int compute_multipoles(qmmm_handle *h, const double *ddm, double *F, int extra_mode)
+{
+    cudaStream_t st = h->stream;
+    CUDA_TRY(cudaMemcpyAsync(h->mult.p, h->mult_init.p, 10 * (size_t)h->natm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const BasisDev b = h->basis();
+    const int mode = MOM_MULT | (F ? MOM_FOCK : 0) | extra_mode;
+    for (int cls = 0; cls < NCLASS; ++cls) {
+        const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
+        if (p1 <= p0) continue;
+        CUDA_TRY(launch_moments(b, cls, p0, p1, ddm, h->phi.p, h->mult.p, F, h->gqm.p, mode, st));
+    }
+    return QMMM_OK;
+}
+
+int qmmm_ewald(qmmm_handle *h, const double *dmat, double *E_II, double *multipoles, double *F_II)
+{
+    if (!h || !dmat) return fail(QMMM_ERR_ARG, "null handle or density");
+    cudaStream_t st = h->stream;
+    int rc;
+    const double *ddm;
+    const size_t n2 = (size_t)h->nao * h->nao;
+    CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    double *Fd = nullptr;
+    if (F_II) {
+        if ((rc = h->F.ensure(n2))) return rc;
+        CUDA_TRY(cudaMemsetAsync(h->F.p, 0, n2 * sizeof(double), st));
+        Fd = h->F.p;
+    }
+    if ((rc = compute_multipoles(h, ddm, Fd, 0))) return rc;
+    CUDA_TRY(launch_energy_terms(ddm, nullptr, h->nao, 0, h->mult.p, h->phi.p, h->natm, h->Epart.p, 0, h->partials.p,
+                                 NPART, h->out4.p, st));
+    if ((rc = copy_out(h, E_II, h->out4.p + 3, 1))) return rc;
+    if ((rc = copy_out(h, multipoles, h->mult.p, 10 * (size_t)h->natm))) return rc;
+    if (F_II && (rc = copy_out(h, F_II, h->F.p, n2))) return rc;
+    CUDA_TRY(cudaEventRecord(h->ev[1], st));
+    if ((rc = check_device_errors(h))) return rc;
+    h->t_sweep = 0.f;
+    cudaEventElapsedTime(&h->t_other, h->ev[0], h->ev[1]);
+    return QMMM_OK;
+}
+
+int qmmm_energy(qmmm_handle *h, const double *dmat, double *E)
+{
+    if (!h || !dmat || !E) return fail(QMMM_ERR_ARG, "null argument");
+    if (!h->V_valid) return fail(QMMM_ERR_STATE, "qmmm_vpot must run at the current geometry first");
+    cudaStream_t st = h->stream;
+    int rc;
+    const double *ddm;
+    const size_t n2 = (size_t)h->nao * h->nao;
+    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    if ((rc = compute_multipoles(h, ddm, nullptr, 0))) return rc;
+    CUDA_TRY(launch_energy_terms(ddm, h->V.p, h->nao, 1, h->mult.p, h->phi.p, h->natm, h->Epart.p,
+                                 enucmm_nblk(h->nI), h->partials.p, NPART, h->out4.p, st));
+    if ((rc = copy_out(h, E, h->out4.p, 4))) return rc;
+    return check_device_errors(h);
+}
+
+int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_dRmm, double *dE_dq)
+{
+    if (!h || !dmat) return fail(QMMM_ERR_ARG, "null handle or density");
+    cudaStream_t st = h->stream;
+    int rc;
+    const double *ddm;
+    const size_t n2 = (size_t)h->nao * h->nao;
+    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    CUDA_TRY(cudaMemsetAsync(h->gqm.p, 0, 3 * (size_t)h->natm * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(h->gchg.p, 0, 4 * (size_t)std::max(h->nI, 1) * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(h->dq_int.p, 0, (size_t)std::max(h->nmm, 1) * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(h->dR_int.p, 0, 3 * (size_t)std::max(h->nmm, 1) * sizeof(double), st));
+    // multipoles and the Pulay term
+    if ((rc = compute_multipoles(h, ddm, nullptr, MOM_PULAY))) return rc;
+    // region-I adjoint sweep
+    const BasisDev b = h->basis();
+    const RegionDev r = h->region();
+    const int ch = chunk_size(h, true);
+    CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    for (int c0 = 0; c0 < h->nI; c0 += ch) {
+        const int c1 = std::min(h->nI, c0 + ch);
+        for (int cls = 0; cls < NCLASS; ++cls) {
+            const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
+            if (p1 <= p0) continue;
+            if (h->precision == QMMM_MIXED)
+                CUDA_TRY(launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
+                                          h->nsm, st));
+            else
+                CUDA_TRY(launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
+                                          h->nsm, st));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(h->ev[1], st));
+    // nuclear-MM region I, multipolar Ewald (MM side + QM tensor part), scatter to MM atoms
+    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, h->gqm.p,
+                           h->gchg.p, 1, st));
+    const EwaldDev e = h->ewald();
+    if (h->nmm > 0) {
+        CUDA_TRY(launch_ewald_mm(e, h->rI.p, h->nI, h->mult.p, h->phi.p, h->ew, h->dq_int.p, h->dR_int.p, h->gchg.p,
+                                 h->gqm.p, st));
+        CUDA_TRY(launch_scatter_region(h->rI_idx.p, h->nI, h->gchg.p, h->dq_int.p, h->dR_int.p, st));
+        CUDA_TRY(launch_unpermute(h->dq_int.p, h->dR_int.p, h->dperm.p, h->nmm, h->dq_out.p, h->dR_out.p, st));
+    } else {
+        CUDA_TRY(launch_ewald_mm(e, h->rI.p, 0, h->mult.p, h->phi.p, h->ew, h->dq_int.p, h->dR_int.p, h->gchg.p,
+                                 h->gqm.p, st));
+    }
+    if ((rc = copy_out(h, dE_dRqm, h->gqm.p, 3 * (size_t)h->natm))) return rc;
+    if (h->nmm > 0) {
+        if ((rc = copy_out(h, dE_dRmm, h->dR_out.p, 3 * (size_t)h->nmm))) return rc;
+        if ((rc = copy_out(h, dE_dq, h->dq_out.p, (size_t)h->nmm))) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(h->ev[2], st));
+    if ((rc = check_device_errors(h))) return rc;
+    cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+    return QMMM_OK;
+}
+
+int qmmm_get_info(const qmmm_handle *h, qmmm_info_t *info)
+{
+    if (!h || !info) return fail(QMMM_ERR_ARG, "null argument");
+    info->nao = h->nao;
+    info->natm = h->natm;
+    info->nshell = h->nshell;
+    info->nmm = h->nmm;
+    info->n_shell_pairs = h->n_sp;
+    info->n_prim_pairs = h->n_pp;
+    info->n_region1 = h->nI;
+    EwaldDev e = h->ewald();
+    info->n_gvec = ((2 * e.kmax[0] + 1) * (2 * e.kmax[1] + 1) * (2 * e.kmax[2] + 1) - 1) / 2;
+    info->n_sigma_classes = h->ncls;
+    info->precision = h->precision;
+    for (int c = 0; c < NCLASS; ++c) {
+        info->n_prim_pairs_class[c] = h->class_off[c + 1] - h->class_off[c];
+        info->n_shell_pairs_class[c] = h->sp_class[c];
+    }
+    return QMMM_OK;
+}
+
+int qmmm_nao(const qmmm_handle *h) { return h ? h->nao : fail(QMMM_ERR_ARG, "null handle"); }
+
+int qmmm_get_potential(qmmm_handle *h, double *v)
+{
+    if (!h || !v) return fail(QMMM_ERR_ARG, "null argument");
+    int rc;
+    if ((rc = copy_out(h, v, h->phi.p, 20 * (size_t)h->natm))) return rc;
+    return check_device_errors(h);
+}
+
+int qmmm_last_timing(const qmmm_handle *h, double *out)
+{
+    if (!h || !out) return fail(QMMM_ERR_ARG, "null argument");
+    out[0] = h->t_sweep;
+    out[1] = h->t_other;
+    return 2;
+}
+
+void qmmm_destroy(qmmm_handle *h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,416 @@
+// device_common.cuh -- device building blocks shared by the sm_103a kernels.
+//
+//  * McMurchie-Davidson Hermite machinery for the region-I integrals of Eq. 9:
+//      g_a g_b = sum_t E^{ab}_t Lambda_t (per Cartesian direction; Lambda_t = d^t/dP^t of the
+//      Gaussian product), and
+//      int Lambda_tuv(r) erf(sqrt(kappa)|r-C|)/|r-C| dr = (2 pi/p) sqrt(kappa/(p+kappa)) R_tuv,
+//      R^{(n)}_000 = (-2 rho)^n F_n(rho |P-C|^2), rho = p kappa / (p + kappa),
+//      R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X_PC R^{(n+1)}_{t,u,v}  (and for u, v).
+//  * Boys function F_m(T): tabulated F_{m+j}(T_k) on a 0.1 grid with a Taylor expansion about
+//    the nearest point and downward recursion F_{m-1} = (2T F_m + e^{-T})/(2m-1) for small T;
+//    F_0 = sqrt(pi)/2 T^{-1/2} with the upward recursion F_{m+1} = ((2m+1) F_m - e^{-T})/(2T)
+//    for large T (the grid-plus-recursion scheme of Helgaker, Jorgensen and Olsen, Molecular
+//    Electronic-Structure Theory, Sec. 9.8).  The tables are written by the host planner.
+//  * 1-D TMA bulk copies (cp.async.bulk) into shared memory with an mbarrier whose wait is
+//    bounded: on time-out the kernel raises an error flag instead of spinning forever.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qmmm {
+
+constexpr int LMAX = 3;                       // highest shell angular momentum
+constexpr int NCLASS = (LMAX + 1) * (LMAX + 2) / 2;
+constexpr double PI = 3.14159265358979323846;
+constexpr double TWO_PI = 6.28318530717958647692;
+constexpr double HALF_SQRT_PI = 0.88622692545275801365;
+
+// Boys tables (rows T_k = k * step; columns m = 0..NCOL-2, last column e^{-T_k})
+constexpr double BOYS_STEP = 0.1;
+constexpr double BOYS_INV_STEP = 10.0;
+constexpr double BOYS_TMAX_D = 36.0;          // FP64 table range; above: asymptotic branch
+constexpr int BOYS_NROW_D = 361;
+constexpr int BOYS_NCOL_D = 17;               // orders 0..15 + exp column (padded row stride)
+constexpr int BOYS_TAYLOR_D = 7;              // terms of the FP64 Taylor expansion
+constexpr float BOYS_TMAX_F = 20.0f;          // FP32 table range
+constexpr int BOYS_NROW_F = 201;
+constexpr int BOYS_NCOL_F = 17;               // orders 0..15 + exp column, odd stride (banks)
+constexpr int BOYS_TAYLOR_F = 5;
+constexpr int BOYS_MAXM = 8;                  // highest order any kernel asks for
+
+// ------------------------------------------------------------------------------------------
+// index helpers (compile-time)
+// ------------------------------------------------------------------------------------------
+__host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+// Hermite (t,u,v) index, ordered by total order then lexicographically (nested over L)
+__host__ __device__ constexpr int hidx(int t, int u, int v)
+{
+    return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+// Cartesian component k of shell l (lexicographic: x^l first)
+__host__ __device__ constexpr int cart_lx(int l, int k)
+{
+    int i = 0;
+    for (int lx = l; lx >= 0; --lx)
+        for (int ly = l - lx; ly >= 0; --ly) {
+            if (i == k) return lx;
+            ++i;
+        }
+    return 0;
+}
+__host__ __device__ constexpr int cart_ly(int l, int k)
+{
+    int i = 0;
+    for (int lx = l; lx >= 0; --lx)
+        for (int ly = l - lx; ly >= 0; --ly) {
+            if (i == k) return ly;
+            ++i;
+        }
+    return 0;
+}
+__host__ __device__ constexpr int cart_lz(int l, int k) { return l - cart_lx(l, k) - cart_ly(l, k); }
+__host__ __device__ constexpr int class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
+
+// ------------------------------------------------------------------------------------------
+// Boys function
+// ------------------------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void boys_f64(double T, double (&F)[M + 1], const double *__restrict__ tab)
+{
+    if (T < BOYS_TMAX_D) {
+        const int k = __double2int_rn(T * BOYS_INV_STEP);
+        const double x = (double)k * BOYS_STEP - T;  // -(T - T_k)
+        const double *row = tab + k * BOYS_NCOL_D;
+        // sum_{j<7} F_{M+j}(T_k) x^j / j!  (Horner)
+        double f = __ldg(row + M + 6);
+        f = __ldg(row + M + 5) + f * x * (1.0 / 6.0);
+        f = __ldg(row + M + 4) + f * x * (1.0 / 5.0);
+        f = __ldg(row + M + 3) + f * x * (1.0 / 4.0);
+        f = __ldg(row + M + 2) + f * x * (1.0 / 3.0);
+        f = __ldg(row + M + 1) + f * x * 0.5;
+        f = __ldg(row + M) + f * x;
+        F[M] = f;
+        if (M > 0) {
+            // e^{-T} = e^{-T_k} e^{x}, |x| <= 0.05: 8-term Taylor of e^x
+            double ex = 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0 + x * (1.0 / 24.0 + x * (1.0 / 120.0 +
+                        x * (1.0 / 720.0 + x * (1.0 / 5040.0)))))));
+            const double e = __ldg(row + BOYS_NCOL_D - 1) * ex;
+            const double T2 = 2.0 * T;
+#pragma unroll
+            for (int m = M; m > 0; --m) F[m - 1] = (T2 * F[m] + e) * (1.0 / (2 * m - 1));
+        }
+    } else {
+        const double rs = rsqrt(T);
+        F[0] = HALF_SQRT_PI * rs;
+        if (M > 0) {
+            const double e = (T < 60.0) ? exp(-T) : 0.0;
+            const double inv2T = 0.5 * rs * rs;
+#pragma unroll
+            for (int m = 0; m < M; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * inv2T;
+        }
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float *__restrict__ tab /* smem */)
+{
+    if (T < BOYS_TMAX_F) {
+        const int k = __float2int_rn(T * 10.0f);
+        const float x = (float)k * 0.1f - T;
+        const float *row = tab + k * BOYS_NCOL_F;
+        float f = row[M + 4];
+        f = row[M + 3] + f * x * 0.25f;
+        f = row[M + 2] + f * x * (1.0f / 3.0f);
+        f = row[M + 1] + f * x * 0.5f;
+        f = row[M] + f * x;
+        F[M] = f;
+        if (M > 0) {
+            const float e = __expf(-T);
+            const float T2 = 2.0f * T;
+#pragma unroll
+            for (int m = M; m > 0; --m) F[m - 1] = (T2 * F[m] + e) * (1.0f / (2 * m - 1));
+        }
+    } else {
+        // one Newton step on rsqrtf: ~1 ulp
+        float rs = rsqrtf(T);
+        rs = rs * (1.5f - 0.5f * T * rs * rs);
+        F[0] = (float)HALF_SQRT_PI * rs;
+        if (M > 0) {
+            const float e = __expf(-T);
+            const float inv2T = 0.5f * rs * rs;
+#pragma unroll
+            for (int m = 0; m < M; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * inv2T;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Hermite R tensors, in place: on entry Fn[n] = pref * (-2 rho)^n F_n(T) for n = 0..L;
+// on exit R[hidx(t,u,v)] = pref * R_tuv for t+u+v <= L.  Each level n is built from level n+1
+// in decreasing total order, so entries of order k only read orders k-1 and k-2 that still
+// hold level n+1 values.
+// ------------------------------------------------------------------------------------------
+template <int L, typename T>
+__device__ __forceinline__ void hermite_R(T (&R)[nherm(L)], const T (&Fn)[L + 1], T X, T Y, T Z)
+{
+    R[0] = Fn[L];
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll
+        for (int k = L - n; k >= 1; --k) {
+#pragma unroll
+            for (int t = k; t >= 0; --t) {
+#pragma unroll
+                for (int u = k - t; u >= 0; --u) {
+                    const int v = k - t - u;
+                    if (t > 0) {
+                        T r = X * R[hidx(t - 1, u, v)];
+                        if (t > 1) r += (T)(t - 1) * R[hidx(t - 2, u, v)];
+                        R[hidx(t, u, v)] = r;
+                    } else if (u > 0) {
+                        T r = Y * R[hidx(t, u - 1, v)];
+                        if (u > 1) r += (T)(u - 1) * R[hidx(t, u - 2, v)];
+                        R[hidx(t, u, v)] = r;
+                    } else {
+                        T r = Z * R[hidx(t, u, v - 1)];
+                        if (v > 1) r += (T)(v - 1) * R[hidx(t, u, v - 2)];
+                        R[hidx(t, u, v)] = r;
+                    }
+                }
+            }
+        }
+        R[0] = Fn[n];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Hermite expansion coefficients in one direction, E[i][j][t] for i <= I, j <= J, with
+// E^{00}_0 = 1 (the Gaussian-product factor K_AB is carried separately):
+//   E^{i+1,j}_t = 1/(2p) E^{ij}_{t-1} + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
+//   E^{i,j+1}_t = 1/(2p) E^{ij}_{t-1} + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1}
+// ------------------------------------------------------------------------------------------
+template <int I, int J, typename T>
+__device__ __forceinline__ void hermite_E(T (&E)[I + 1][J + 1][I + J + 1], T XPA, T XPB, T inv2p)
+{
+#pragma unroll
+    for (int i = 0; i <= I; ++i)
+#pragma unroll
+        for (int j = 0; j <= J; ++j)
+#pragma unroll
+            for (int t = 0; t <= I + J; ++t) E[i][j][t] = (T)0;
+    E[0][0][0] = (T)1;
+#pragma unroll
+    for (int i = 0; i <= I; ++i)
+#pragma unroll
+        for (int j = 0; j <= J; ++j) {
+            if (i == 0 && j == 0) continue;
+            const bool up_i = i > 0;
+            const int pi = up_i ? i - 1 : i, pj = up_i ? j : j - 1;
+            const T X = up_i ? XPA : XPB;
+#pragma unroll
+            for (int t = 0; t <= i + j; ++t) {
+                T e = (T)0;
+                if (t > 0) e += inv2p * E[pi][pj][t - 1];
+                if (t <= pi + pj) e += X * E[pi][pj][t];
+                if (t + 1 <= pi + pj) e += (T)(t + 1) * E[pi][pj][t + 1];
+                E[i][j][t] = e;
+            }
+        }
+}
+
+// ------------------------------------------------------------------------------------------
+// warp helpers
+// ------------------------------------------------------------------------------------------
+constexpr unsigned FULL = 0xffffffffu;
+
+// Segmented suffix sum over contiguous segments: after the call, the first lane of every
+// segment holds the segment total.  take[k] says whether lane+2^k lies in the same segment.
+template <typename T>
+__device__ __forceinline__ T seg_reduce(T v, const bool (&take)[5])
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        T o = __shfl_down_sync(FULL, v, 1 << k);
+        if (take[k]) v += o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void seg_setup(int key, int lane, bool (&take)[5], bool &head)
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        int o = __shfl_down_sync(FULL, key, 1 << k);
+        take[k] = (lane + (1 << k) < 32) && (o == key);
+    }
+    int prev = __shfl_up_sync(FULL, key, 1);
+    head = (lane == 0) || (prev != key);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) v += __shfl_xor_sync(FULL, v, k);
+    return v;
+}
+
+// ------------------------------------------------------------------------------------------
+// TMA bulk copy global -> shared with a bounded mbarrier wait
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Error flags written by kernels (read back by the host after the call).
+enum : int { DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
+
+// Stage up to three segments (sizes multiples of 16 bytes, all addresses 16-byte aligned) from
+// global to shared memory with the TMA bulk-copy engine, completing on one mbarrier.  Every
+// thread of the block must call it.  Returns false on every thread (and sets *err) if the copies
+// did not complete within the iteration budget.
+struct Seg { void *dst; const void *src; unsigned bytes; };
+
+__device__ __forceinline__ bool stage_segments(const Seg *seg, int nseg, uint64_t *bar, int *err)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned total = 0;
+        for (int k = 0; k < nseg; ++k) total += seg[k].bytes;
+        mbar_arrive_expect_tx(bar, total);
+        for (int k = 0; k < nseg; ++k) {
+            // pieces of at most 64 KiB, one bulk copy each
+            const char *s = (const char *)seg[k].src;
+            char *d = (char *)seg[k].dst;
+            unsigned left = seg[k].bytes;
+            while (left) {
+                const unsigned n = left > 65536u ? 65536u : left;
+                bulk_g2s(d, s, n, bar);
+                d += n; s += n; left -= n;
+            }
+        }
+    }
+    bool done = false;
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(bar, 0)) { done = true; break; }
+    }
+    // block-uniform outcome: if any thread gave up, every thread returns
+    const int fail = __syncthreads_or(!done);
+    if (fail && threadIdx.x == 0 && err) atomicOr(err, DEVERR_TIMEOUT);
+    return !fail;
+}
+
+__device__ __forceinline__ bool stage_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *bar, int *err)
+{
+    Seg s{dst, src, bytes};
+    return stage_segments(&s, 1, bar, err);
+}
+
+// double-float accumulation: (hi, lo) += x with an error-free two-sum
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float v = s - hi;
+    const float e = (hi - (s - v)) + (x - v);
+    hi = s;
+    lo += e;
+}
+
+// ------------------------------------------------------------------------------------------
+// multipole interaction tensors of a radial function (Ewald kernels, FP64)
+//   T = f, T_a = d_a f, T_ab = 1/2 d_ab f, T_abc = 1/6 d_abc f  (derivatives w.r.t. R_j),
+//   d_a f = x_a g1, d_ab f = delta_ab g1 + x_a x_b g2,
+//   d_abc f = (delta_ab x_c + delta_ac x_b + delta_bc x_a) g2 + x_a x_b x_c g3,
+// with g1 = f'/r, g2 = g1'/r, g3 = g2'/r.  For 1/r: g1 = -r^-3, g2 = 3 r^-5, g3 = -15 r^-7.
+// For erfc(beta r)/r (SI screened tensors): g1 = -f3, g2 = 3 f5, g3 = -15 f7.
+// Component order: 0 | x y z | xx xy xz yy yz zz | xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void radial_tensor(double f, double g1, double g2, double g3, double x, double y,
+                                              double z, double *T /* [20] */, int order /* 1..3 */)
+{
+    T[0] = f;
+    T[1] = x * g1; T[2] = y * g1; T[3] = z * g1;
+    if (order < 2) return;
+    T[4] = 0.5 * (g1 + x * x * g2);
+    T[5] = 0.5 * (x * y * g2);
+    T[6] = 0.5 * (x * z * g2);
+    T[7] = 0.5 * (g1 + y * y * g2);
+    T[8] = 0.5 * (y * z * g2);
+    T[9] = 0.5 * (g1 + z * z * g2);
+    if (order < 3) return;
+    const double s6 = 1.0 / 6.0;
+    T[10] = s6 * (3.0 * x * g2 + x * x * x * g3);       // xxx
+    T[11] = s6 * (y * g2 + x * x * y * g3);             // xxy
+    T[12] = s6 * (z * g2 + x * x * z * g3);             // xxz
+    T[13] = s6 * (x * g2 + x * y * y * g3);             // xyy
+    T[14] = s6 * (x * y * z * g3);                      // xyz
+    T[15] = s6 * (x * g2 + x * z * z * g3);             // xzz
+    T[16] = s6 * (3.0 * y * g2 + y * y * y * g3);       // yyy
+    T[17] = s6 * (z * g2 + y * y * z * g3);             // yyz
+    T[18] = s6 * (y * g2 + y * z * z * g3);             // yzz
+    T[19] = s6 * (3.0 * z * g2 + z * z * z * g3);       // zzz
+}
+
+__device__ __forceinline__ void point_radial(double r2, double &f, double &g1, double &g2, double &g3)
+{
+    const double ri = rsqrt(r2), ri2 = ri * ri;
+    f = ri;
+    g1 = -f * ri2;
+    g2 = -3.0 * g1 * ri2;
+    g3 = -5.0 * g2 * ri2;
+}
+
+__device__ __forceinline__ void screened_radial(double r2, double beta, double &f, double &g1, double &g2,
+                                                double &g3)
+{
+    const double r = sqrt(r2), ri2 = 1.0 / r2;
+    const double e = exp(-beta * beta * r2);
+    const double c = beta * (2.0 / 1.7724538509055160273);  // 2 beta / sqrt(pi)
+    const double f1 = erfc(beta * r) / r;
+    const double f3 = (f1 + c * e) * ri2;
+    const double b2 = beta * beta;
+    const double f5 = (f3 + (2.0 / 3.0) * b2 * c * e) * ri2;
+    const double f7 = (f5 + (4.0 / 15.0) * b2 * b2 * c * e) * ri2;
+    f = f1; g1 = -f3; g2 = 3.0 * f5; g3 = -15.0 * f7;
+}
+
+// weights of the 10 stored (Q, mu, theta) components in a full (a,b) contraction
+__device__ __forceinline__ double w10(int k) { return (k == 5 || k == 6 || k == 8) ? 2.0 : 1.0; }
+
+}  // namespace qmmm

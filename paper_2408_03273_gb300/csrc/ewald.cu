@@ -1,0 +1,855 @@
+// ewald.cu -- region I and the multipolar Ewald interaction between QM multipoles and MM charges
+// (Eq. 6, QM-MM lines; Eq. 10; SI "Multipolar Ewald"), FP64 throughout.
+//
+// Region-II potential at QM atom j (20 Taylor components c):
+//   v_j,c = sum_i q_i [ psi_c(R_j - R_i) - sum_{L: i+L in I} T_c - sum_{L: i+L not in I} That_c(1/sigma_i) ]
+//   psi = psi_SR (erfc(alpha r)/r tensors over images within the Ewald cutoff)
+//       + psi_LR ((4 pi / V) sum_{G != 0} exp(-G^2/4alpha^2)/G^2 cos(G.(R_j - R_i)) and its
+//         derivatives, prefactors (iG)^n / n!)
+//       - pi/(V alpha^2) on the monopole (neutralising background).
+// The reciprocal part uses the structure factor S(G) = sum_i q_i exp(i G.R_i), evaluated over the
+// half space of the cube |n_c| <= kmax (the -G partner is its conjugate) with separable phases
+// exp(i G.R) = X(n_x) Y(n_y) Z(n_z): a thread owns one (n_x, n_y) line and eight n_z values, so each
+// (G, charge) term costs one complex multiply-add.
+// The adjoint needs the same tensors contracted with the multipoles, at every MM site:
+//   dE/dq_i = sum_j sum_c w_c M_j,c Psi_c(j,i),  dE/dR_i = -q_i sum_j sum_c w_c M_j,c dPsi_c/dR_j.
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "qmmm_internal.h"
+
+namespace qmmm {
+
+// ---------------------------------------------------------------------------------------------
+// region I
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool in_region1(const EwaldDev &e, double x, double y, double z)
+{
+    const double dx = x - e.centre[0], dy = y - e.centre[1], dz = z - e.centre[2];
+    return dx * dx + dy * dy + dz * dz < e.rcut * e.rcut;
+}
+
+// Images of MM charge i that lie in region I, in (nx, ny, nz) order; calls f(pos, n) for each.
+template <typename Fn>
+__device__ __forceinline__ int region1_images(const EwaldDev &e, int i, Fn f)
+{
+    const double x = e.mm_xyz[3 * i], y = e.mm_xyz[3 * i + 1], z = e.mm_xyz[3 * i + 2];
+    const double n0x = -rint((x - e.centre[0]) / e.box[0]);
+    const double n0y = -rint((y - e.centre[1]) / e.box[1]);
+    const double n0z = -rint((z - e.centre[2]) / e.box[2]);
+    const int mx = (int)ceil(e.rcut / e.box[0]), my = (int)ceil(e.rcut / e.box[1]), mz = (int)ceil(e.rcut / e.box[2]);
+    int cnt = 0;
+    for (int a = -mx; a <= mx; ++a)
+        for (int b = -my; b <= my; ++b)
+            for (int c = -mz; c <= mz; ++c) {
+                const double px = x + (n0x + a) * e.box[0];
+                const double py = y + (n0y + b) * e.box[1];
+                const double pz = z + (n0z + c) * e.box[2];
+                if (in_region1(e, px, py, pz)) {
+                    f(px, py, pz, cnt);
+                    ++cnt;
+                }
+            }
+    return cnt;
+}
+
+__global__ void k_region1_count(EwaldDev e, int *blk_count, int *cls_count)
+{
+    __shared__ int ws[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
+    if (i < e.nmm) {
+        cnt = region1_images(e, i, [](double, double, double, int) {});
+        if (cnt) atomicAdd(cls_count + e.mm_cls[i], cnt);
+    }
+    int s = cnt;
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(FULL, s, k);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        blk_count[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of nblk counts in place; blk[nblk] receives the total (single block)
+__global__ void k_scan_blocks(int *blk, int nblk)
+{
+    __shared__ int carry;
+    __shared__ int ws[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblk; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblk ? blk[i] : 0;
+        // inclusive warp scan
+        int x = v;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const int o = __shfl_up_sync(FULL, x, k);
+            if ((threadIdx.x & 31) >= k) x += o;
+        }
+        if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int y = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
+#pragma unroll
+            for (int k = 1; k < 32; k <<= 1) {
+                const int o = __shfl_up_sync(FULL, y, k);
+                if (threadIdx.x >= k) y += o;
+            }
+            ws[threadIdx.x] = y;
+        }
+        __syncthreads();
+        const int wpre = (threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0;
+        const int excl = carry + wpre + x - v;
+        const int tot = ws[(blockDim.x >> 5) - 1];
+        __syncthreads();
+        if (i < nblk) blk[i] = excl;
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) blk[nblk] = carry;
+}
+
+__global__ void k_region1_fill(EwaldDev e, const int *blk_off, double4_32a *chg, float4 *hi, float4 *lo, int *idx)
+{
+    __shared__ int ws[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
+    if (i < e.nmm) cnt = region1_images(e, i, [](double, double, double, int) {});
+    // block exclusive scan of cnt
+    int x = cnt;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const int o = __shfl_up_sync(FULL, x, k);
+        if ((threadIdx.x & 31) >= k) x += o;
+    }
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int y = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const int o = __shfl_up_sync(FULL, y, k);
+            if (threadIdx.x >= k) y += o;
+        }
+        ws[threadIdx.x] = y;
+    }
+    __syncthreads();
+    const int wpre = (threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0;
+    const int base = blk_off[blockIdx.x] + wpre + x - cnt;
+    if (i < e.nmm && cnt) {
+        const double q = e.mm_q[i];
+        region1_images(e, i, [&](double px, double py, double pz, int k) {
+            const int o = base + k;
+            double4_32a c;
+            c.x = px; c.y = py; c.z = pz; c.w = q;
+            chg[o] = c;
+            const double rx = px - e.centre[0], ry = py - e.centre[1], rz = pz - e.centre[2];
+            const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+            hi[o] = make_float4(hx, hy, hz, (float)q);
+            lo[o] = make_float4((float)(rx - hx), (float)(ry - hy), (float)(rz - hz), 0.0f);
+            idx[o] = i;
+        });
+    }
+}
+
+cudaError_t launch_region1_count(const EwaldDev &e, int *blk_count, int *cls_count, int nblk, cudaStream_t st)
+{
+    k_region1_count<<<nblk, 256, 0, st>>>(e, blk_count, cls_count);
+    return cudaGetLastError();
+}
+cudaError_t launch_scan_blocks(int *blk, int nblk, cudaStream_t st)
+{
+    k_scan_blocks<<<1, 1024, 0, st>>>(blk, nblk);
+    return cudaGetLastError();
+}
+cudaError_t launch_region1_fill(const EwaldDev &e, const int *blk_off, double4_32a *chg, float4 *hi, float4 *lo,
+                                int *idx, int nblk, cudaStream_t st)
+{
+    k_region1_fill<<<nblk, 256, 0, st>>>(e, blk_off, chg, hi, lo, idx);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// block reduction of NV doubles into out[] (deterministic: fixed tree)
+// ---------------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double *out, double *scratch /* 32*NV */)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[w * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int ww = 0; ww < nw; ++ww) s += scratch[ww * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// QM-site potential: real space (psi_SR and the T-hat correction of Eq. 10)
+// grid (nslice, natm); partial[(j*nslice + slice)*20 + c]
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_phi_real(EwaldDev e, double *partial)
+{
+    __shared__ double scratch[8 * 20];
+    const int j = blockIdx.y, nslice = gridDim.x;
+    const double Rx = e.qm_xyz[3 * j], Ry = e.qm_xyz[3 * j + 1], Rz = e.qm_xyz[3 * j + 2];
+    const double rc2 = e.ewald_rc * e.ewald_rc;
+    double acc[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
+    double T[20];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nmm; i += nslice * blockDim.x) {
+        const double q = e.mm_q[i], beta = e.mm_beta[i];
+        const double xi = e.mm_xyz[3 * i], yi = e.mm_xyz[3 * i + 1], zi = e.mm_xyz[3 * i + 2];
+        const double dx0 = Rx - xi, dy0 = Ry - yi, dz0 = Rz - zi;
+        const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
+        const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
+        for (int a = -e.img[0]; a <= e.img[0]; ++a)
+            for (int b = -e.img[1]; b <= e.img[1]; ++b)
+                for (int c = -e.img[2]; c <= e.img[2]; ++c) {
+                    const double sx = (nx0 + a) * e.box[0], sy = (ny0 + b) * e.box[1], sz = (nz0 + c) * e.box[2];
+                    const double x = dx0 - sx, y = dy0 - sy, z = dz0 - sz;
+                    const double r2 = x * x + y * y + z * z;
+                    if (r2 < rc2) {
+                        double f, g1, g2, g3;
+                        screened_radial(r2, e.alpha, f, g1, g2, g3);
+                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+#pragma unroll
+                        for (int k = 0; k < 20; ++k) acc[k] += q * T[k];
+                    }
+                    if (r2 < rhat2 && !in_region1(e, xi + sx, yi + sy, zi + sz)) {
+                        double f, g1, g2, g3;
+                        screened_radial(r2, beta, f, g1, g2, g3);
+                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+#pragma unroll
+                        for (int k = 0; k < 20; ++k) acc[k] -= q * T[k];
+                    }
+                }
+    }
+    block_reduce_store<20>(acc, partial + ((size_t)j * nslice + blockIdx.x) * 20, scratch);
+}
+
+// region-I point tensors: grid natm; out[j*20 + c]
+__global__ void __launch_bounds__(256) k_phi_region1(EwaldDev e, const double4_32a *rI, int nI, double *out)
+{
+    __shared__ double scratch[8 * 20];
+    const int j = blockIdx.x;
+    const double Rx = e.qm_xyz[3 * j], Ry = e.qm_xyz[3 * j + 1], Rz = e.qm_xyz[3 * j + 2];
+    double acc[20], T[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
+    for (int k = threadIdx.x; k < nI; k += blockDim.x) {
+        const double4_32a c = rI[k];
+        const double x = Rx - c.x, y = Ry - c.y, z = Rz - c.z;
+        double f, g1, g2, g3;
+        point_radial(x * x + y * y + z * z, f, g1, g2, g3);
+        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+#pragma unroll
+        for (int m = 0; m < 20; ++m) acc[m] -= c.w * T[m];
+    }
+    block_reduce_store<20>(acc, out + (size_t)j * 20, scratch);
+}
+
+// ---------------------------------------------------------------------------------------------
+// reciprocal space: structure factor over the dense box nx in [0,kx], ny in [-ky,ky], nz in [-kz,kz]
+// ---------------------------------------------------------------------------------------------
+constexpr int SF_TILE = 32;  // charges per shared-memory phase tile
+constexpr int SF_NZ = 8;     // nz values per thread
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// Phase tables e^{i 2 pi n x / L} for n = 0..nmax by repeated multiplication (relative error
+// grows by about one rounding per step).
+__device__ __forceinline__ void phase_row(double2 *dst, double frac /* x/L */, int nmax, int stride)
+{
+    double s, c;
+    sincospi(2.0 * frac, &s, &c);
+    const double2 e1 = make_double2(c, s);
+    double2 z = make_double2(1.0, 0.0);
+    for (int n = 0; n <= nmax; ++n) {
+        dst[n * stride] = z;
+        z = cmul(z, e1);
+    }
+}
+
+// grid (ceil(items/256), nslice); items = NL * NZC; partial[slice][NL][2kz+1]; `tile` charges
+// (<= SF_TILE) per shared-memory phase tile
+__global__ void __launch_bounds__(256) k_structure_factor(EwaldDev e, double2 *partial, int tile)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NX = kx + 1, NY = 2 * ky + 1, NZ = 2 * kz + 1;
+    const int NZC = (NZ + SF_NZ - 1) / SF_NZ;
+    const int NL = NX * NY;
+    double2 *px = reinterpret_cast<double2 *>(smem_raw);   // [tile][NX]
+    double2 *py = px + tile * NX;                            // [tile][NY] (index n+ky)
+    double2 *pz = py + tile * NY;                            // [tile][NZ]
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = item < NL * NZC;
+    const int line = active ? item / NZC : 0, zc = active ? item % NZC : 0;
+    const int nx = line / NY, iy = line % NY, iz0 = zc * SF_NZ;
+    double2 acc[SF_NZ];
+#pragma unroll
+    for (int k = 0; k < SF_NZ; ++k) acc[k] = make_double2(0.0, 0.0);
+
+    const int nslice = gridDim.y;
+    const int per = (e.nmm + nslice - 1) / nslice;
+    const int i0 = blockIdx.y * per, i1 = min(e.nmm, i0 + per);
+    for (int t0 = i0; t0 < i1; t0 += tile) {
+        const int nt = min(tile, i1 - t0);
+        __syncthreads();
+        // 3 * nt rows of phases; negative n from the conjugate of positive n
+        for (int r = threadIdx.x; r < 3 * tile; r += blockDim.x) {
+            const int c = r / 3, d = r % 3;
+            if (c >= nt) continue;
+            const double x = e.mm_xyz[3 * (t0 + c) + d] / e.box[d];
+            if (d == 0) {
+                phase_row(px + c * NX, x, kx, 1);
+                const double q = e.mm_q[t0 + c];
+                for (int n = 0; n < NX; ++n) px[c * NX + n] = make_double2(q * px[c * NX + n].x, q * px[c * NX + n].y);
+            } else if (d == 1) {
+                phase_row(py + c * NY + ky, x, ky, 1);
+                for (int n = 1; n <= ky; ++n) {
+                    const double2 v = py[c * NY + ky + n];
+                    py[c * NY + ky - n] = make_double2(v.x, -v.y);
+                }
+            } else {
+                phase_row(pz + c * NZ + kz, x, kz, 1);
+                for (int n = 1; n <= kz; ++n) {
+                    const double2 v = pz[c * NZ + kz + n];
+                    pz[c * NZ + kz - n] = make_double2(v.x, -v.y);
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+            for (int c = 0; c < nt; ++c) {
+                const double2 a = cmul(px[c * NX + nx], py[c * NY + iy]);
+                const double2 *zr = pz + c * NZ;
+#pragma unroll
+                for (int k = 0; k < SF_NZ; ++k) {
+                    const int iz = iz0 + k;
+                    const double2 b = zr[iz < NZ ? iz : NZ - 1];
+                    acc[k].x = fma(a.x, b.x, fma(-a.y, b.y, acc[k].x));
+                    acc[k].y = fma(a.x, b.y, fma(a.y, b.x, acc[k].y));
+                }
+            }
+        }
+    }
+    if (active) {
+        double2 *dst = partial + ((size_t)blockIdx.y * NL + line) * NZ;
+#pragma unroll
+        for (int k = 0; k < SF_NZ; ++k)
+            if (iz0 + k < NZ) dst[iz0 + k] = acc[k];
+    }
+}
+
+__global__ void k_sum_slices(const double2 *partial, int nslice, int n, double2 *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int sl = 0; sl < nslice; ++sl) {
+        const double2 v = partial[(size_t)sl * n + k];
+        s.x += v.x; s.y += v.y;
+    }
+    out[k] = s;
+}
+
+// reciprocal factor of a dense index: 2 g(G) on the half space (n_x > 0, or n_x = 0 and
+// (n_y > 0 or (n_y = 0 and n_z > 0))), zero elsewhere; written at plan time.
+__global__ void k_gfac(EwaldDev e, double *gfac)
+{
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int nx = k / (NY * NZ), ny = (k / NZ) % NY - ky, nz = k % NZ - kz;
+    const bool half = nx > 0 || (nx == 0 && (ny > 0 || (ny == 0 && nz > 0)));
+    if (!half) { gfac[k] = 0.0; return; }
+    const double V = e.box[0] * e.box[1] * e.box[2];
+    const double Gx = TWO_PI * nx / e.box[0], Gy = TWO_PI * ny / e.box[1], Gz = TWO_PI * nz / e.box[2];
+    const double G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+    gfac[k] = 2.0 * 4.0 * PI / V * exp(-G2 / (4.0 * e.alpha * e.alpha)) / G2;
+}
+
+// QM-site reciprocal part + combination: grid natm
+__global__ void __launch_bounds__(256) k_phi_recip_combine(EwaldDev e, const double2 *S, const double *gfac,
+                                                            const double *, int, const double *, double,
+                                                            double *phi)
+{
+    __shared__ double scratch[8 * 20];
+    __shared__ double res[20];
+    const int j = blockIdx.x;
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
+    const double Rx = e.qm_xyz[3 * j], Ry = e.qm_xyz[3 * j + 1], Rz = e.qm_xyz[3 * j + 2];
+    double acc[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double g = gfac[k];
+        if (g == 0.0) continue;
+        const int nx = k / (NY * NZ), ny = (k / NZ) % NY - ky, nz = k % NZ - kz;
+        const double Gx = TWO_PI * nx / e.box[0], Gy = TWO_PI * ny / e.box[1], Gz = TWO_PI * nz / e.box[2];
+        double s, c;
+        sincos(Gx * Rx + Gy * Ry + Gz * Rz, &s, &c);
+        const double2 Sk = S[k];
+        // exp(i G.R_j) conj(S)
+        const double re = g * (c * Sk.x + s * Sk.y);
+        const double im = g * (s * Sk.x - c * Sk.y);
+        const double G[3] = {Gx, Gy, Gz};
+        acc[0] += re;
+        acc[1] -= Gx * im; acc[2] -= Gy * im; acc[3] -= Gz * im;
+        acc[4] -= 0.5 * Gx * Gx * re; acc[5] -= 0.5 * Gx * Gy * re; acc[6] -= 0.5 * Gx * Gz * re;
+        acc[7] -= 0.5 * Gy * Gy * re; acc[8] -= 0.5 * Gy * Gz * re; acc[9] -= 0.5 * Gz * Gz * re;
+        const double s6 = im / 6.0;
+        acc[10] += s6 * G[0] * G[0] * G[0]; acc[11] += s6 * G[0] * G[0] * G[1]; acc[12] += s6 * G[0] * G[0] * G[2];
+        acc[13] += s6 * G[0] * G[1] * G[1]; acc[14] += s6 * G[0] * G[1] * G[2]; acc[15] += s6 * G[0] * G[2] * G[2];
+        acc[16] += s6 * G[1] * G[1] * G[1]; acc[17] += s6 * G[1] * G[1] * G[2]; acc[18] += s6 * G[1] * G[2] * G[2];
+        acc[19] += s6 * G[2] * G[2] * G[2];
+    }
+    block_reduce_store<20>(acc, res, scratch);
+    if (threadIdx.x < 20) phi[(size_t)j * 20 + threadIdx.x] = res[threadIdx.x];
+}
+
+int ewald_dense_size(const EwaldDev &e)
+{
+    return (e.kmax[0] + 1) * (2 * e.kmax[1] + 1) * (2 * e.kmax[2] + 1);
+}
+static int sf_items(const EwaldDev &e)
+{
+    const int NZ = 2 * e.kmax[2] + 1;
+    return (e.kmax[0] + 1) * (2 * e.kmax[1] + 1) * ((NZ + SF_NZ - 1) / SF_NZ);
+}
+int ewald_sf_nslice(const EwaldDev &e)
+{
+    const int bx = (sf_items(e) + 255) / 256;
+    int ns = (2 * 152 + bx - 1) / bx;
+    if (ns > 64) ns = 64;
+    if (ns > e.nmm / SF_TILE + 1) ns = e.nmm / SF_TILE + 1;
+    if (ns < 1) ns = 1;
+    return ns;
+}
+int ewald_real_nslice(const EwaldDev &e, int nsm)
+{
+    int ns = (2 * nsm + e.natm - 1) / (e.natm > 0 ? e.natm : 1);
+    if (ns > (e.nmm + 255) / 256) ns = (e.nmm + 255) / 256;
+    if (ns < 1) ns = 1;
+    return ns;
+}
+cudaError_t launch_gfac(const EwaldDev &e, double *gfac, cudaStream_t st)
+{
+    const int n = ewald_dense_size(e);
+    k_gfac<<<(n + 255) / 256, 256, 0, st>>>(e, gfac);
+    return cudaGetLastError();
+}
+
+__global__ void k_sum1(const double *x, int n, int stride, double *out)
+{
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += x[(size_t)k * stride];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        out[0] = t;
+    }
+}
+cudaError_t launch_sum(const double *x, int n, double *out, cudaStream_t st)
+{
+    k_sum1<<<1, 1024, 0, st>>>(x, n, 1, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_sum_strided(const double *x, int n, int stride, double *out, cudaStream_t st)
+{
+    k_sum1<<<1, 1024, 0, st>>>(x, n, stride, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_phi_final(EwaldDev e, const double *res_recip, const double *preal, int nslice, const double *pr1,
+                            const double *sums, double *phi)
+{
+    const int j = blockIdx.x, k = threadIdx.x;
+    if (k >= 20) return;
+    double v = res_recip[(size_t)j * 20 + k];
+    for (int sl = 0; sl < nslice; ++sl) v += preal[((size_t)j * nslice + sl) * 20 + k];
+    v += pr1[(size_t)j * 20 + k];
+    if (k == 0) v += -PI / (e.box[0] * e.box[1] * e.box[2] * e.alpha * e.alpha) * sums[0];
+    phi[(size_t)j * 20 + k] = v;
+}
+
+cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, const EwaldBuf &w, double *phi,
+                             cudaStream_t st)
+{
+    cudaError_t err;
+    // sum of MM charges (background)
+    if ((err = launch_sum(e.mm_q, e.nmm, w.sums, st)) != cudaSuccess) return err;
+    // real space
+    {
+        dim3 grid(w.real_nslice, e.natm);
+        k_phi_real<<<grid, 256, 0, st>>>(e, w.preal);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    k_phi_region1<<<e.natm, 256, 0, st>>>(e, rI, nI, w.pr1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // structure factor
+    {
+        const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+        const size_t row = (size_t)(NX + NY + NZ) * sizeof(double2);
+        int tile = (int)std::min<size_t>(SF_TILE, (200u * 1024u) / row);
+        if (tile < 1) tile = 1;
+        const size_t smem = (size_t)tile * row;
+        static size_t attr = 0;
+        if (smem > 48 * 1024 && smem > attr) {
+            if ((err = cudaFuncSetAttribute(k_structure_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem)) != cudaSuccess)
+                return err;
+            attr = smem;
+        }
+        dim3 grid((sf_items(e) + 255) / 256, w.sf_nslice);
+        k_structure_factor<<<grid, 256, smem, st>>>(e, w.Spart, tile);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        const int n = ewald_dense_size(e);
+        k_sum_slices<<<(n + 255) / 256, 256, 0, st>>>(w.Spart, w.sf_nslice, n, w.S);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    // reciprocal part at the QM sites into phi (temporarily), then the final combination
+    k_phi_recip_combine<<<e.natm, 256, 0, st>>>(e, w.S, w.gfac, nullptr, 0, nullptr, 0.0, phi);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    k_phi_final<<<e.natm, 32, 0, st>>>(e, phi, w.preal, w.real_nslice, w.pr1, w.sums, phi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// MM-side adjoint
+// ---------------------------------------------------------------------------------------------
+// contraction helpers: potential sum_c w_c M_c T_c and field d/dR_j of it
+__device__ __forceinline__ void contract_pot_field(const double *M, const double *T, double &pot, double (&fld)[3])
+{
+    pot = M[0] * T[0] + M[1] * T[1] + M[2] * T[2] + M[3] * T[3] + M[4] * T[4] + 2.0 * M[5] * T[5] +
+          2.0 * M[6] * T[6] + M[7] * T[7] + 2.0 * M[8] * T[8] + M[9] * T[9];
+    // d_x T_0 = T_x; d_x T_a = 2 T_ax; d_x T_ab = 3 T_abx   (index tables of the symmetric tensors)
+    const int I2[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
+    const int I3[3][3][3] = {{{10, 11, 12}, {11, 13, 14}, {12, 14, 15}},
+                             {{11, 13, 14}, {13, 16, 17}, {14, 17, 18}},
+                             {{12, 14, 15}, {14, 17, 18}, {15, 18, 19}}};
+    const int P2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        double g = M[0] * T[1 + x];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g += 2.0 * M[1 + a] * T[I2[a][x]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g += 3.0 * w10(4 + k) * M[4 + k] * T[I3[P2[k][0]][P2[k][1]][x]];
+        fld[x] = g;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mm_real(EwaldDev e, const double *mult, double *dq, double *dR)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= e.nmm) return;
+    const double q = e.mm_q[i], beta = e.mm_beta[i];
+    const double xi = e.mm_xyz[3 * i], yi = e.mm_xyz[3 * i + 1], zi = e.mm_xyz[3 * i + 2];
+    const double rc2 = e.ewald_rc * e.ewald_rc;
+    const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
+    double pot = 0.0, fld[3] = {0.0, 0.0, 0.0}, T[20];
+    for (int j = 0; j < e.natm; ++j) {
+        const double dx0 = __ldg(e.qm_xyz + 3 * j) - xi, dy0 = __ldg(e.qm_xyz + 3 * j + 1) - yi,
+                     dz0 = __ldg(e.qm_xyz + 3 * j + 2) - zi;
+        const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
+        for (int a = -e.img[0]; a <= e.img[0]; ++a)
+            for (int b = -e.img[1]; b <= e.img[1]; ++b)
+                for (int c = -e.img[2]; c <= e.img[2]; ++c) {
+                    const double sx = (nx0 + a) * e.box[0], sy = (ny0 + b) * e.box[1], sz = (nz0 + c) * e.box[2];
+                    const double x = dx0 - sx, y = dy0 - sy, z = dz0 - sz;
+                    const double r2 = x * x + y * y + z * z;
+                    const bool sr = r2 < rc2;
+                    const bool hat = r2 < rhat2 && !in_region1(e, xi + sx, yi + sy, zi + sz);
+                    if (!sr && !hat) continue;
+                    double Mj[10];
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) Mj[k] = __ldg(mult + 10 * j + k);
+                    double f, g1, g2, g3, p, fl[3];
+                    if (sr) {
+                        screened_radial(r2, e.alpha, f, g1, g2, g3);
+                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+                        contract_pot_field(Mj, T, p, fl);
+                        pot += p; fld[0] += fl[0]; fld[1] += fl[1]; fld[2] += fl[2];
+                    }
+                    if (hat) {
+                        screened_radial(r2, beta, f, g1, g2, g3);
+                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+                        contract_pot_field(Mj, T, p, fl);
+                        pot -= p; fld[0] -= fl[0]; fld[1] -= fl[1]; fld[2] -= fl[2];
+                    }
+                }
+    }
+    dq[i] += pot;
+    dR[3 * i] += -q * fld[0];
+    dR[3 * i + 1] += -q * fld[1];
+    dR[3 * i + 2] += -q * fld[2];
+}
+
+// minus the point tensors over region I, per region-I image (gchg += : [dC_x, dC_y, dC_z, dq])
+__global__ void __launch_bounds__(256) k_mm_region1(EwaldDev e, const double4_32a *rI, int nI, const double *mult,
+                                                     double *gchg)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nI) return;
+    const double4_32a c = rI[k];
+    double pot = 0.0, fld[3] = {0.0, 0.0, 0.0}, T[20];
+    for (int j = 0; j < e.natm; ++j) {
+        const double x = __ldg(e.qm_xyz + 3 * j) - c.x, y = __ldg(e.qm_xyz + 3 * j + 1) - c.y,
+                     z = __ldg(e.qm_xyz + 3 * j + 2) - c.z;
+        double f, g1, g2, g3, p, fl[3], Mj[10];
+#pragma unroll
+        for (int m = 0; m < 10; ++m) Mj[m] = __ldg(mult + 10 * j + m);
+        point_radial(x * x + y * y + z * z, f, g1, g2, g3);
+        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+        contract_pot_field(Mj, T, p, fl);
+        pot += p; fld[0] += fl[0]; fld[1] += fl[1]; fld[2] += fl[2];
+    }
+    gchg[4 * (size_t)k + 0] += c.w * fld[0];
+    gchg[4 * (size_t)k + 1] += c.w * fld[1];
+    gchg[4 * (size_t)k + 2] += c.w * fld[2];
+    gchg[4 * (size_t)k + 3] -= pot;
+}
+
+// A(G) = 2 g(G) sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G) on the dense box
+__global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *gfac, const double *mult, double2 *A)
+{
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double g = gfac[k];
+    if (g == 0.0) { A[k] = make_double2(0.0, 0.0); return; }
+    const int nx = k / (NY * NZ), ny = (k / NZ) % NY - ky, nz = k % NZ - kz;
+    const double Gx = TWO_PI * nx / e.box[0], Gy = TWO_PI * ny / e.box[1], Gz = TWO_PI * nz / e.box[2];
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < e.natm; ++j) {
+        const double *M = mult + 10 * j;
+        const double mr = M[0] - 0.5 * (M[4] * Gx * Gx + 2.0 * M[5] * Gx * Gy + 2.0 * M[6] * Gx * Gz + M[7] * Gy * Gy +
+                                        2.0 * M[8] * Gy * Gz + M[9] * Gz * Gz);
+        const double mi = Gx * M[1] + Gy * M[2] + Gz * M[3];
+        double s, c;
+        sincos(Gx * e.qm_xyz[3 * j] + Gy * e.qm_xyz[3 * j + 1] + Gz * e.qm_xyz[3 * j + 2], &s, &c);
+        re += c * mr - s * mi;
+        im += s * mr + c * mi;
+    }
+    A[k] = make_double2(g * re, g * im);
+}
+
+// dq_i += sum_G Re[A(G) exp(-iG.R_i)],  dR_i += q_i sum_G G Im[A(G) exp(-iG.R_i)]
+__global__ void __launch_bounds__(128) k_mm_recip(EwaldDev e, const double2 *__restrict__ A, double *dq, double *dR)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= e.nmm) return;
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1;
+    const double fx = e.mm_xyz[3 * i] / e.box[0], fy = e.mm_xyz[3 * i + 1] / e.box[1], fz = e.mm_xyz[3 * i + 2] / e.box[2];
+    double s, c;
+    sincospi(-2.0 * fx, &s, &c);
+    const double2 ex1 = make_double2(c, s);
+    sincospi(-2.0 * fy, &s, &c);
+    const double2 ey1 = make_double2(c, s);
+    sincospi(-2.0 * fz, &s, &c);
+    const double2 ez1 = make_double2(c, s);
+    sincospi(2.0 * ky * fy, &s, &c);
+    const double2 ey0 = make_double2(c, s);   // n_y = -ky
+    sincospi(2.0 * kz * fz, &s, &c);
+    const double2 ez0 = make_double2(c, s);   // n_z = -kz
+    const double gzs = TWO_PI / e.box[2];
+    double pot = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    double2 px = make_double2(1.0, 0.0);
+    for (int nx = 0; nx <= kx; ++nx) {
+        double2 py = ey0;
+        const double Gx = TWO_PI * nx / e.box[0];
+        for (int iy = 0; iy < NY; ++iy) {
+            const double Gy = TWO_PI * (iy - ky) / e.box[1];
+            const double2 pxy = cmul(px, py);
+            const double2 *Ar = A + ((size_t)nx * NY + iy) * NZ;
+            double2 pz = ez0;
+            double are = 0.0, aim = 0.0, aimz = 0.0;
+            for (int iz = 0; iz < NZ; ++iz) {
+                const double2 a = __ldg(Ar + iz);
+                const double2 ph = cmul(pxy, pz);
+                const double re = a.x * ph.x - a.y * ph.y;
+                const double im = a.x * ph.y + a.y * ph.x;
+                are += re;
+                aim += im;
+                aimz += (iz - kz) * im;
+                pz = cmul(pz, ez1);
+            }
+            pot += are;
+            f0 += Gx * aim;
+            f1 += Gy * aim;
+            f2 += gzs * aimz;
+            py = cmul(py, ey1);
+        }
+        px = cmul(px, ex1);
+    }
+    const double q = e.mm_q[i];
+    dq[i] += pot;
+    dR[3 * i] += q * f0;
+    dR[3 * i + 1] += q * f1;
+    dR[3 * i + 2] += q * f2;
+}
+
+__global__ void k_mm_background(EwaldDev e, const double *sums, double *dq)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= e.nmm) return;
+    dq[i] += -PI / (e.box[0] * e.box[1] * e.box[2] * e.alpha * e.alpha) * sums[1];
+}
+
+// QM tensor gradient: dE/dR_j,x = sum_c w_c M_j,c d_x v_j,c (d_x v_0 = v_x, d_x v_a = 2 v_ax, d_x v_ab = 3 v_abx)
+__global__ void k_qm_tensor_grad(int natm, const double *mult, const double *phi, double *gqm)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= natm) return;
+    double p, fl[3];
+    contract_pot_field(mult + 10 * j, phi + 20 * j, p, fl);
+    gqm[3 * j] += fl[0];
+    gqm[3 * j + 1] += fl[1];
+    gqm[3 * j + 2] += fl[2];
+}
+
+cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, const double *mult, const double *phi,
+                            const EwaldBuf &w, double *dq_int, double *dR_int, double *gchg, double *gqm,
+                            cudaStream_t st)
+{
+    cudaError_t err;
+    if ((err = launch_sum_strided(mult, e.natm, 10, w.sums + 1, st)) != cudaSuccess) return err;
+    if (e.nmm > 0) {
+        k_mm_real<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, mult, dq_int, dR_int);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (nI > 0) {
+        k_mm_region1<<<(nI + 255) / 256, 256, 0, st>>>(e, rI, nI, mult, gchg);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (e.nmm > 0) {
+        const int n = ewald_dense_size(e);
+        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        k_mm_recip<<<(e.nmm + 127) / 128, 128, 0, st>>>(e, w.A, dq_int, dR_int);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        k_mm_background<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, w.sums, dq_int);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    k_qm_tensor_grad<<<(e.natm + 63) / 64, 64, 0, st>>>(e.natm, mult, phi, gqm);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// region-I nuclear-MM term  sum_j Z_j q_C erf(r/sigma_C)/r  (1/r for point charges)
+// ---------------------------------------------------------------------------------------------
+int enucmm_nblk(int nI) { return nI > 0 ? (nI + 255) / 256 : 1; }
+
+__global__ void __launch_bounds__(256) k_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI,
+                                                const int *rI_idx, int nI, const double *mm_beta, double *Epart,
+                                                double *gqm, double *gchg, int want_grad)
+{
+    __shared__ double ws[8];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = k < nI;
+    double4_32a c;
+    c.x = c.y = c.z = c.w = 0.0;
+    double beta = 0.0;
+    if (act) {
+        c = rI[k];
+        beta = mm_beta[rI_idx[k]];
+    }
+    double E = 0.0, dq = 0.0, dC[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < natm; ++j) {
+        double g[3] = {0.0, 0.0, 0.0};
+        if (act) {
+            const double x = qm_xyz[3 * j] - c.x, y = qm_xyz[3 * j + 1] - c.y, z = qm_xyz[3 * j + 2] - c.z;
+            const double r2 = x * x + y * y + z * z, r = sqrt(r2);
+            double f, fp;
+            if (beta > 0.0) {
+                f = erf(beta * r) / r;
+                fp = (beta * (2.0 / 1.7724538509055160273) * exp(-beta * beta * r2) - f) / r;
+            } else {
+                f = 1.0 / r;
+                fp = -f / r;
+            }
+            const double Zj = Z[j];
+            E += Zj * c.w * f;
+            dq += Zj * f;
+            const double s = Zj * c.w * fp / r;
+            g[0] = s * x; g[1] = s * y; g[2] = s * z;
+            dC[0] -= g[0]; dC[1] -= g[1]; dC[2] -= g[2];
+        }
+        if (want_grad) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const double v = warp_sum(g[x]);
+                if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(gqm + 3 * j + x, v);
+            }
+        }
+    }
+    if (want_grad && act) {
+        gchg[4 * (size_t)k + 0] += dC[0];
+        gchg[4 * (size_t)k + 1] += dC[1];
+        gchg[4 * (size_t)k + 2] += dC[2];
+        gchg[4 * (size_t)k + 3] += dq;
+    }
+    E = warp_sum(E);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = E;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        Epart[blockIdx.x] = t;
+    }
+}
+
+cudaError_t launch_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI, const int *rI_idx,
+                          int nI, const double *mm_beta, double *Epart, double *gqm, double *gchg, int want_grad,
+                          cudaStream_t st)
+{
+    k_enucmm<<<enucmm_nblk(nI), 256, 0, st>>>(qm_xyz, Z, natm, rI, rI_idx, nI, mm_beta, Epart, gqm, gchg, want_grad);
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_region(const int *rI_idx, int nI, const double *gchg, double *dq, double *dR)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nI) return;
+    const int i = rI_idx[k];
+    atomicAdd(dR + 3 * i, gchg[4 * (size_t)k]);
+    atomicAdd(dR + 3 * i + 1, gchg[4 * (size_t)k + 1]);
+    atomicAdd(dR + 3 * i + 2, gchg[4 * (size_t)k + 2]);
+    atomicAdd(dq + i, gchg[4 * (size_t)k + 3]);
+}
+
+cudaError_t launch_scatter_region(const int *rI_idx, int nI, const double *gchg, double *dq_int, double *dR_int,
+                                  cudaStream_t st)
+{
+    if (nI <= 0) return cudaSuccess;
+    k_scatter_region<<<(nI + 255) / 256, 256, 0, st>>>(rI_idx, nI, gchg, dq_int, dR_int);
+    return cudaGetLastError();
+}
+
+}  // namespace qmmm

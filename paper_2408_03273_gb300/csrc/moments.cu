@@ -1,0 +1,167 @@
+// moments.cu -- overlap-type moment integrals about the atom centres and what is built from
+// them: Mulliken charge/dipole/quadrupole (SI, "Multipolar Ewald"), the region-II Fock term of
+// Eqs. 11-14 and the multipole Pulay gradient of Eq. 15.
+//
+// One lane per primitive pair (same class-sorted tiles as the V kernels).  In one direction the
+// moment about a centre K is
+//   <i| (x-K)^e |j> = sum_t E^{ij}_t M^e_t,  M^0 = (1), M^1 = (X_PK, 1),
+//   M^2 = (X_PK^2 + 1/(2p), 2 X_PK, 2)   (times sqrt(pi/p), folded into the prefactor).
+// With the local potential polynomial W_k(r) = sum_c w_c v_k,c O_c(r - R_k) of atom k
+// (w = 1, or 2 for the off-diagonal theta components), the multipole energy is
+// E_II = sum_k Z_k v_k,0 - sum_{mu in k, nu} gamma_{nu mu} <mu|W_k|nu>, hence
+//   F_{mu nu} = -1/2 (<mu|W_{k(mu)}|nu> + <mu|W_{k(nu)}|nu>),
+// and moving the centre B of nu by d changes <mu|W_k|nu> by <mu|W_k|d nu/dB> with
+// d g_b/dB_x = 2b g_{b+1x} - b_x g_{b-1x}; moving atom k (mu and the operator) gives minus that.
+#include "pp_tile.cuh"
+
+namespace qmmm {
+
+__constant__ int c_opx[10] = {0, 1, 0, 0, 2, 1, 1, 0, 0, 0};
+__constant__ int c_opy[10] = {0, 0, 1, 0, 0, 1, 0, 2, 1, 0};
+__constant__ int c_opz[10] = {0, 0, 0, 1, 0, 0, 1, 0, 1, 2};
+__constant__ double c_w10[10] = {1, 1, 1, 1, 1, 2, 2, 1, 2, 1};
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(128)
+k_moments(BasisDev bd, int pp_begin, int pp_end, const double *__restrict__ dm, const double *__restrict__ phi,
+          double *__restrict__ mult, double *__restrict__ F, double *__restrict__ gqm, int mode)
+{
+    constexpr int L = LA + LB, NA = ncart(LA), NB = ncart(LB);
+    constexpr int I = LA + 1, J = LB + 1;
+    const int lane = threadIdx.x & 31;
+    const int i = pp_begin + (blockIdx.x * blockDim.x + threadIdx.x);
+    if (pp_begin + (int)((blockIdx.x * blockDim.x + (threadIdx.x & ~31))) >= pp_end) return;  // whole warp out
+    const PPLane pl = load_pp(bd, i, pp_end);
+    const bool mirror = pl.sp.shA != pl.sp.shB;
+    const bool pulay = (mode & MOM_PULAY) && pl.atomA != pl.atomB;
+
+    // 1-D moment tables about centre A (atom of shell A) and centre B, per direction
+    double SA[3][I + 1][J + 1][3], SB[3][I + 1][J + 1][3];
+    {
+        double E[I + 1][J + 1][I + J + 1];
+        const double h = 0.5 * pl.ip;
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            hermite_E<I, J, double>(E, pl.P[d] - pl.A[d], pl.P[d] - pl.B[d], h);
+            const double XA = pl.P[d] - pl.A[d], XB = pl.P[d] - pl.B[d];
+#pragma unroll
+            for (int a = 0; a <= I; ++a)
+#pragma unroll
+                for (int b = 0; b <= J; ++b) {
+                    const double e0 = E[a][b][0], e1 = (a + b >= 1) ? E[a][b][1] : 0.0,
+                                 e2 = (a + b >= 2) ? E[a][b][2] : 0.0;
+                    SA[d][a][b][0] = e0;
+                    SA[d][a][b][1] = XA * e0 + e1;
+                    SA[d][a][b][2] = (XA * XA + h) * e0 + 2.0 * XA * e1 + 2.0 * e2;
+                    SB[d][a][b][0] = e0;
+                    SB[d][a][b][1] = XB * e0 + e1;
+                    SB[d][a][b][2] = (XB * XB + h) * e0 + 2.0 * XB * e1 + 2.0 * e2;
+                }
+        }
+    }
+    const double spp = PI * pl.ip;
+    const double coef = pl.active ? pl.cab * spp * sqrt(spp) : 0.0;
+    double wA[10], wB[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        wA[k] = c_w10[k] * phi[20 * pl.atomA + k];
+        wB[k] = c_w10[k] * phi[20 * pl.atomB + k];
+    }
+
+    bool take[5], head;
+    seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
+
+    double mA[10], mB[10], g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) mA[k] = mB[k] = 0.0;
+
+#pragma unroll 1
+    for (int ia = 0; ia < NA; ++ia) {
+#pragma unroll 1
+        for (int ib = 0; ib < NB; ++ib) {
+            const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+            const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+            const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
+            double g_ba = 0.0, g_ab = 0.0;
+            if (pl.active && (mode & (MOM_MULT | MOM_PULAY))) {
+                g_ba = dm[c * bd.nao + r];
+                g_ab = dm[r * bd.nao + c];
+            }
+            double fA = 0.0, fB = 0.0;
+#pragma unroll
+            for (int op = 0; op < 10; ++op) {
+                const int ox = c_opx[op], oy = c_opy[op], oz = c_opz[op];
+                const double sa = SA[0][ax][bx][ox] * SA[1][ay][by][oy] * SA[2][az][bz][oz];
+                const double sb = SB[0][ax][bx][ox] * SB[1][ay][by][oy] * SB[2][az][bz][oz];
+                mA[op] -= g_ba * sa;
+                mB[op] -= g_ab * sb;
+                fA += wA[op] * sa;
+                fB += wB[op] * sb;
+                if (pulay) {
+                    // G1: d/dB of <a|W_A|b>;  G2: d/dA of <a|W_B|b>
+                    const double dBx = 2.0 * pl.b * SA[0][ax][bx + 1][ox] - (bx > 0 ? bx * SA[0][ax][bx - 1][ox] : 0.0);
+                    const double dBy = 2.0 * pl.b * SA[1][ay][by + 1][oy] - (by > 0 ? by * SA[1][ay][by - 1][oy] : 0.0);
+                    const double dBz = 2.0 * pl.b * SA[2][az][bz + 1][oz] - (bz > 0 ? bz * SA[2][az][bz - 1][oz] : 0.0);
+                    const double dAx = 2.0 * pl.a * SB[0][ax + 1][bx][ox] - (ax > 0 ? ax * SB[0][ax - 1][bx][ox] : 0.0);
+                    const double dAy = 2.0 * pl.a * SB[1][ay + 1][by][oy] - (ay > 0 ? ay * SB[1][ay - 1][by][oy] : 0.0);
+                    const double dAz = 2.0 * pl.a * SB[2][az + 1][bz][oz] - (az > 0 ? az * SB[2][az - 1][bz][oz] : 0.0);
+                    const double ga = g_ba * wA[op], gb = g_ab * wB[op];
+                    const double sAy = SA[1][ay][by][oy], sAz = SA[2][az][bz][oz], sAx = SA[0][ax][bx][ox];
+                    const double sBy = SB[1][ay][by][oy], sBz = SB[2][az][bz][oz], sBx = SB[0][ax][bx][ox];
+                    g[0] += ga * dBx * sAy * sAz - gb * dAx * sBy * sBz;
+                    g[1] += ga * sAx * dBy * sAz - gb * sBx * dAy * sBz;
+                    g[2] += ga * sAx * sAy * dBz - gb * sBx * sBy * dAz;
+                }
+            }
+            if (mode & MOM_FOCK) {
+                const double f = seg_reduce(-0.5 * coef * (fA + fB), take);
+                if (head && pl.active) {
+                    atomicAdd(F + r * bd.nao + c, f);
+                    if (mirror) atomicAdd(F + c * bd.nao + r, f);
+                }
+            }
+        }
+    }
+    if (mode & MOM_MULT) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            const double va = seg_reduce(coef * mA[k], take);
+            const double vb = seg_reduce(mirror ? coef * mB[k] : 0.0, take);
+            if (head && pl.active) {
+                atomicAdd(mult + 10 * pl.atomA + k, va);
+                if (mirror) atomicAdd(mult + 10 * pl.atomB + k, vb);
+            }
+        }
+    }
+    if (mode & MOM_PULAY) {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const double v = seg_reduce(pulay ? coef * g[x] : 0.0, take);
+            if (head && pl.active && pl.atomA != pl.atomB) {
+                atomicAdd(gqm + 3 * pl.atomA + x, v);
+                atomicAdd(gqm + 3 * pl.atomB + x, -v);
+            }
+        }
+    }
+}
+
+template <int LA, int LB>
+struct Moments {
+    static cudaError_t run(const BasisDev &bd, int pp_begin, int pp_end, const double *dm, const double *phi,
+                           double *mult, double *F, double *gqm, int mode, cudaStream_t st)
+    {
+        const int n = pp_end - pp_begin;
+        const int grid = (n + 127) / 128;
+        k_moments<LA, LB><<<grid, 128, 0, st>>>(bd, pp_begin, pp_end, dm, phi, mult, F, gqm, mode);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_moments(const BasisDev &b, int cls, int pp_begin, int pp_end, const double *dm,
+                           const double *phi, double *mult, double *F, double *gqm, int mode, cudaStream_t st)
+{
+    if (pp_end <= pp_begin) return cudaSuccess;
+    return dispatch_class<Moments>(cls, b, pp_begin, pp_end, dm, phi, mult, F, gqm, mode, st);
+}
+
+}  // namespace qmmm

@@ -1,0 +1,71 @@
+// pp_tile.cuh -- one lane per primitive pair: geometry of the Gaussian product and the
+// class-template dispatch shared by the V, adjoint and moment kernels.
+//
+// Work layout: primitive pairs of one angular class (l_A, l_B), sorted by shell pair, are cut
+// into tiles of 32; a warp owns a tile (lane = primitive pair) and sweeps region-I charges that
+// the block staged into shared memory.  Primitive pairs of one shell pair are contiguous lanes,
+// so per-shell-pair sums are segmented warp-shuffle reductions.
+#pragma once
+#include "device_common.cuh"
+#include "qmmm_internal.h"
+
+namespace qmmm {
+
+struct PPLane {
+    int s;             // shell-pair index
+    SPair sp;
+    int atomA, atomB;
+    double a, b, p, ip;
+    double A[3], B[3], P[3];
+    double cab;        // c_a c_b K_AB (normalised contraction coefficients times Gaussian-product factor)
+    bool active;
+};
+
+__device__ __forceinline__ PPLane load_pp(const BasisDev &bd, int i, int pp_end)
+{
+    PPLane L;
+    L.active = i < pp_end;
+    const uint32_t code = __ldg(bd.pp + (L.active ? i : pp_end - 1));
+    L.s = (int)(code >> 8);
+    const int ka = (code >> 4) & 15, kb = code & 15;
+    L.sp = bd.sp[L.s];
+    const int pa = __ldg(bd.shell_off + L.sp.shA) + ka, pb = __ldg(bd.shell_off + L.sp.shB) + kb;
+    L.atomA = __ldg(bd.shell_atom + L.sp.shA);
+    L.atomB = __ldg(bd.shell_atom + L.sp.shB);
+    L.a = __ldg(bd.exps + pa);
+    L.b = __ldg(bd.exps + pb);
+    L.p = L.a + L.b;
+    L.ip = 1.0 / L.p;
+    double ab2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        L.A[x] = bd.qm_xyz[3 * L.atomA + x];
+        L.B[x] = bd.qm_xyz[3 * L.atomB + x];
+        L.P[x] = (L.a * L.A[x] + L.b * L.B[x]) * L.ip;
+        const double d = L.A[x] - L.B[x];
+        ab2 += d * d;
+    }
+    L.cab = L.active ? __ldg(bd.ncoef + pa) * __ldg(bd.ncoef + pb) * exp(-L.a * L.b * L.ip * ab2) : 0.0;
+    return L;
+}
+
+// Dispatch a functor templated on (LA, LB) for a runtime class index (l_A >= l_B).
+template <template <int, int> class K, typename... Args>
+cudaError_t dispatch_class(int cls, Args &&...args)
+{
+    switch (cls) {
+    case class_of(0, 0): return K<0, 0>::run(args...);
+    case class_of(1, 0): return K<1, 0>::run(args...);
+    case class_of(1, 1): return K<1, 1>::run(args...);
+    case class_of(2, 0): return K<2, 0>::run(args...);
+    case class_of(2, 1): return K<2, 1>::run(args...);
+    case class_of(2, 2): return K<2, 2>::run(args...);
+    case class_of(3, 0): return K<3, 0>::run(args...);
+    case class_of(3, 1): return K<3, 1>::run(args...);
+    case class_of(3, 2): return K<3, 2>::run(args...);
+    case class_of(3, 3): return K<3, 3>::run(args...);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace qmmm

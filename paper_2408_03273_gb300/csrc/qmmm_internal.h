@@ -1,0 +1,131 @@
+// qmmm_internal.h -- handle layout and kernel-launcher declarations of the GB300 library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qmmm.h"
+
+namespace qmmm {
+
+constexpr int MAX_SIGMA_CLASSES = 64;
+constexpr int MAX_NPRIM = 16;
+constexpr int CHUNK_F64 = 4096;  // region-I charges per V-forward launch (FP64: 32 B each)
+constexpr int CHUNK_GRAD = 2560; // per adjoint launch (charge + per-charge accumulators)
+constexpr int CHUNK_F32 = 4096;  // mixed path
+
+// Per shell pair: shells (A, B) with l_A >= l_B, their AO offsets.
+struct SPair { int shA, shB, aoA, aoB; };
+
+// Everything a pp-tile kernel needs (device pointers).
+struct BasisDev {
+    const int *shell_atom, *shell_off, *shell_ao;
+    const double *exps, *ncoef;
+    const double *qm_xyz;   // natm*3
+    const SPair *sp;
+    const uint32_t *pp;     // packed (sp << 8) | (ka << 4) | kb, class-sorted
+    int nao, natm;
+};
+
+struct RegionDev {
+    const double4_32a *chg;         // region-I images (x, y, z, q), class-major
+    const float4 *chg_hi;       // FP32 coordinates relative to the QM centre (hi part), w = q
+    const float4 *chg_lo;       // lo parts (x, y, z), w = 0
+    const int *idx;             // internal MM index of each image
+    const int *cls_off;         // [ncls+1] class offsets in the list
+    const double *cls_kappa;    // [ncls] exponent 1/sigma^2 (<= 0: point charge)
+    int ncls;
+    int n;
+    double centre[3];
+};
+
+struct qmmm_handle_impl;
+
+// launchers (defined in the .cu files); all return a cudaError_t of the last launch
+cudaError_t launch_vpot_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm,
+                            cudaStream_t st);
+cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                            int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm,
+                            cudaStream_t st);
+cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                             int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
+                             double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, cudaStream_t st);
+cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                             int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
+                             double *gchg, int *err, int nsm, cudaStream_t st);
+
+// moments / multipoles / Fock / Pulay (mode bits below)
+enum { MOM_MULT = 1, MOM_FOCK = 2, MOM_PULAY = 4 };
+cudaError_t launch_moments(const BasisDev &b, int cls, int pp_begin, int pp_end, const double *dm,
+                           const double *phi /* natm*20 */, double *mult /* natm*10 */, double *F,
+                           double *gqm, int mode, cudaStream_t st);
+
+// region I and Ewald
+struct EwaldDev {
+    const double *qm_xyz;       // natm*3
+    const double *mm_xyz;       // nmm*3 (internal order)
+    const double *mm_q;         // nmm
+    const double *mm_beta;      // nmm: 1/sigma (0: point charge)
+    const int *mm_cls;          // nmm: sigma class
+    int natm, nmm;
+    double box[3];
+    double centre[3];
+    double rcut;                // region-I radius
+    double ewald_rc;
+    double alpha;
+    int img[3];                 // image search half-width beyond the minimum image
+    const double4_32a *G;           // (Gx, Gy, Gz, 2 g(G)) half space
+    int nG;
+    int kmax[3];
+};
+cudaError_t launch_region1_count(const EwaldDev &e, int *blk_count, int *cls_count, int nblk, cudaStream_t st);
+cudaError_t launch_region1_fill(const EwaldDev &e, const int *blk_off, double4_32a *chg, float4 *hi, float4 *lo,
+                                int *idx, int nblk, cudaStream_t st);
+cudaError_t launch_scan_blocks(int *blk_count, int nblk, cudaStream_t st);
+
+// Scratch of the Ewald kernels (device buffers owned by the handle).
+struct EwaldBuf {
+    double *gfac = nullptr;      // dense (kx+1)(2ky+1)(2kz+1): 2 g(G) on the half space, else 0
+    double2 *S = nullptr;        // dense MM structure factor
+    double2 *Spart = nullptr;    // per-slice partial structure factors
+    int sf_nslice = 1;
+    double *preal = nullptr;     // natm * real_nslice * 20
+    int real_nslice = 1;
+    double *pr1 = nullptr;       // natm * 20
+    double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
+    double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
+};
+int ewald_dense_size(const EwaldDev &e);
+int ewald_sf_nslice(const EwaldDev &e);
+int ewald_real_nslice(const EwaldDev &e, int nsm);
+cudaError_t launch_gfac(const EwaldDev &e, double *gfac, cudaStream_t st);
+// v_j,c (natm*20) at the current geometry
+cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, const EwaldBuf &w, double *phi,
+                             cudaStream_t st);
+// MM-side adjoint of the multipole energy and the QM tensor gradient:
+//   dq_int[nmm] +=, dR_int[nmm*3] += (internal order), gchg[nI*4] += (region-I T part), gqm[natm*3] +=
+cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, const double *mult, const double *phi,
+                            const EwaldBuf &w, double *dq_int, double *dR_int, double *gchg, double *gqm,
+                            cudaStream_t st);
+// region-I nuclear-MM term: Epart[nblk] partial energies (nblk = ceil(nI/256)); optional gradients
+int enucmm_nblk(int nI);
+cudaError_t launch_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI, const int *rI_idx,
+                          int nI, const double *mm_beta, double *Epart, double *gqm, double *gchg, int want_grad,
+                          cudaStream_t st);
+cudaError_t launch_scatter_region(const int *rI_idx, int nI, const double *gchg, double *dq_int, double *dR_int,
+                                  cudaStream_t st);
+// out4 = {total, E_I = sum dm V (if have_V), E_nuc (sum of Epart), E_II = sum w M v}; partials: scratch[npart]
+cudaError_t launch_energy_terms(const double *dm, const double *V, int nao, int have_V, const double *mult,
+                                const double *phi, int natm, const double *Epart, int nEpart, double *partials,
+                                int npart, double *out4, cudaStream_t st);
+cudaError_t launch_gather_mm(const double *xyz_user, const double *q_user, const int *perm, int nmm, double *xyz,
+                             double *q, cudaStream_t st);
+cudaError_t launch_unpermute(const double *dq_int, const double *dR_int, const int *perm, int nmm, double *dq,
+                             double *dR, cudaStream_t st);
+cudaError_t launch_sum(const double *x, int n, double *out, cudaStream_t st);  // out[0] = sum x (one block)
+cudaError_t launch_sum_strided(const double *x, int n, int stride, double *out, cudaStream_t st);
+
+}  // namespace qmmm

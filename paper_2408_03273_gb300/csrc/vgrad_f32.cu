@@ -1,0 +1,234 @@
+// vgrad_f32.cu -- adjoint of the region-I term, mixed precision (see vgrad_f64.cu for the
+// derivative algebra).  The density-folded Hermite coefficients D0, Dx, Dy, Dz are built in
+// FP64 once per primitive pair and rounded to FP32; the per-charge Boys/R recursion to order L+1
+// and the seven contractions run in FP32.  Per-pair sums go through FP32 partials over 16
+// charges into FP64 registers; per-charge sums are warp butterflies in FP32 added into FP64
+// shared-memory accumulators.
+#include "pp_tile.cuh"
+
+namespace qmmm {
+
+constexpr int GFOLD = 16;
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(256, 1)
+k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
+            const float *__restrict__ boys_g, unsigned boys_bytes, const double *__restrict__ dm,
+            double *__restrict__ gqm, double *__restrict__ gchg, int *err)
+{
+    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1), NA = ncart(LA), NB = ncart(LB);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    const int nch = ch_end - ch_begin;
+    float4 *chi = reinterpret_cast<float4 *>(smem_raw);
+    float4 *clo = chi + nch;
+    float *tab = reinterpret_cast<float *>(clo + nch);
+    double *acc = reinterpret_cast<double *>(smem_raw + (size_t)nch * 2 * sizeof(float4) + boys_bytes);
+    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) acc[k] = 0.0;
+    {
+        Seg s[3] = {{chi, rg.chg_hi + ch_begin, (unsigned)(nch * sizeof(float4))},
+                    {clo, rg.chg_lo + ch_begin, (unsigned)(nch * sizeof(float4))},
+                    {tab, boys_g, boys_bytes}};
+        if (!stage_segments(s, 3, &bar, err)) return;
+    }
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int ntile = (pp_end - pp_begin + 31) >> 5;
+    for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
+        const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
+        const bool mirror = pl.sp.shA != pl.sp.shB;
+        const double coef = TWO_PI * pl.ip * pl.cab;
+        const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
+        float Ph[3], Plo[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const double d = pl.P[x] - rg.centre[x];
+            Ph[x] = (float)d;
+            Plo[x] = (float)(d - (double)Ph[x]);
+        }
+
+        float D0[NH], Dx[NH], Dy[NH], Dz[NH];
+        {
+            double d0[NH], dx[NH], dy[NH], dz[NH];
+#pragma unroll
+            for (int k = 0; k < NH; ++k) d0[k] = dx[k] = dy[k] = dz[k] = 0.0;
+            double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
+            hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
+            hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
+            hermite_E<LA + 1, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+#pragma unroll
+            for (int ia = 0; ia < NA; ++ia) {
+#pragma unroll
+                for (int ib = 0; ib < NB; ++ib) {
+                    const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+                    const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+                    double g = 0.0;
+                    if (pl.active) {
+                        const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
+                        g = dm[r * bd.nao + c];
+                        if (mirror) g += dm[c * bd.nao + r];
+                        g *= coef;
+                    }
+                    double dEx[L + 1], dEy[L + 1], dEz[L + 1];
+#pragma unroll
+                    for (int t = 0; t <= ax + bx; ++t) {
+                        double e = 2.0 * pl.a * Ex[ax + 1][bx][t];
+                        if (ax > 0) e -= ax * Ex[ax - 1][bx][t];
+                        if (t > 0) e -= aop * Ex[ax][bx][t - 1];
+                        dEx[t] = e;
+                    }
+#pragma unroll
+                    for (int u = 0; u <= ay + by; ++u) {
+                        double e = 2.0 * pl.a * Ey[ay + 1][by][u];
+                        if (ay > 0) e -= ay * Ey[ay - 1][by][u];
+                        if (u > 0) e -= aop * Ey[ay][by][u - 1];
+                        dEy[u] = e;
+                    }
+#pragma unroll
+                    for (int w = 0; w <= az + bz; ++w) {
+                        double e = 2.0 * pl.a * Ez[az + 1][bz][w];
+                        if (az > 0) e -= az * Ez[az - 1][bz][w];
+                        if (w > 0) e -= aop * Ez[az][bz][w - 1];
+                        dEz[w] = e;
+                    }
+#pragma unroll
+                    for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                        for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                            for (int w = 0; w <= az + bz; ++w) {
+                                const int k = hidx(t, u, w);
+                                const double ex = Ex[ax][bx][t], ey = Ey[ay][by][u], ez = Ez[az][bz][w];
+                                d0[k] += g * ex * ey * ez;
+                                dx[k] += g * dEx[t] * ey * ez;
+                                dy[k] += g * ex * dEy[u] * ez;
+                                dz[k] += g * ex * ey * dEz[w];
+                            }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NH; ++k) {
+                D0[k] = (float)d0[k];
+                Dx[k] = (float)dx[k];
+                Dy[k] = (float)dy[k];
+                Dz[k] = (float)dz[k];
+            }
+        }
+
+        double sdx = 0, sdy = 0, sdz = 0, sex = 0, sey = 0, sez = 0;
+        for (int c = 0; c < rg.ncls; ++c) {
+            const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
+            const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
+            if (lo >= hi) continue;
+            const double kap = __ldg(rg.cls_kappa + c);
+            const double td = kap > 0.0 ? kap / (pl.p + kap) : 1.0;
+            const float rho = (float)(pl.p * td), m2rho = -2.0f * rho, sq = (float)sqrt(td);
+            for (int j0 = lo; j0 < hi; j0 += GFOLD) {
+                const int j1 = min(hi, j0 + GFOLD);
+                float tdx = 0, tdy = 0, tdz = 0, tex = 0, tey = 0, tez = 0;
+                for (int j = j0; j < j1; ++j) {
+                    const float4 ch = chi[j], cl = clo[j];
+                    const float X = (Ph[0] - ch.x) + (Plo[0] - cl.x);
+                    const float Y = (Ph[1] - ch.y) + (Plo[1] - cl.y);
+                    const float Z = (Ph[2] - ch.z) + (Plo[2] - cl.z);
+                    const float T = rho * (X * X + Y * Y + Z * Z);
+                    float F[L + 2];
+                    boys_f32<L + 1>(T, F, tab);
+                    float Fn[L + 2];
+                    float sc = sq;
+#pragma unroll
+                    for (int n = 0; n <= L + 1; ++n) {
+                        Fn[n] = sc * F[n];
+                        sc *= m2rho;
+                    }
+                    float R[NH1];
+                    hermite_R<L + 1, float>(R, Fn, X, Y, Z);
+                    float e0 = 0, ex = 0, ey = 0, ez = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+                    for (int t = 0; t <= L; ++t)
+#pragma unroll
+                        for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                            for (int w = 0; w <= L - t - u; ++w) {
+                                const int k = hidx(t, u, w);
+                                e0 += D0[k] * R[k];
+                                ex += D0[k] * R[hidx(t + 1, u, w)];
+                                ey += D0[k] * R[hidx(t, u + 1, w)];
+                                ez += D0[k] * R[hidx(t, u, w + 1)];
+                                dx += Dx[k] * R[k];
+                                dy += Dy[k] * R[k];
+                                dz += Dz[k] * R[k];
+                            }
+                    const float q = ch.w;
+                    tdx += q * dx; tdy += q * dy; tdz += q * dz;
+                    tex += q * ex; tey += q * ey; tez += q * ez;
+                    const float v0 = warp_sum(-e0), v1 = warp_sum(q * ex), v2 = warp_sum(q * ey), v3 = warp_sum(q * ez);
+                    const float mine = lane == 0 ? v1 : lane == 1 ? v2 : lane == 2 ? v3 : v0;
+                    if (lane < 4) atomicAdd(acc + 4 * j + lane, (double)mine);
+                }
+                sdx += tdx; sdy += tdy; sdz += tdz;
+                sex += tex; sey += tey; sez += tez;
+            }
+        }
+        double g[6] = {-(sdx + aop * sex), -(sdy + aop * sey), -(sdz + aop * sez),
+                       sdx - bop * sex, sdy - bop * sey, sdz - bop * sez};
+        bool take[5], head;
+        seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g[k] = seg_reduce(g[k], take);
+        if (head && pl.active) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                atomicAdd(gqm + 3 * pl.atomA + x, g[x]);
+                atomicAdd(gqm + 3 * pl.atomB + x, g[3 + x]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) {
+        const double v = acc[k];
+        if (v != 0.0) atomicAdd(gchg + 4 * (size_t)ch_begin + k, v);
+    }
+}
+
+inline unsigned boys32_bytes_g()
+{
+    return (unsigned)(((BOYS_NROW_F * BOYS_NCOL_F + 3) / 4) * 4 * sizeof(float));
+}
+
+template <int LA, int LB>
+struct VgradF32 {
+    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                           int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
+                           int nsm, cudaStream_t st)
+    {
+        const unsigned tb = boys32_bytes_g();
+        const size_t per = 2 * sizeof(float4) + 4 * sizeof(double);
+        const size_t smem = (size_t)(ch_end - ch_begin) * per + tb;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(CHUNK_GRAD * per + tb));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int ntile = (pp_end - pp_begin + 31) / 32;
+        int grid = (ntile + 7) / 8;
+        if (grid > nsm) grid = nsm;
+        if (grid < 1) return cudaSuccess;
+        k_vgrad_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, dm, gqm,
+                                                     gchg, err);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                             int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
+                             double *gchg, int *err, int nsm, cudaStream_t st)
+{
+    if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
+    return dispatch_class<VgradF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                    st);
+}
+
+}  // namespace qmmm

@@ -1,0 +1,205 @@
+// vgrad_f64.cu -- adjoint of the region-I term: gradient of E_I = sum gamma_{mu nu} V_{mu nu}
+// (Eq. 9) with respect to the QM centres, the MM image positions and the MM charges, FP64.
+//
+// Per primitive pair the density is folded into Hermite coefficients once,
+//   D0_tuv = sum_ab g_ab E^x_t E^y_u E^z_v,   Dx_tuv = sum_ab g_ab E'^x_t E^y_u E^z_v, ...
+// with g_ab the density element (plus its mirror) times the pair prefactor and
+//   E'^{ij}_t = dE^{ij}_t / dX_AB = 2a E^{i+1,j}_t - i E^{i-1,j}_t - (a/p) E^{ij}_{t-1}.
+// Moving A shifts P by a/p, so with e_a = sum D0_tuv R_{tuv + 1_a} and d_a = sum Da_tuv R_tuv
+// (R recomputed up to L+1 for every charge, never stored):
+//   dI/dA_a = d_a + (a/p) e_a,   dI/dB_a = -d_a + (b/p) e_a,   dI/dC_a = -e_a,
+// and E contains -q_C I.  Per-pair sums over charges stay in registers; per-charge sums over the
+// 32 primitive pairs of a tile use a warp butterfly and go to shared-memory accumulators that
+// are flushed to global memory once per block.
+#include "pp_tile.cuh"
+
+namespace qmmm {
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(256, 1)
+k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
+            const double *__restrict__ boys, const double *__restrict__ dm, double *__restrict__ gqm,
+            double *__restrict__ gchg, int *err)
+{
+    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1), NA = ncart(LA), NB = ncart(LB);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    const int nch = ch_end - ch_begin;
+    double4_32a *chg = reinterpret_cast<double4_32a *>(smem_raw);
+    double *acc = reinterpret_cast<double *>(smem_raw + (size_t)nch * sizeof(double4_32a));
+    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) acc[k] = 0.0;
+    if (!stage_to_smem(chg, rg.chg + ch_begin, (unsigned)(nch * sizeof(double4_32a)), &bar, err)) return;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int ntile = (pp_end - pp_begin + 31) >> 5;
+    for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
+        const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
+        const bool mirror = pl.sp.shA != pl.sp.shB;
+        const double coef = TWO_PI * pl.ip * pl.cab;
+        const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
+
+        double D0[NH], Dx[NH], Dy[NH], Dz[NH];
+#pragma unroll
+        for (int k = 0; k < NH; ++k) D0[k] = Dx[k] = Dy[k] = Dz[k] = 0.0;
+        {
+            double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
+            hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
+            hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
+            hermite_E<LA + 1, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+#pragma unroll
+            for (int ia = 0; ia < NA; ++ia) {
+#pragma unroll
+                for (int ib = 0; ib < NB; ++ib) {
+                    const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+                    const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+                    double g = 0.0;
+                    if (pl.active) {
+                        const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
+                        g = dm[r * bd.nao + c];
+                        if (mirror) g += dm[c * bd.nao + r];
+                        g *= coef;
+                    }
+                    // derivative coefficients along each direction (t runs to i+j; E'_{i+j+1} = 0)
+                    double dEx[L + 1], dEy[L + 1], dEz[L + 1];
+#pragma unroll
+                    for (int t = 0; t <= ax + bx; ++t) {
+                        double e = 2.0 * pl.a * Ex[ax + 1][bx][t];
+                        if (ax > 0) e -= ax * Ex[ax - 1][bx][t];
+                        if (t > 0) e -= aop * Ex[ax][bx][t - 1];
+                        dEx[t] = e;
+                    }
+#pragma unroll
+                    for (int u = 0; u <= ay + by; ++u) {
+                        double e = 2.0 * pl.a * Ey[ay + 1][by][u];
+                        if (ay > 0) e -= ay * Ey[ay - 1][by][u];
+                        if (u > 0) e -= aop * Ey[ay][by][u - 1];
+                        dEy[u] = e;
+                    }
+#pragma unroll
+                    for (int w = 0; w <= az + bz; ++w) {
+                        double e = 2.0 * pl.a * Ez[az + 1][bz][w];
+                        if (az > 0) e -= az * Ez[az - 1][bz][w];
+                        if (w > 0) e -= aop * Ez[az][bz][w - 1];
+                        dEz[w] = e;
+                    }
+#pragma unroll
+                    for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                        for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                            for (int w = 0; w <= az + bz; ++w) {
+                                const int k = hidx(t, u, w);
+                                const double ex = Ex[ax][bx][t], ey = Ey[ay][by][u], ez = Ez[az][bz][w];
+                                D0[k] += g * ex * ey * ez;
+                                Dx[k] += g * dEx[t] * ey * ez;
+                                Dy[k] += g * ex * dEy[u] * ez;
+                                Dz[k] += g * ex * ey * dEz[w];
+                            }
+                }
+            }
+        }
+
+        double sdx = 0, sdy = 0, sdz = 0, sex = 0, sey = 0, sez = 0;
+        for (int c = 0; c < rg.ncls; ++c) {
+            const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
+            const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
+            if (lo >= hi) continue;
+            const double kap = __ldg(rg.cls_kappa + c);
+            const double t = kap > 0.0 ? kap / (pl.p + kap) : 1.0;
+            const double rho = pl.p * t, m2rho = -2.0 * rho, sq = sqrt(t);
+            for (int j = lo; j < hi; ++j) {
+                const double4_32a ch = chg[j];
+                const double X = pl.P[0] - ch.x, Y = pl.P[1] - ch.y, Z = pl.P[2] - ch.z;
+                const double T = rho * (X * X + Y * Y + Z * Z);
+                double F[L + 2];
+                boys_f64<L + 1>(T, F, boys);
+                double Fn[L + 2];
+                double sc = sq;
+#pragma unroll
+                for (int n = 0; n <= L + 1; ++n) {
+                    Fn[n] = sc * F[n];
+                    sc *= m2rho;
+                }
+                double R[NH1];
+                hermite_R<L + 1, double>(R, Fn, X, Y, Z);
+                double e0 = 0, ex = 0, ey = 0, ez = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+                for (int t = 0; t <= L; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                        for (int w = 0; w <= L - t - u; ++w) {
+                            const int k = hidx(t, u, w);
+                            e0 += D0[k] * R[k];
+                            ex += D0[k] * R[hidx(t + 1, u, w)];
+                            ey += D0[k] * R[hidx(t, u + 1, w)];
+                            ez += D0[k] * R[hidx(t, u, w + 1)];
+                            dx += Dx[k] * R[k];
+                            dy += Dy[k] * R[k];
+                            dz += Dz[k] * R[k];
+                        }
+                const double q = ch.w;
+                sdx += q * dx; sdy += q * dy; sdz += q * dz;
+                sex += q * ex; sey += q * ey; sez += q * ez;
+                // per-charge: dE/dq_C += -e0, dE/dC += q e
+                double v0 = warp_sum(-e0), v1 = warp_sum(q * ex), v2 = warp_sum(q * ey), v3 = warp_sum(q * ez);
+                const double mine = lane == 0 ? v1 : lane == 1 ? v2 : lane == 2 ? v3 : v0;
+                if (lane < 4) atomicAdd(acc + 4 * j + lane, mine);
+            }
+        }
+        // dE/dA = -(sd + a/p se), dE/dB = sd - b/p se
+        double g[6] = {-(sdx + aop * sex), -(sdy + aop * sey), -(sdz + aop * sez),
+                       sdx - bop * sex, sdy - bop * sey, sdz - bop * sez};
+        bool take[5], head;
+        seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g[k] = seg_reduce(g[k], take);
+        if (head && pl.active) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                atomicAdd(gqm + 3 * pl.atomA + x, g[x]);
+                atomicAdd(gqm + 3 * pl.atomB + x, g[3 + x]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) {
+        const double v = acc[k];
+        if (v != 0.0) atomicAdd(gchg + 4 * (size_t)ch_begin + k, v);
+    }
+}
+
+template <int LA, int LB>
+struct VgradF64 {
+    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                           int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
+                           int nsm, cudaStream_t st)
+    {
+        const size_t smem = (size_t)(ch_end - ch_begin) * (sizeof(double4_32a) + 4 * sizeof(double));
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(CHUNK_GRAD * (sizeof(double4_32a) + 4 * sizeof(double))));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int ntile = (pp_end - pp_begin + 31) / 32;
+        int grid = (ntile + 7) / 8;
+        if (grid > nsm) grid = nsm;
+        if (grid < 1) return cudaSuccess;
+        k_vgrad_f64<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm,
+                                                     gchg, err);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                             int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
+                             double *gchg, int *err, int nsm, cudaStream_t st)
+{
+    if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
+    return dispatch_class<VgradF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                    st);
+}
+
+}  // namespace qmmm

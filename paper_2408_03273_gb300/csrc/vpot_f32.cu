@@ -1,0 +1,163 @@
+// vpot_f32.cu -- region-I matrix of Eq. 9, mixed precision.
+//
+// Same tile layout as the FP64 kernel.  The per-(primitive pair, charge) work -- the Boys
+// function, the Hermite R recursion and the charge sum -- runs in FP32; everything done once per
+// primitive pair (Gaussian product, prefactors, E-contraction, reductions) stays FP64.
+//   * Positions enter as FP32 hi/lo pairs relative to the QM centre: X_PC = (P_hi - C_hi) +
+//     (P_lo - C_lo), so the difference is accurate to FP32 rounding of X_PC itself.
+//   * Charge sums use FP32 partials over 16 charges folded into a double-float (hi, lo) pair by
+//     an error-free two-sum, so summation error does not grow with the number of charges.
+//   * The FP32 Boys table lives in shared memory (staged with the charges by TMA), with an odd
+//     row stride so that lanes reading different rows hit different banks.
+#include "pp_tile.cuh"
+
+namespace qmmm {
+
+constexpr int FOLD = 16;
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(256, 1)
+k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
+           const float *__restrict__ boys_g, unsigned boys_bytes, double *__restrict__ V, int *err)
+{
+    constexpr int L = LA + LB, NH = nherm(L), NA = ncart(LA), NB = ncart(LB);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    const int nch = ch_end - ch_begin;
+    float4 *chi = reinterpret_cast<float4 *>(smem_raw);
+    float4 *clo = chi + nch;
+    float *tab = reinterpret_cast<float *>(clo + nch);
+    {
+        Seg s[3] = {{chi, rg.chg_hi + ch_begin, (unsigned)(nch * sizeof(float4))},
+                    {clo, rg.chg_lo + ch_begin, (unsigned)(nch * sizeof(float4))},
+                    {tab, boys_g, boys_bytes}};
+        if (!stage_segments(s, 3, &bar, err)) return;
+    }
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int ntile = (pp_end - pp_begin + 31) >> 5;
+    for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
+        const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
+        float Ph[3], Plo[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const double d = pl.P[x] - rg.centre[x];
+            Ph[x] = (float)d;
+            Plo[x] = (float)(d - (double)Ph[x]);
+        }
+        float Wh[NH], Wl[NH];
+#pragma unroll
+        for (int k = 0; k < NH; ++k) Wh[k] = Wl[k] = 0.0f;
+
+        for (int c = 0; c < rg.ncls; ++c) {
+            const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
+            const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
+            if (lo >= hi) continue;
+            const double kap = __ldg(rg.cls_kappa + c);
+            const double td = kap > 0.0 ? kap / (pl.p + kap) : 1.0;
+            const float rho = (float)(pl.p * td), m2rho = -2.0f * rho, sq = (float)sqrt(td);
+            for (int j0 = lo; j0 < hi; j0 += FOLD) {
+                const int j1 = min(hi, j0 + FOLD);
+                float Wt[NH];
+#pragma unroll
+                for (int k = 0; k < NH; ++k) Wt[k] = 0.0f;
+                for (int j = j0; j < j1; ++j) {
+                    const float4 ch = chi[j], cl = clo[j];
+                    const float X = (Ph[0] - ch.x) + (Plo[0] - cl.x);
+                    const float Y = (Ph[1] - ch.y) + (Plo[1] - cl.y);
+                    const float Z = (Ph[2] - ch.z) + (Plo[2] - cl.z);
+                    const float T = rho * (X * X + Y * Y + Z * Z);
+                    float F[L + 1];
+                    boys_f32<L>(T, F, tab);
+                    float Fn[L + 1];
+                    float sc = ch.w * sq;
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        Fn[n] = sc * F[n];
+                        sc *= m2rho;
+                    }
+                    float R[NH];
+                    hermite_R<L, float>(R, Fn, X, Y, Z);
+#pragma unroll
+                    for (int k = 0; k < NH; ++k) Wt[k] += R[k];
+                }
+#pragma unroll
+                for (int k = 0; k < NH; ++k) df_add(Wh[k], Wl[k], Wt[k]);
+            }
+        }
+        double W[NH];
+#pragma unroll
+        for (int k = 0; k < NH; ++k) W[k] = (double)Wh[k] + (double)Wl[k];
+
+        double Ex[LA + 1][LB + 1][L + 1], Ey[LA + 1][LB + 1][L + 1], Ez[LA + 1][LB + 1][L + 1];
+        hermite_E<LA, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
+        hermite_E<LA, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
+        hermite_E<LA, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+        const double coef = -TWO_PI * pl.ip * pl.cab;
+
+        bool take[5], head;
+        seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
+        const bool mirror = pl.sp.shA != pl.sp.shB;
+#pragma unroll
+        for (int ia = 0; ia < NA; ++ia) {
+#pragma unroll
+            for (int ib = 0; ib < NB; ++ib) {
+                const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+                const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+                double v = 0.0;
+#pragma unroll
+                for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                    for (int u = 0; u <= ay + by; ++u) {
+                        const double exy = Ex[ax][bx][t] * Ey[ay][by][u];
+#pragma unroll
+                        for (int w = 0; w <= az + bz; ++w) v += exy * Ez[az][bz][w] * W[hidx(t, u, w)];
+                    }
+                v = seg_reduce(coef * v, take);
+                if (head && pl.active) {
+                    const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
+                    atomicAdd(V + r * bd.nao + c, v);
+                    if (mirror) atomicAdd(V + c * bd.nao + r, v);
+                }
+            }
+        }
+    }
+}
+
+inline unsigned boys32_bytes()
+{
+    return (unsigned)(((BOYS_NROW_F * BOYS_NCOL_F + 3) / 4) * 4 * sizeof(float));
+}
+
+template <int LA, int LB>
+struct VpotF32 {
+    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                           int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st)
+    {
+        const unsigned tb = boys32_bytes();
+        const size_t smem = (size_t)(ch_end - ch_begin) * 2 * sizeof(float4) + tb;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(CHUNK_F32 * 2 * sizeof(float4) + tb));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int ntile = (pp_end - pp_begin + 31) / 32;
+        int grid = (ntile + 7) / 8;
+        if (grid > nsm) grid = nsm;
+        if (grid < 1) return cudaSuccess;
+        k_vpot_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, V, err);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
+                            int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm,
+                            cudaStream_t st)
+{
+    if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
+    return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+}
+
+}  // namespace qmmm

@@ -1,0 +1,38 @@
+"""Helpers for the GPU parity tests: build a handle from a workload and compare with the oracle."""
+import numpy as np
+
+# tolerances: the FP64 path against the FP64 oracle, and the mixed-precision path
+TOL_FP64 = 1e-10
+TOL_MIXED = 1e-6
+
+
+def rel_max(got, ref):
+    """max |got - ref| / max |ref| (elementwise parity scaled by the largest reference value)."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def rel_fro(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def energy_scale(e):
+    return abs(e["E_I_elec"]) + abs(e["E_nuc_mm"]) + abs(e["E_II"])
+
+
+def gpu_all(s, precision=0, screen_tol=-1.0):
+    """Run the whole path through the C ABI on host arrays; returns a dict like the oracle's."""
+    import paper_2408_03273_gb300 as q
+    h = q.Handle(s, precision=precision, screen_tol=screen_tol)
+    try:
+        V, En = h.vpot()
+        E = h.energy(s.dm)
+        EII, M, F = h.ewald(s.dm, want_F=True)
+        phi = h.potential()
+        gq, gm, gc = h.forces(s.dm)
+        return {"V": V, "E_nuc_mm": float(En[0]), "E": float(E[0]), "E_I_elec": float(E[1]), "E_II": float(E[3]),
+                "M": M, "F": F, "phi": phi, "dE_dRqm": gq, "dE_dRmm": gm, "dE_dq": gc, "info": h.info,
+                "timing": h.last_timing()}
+    finally:
+        h.close()
