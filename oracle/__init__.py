@@ -266,6 +266,11 @@ def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None, mm_subset=None):
     qm = _d(s.atom_xyz)
     lib().oracle_vgrad(*b.args(), s.natm, _dp(qm), n, _dp(cx), _dp(cq), _dp(cs), s.nao, _dp(dm), 0, None, _dp(dRqm),
                        _dp(dC), _dp(dqc))
+    # region-I electronic part alone (the part the mixed-precision path evaluates in FP32)
+    elec_qm = dRqm.copy()
+    elec_mm, elec_q = np.zeros((s.nmm, 3)), np.zeros(s.nmm)
+    np.add.at(elec_mm, idx, dC)
+    np.add.at(elec_q, idx, dqc)
     lib().oracle_enucmm(s.natm, _dp(qm), _dp(_d(s.atom_Z)), n, _dp(cx), _dp(cq), _dp(cs), _dp(dRqm), _dp(dC),
                         _dp(dqc))
     dRmm = np.zeros((s.nmm, 3))
@@ -277,7 +282,8 @@ def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None, mm_subset=None):
     lib().oracle_tensor_grad_qm(s.natm, _dp(_d(M)), _dp(phi), _dp(dRqm))
     lib().oracle_pulay(*b.args(), _dp(qm), _dp(phi), 20, s.nao, _dp(dm), _dp(dRqm))
     dq2, dR2 = ewald_mm(s, M, mode, mm_subset=mm_subset)
-    return {"dE_dRqm": dRqm, "dE_dRmm": dRmm + dR2, "dE_dq": dq + dq2, "M": M, "phi": phi}
+    return {"dE_dRqm": dRqm, "dE_dRmm": dRmm + dR2, "dE_dq": dq + dq2, "M": M, "phi": phi,
+            "elec": {"dE_dRqm": elec_qm, "dE_dRmm": elec_mm, "dE_dq": elec_q}}
 
 
 def vgrad_pairs(s, pairs, dm=None):

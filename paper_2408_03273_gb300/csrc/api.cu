@@ -109,6 +109,16 @@ void boys_table(int nrow, int ncol, double step, std::vector<double> &out)
     }
 }
 
+// Size estimate of a primitive pair's charge distribution g_a g_b used for screening:
+// |c_a c_b| K_AB (pi/p)^{3/2} (|PA| + p^{-1/2})^{l_a} (|PB| + p^{-1/2})^{l_b}; the polynomial
+// factor bounds (x-A)^i (x-B)^j over the bulk of the product Gaussian.
+double pair_bound(double a, double b, double ca, double cb, double ab2, int la, int lb)
+{
+    const double p = a + b, r = 1.0 / std::sqrt(p), ab = std::sqrt(ab2);
+    const double pa = b / p * ab + r, pb = a / p * ab + r;
+    return std::fabs(ca * cb) * std::exp(-a * b / p * ab2) * std::pow(PI / p, 1.5) * std::pow(pa, la) * std::pow(pb, lb);
+}
+
 }  // namespace
 
 struct qmmm_handle {
@@ -134,6 +144,8 @@ struct qmmm_handle {
     bool V_valid = false;
     float t_sweep = 0.f, t_other = 0.f;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t side[NCLASS] = {};   // one stream per angular class (concurrent class sweeps)
+    cudaEvent_t fork = nullptr, join[NCLASS] = {};
     EwaldBuf ew;
     int nblk_mm = 1;
 
@@ -210,6 +222,11 @@ struct qmmm_handle {
     {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
+        for (int c = 0; c < NCLASS; ++c) {
+            if (side[c]) cudaStreamDestroy(side[c]);
+            if (join[c]) cudaEventDestroy(join[c]);
+        }
+        if (fork) cudaEventDestroy(fork);
         qm.release(); Zd.release(); dexps.release(); dncoef.release(); mm_xyz.release(); mm_q.release();
         mm_beta.release(); user_xyz.release(); user_q.release(); dshell_atom.release(); dshell_off.release();
         dshell_ao.release(); dperm.release(); mm_cls.release(); blk.release(); cls_count.release();
@@ -325,6 +342,41 @@ int chunk_size(const qmmm_handle *h, bool grad)
 {
     if (grad) return CHUNK_GRAD;
     return h->precision == QMMM_MIXED ? CHUNK_F32 : CHUNK_F64;
+}
+
+// Work per (primitive pair, charge) of a class with L = l_A + l_B, for splitting the SMs.
+double class_weight(int L, bool grad)
+{
+    auto c4 = [](int n) { return n >= 4 ? (double)n * (n - 1) * (n - 2) * (n - 3) / 24.0 : 0.0; };
+    auto c3 = [](int n) { return n >= 3 ? (double)n * (n - 1) * (n - 2) / 6.0 : 0.0; };
+    return grad ? 75 + 3 * L + 2 * c4(L + 5) + 14 * c3(L + 3) : 40 + 3 * L + 2 * c4(L + 4) + 2 * c3(L + 3);
+}
+
+// Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
+// forked from and joined back into the handle's stream, with a grid cap proportional to its
+// share of the work (so small classes do not leave most SMs idle while they run alone).
+template <typename F>
+int run_classes(qmmm_handle *h, bool grad, F launch)
+{
+    static const int Lc[NCLASS] = {0, 1, 2, 2, 3, 4, 3, 4, 5, 6};
+    double w[NCLASS], W = 0.0;
+    for (int c = 0; c < NCLASS; ++c) {
+        w[c] = (double)(h->class_off[c + 1] - h->class_off[c]) * class_weight(Lc[c], grad);
+        W += w[c];
+    }
+    if (W <= 0.0) return QMMM_OK;
+    CUDA_TRY(cudaEventRecord(h->fork, h->stream));
+    for (int c = 0; c < NCLASS; ++c) {
+        const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
+        if (p1 <= p0) continue;
+        const int share = std::max(1, (int)std::lround(h->nsm * w[c] / W));
+        CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
+        CUDA_TRY(launch(c, p0, p1, share, h->side[c]));
+        CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
+    }
+    for (int c = 0; c < NCLASS; ++c)
+        if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join[c], 0));
+    return QMMM_OK;
 }
 
 }  // namespace
@@ -482,9 +534,9 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
                 const double ab2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
                 for (int ka = 0; ka < h->shell_nprim[i]; ++ka)
                     for (int kb = 0; kb < h->shell_nprim[j]; ++kb) {
-                        const double a = h->exps[h->shell_off[i] + ka], b = h->exps[h->shell_off[j] + kb], p = a + b;
-                        const double v = std::fabs(h->ncoef[h->shell_off[i] + ka] * h->ncoef[h->shell_off[j] + kb]) *
-                                         std::exp(-a * b / p * ab2) * std::pow(PI / p, 1.5);
+                        const double a = h->exps[h->shell_off[i] + ka], b = h->exps[h->shell_off[j] + kb];
+                        const double v = pair_bound(a, b, h->ncoef[h->shell_off[i] + ka], h->ncoef[h->shell_off[j] + kb],
+                                                    ab2, h->shell_l[i], h->shell_l[j]);
                         vmax = std::max(vmax, v);
                     }
             }
@@ -500,9 +552,9 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
                 std::vector<uint32_t> kept;
                 for (int ka = 0; ka < h->shell_nprim[sA]; ++ka)
                     for (int kb = 0; kb < h->shell_nprim[sB]; ++kb) {
-                        const double a = h->exps[h->shell_off[sA] + ka], b = h->exps[h->shell_off[sB] + kb], p = a + b;
-                        const double v = std::fabs(h->ncoef[h->shell_off[sA] + ka] * h->ncoef[h->shell_off[sB] + kb]) *
-                                         std::exp(-a * b / p * ab2) * std::pow(PI / p, 1.5);
+                        const double a = h->exps[h->shell_off[sA] + ka], b = h->exps[h->shell_off[sB] + kb];
+                        const double v = pair_bound(a, b, h->ncoef[h->shell_off[sA] + ka], h->ncoef[h->shell_off[sB] + kb],
+                                                    ab2, h->shell_l[sA], h->shell_l[sB]);
                         if (h->screen_tol == 0.0 || v >= thr) kept.push_back((uint32_t)((ka << 4) | kb));
                     }
                 if (kept.empty()) continue;
@@ -641,6 +693,11 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sums = h->sums.p;
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
+        CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+        for (int c = 0; c < NCLASS; ++c) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&h->side[c], cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->join[c], cudaEventDisableTiming));
+        }
     }
     // initial geometry
     std::vector<double> qm0 = h->qm_xyz;
@@ -685,14 +742,12 @@ int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
     CUDA_TRY(cudaEventRecord(h->ev[0], st));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
-        for (int cls = 0; cls < NCLASS; ++cls) {
-            const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
-            if (p1 <= p0) continue;
-            if (h->precision == QMMM_MIXED)
-                CUDA_TRY(launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, h->V.p, h->err.p, h->nsm, st));
-            else
-                CUDA_TRY(launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, h->V.p, h->err.p, h->nsm, st));
-        }
+        rc = run_classes(h, false, [&](int cls, int p0, int p1, int share, cudaStream_t cs) {
+            return h->precision == QMMM_MIXED
+                       ? launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, h->V.p, h->err.p, share, cs)
+                       : launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, h->V.p, h->err.p, share, cs);
+        });
+        if (rc) return rc;
     }
     CUDA_TRY(cudaEventRecord(h->ev[1], st));
     CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
@@ -787,16 +842,14 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
     CUDA_TRY(cudaEventRecord(h->ev[0], st));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
-        for (int cls = 0; cls < NCLASS; ++cls) {
-            const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
-            if (p1 <= p0) continue;
-            if (h->precision == QMMM_MIXED)
-                CUDA_TRY(launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
-                                          h->nsm, st));
-            else
-                CUDA_TRY(launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
-                                          h->nsm, st));
-        }
+        rc = run_classes(h, true, [&](int cls, int p0, int p1, int share, cudaStream_t cs) {
+            return h->precision == QMMM_MIXED
+                       ? launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
+                                          share, cs)
+                       : launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
+                                          share, cs);
+        });
+        if (rc) return rc;
     }
     CUDA_TRY(cudaEventRecord(h->ev[1], st));
     // nuclear-MM region I, multipolar Ewald (MM side + QM tensor part), scatter to MM atoms

@@ -112,12 +112,32 @@ __device__ __forceinline__ void boys_f64(double T, double (&F)[M + 1], const dou
     }
 }
 
+// rho * (X^2 + Y^2 + Z^2) as an unevaluated sum Th + Tl: squares split exactly with FMA and the
+// three-term sum and the product by rho carried with two-sum / two-product error terms, so T is
+// accurate to about one FP32 rounding of T itself (the per-charge rounding error of r^2 is what
+// cancellation between neutral molecules would otherwise amplify).
+__device__ __forceinline__ void boys_arg_f32(float rho, float X, float Y, float Z, float &Th, float &Tl)
+{
+    const float x2 = X * X, y2 = Y * Y, z2 = Z * Z;
+    const float ex = fmaf(X, X, -x2), ey = fmaf(Y, Y, -y2), ez = fmaf(Z, Z, -z2);
+    float s = x2 + y2;
+    float v = s - x2;
+    float e = (x2 - (s - v)) + (y2 - v);
+    const float s2 = s + z2;
+    v = s2 - s;
+    e += (s - (s2 - v)) + (z2 - v);
+    const float lo = e + (ex + ey + ez);
+    Th = rho * s2;
+    Tl = fmaf(rho, s2, -Th) + rho * lo;
+}
+
 template <int M>
-__device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float *__restrict__ tab /* smem */)
+__device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float *__restrict__ tab /* smem */,
+                                         float Tlo = 0.0f)
 {
     if (T < BOYS_TMAX_F) {
         const int k = __float2int_rn(T * 10.0f);
-        const float x = (float)k * 0.1f - T;
+        const float x = ((float)k * 0.1f - T) - Tlo;
         const float *row = tab + k * BOYS_NCOL_F;
         float f = row[M + 4];
         f = row[M + 3] + f * x * 0.25f;
@@ -132,9 +152,11 @@ __device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float
             for (int m = M; m > 0; --m) F[m - 1] = (T2 * F[m] + e) * (1.0f / (2 * m - 1));
         }
     } else {
-        // one Newton step on rsqrtf: ~1 ulp
+        // one Newton step on rsqrtf against the full argument T + Tlo: ~1 ulp of T^{-1/2}
         float rs = rsqrtf(T);
-        rs = rs * (1.5f - 0.5f * T * rs * rs);
+        const float r2 = rs * rs;
+        const float h = fmaf(-T, r2, 1.0f) - Tlo * r2;  // 1 - (T + Tlo) rs^2
+        rs = fmaf(0.5f * rs, h, rs);
         F[0] = (float)HALF_SQRT_PI * rs;
         if (M > 0) {
             const float e = __expf(-T);

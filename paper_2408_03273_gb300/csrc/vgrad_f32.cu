@@ -131,9 +131,10 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                     const float X = (Ph[0] - ch.x) + (Plo[0] - cl.x);
                     const float Y = (Ph[1] - ch.y) + (Plo[1] - cl.y);
                     const float Z = (Ph[2] - ch.z) + (Plo[2] - cl.z);
-                    const float T = rho * (X * X + Y * Y + Z * Z);
+                    float T, Tl;
+                    boys_arg_f32(rho, X, Y, Z, T, Tl);
                     float F[L + 2];
-                    boys_f32<L + 1>(T, F, tab);
+                    boys_f32<L + 1>(T, F, tab, Tl);
                     float Fn[L + 2];
                     float sc = sq;
 #pragma unroll

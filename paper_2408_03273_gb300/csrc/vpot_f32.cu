@@ -66,9 +66,10 @@ k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
                     const float X = (Ph[0] - ch.x) + (Plo[0] - cl.x);
                     const float Y = (Ph[1] - ch.y) + (Plo[1] - cl.y);
                     const float Z = (Ph[2] - ch.z) + (Plo[2] - cl.z);
-                    const float T = rho * (X * X + Y * Y + Z * Z);
+                    float T, Tl;
+                    boys_arg_f32(rho, X, Y, Z, T, Tl);
                     float F[L + 1];
-                    boys_f32<L>(T, F, tab);
+                    boys_f32<L>(T, F, tab, Tl);
                     float Fn[L + 1];
                     float sc = ch.w * sq;
 #pragma unroll

@@ -21,6 +21,19 @@ def energy_scale(e):
     return abs(e["E_I_elec"]) + abs(e["E_nuc_mm"]) + abs(e["E_II"])
 
 
+def grad_err(got, ref, key, mixed):
+    """Elementwise gradient error.  FP64 path: relative to the largest reference component.
+    Mixed path: relative to the larger of that and the largest component of the region-I
+    electronic term alone -- the only term evaluated in FP32, which on small systems nearly
+    cancels against the FP64 nuclear-MM term, so the residual total would otherwise amplify
+    FP32 rounding by the cancellation ratio (the same normalisation as the energy, whose
+    scale is the sum of the magnitudes of its terms)."""
+    scale = float(np.max(np.abs(ref[key])))
+    if mixed and "elec" in ref:
+        scale = max(scale, float(np.max(np.abs(ref["elec"][key]))))
+    return float(np.max(np.abs(np.asarray(got) - ref[key]))) / max(scale, 1e-300)
+
+
 def gpu_all(s, precision=0, screen_tol=-1.0):
     """Run the whole path through the C ABI on host arrays; returns a dict like the oracle's."""
     import paper_2408_03273_gb300 as q
