@@ -158,6 +158,25 @@ void qmmm_destroy(qmmm_handle *h);
 const char *qmmm_strerror(int code);
 const char *qmmm_last_error(void);
 
+/* Allocation-free nuclear-MM energy, for callers that must not allocate device memory while
+ * they run (an MD engine that reserves all its device memory at start-up and calls this from its
+ * time step, where a cudaMalloc would implicitly synchronise the device; a plugin whose memory
+ * belongs to the host program's pool allocator).  The paper has no counterpart: it is a variant
+ * of the kernel behind qmmm_vpot's E_nuc_mm, taking the charges directly instead of a handle.
+ *   E[0] = sum_j sum_i Z[j] q_i erf(r_ij / sigma[i]) / r_ij  (1/r_ij where sigma[i] <= 0),
+ *   qm_xyz[natm*3], Z[natm], charges[ncharge*4] = (x, y, z, q) per charge (bohr, e),
+ *   sigma[ncharge] (bohr), E[1]: all DEVICE memory owned by the caller.  Work is queued on
+ *   `stream` (a cudaStream_t; NULL = legacy stream) and the call returns without waiting.
+ * Scratch is a fixed array inside the library (one double per 256 charges, at most 262144
+ * charges per call: larger ncharge returns QMMM_ERR_ARG); every GPU that loads the library holds
+ * it until the process exits.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls on a device share the array, so calls whose work overlaps on the GPU race
+ * and give wrong results: serialise them (one stream, or events).  Nothing is allocated or freed.
+ * Errors: QMMM_ERR_ARG (null/host pointer, negative or too large size), QMMM_ERR_CUDA. */
+int qmmm_nuclear_mm_energy_static(int natm, const double *qm_xyz, const double *Z, int ncharge,
+                                  const double *charges, const double *sigma, double *E, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

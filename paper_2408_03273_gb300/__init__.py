@@ -29,6 +29,7 @@ from ._lib import (  # noqa: F401
     qmmm_last_error,
     qmmm_last_timing,
     qmmm_nao,
+    qmmm_nuclear_mm_energy_static,
     qmmm_set_positions,
     qmmm_set_precision,
     qmmm_set_stream,

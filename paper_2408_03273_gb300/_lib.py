@@ -59,7 +59,7 @@ _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
-           "qmmm_destroy", "qmmm_strerror", "qmmm_last_error")
+           "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
 
 def library_path() -> str:
@@ -94,6 +94,8 @@ def load(build_if_needed: bool = True):
         "qmmm_destroy": (None, [c_void_p]),
         "qmmm_strerror": (ctypes.c_char_p, [c_int]),
         "qmmm_last_error": (ctypes.c_char_p, []),
+        "qmmm_nuclear_mm_energy_static": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                                  c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -264,3 +266,15 @@ def qmmm_strerror(code):
 
 def qmmm_last_error():
     return load().qmmm_last_error().decode()
+
+
+def qmmm_nuclear_mm_energy_static(qm_xyz, Z, charges, sigma, E, stream=None):
+    """Allocation-free nuclear-MM energy for callers that cannot allocate device memory while
+    they run: every argument is a CUDA float64 tensor the caller owns (qm_xyz[natm,3], Z[natm],
+    charges[n,4] = x, y, z, q, sigma[n], E[1]); work is queued on ``stream`` and not waited for."""
+    s = getattr(stream, "cuda_stream", stream)
+    natm = int(qm_xyz.shape[0])
+    n = int(charges.shape[0])
+    _check(load().qmmm_nuclear_mm_energy_static(natm, _ptr(qm_xyz), _ptr(Z), n, _ptr(charges), _ptr(sigma), _ptr(E),
+                                                c_void_p(s) if s else None), "qmmm_nuclear_mm_energy_static")
+    return E

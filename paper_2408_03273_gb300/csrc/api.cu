@@ -35,6 +35,12 @@ int fail(int code, const std::string &msg)
     return code;
 }
 
+}  // namespace
+
+void qmmm::set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
 #define CUDA_TRY(call)                                                                          \
     do {                                                                                        \
         cudaError_t _e = (call);                                                                \

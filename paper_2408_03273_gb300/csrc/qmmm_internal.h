@@ -128,4 +128,7 @@ cudaError_t launch_unpermute(const double *dq_int, const double *dR_int, const i
 cudaError_t launch_sum(const double *x, int n, double *out, cudaStream_t st);  // out[0] = sum x (one block)
 cudaError_t launch_sum_strided(const double *x, int n, int stride, double *out, cudaStream_t st);
 
+// record the detail message returned by qmmm_last_error()
+void set_last_error(const std::string &msg);
+
 }  // namespace qmmm
