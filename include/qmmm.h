@@ -77,8 +77,8 @@ typedef struct {
                            times the largest value are dropped; 0 disables; < 0: [1e-14]       */
     int region_mode;    /* 0: sphere of radius cutoff about the QM centre [0]                  */
     double ewald_rcut;  /* Ewald real-space cutoff (bohr); <= 0: equal to cutoff [cutoff]       */
-    int kmax[3];        /* reciprocal cube half-widths; 0: chosen so that exp(-G^2/4alpha^2)
-                           < 1e-8 at the edge                                                  */
+    int kmax[3];        /* reciprocal cube half-widths (<= 56); 0: chosen so that
+                           exp(-G^2/4alpha^2) < 1e-8 at the edge                               */
     int full_cell_test; /* reserved, must be 0                                                 */
 } qmmm_options;
 

@@ -165,7 +165,7 @@ struct qmmm_handle {
     DBuf<double> dcls_kappa, gfac, preal, pr1, sums, phi, boys64, V, dm, F, mult, mult_init, gqm, gchg, dq_int,
         dR_int, dq_out, dR_out, Epart, partials, out4;
     DBuf<float> boys32;
-    DBuf<double2> S, Spart, A;
+    DBuf<double2> S, Spart, A, Az;
     DBuf<int> err;
 
     BasisDev basis() const
@@ -241,7 +241,7 @@ struct qmmm_handle {
         phi.release(); boys64.release(); V.release(); dm.release(); F.release(); mult.release();
         mult_init.release(); gqm.release(); gchg.release(); dq_int.release(); dR_int.release();
         dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
-        boys32.release(); S.release(); Spart.release(); A.release(); err.release();
+        boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); err.release();
     }
 };
 
@@ -447,7 +447,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         if ((int)w.size() > MAX_SIGMA_CLASSES) return fail(QMMM_ERR_ARG, "more than 64 distinct Gaussian widths");
     }
     for (int x = 0; x < 3; ++x)
-        if (opts && opts->kmax[x] > 200) return fail(QMMM_ERR_ARG, "kmax too large (> 200)");
+        if (opts && opts->kmax[x] > 56) return fail(QMMM_ERR_ARG, "kmax too large (> 56)");
 
     auto h = new qmmm_handle();
     std::unique_ptr<qmmm_handle> guard(h);
@@ -470,7 +470,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
             const double gmax = 2.0 * ewald_alpha * std::sqrt(std::log(1e8));
             k = (int)std::ceil(gmax * box[x] / (2.0 * PI));
         }
-        if (k > 200) return fail(QMMM_ERR_ARG, "kmax too large (> 200)");
+        if (k > 56) return fail(QMMM_ERR_ARG, "kmax too large (> 56)");
         h->kmax[x] = k;
     }
 
@@ -684,9 +684,9 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         // Ewald buffers
         EwaldDev e = h->ewald();
         const int nd = ewald_dense_size(e);
-        h->ew.sf_nslice = ewald_sf_nslice(e);
+        h->ew.sf_nslice = ewald_sf_nslice(e, h->nsm);
         h->ew.real_nslice = ewald_real_nslice(e, h->nsm);
-        if ((rc = h->gfac.ensure(nd)) || (rc = h->S.ensure(nd)) || (rc = h->A.ensure(nd)) ||
+        if ((rc = h->gfac.ensure(nd)) || (rc = h->S.ensure(nd)) || (rc = h->A.ensure(nd)) || (rc = h->Az.ensure(nd)) ||
             (rc = h->Spart.ensure((size_t)nd * h->ew.sf_nslice)) ||
             (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
             return rc;
@@ -696,6 +696,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.preal = h->preal.p;
         h->ew.pr1 = h->pr1.p;
         h->ew.A = h->A.p;
+        h->ew.Az = h->Az.p;
         h->ew.sums = h->sums.p;
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));

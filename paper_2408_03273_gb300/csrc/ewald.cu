@@ -294,10 +294,11 @@ __global__ void __launch_bounds__(256) k_structure_factor(EwaldDev e, double2 *p
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
     const int NX = kx + 1, NY = 2 * ky + 1, NZ = 2 * kz + 1;
     const int NZC = (NZ + SF_NZ - 1) / SF_NZ;
+    const int NZP = NZC * SF_NZ;                             // z rows padded with zeros to a multiple of 8
     const int NL = NX * NY;
     double2 *px = reinterpret_cast<double2 *>(smem_raw);   // [tile][NX]
     double2 *py = px + tile * NX;                            // [tile][NY] (index n+ky)
-    double2 *pz = py + tile * NY;                            // [tile][NZ]
+    double2 *pz = py + tile * NY;                            // [tile][NZP]
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = item < NL * NZC;
     const int line = active ? item / NZC : 0, zc = active ? item % NZC : 0;
@@ -328,23 +329,24 @@ __global__ void __launch_bounds__(256) k_structure_factor(EwaldDev e, double2 *p
                     py[c * NY + ky - n] = make_double2(v.x, -v.y);
                 }
             } else {
-                phase_row(pz + c * NZ + kz, x, kz, 1);
+                phase_row(pz + c * NZP + kz, x, kz, 1);
                 for (int n = 1; n <= kz; ++n) {
-                    const double2 v = pz[c * NZ + kz + n];
-                    pz[c * NZ + kz - n] = make_double2(v.x, -v.y);
+                    const double2 v = pz[c * NZP + kz + n];
+                    pz[c * NZP + kz - n] = make_double2(v.x, -v.y);
                 }
+                for (int n = NZ; n < NZP; ++n) pz[c * NZP + n] = make_double2(0.0, 0.0);
             }
         }
         __syncthreads();
         if (active) {
             for (int c = 0; c < nt; ++c) {
                 const double2 a = cmul(px[c * NX + nx], py[c * NY + iy]);
-                const double2 *zr = pz + c * NZ;
+                const double nay = -a.y;
+                const double2 *zr = pz + c * NZP + iz0;
 #pragma unroll
                 for (int k = 0; k < SF_NZ; ++k) {
-                    const int iz = iz0 + k;
-                    const double2 b = zr[iz < NZ ? iz : NZ - 1];
-                    acc[k].x = fma(a.x, b.x, fma(-a.y, b.y, acc[k].x));
+                    const double2 b = zr[k];  // rows are padded by SF_NZ - 1 entries
+                    acc[k].x = fma(a.x, b.x, fma(nay, b.y, acc[k].x));
                     acc[k].y = fma(a.x, b.y, fma(a.y, b.x, acc[k].y));
                 }
             }
@@ -436,11 +438,34 @@ static int sf_items(const EwaldDev &e)
     const int NZ = 2 * e.kmax[2] + 1;
     return (e.kmax[0] + 1) * (2 * e.kmax[1] + 1) * ((NZ + SF_NZ - 1) / SF_NZ);
 }
-int ewald_sf_nslice(const EwaldDev &e)
+// shared memory of one structure-factor block and its phase-tile depth
+static size_t sf_smem(const EwaldDev &e, int *tile_out)
 {
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    const int NZP = (NZ + SF_NZ - 1) / SF_NZ * SF_NZ;
+    const size_t row = (size_t)(NX + NY + NZP) * sizeof(double2);
+    int tile = (int)std::min<size_t>(SF_TILE, (200u * 1024u) / row);
+    if (tile < 1) tile = 1;
+    if (tile_out) *tile_out = tile;
+    return (size_t)tile * row;
+}
+
+// Charge slices of the structure factor: the grid (line blocks x slices) is sized to one full
+// wave of resident blocks, so no partial last wave leaves most SMs idle.
+int ewald_sf_nslice(const EwaldDev &e, int nsm)
+{
+    const size_t smem = sf_smem(e, nullptr);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_structure_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_structure_factor, 256, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
     const int bx = (sf_items(e) + 255) / 256;
-    int ns = (2 * 152 + bx - 1) / bx;
-    if (ns > 64) ns = 64;
+    int ns = (nsm * per_sm) / bx;
+    if (ns > 256) ns = 256;
     if (ns > e.nmm / SF_TILE + 1) ns = e.nmm / SF_TILE + 1;
     if (ns < 1) ns = 1;
     return ns;
@@ -512,11 +537,8 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // structure factor
     {
-        const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
-        const size_t row = (size_t)(NX + NY + NZ) * sizeof(double2);
-        int tile = (int)std::min<size_t>(SF_TILE, (200u * 1024u) / row);
-        if (tile < 1) tile = 1;
-        const size_t smem = (size_t)tile * row;
+        int tile = 1;
+        const size_t smem = sf_smem(e, &tile);
         static size_t attr = 0;
         if (smem > 48 * 1024 && smem > attr) {
             if ((err = cudaFuncSetAttribute(k_structure_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -634,15 +656,21 @@ __global__ void __launch_bounds__(256) k_mm_region1(EwaldDev e, const double4_32
     gchg[4 * (size_t)k + 3] -= pot;
 }
 
-// A(G) = 2 g(G) sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G) on the dense box
-__global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *gfac, const double *mult, double2 *A)
+// A(G) = 2 g(G) sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G) on the dense box, and
+// Az(G) = G_z A(G) (the z-field channel of the MM-side sum)
+__global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *gfac, const double *mult, double2 *A,
+                                                      double2 *Az)
 {
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
     const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const double g = gfac[k];
-    if (g == 0.0) { A[k] = make_double2(0.0, 0.0); return; }
+    if (g == 0.0) {
+        A[k] = make_double2(0.0, 0.0);
+        Az[k] = make_double2(0.0, 0.0);
+        return;
+    }
     const int nx = k / (NY * NZ), ny = (k / NZ) % NY - ky, nz = k % NZ - kz;
     const double Gx = TWO_PI * nx / e.box[0], Gy = TWO_PI * ny / e.box[1], Gz = TWO_PI * nz / e.box[2];
     double re = 0.0, im = 0.0;
@@ -657,16 +685,30 @@ __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *
         im += s * mr + c * mi;
     }
     A[k] = make_double2(g * re, g * im);
+    Az[k] = make_double2(Gz * g * re, Gz * g * im);
 }
 
-// dq_i += sum_G Re[A(G) exp(-iG.R_i)],  dR_i += q_i sum_G G Im[A(G) exp(-iG.R_i)]
-__global__ void __launch_bounds__(128) k_mm_recip(EwaldDev e, const double2 *__restrict__ A, double *dq, double *dR)
+// dq_i += sum_G Re[A(G) exp(-iG.R_i)],  dR_i += q_i sum_G G Im[A(G) exp(-iG.R_i)].
+// One thread per MM charge.  exp(-iG.R) = X(n_x) Y(n_y) Z(n_z): each thread keeps its Z row in
+// shared memory (structure of arrays, so a warp reads consecutive words), and for every
+// (n_x, n_y) line forms the two complex sums B = sum_nz A Z and Bz = sum_nz Az Z (8 FMA per G),
+// then applies X(n_x) Y(n_y) once per line.  X and Y advance by recurrence.
+constexpr int MMR_THREADS = 128;
+
+__global__ void __launch_bounds__(MMR_THREADS) k_mm_recip(EwaldDev e, const double2 *__restrict__ A,
+                                                          const double2 *__restrict__ Az, double *dq, double *dR)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= e.nmm) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
     const int NY = 2 * ky + 1, NZ = 2 * kz + 1;
-    const double fx = e.mm_xyz[3 * i] / e.box[0], fy = e.mm_xyz[3 * i + 1] / e.box[1], fz = e.mm_xyz[3 * i + 2] / e.box[2];
+    double *zre = reinterpret_cast<double *>(smem_raw);   // [NZ][MMR_THREADS]
+    double *zim = zre + (size_t)NZ * MMR_THREADS;          // [NZ][MMR_THREADS]
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + t;
+    const bool act = i < e.nmm;
+    const int ii = act ? i : 0;
+    const double fx = e.mm_xyz[3 * ii] / e.box[0], fy = e.mm_xyz[3 * ii + 1] / e.box[1],
+                 fz = e.mm_xyz[3 * ii + 2] / e.box[2];
     double s, c;
     sincospi(-2.0 * fx, &s, &c);
     const double2 ex1 = make_double2(c, s);
@@ -677,37 +719,50 @@ __global__ void __launch_bounds__(128) k_mm_recip(EwaldDev e, const double2 *__r
     sincospi(2.0 * ky * fy, &s, &c);
     const double2 ey0 = make_double2(c, s);   // n_y = -ky
     sincospi(2.0 * kz * fz, &s, &c);
-    const double2 ez0 = make_double2(c, s);   // n_z = -kz
-    const double gzs = TWO_PI / e.box[2];
+    double2 pz = make_double2(c, s);          // n_z = -kz
+    for (int iz = 0; iz < NZ; ++iz) {
+        zre[(size_t)iz * MMR_THREADS + t] = pz.x;
+        zim[(size_t)iz * MMR_THREADS + t] = pz.y;
+        pz = cmul(pz, ez1);
+    }
     double pot = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
     double2 px = make_double2(1.0, 0.0);
     for (int nx = 0; nx <= kx; ++nx) {
         double2 py = ey0;
         const double Gx = TWO_PI * nx / e.box[0];
         for (int iy = 0; iy < NY; ++iy) {
-            const double Gy = TWO_PI * (iy - ky) / e.box[1];
-            const double2 pxy = cmul(px, py);
-            const double2 *Ar = A + ((size_t)nx * NY + iy) * NZ;
-            double2 pz = ez0;
-            double are = 0.0, aim = 0.0, aimz = 0.0;
-            for (int iz = 0; iz < NZ; ++iz) {
-                const double2 a = __ldg(Ar + iz);
-                const double2 ph = cmul(pxy, pz);
-                const double re = a.x * ph.x - a.y * ph.y;
-                const double im = a.x * ph.y + a.y * ph.x;
-                are += re;
-                aim += im;
-                aimz += (iz - kz) * im;
-                pz = cmul(pz, ez1);
+            // lines with n_x = 0 and n_y < 0 lie outside the half space (their A is zero)
+            if (nx > 0 || iy >= ky) {
+                const double2 *Ar = A + ((size_t)nx * NY + iy) * NZ;
+                const double2 *Azr = Az + ((size_t)nx * NY + iy) * NZ;
+                double br = 0.0, bi = 0.0, bzr = 0.0, bzi = 0.0;
+                for (int iz = 0; iz < NZ; ++iz) {
+                    const double2 a = __ldg(Ar + iz), az = __ldg(Azr + iz);
+                    const double pr = zre[(size_t)iz * MMR_THREADS + t], pi = zim[(size_t)iz * MMR_THREADS + t];
+                    br = fma(a.x, pr, br);
+                    br = fma(-a.y, pi, br);
+                    bi = fma(a.x, pi, bi);
+                    bi = fma(a.y, pr, bi);
+                    bzr = fma(az.x, pr, bzr);
+                    bzr = fma(-az.y, pi, bzr);
+                    bzi = fma(az.x, pi, bzi);
+                    bzi = fma(az.y, pr, bzi);
+                }
+                const double2 pxy = cmul(px, py);
+                const double re = pxy.x * br - pxy.y * bi;
+                const double im = pxy.x * bi + pxy.y * br;
+                const double imz = pxy.x * bzi + pxy.y * bzr;
+                const double Gy = TWO_PI * (iy - ky) / e.box[1];
+                pot += re;
+                f0 += Gx * im;
+                f1 += Gy * im;
+                f2 += imz;
             }
-            pot += are;
-            f0 += Gx * aim;
-            f1 += Gy * aim;
-            f2 += gzs * aimz;
             py = cmul(py, ey1);
         }
         px = cmul(px, ex1);
     }
+    if (!act) return;
     const double q = e.mm_q[i];
     dq[i] += pot;
     dR[3 * i] += q * f0;
@@ -750,9 +805,17 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
     }
     if (e.nmm > 0) {
         const int n = ewald_dense_size(e);
-        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A);
+        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A, w.Az);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        k_mm_recip<<<(e.nmm + 127) / 128, 128, 0, st>>>(e, w.A, dq_int, dR_int);
+        const size_t smem = (size_t)2 * (2 * e.kmax[2] + 1) * MMR_THREADS * sizeof(double);
+        static size_t attr = 0;
+        if (smem > 48 * 1024 && smem > attr) {
+            if ((err = cudaFuncSetAttribute(k_mm_recip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return err;
+            attr = smem;
+        }
+        k_mm_recip<<<(e.nmm + MMR_THREADS - 1) / MMR_THREADS, MMR_THREADS, smem, st>>>(e, w.A, w.Az, dq_int, dR_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         k_mm_background<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, w.sums, dq_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

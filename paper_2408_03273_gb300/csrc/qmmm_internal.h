@@ -96,10 +96,11 @@ struct EwaldBuf {
     int real_nslice = 1;
     double *pr1 = nullptr;       // natm * 20
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
+    double2 *Az = nullptr;       // G_z times A
     double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
 };
 int ewald_dense_size(const EwaldDev &e);
-int ewald_sf_nslice(const EwaldDev &e);
+int ewald_sf_nslice(const EwaldDev &e, int nsm);
 int ewald_real_nslice(const EwaldDev &e, int nsm);
 cudaError_t launch_gfac(const EwaldDev &e, double *gfac, cudaStream_t st);
 // v_j,c (natm*20) at the current geometry

@@ -1,9 +1,11 @@
 // vgrad_f32.cu -- adjoint of the region-I term, mixed precision (see vgrad_f64.cu for the
 // derivative algebra).  The density-folded Hermite coefficients D0, Dx, Dy, Dz are built in
 // FP64 once per primitive pair and rounded to FP32; the per-charge Boys/R recursion to order L+1
-// and the seven contractions run in FP32.  Per-pair sums go through FP32 partials over 16
-// charges into FP64 registers; per-charge sums are warp butterflies in FP32 added into FP64
-// shared-memory accumulators.
+// and the seven contractions run in FP32, with no FP64 instruction inside the charge loop.
+// Per-pair sums go through FP32 partials over 16 charges folded into double-float pairs;
+// per-charge sums over the warp's 32 primitive pairs use a reduce-scatter (6 shuffles for four
+// values) and compensated FP32 shared-memory atomics: the atomic returns the old value, so the
+// rounding error of every addition is recovered exactly and kept in a second FP32 word.
 #include "pp_tile.cuh"
 
 namespace qmmm {
@@ -23,8 +25,10 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     float4 *chi = reinterpret_cast<float4 *>(smem_raw);
     float4 *clo = chi + nch;
     float *tab = reinterpret_cast<float *>(clo + nch);
-    double *acc = reinterpret_cast<double *>(smem_raw + (size_t)nch * 2 * sizeof(float4) + boys_bytes);
-    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) acc[k] = 0.0;
+    // per-charge accumulators as FP32 (hi, lo) pairs: acc_hi[4 nch], acc_lo[4 nch]
+    float *acc_hi = reinterpret_cast<float *>(smem_raw + (size_t)nch * 2 * sizeof(float4) + boys_bytes);
+    float *acc_lo = acc_hi + 4 * nch;
+    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) acc_hi[k] = acc_lo[k] = 0.0f;
     {
         Seg s[3] = {{chi, rg.chg_hi + ch_begin, (unsigned)(nch * sizeof(float4))},
                     {clo, rg.chg_lo + ch_begin, (unsigned)(nch * sizeof(float4))},
@@ -115,7 +119,8 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
             }
         }
 
-        double sdx = 0, sdy = 0, sdz = 0, sex = 0, sey = 0, sez = 0;
+        // per-pair sums over charges as double-float pairs (no FP64 instruction in the charge loop)
+        float sh[6] = {0, 0, 0, 0, 0, 0}, sl[6] = {0, 0, 0, 0, 0, 0};
         for (int c = 0; c < rg.ncls; ++c) {
             const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
             const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
@@ -163,14 +168,39 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                     const float q = ch.w;
                     tdx += q * dx; tdy += q * dy; tdz += q * dz;
                     tex += q * ex; tey += q * ey; tez += q * ez;
-                    const float v0 = warp_sum(-e0), v1 = warp_sum(q * ex), v2 = warp_sum(q * ey), v3 = warp_sum(q * ez);
-                    const float mine = lane == 0 ? v1 : lane == 1 ? v2 : lane == 2 ? v3 : v0;
-                    if (lane < 4) atomicAdd(acc + 4 * j + lane, (double)mine);
+                    // per-charge sums over the 32 primitive pairs: 4 values -> halve twice (each lane
+                    // keeps one component summed over 4 lanes), then a 3-step butterfly; lane 8c ends
+                    // with component c = (dC_x, dC_y, dC_z, dq)
+                    float v0 = q * ex, v1 = q * ey, v2 = q * ez, v3 = -e0;
+                    {
+                        const bool up = lane & 16;
+                        float k0 = up ? v2 : v0, k1 = up ? v3 : v1;
+                        const float s0 = up ? v0 : v2, s1 = up ? v1 : v3;
+                        k0 += __shfl_xor_sync(FULL, s0, 16);
+                        k1 += __shfl_xor_sync(FULL, s1, 16);
+                        const bool up8 = lane & 8;
+                        float k = up8 ? k1 : k0;
+                        k += __shfl_xor_sync(FULL, up8 ? k0 : k1, 8);
+                        k += __shfl_xor_sync(FULL, k, 4);
+                        k += __shfl_xor_sync(FULL, k, 2);
+                        k += __shfl_xor_sync(FULL, k, 1);
+                        if ((lane & 7) == 0) {
+                            // component index: bit 4 -> (2,3) vs (0,1); bit 3 -> second of the pair
+                            const int comp = ((lane >> 4) << 1) | ((lane >> 3) & 1);
+                            // compensated atomic: recover the rounding error of the addition exactly
+                            float *h = acc_hi + 4 * j + comp;
+                            const float old = atomicAdd(h, k);
+                            const float sum = old + k, bv = sum - old;
+                            atomicAdd(acc_lo + 4 * j + comp, (old - (sum - bv)) + (k - bv));
+                        }
+                    }
                 }
-                sdx += tdx; sdy += tdy; sdz += tdz;
-                sex += tex; sey += tey; sez += tez;
+                df_add(sh[0], sl[0], tdx); df_add(sh[1], sl[1], tdy); df_add(sh[2], sl[2], tdz);
+                df_add(sh[3], sl[3], tex); df_add(sh[4], sl[4], tey); df_add(sh[5], sl[5], tez);
             }
         }
+        const double sdx = (double)sh[0] + sl[0], sdy = (double)sh[1] + sl[1], sdz = (double)sh[2] + sl[2];
+        const double sex = (double)sh[3] + sl[3], sey = (double)sh[4] + sl[4], sez = (double)sh[5] + sl[5];
         double g[6] = {-(sdx + aop * sex), -(sdy + aop * sey), -(sdz + aop * sez),
                        sdx - bop * sex, sdy - bop * sey, sdz - bop * sez};
         bool take[5], head;
@@ -187,7 +217,7 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     }
     __syncthreads();
     for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) {
-        const double v = acc[k];
+        const double v = (double)acc_hi[k] + (double)acc_lo[k];
         if (v != 0.0) atomicAdd(gchg + 4 * (size_t)ch_begin + k, v);
     }
 }
