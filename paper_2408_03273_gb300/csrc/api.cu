@@ -166,6 +166,7 @@ struct qmmm_handle {
         dR_int, dq_out, dR_out, Epart, partials, out4;
     DBuf<float> boys32;
     DBuf<double2> S, Spart, A, Az;
+    DBuf<float4> Adf, Azdf;
     DBuf<int> err;
 
     BasisDev basis() const
@@ -242,6 +243,7 @@ struct qmmm_handle {
         mult_init.release(); gqm.release(); gchg.release(); dq_int.release(); dR_int.release();
         dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
         boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); err.release();
+        Adf.release(); Azdf.release();
     }
 };
 
@@ -339,7 +341,7 @@ int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, co
         h->cls_off_I.assign(h->ncls + 1, 0);
     }
     // region-II potential at the QM sites
-    CUDA_TRY(launch_ewald_phi(e, h->rI.p, h->nI, h->ew, h->phi.p, st));
+    CUDA_TRY(launch_ewald_phi(e, h->rI.p, h->nI, h->ew, h->phi.p, h->precision == QMMM_MIXED, st));
     h->V_valid = false;
     return check_device_errors(h);
 }
@@ -687,6 +689,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sf_nslice = ewald_sf_nslice(e, h->nsm);
         h->ew.real_nslice = ewald_real_nslice(e, h->nsm);
         if ((rc = h->gfac.ensure(nd)) || (rc = h->S.ensure(nd)) || (rc = h->A.ensure(nd)) || (rc = h->Az.ensure(nd)) ||
+            (rc = h->Adf.ensure(nd)) || (rc = h->Azdf.ensure(nd)) ||
             (rc = h->Spart.ensure((size_t)nd * h->ew.sf_nslice)) ||
             (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
             return rc;
@@ -697,6 +700,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.pr1 = h->pr1.p;
         h->ew.A = h->A.p;
         h->ew.Az = h->Az.p;
+        h->ew.Adf = h->Adf.p;
+        h->ew.Azdf = h->Azdf.p;
         h->ew.sums = h->sums.p;
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
@@ -865,12 +870,12 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
     const EwaldDev e = h->ewald();
     if (h->nmm > 0) {
         CUDA_TRY(launch_ewald_mm(e, h->rI.p, h->nI, h->mult.p, h->phi.p, h->ew, h->dq_int.p, h->dR_int.p, h->gchg.p,
-                                 h->gqm.p, st));
+                                 h->gqm.p, h->precision == QMMM_MIXED, st));
         CUDA_TRY(launch_scatter_region(h->rI_idx.p, h->nI, h->gchg.p, h->dq_int.p, h->dR_int.p, st));
         CUDA_TRY(launch_unpermute(h->dq_int.p, h->dR_int.p, h->dperm.p, h->nmm, h->dq_out.p, h->dR_out.p, st));
     } else {
         CUDA_TRY(launch_ewald_mm(e, h->rI.p, 0, h->mult.p, h->phi.p, h->ew, h->dq_int.p, h->dR_int.p, h->gchg.p,
-                                 h->gqm.p, st));
+                                 h->gqm.p, h->precision == QMMM_MIXED, st));
     }
     if ((rc = copy_out(h, dE_dRqm, h->gqm.p, 3 * (size_t)h->natm))) return rc;
     if (h->nmm > 0) {

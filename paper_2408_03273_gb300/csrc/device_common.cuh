@@ -375,6 +375,83 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x)
 }
 
 // ------------------------------------------------------------------------------------------
+// double-float numbers h + l (|l| <= ulp(h)/2): about 47 significant bits from FP32 pipes.
+// Products use the exact FMA residual, sums the two-sum error; a double-float accumulator
+// (ah, al) adds exact hi*hi products with a two-sum and lets the small terms collect in al.
+// ------------------------------------------------------------------------------------------
+struct f2 {
+    float h, l;
+};
+
+__device__ __forceinline__ f2 f2_from(double x)
+{
+    const float h = (float)x;
+    return f2{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double f2_to(f2 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double f2_to(float h, float l) { return (double)h + (double)l; }
+
+__device__ __forceinline__ f2 f2_fast2sum(float a, float b)
+{
+    const float s = a + b;
+    return f2{s, b - (s - a)};
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    const float s = a.h + b.h;
+    const float v = s - a.h;
+    float e = (a.h - (s - v)) + (b.h - v);
+    e += a.l + b.l;
+    return f2_fast2sum(s, e);
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return f2_fast2sum(p, e);
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return f2{-a.h, -a.l}; }
+
+// (ah, al) += a * b
+__device__ __forceinline__ void f2_mac(float &ah, float &al, f2 a, f2 b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p);
+    const float s = ah + p;
+    const float v = s - ah;
+    const float t = (ah - (s - v)) + (p - v);
+    ah = s;
+    al += t + e;
+    al = fmaf(a.h, b.l, al);
+    al = fmaf(a.l, b.h, al);
+}
+
+// complex double-float: (re, im) as f2 pairs, stored as float4 (re.h, re.l, im.h, im.l)
+struct c2 {
+    f2 re, im;
+};
+__device__ __forceinline__ c2 c2_from(float4 v) { return c2{f2{v.x, v.y}, f2{v.z, v.w}}; }
+__device__ __forceinline__ float4 c2_pack(double re, double im)
+{
+    const f2 a = f2_from(re), b = f2_from(im);
+    return make_float4(a.h, a.l, b.h, b.l);
+}
+__device__ __forceinline__ c2 c2_mul(c2 a, c2 b)
+{
+    return c2{f2_add(f2_mul(a.re, b.re), f2_neg(f2_mul(a.im, b.im))), f2_add(f2_mul(a.re, b.im), f2_mul(a.im, b.re))};
+}
+// complex accumulator (4 floats) += a * b
+__device__ __forceinline__ void c2_mac(float (&acc)[4], c2 a, c2 b)
+{
+    f2_mac(acc[0], acc[1], a.re, b.re);
+    f2_mac(acc[0], acc[1], f2_neg(a.im), b.im);
+    f2_mac(acc[2], acc[3], a.re, b.im);
+    f2_mac(acc[2], acc[3], a.im, b.re);
+}
+
+// ------------------------------------------------------------------------------------------
 // multipole interaction tensors of a radial function (Ewald kernels, FP64)
 //   T = f, T_a = d_a f, T_ab = 1/2 d_ab f, T_abc = 1/6 d_abc f  (derivatives w.r.t. R_j),
 //   d_a f = x_a g1, d_ab f = delta_ab g1 + x_a x_b g2,

@@ -360,6 +360,85 @@ __global__ void __launch_bounds__(256) k_structure_factor(EwaldDev e, double2 *p
     }
 }
 
+// Double-float variant (mixed-precision path): the same tiling, with phases and the eight
+// accumulators as FP32 (hi, lo) pairs -- each (G, charge) term is an error-free complex
+// multiply-add of about 48 FP32 operations instead of 4 FP64 FMAs (~47-bit accuracy per term).
+__device__ __forceinline__ void phase_row_df(float4 *dst, double frac, int nmax, double scale)
+{
+    double s, c;
+    sincospi(2.0 * frac, &s, &c);
+    const double2 e1 = make_double2(c, s);
+    double2 z = make_double2(1.0, 0.0);
+    for (int n = 0; n <= nmax; ++n) {
+        dst[n] = c2_pack(scale * z.x, scale * z.y);
+        z = cmul(z, e1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_structure_factor_df(EwaldDev e, double2 *partial, int tile)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NX = kx + 1, NY = 2 * ky + 1, NZ = 2 * kz + 1;
+    const int NZC = (NZ + SF_NZ - 1) / SF_NZ;
+    const int NZP = NZC * SF_NZ;
+    const int NL = NX * NY;
+    float4 *px = reinterpret_cast<float4 *>(smem_raw);  // [tile][NX]
+    float4 *py = px + tile * NX;                          // [tile][NY]
+    float4 *pz = py + tile * NY;                          // [tile][NZP]
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = item < NL * NZC;
+    const int line = active ? item / NZC : 0, zc = active ? item % NZC : 0;
+    const int nx = line / NY, iy = line % NY, iz0 = zc * SF_NZ;
+    float acc[SF_NZ][4];
+#pragma unroll
+    for (int k = 0; k < SF_NZ; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
+
+    const int nslice = gridDim.y;
+    const int per = (e.nmm + nslice - 1) / nslice;
+    const int i0 = blockIdx.y * per, i1 = min(e.nmm, i0 + per);
+    for (int t0 = i0; t0 < i1; t0 += tile) {
+        const int nt = min(tile, i1 - t0);
+        __syncthreads();
+        for (int r = threadIdx.x; r < 3 * tile; r += blockDim.x) {
+            const int c = r / 3, d = r % 3;
+            if (c >= nt) continue;
+            const double x = e.mm_xyz[3 * (t0 + c) + d] / e.box[d];
+            if (d == 0) {
+                phase_row_df(px + c * NX, x, kx, e.mm_q[t0 + c]);
+            } else if (d == 1) {
+                phase_row_df(py + c * NY + ky, x, ky, 1.0);
+                for (int n = 1; n <= ky; ++n) {
+                    const float4 v = py[c * NY + ky + n];
+                    py[c * NY + ky - n] = make_float4(v.x, v.y, -v.z, -v.w);
+                }
+            } else {
+                phase_row_df(pz + c * NZP + kz, x, kz, 1.0);
+                for (int n = 1; n <= kz; ++n) {
+                    const float4 v = pz[c * NZP + kz + n];
+                    pz[c * NZP + kz - n] = make_float4(v.x, v.y, -v.z, -v.w);
+                }
+                for (int n = NZ; n < NZP; ++n) pz[c * NZP + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            for (int c = 0; c < nt; ++c) {
+                const c2 a = c2_mul(c2_from(px[c * NX + nx]), c2_from(py[c * NY + iy]));
+                const float4 *zr = pz + c * NZP + iz0;
+#pragma unroll
+                for (int k = 0; k < SF_NZ; ++k) c2_mac(acc[k], a, c2_from(zr[k]));
+            }
+        }
+    }
+    if (active) {
+        double2 *dst = partial + ((size_t)blockIdx.y * NL + line) * NZ;
+#pragma unroll
+        for (int k = 0; k < SF_NZ; ++k)
+            if (iz0 + k < NZ) dst[iz0 + k] = make_double2(f2_to(acc[k][0], acc[k][1]), f2_to(acc[k][2], acc[k][3]));
+    }
+}
+
 __global__ void k_sum_slices(const double2 *partial, int nslice, int n, double2 *out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -522,7 +601,7 @@ __global__ void k_phi_final(EwaldDev e, const double *res_recip, const double *p
 }
 
 cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, const EwaldBuf &w, double *phi,
-                             cudaStream_t st)
+                             bool df, cudaStream_t st)
 {
     cudaError_t err;
     // sum of MM charges (background)
@@ -539,15 +618,19 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
     {
         int tile = 1;
         const size_t smem = sf_smem(e, &tile);
-        static size_t attr = 0;
-        if (smem > 48 * 1024 && smem > attr) {
-            if ((err = cudaFuncSetAttribute(k_structure_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem)) != cudaSuccess)
+        static size_t attr = 0, attr_df = 0;
+        size_t &a = df ? attr_df : attr;
+        if (smem > 48 * 1024 && smem > a) {
+            if ((err = cudaFuncSetAttribute(df ? (const void *)k_structure_factor_df : (const void *)k_structure_factor,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
                 return err;
-            attr = smem;
+            a = smem;
         }
         dim3 grid((sf_items(e) + 255) / 256, w.sf_nslice);
-        k_structure_factor<<<grid, 256, smem, st>>>(e, w.Spart, tile);
+        if (df)
+            k_structure_factor_df<<<grid, 256, smem, st>>>(e, w.Spart, tile);
+        else
+            k_structure_factor<<<grid, 256, smem, st>>>(e, w.Spart, tile);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         const int n = ewald_dense_size(e);
         k_sum_slices<<<(n + 255) / 256, 256, 0, st>>>(w.Spart, w.sf_nslice, n, w.S);
@@ -659,7 +742,7 @@ __global__ void __launch_bounds__(256) k_mm_region1(EwaldDev e, const double4_32
 // A(G) = 2 g(G) sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G) on the dense box, and
 // Az(G) = G_z A(G) (the z-field channel of the MM-side sum)
 __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *gfac, const double *mult, double2 *A,
-                                                      double2 *Az)
+                                                      double2 *Az, float4 *Adf, float4 *Azdf)
 {
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
     const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
@@ -669,6 +752,10 @@ __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *
     if (g == 0.0) {
         A[k] = make_double2(0.0, 0.0);
         Az[k] = make_double2(0.0, 0.0);
+        if (Adf) {
+            Adf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Azdf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         return;
     }
     const int nx = k / (NY * NZ), ny = (k / NZ) % NY - ky, nz = k % NZ - kz;
@@ -686,6 +773,10 @@ __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *
     }
     A[k] = make_double2(g * re, g * im);
     Az[k] = make_double2(Gz * g * re, Gz * g * im);
+    if (Adf) {
+        Adf[k] = c2_pack(g * re, g * im);
+        Azdf[k] = c2_pack(Gz * g * re, Gz * g * im);
+    }
 }
 
 // dq_i += sum_G Re[A(G) exp(-iG.R_i)],  dR_i += q_i sum_G G Im[A(G) exp(-iG.R_i)].
@@ -770,6 +861,83 @@ __global__ void __launch_bounds__(MMR_THREADS) k_mm_recip(EwaldDev e, const doub
     dR[3 * i + 2] += q * f2;
 }
 
+// Double-float variant of k_mm_recip (mixed-precision path): Z rows, A and Az as FP32 (hi, lo)
+// pairs; the two complex dot products per line are error-free multiply-adds, the per-line
+// combination and the X, Y recurrences run in double-float arithmetic.
+__global__ void __launch_bounds__(MMR_THREADS) k_mm_recip_df(EwaldDev e, const float4 *__restrict__ A,
+                                                             const float4 *__restrict__ Az, double *dq, double *dR)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float2 gyt[2 * 56 + 1];
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1;
+    float4 *zs = reinterpret_cast<float4 *>(smem_raw);  // [NZ][MMR_THREADS]
+    const int t = threadIdx.x;
+    for (int iy = t; iy < NY; iy += blockDim.x) {
+        const f2 g = f2_from(TWO_PI * (iy - ky) / e.box[1]);
+        gyt[iy] = make_float2(g.h, g.l);
+    }
+    const int i = blockIdx.x * blockDim.x + t;
+    const bool act = i < e.nmm;
+    const int ii = act ? i : 0;
+    const double fx = e.mm_xyz[3 * ii] / e.box[0], fy = e.mm_xyz[3 * ii + 1] / e.box[1],
+                 fz = e.mm_xyz[3 * ii + 2] / e.box[2];
+    double s, c;
+    sincospi(-2.0 * fx, &s, &c);
+    const c2 ex1{f2_from(c), f2_from(s)};
+    sincospi(-2.0 * fy, &s, &c);
+    const c2 ey1{f2_from(c), f2_from(s)};
+    sincospi(-2.0 * fz, &s, &c);
+    const double2 ez1 = make_double2(c, s);
+    sincospi(2.0 * ky * fy, &s, &c);
+    const c2 ey0{f2_from(c), f2_from(s)};
+    sincospi(2.0 * kz * fz, &s, &c);
+    double2 pz = make_double2(c, s);
+    for (int iz = 0; iz < NZ; ++iz) {
+        zs[(size_t)iz * MMR_THREADS + t] = c2_pack(pz.x, pz.y);
+        pz = cmul(pz, ez1);
+    }
+    __syncthreads();
+    f2 pot{0.f, 0.f}, f1{0.f, 0.f}, f2z{0.f, 0.f};
+    double f0 = 0.0;
+    c2 px{f2{1.f, 0.f}, f2{0.f, 0.f}};
+    for (int nx = 0; nx <= kx; ++nx) {
+        c2 py = ey0;
+        f2 sim{0.f, 0.f};
+        for (int iy = 0; iy < NY; ++iy) {
+            if (nx > 0 || iy >= ky) {
+                const float4 *Ar = A + ((size_t)nx * NY + iy) * NZ;
+                const float4 *Azr = Az + ((size_t)nx * NY + iy) * NZ;
+                float B[4] = {0.f, 0.f, 0.f, 0.f}, Bz[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int iz = 0; iz < NZ; ++iz) {
+                    const c2 z = c2_from(zs[(size_t)iz * MMR_THREADS + t]);
+                    c2_mac(B, c2_from(__ldg(Ar + iz)), z);
+                    c2_mac(Bz, c2_from(__ldg(Azr + iz)), z);
+                }
+                const c2 pxy = c2_mul(px, py);
+                const c2 b{f2_add(f2{B[0], 0.f}, f2{B[1], 0.f}), f2_add(f2{B[2], 0.f}, f2{B[3], 0.f})};
+                const f2 bzr = f2_add(f2{Bz[0], 0.f}, f2{Bz[1], 0.f}), bzi = f2_add(f2{Bz[2], 0.f}, f2{Bz[3], 0.f});
+                const c2 pr = c2_mul(pxy, b);
+                const f2 imz = f2_add(f2_mul(pxy.re, bzi), f2_mul(pxy.im, bzr));
+                pot = f2_add(pot, pr.re);
+                sim = f2_add(sim, pr.im);
+                const float2 gy = gyt[iy];
+                f1 = f2_add(f1, f2_mul(f2{gy.x, gy.y}, pr.im));
+                f2z = f2_add(f2z, imz);
+            }
+            py = c2_mul(py, ey1);
+        }
+        f0 += TWO_PI * nx / e.box[0] * f2_to(sim);
+        px = c2_mul(px, ex1);
+    }
+    if (!act) return;
+    const double q = e.mm_q[i];
+    dq[i] += f2_to(pot);
+    dR[3 * i] += q * f0;
+    dR[3 * i + 1] += q * f2_to(f1);
+    dR[3 * i + 2] += q * f2_to(f2z);
+}
+
 __global__ void k_mm_background(EwaldDev e, const double *sums, double *dq)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -790,7 +958,7 @@ __global__ void k_qm_tensor_grad(int natm, const double *mult, const double *phi
 }
 
 cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, const double *mult, const double *phi,
-                            const EwaldBuf &w, double *dq_int, double *dR_int, double *gchg, double *gqm,
+                            const EwaldBuf &w, double *dq_int, double *dR_int, double *gchg, double *gqm, bool df,
                             cudaStream_t st)
 {
     cudaError_t err;
@@ -805,17 +973,23 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
     }
     if (e.nmm > 0) {
         const int n = ewald_dense_size(e);
-        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A, w.Az);
+        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A, w.Az, df ? w.Adf : nullptr,
+                                                         df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        const size_t smem = (size_t)2 * (2 * e.kmax[2] + 1) * MMR_THREADS * sizeof(double);
-        static size_t attr = 0;
-        if (smem > 48 * 1024 && smem > attr) {
-            if ((err = cudaFuncSetAttribute(k_mm_recip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess)
+        const size_t smem = (size_t)2 * (2 * e.kmax[2] + 1) * MMR_THREADS * sizeof(double);  // = NZ float4 per thread
+        static size_t attr = 0, attr_df = 0;
+        size_t &a = df ? attr_df : attr;
+        if (smem > 48 * 1024 && smem > a) {
+            if ((err = cudaFuncSetAttribute(df ? (const void *)k_mm_recip_df : (const void *)k_mm_recip,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
                 return err;
-            attr = smem;
+            a = smem;
         }
-        k_mm_recip<<<(e.nmm + MMR_THREADS - 1) / MMR_THREADS, MMR_THREADS, smem, st>>>(e, w.A, w.Az, dq_int, dR_int);
+        const int nb = (e.nmm + MMR_THREADS - 1) / MMR_THREADS;
+        if (df)
+            k_mm_recip_df<<<nb, MMR_THREADS, smem, st>>>(e, w.Adf, w.Azdf, dq_int, dR_int);
+        else
+            k_mm_recip<<<nb, MMR_THREADS, smem, st>>>(e, w.A, w.Az, dq_int, dR_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         k_mm_background<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, w.sums, dq_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -97,6 +97,8 @@ struct EwaldBuf {
     double *pr1 = nullptr;       // natm * 20
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
     double2 *Az = nullptr;       // G_z times A
+    float4 *Adf = nullptr;       // A and Az as double-float (re.h, re.l, im.h, im.l), mixed path
+    float4 *Azdf = nullptr;
     double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
 };
 int ewald_dense_size(const EwaldDev &e);
@@ -104,12 +106,13 @@ int ewald_sf_nslice(const EwaldDev &e, int nsm);
 int ewald_real_nslice(const EwaldDev &e, int nsm);
 cudaError_t launch_gfac(const EwaldDev &e, double *gfac, cudaStream_t st);
 // v_j,c (natm*20) at the current geometry
+// df: double-float reciprocal sums (mixed-precision path) instead of FP64
 cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, const EwaldBuf &w, double *phi,
-                             cudaStream_t st);
+                             bool df, cudaStream_t st);
 // MM-side adjoint of the multipole energy and the QM tensor gradient:
 //   dq_int[nmm] +=, dR_int[nmm*3] += (internal order), gchg[nI*4] += (region-I T part), gqm[natm*3] +=
 cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, const double *mult, const double *phi,
-                            const EwaldBuf &w, double *dq_int, double *dR_int, double *gchg, double *gqm,
+                            const EwaldBuf &w, double *dq_int, double *dR_int, double *gchg, double *gqm, bool df,
                             cudaStream_t st);
 // region-I nuclear-MM term: Epart[nblk] partial energies (nblk = ceil(nI/256)); optional gradients
 int enucmm_nblk(int nI);
