@@ -49,6 +49,22 @@ __device__ __forceinline__ PPLane load_pp(const BasisDev &bd, int i, int pp_end)
     return L;
 }
 
+// Inverse of class_of: the angular momenta of a class index.
+__host__ __device__ constexpr int la_of_class(int c)
+{
+    int la = 0;
+    while ((la + 1) * (la + 2) / 2 <= c) ++la;
+    return la;
+}
+__host__ __device__ constexpr int lb_of_class(int c) { return c - la_of_class(c) * (la_of_class(c) + 1) / 2; }
+static_assert(la_of_class(class_of(3, 2)) == 3 && lb_of_class(class_of(3, 2)) == 2, "class index inverse");
+
+// Class-split compilation.  A sweep source (vpot_*.cu, vgrad_*.cu) is compiled once per angular
+// class with -DQMMM_SPLIT_CLASS=<class index>, which defines that class's kernel and explicitly
+// instantiates its launcher, and once without, which compiles only the runtime dispatcher below;
+// the launchers are declared (not defined) there and resolved at link time.  The unrolled
+// high-l kernels are large, so this keeps every compilation short and lets them run in parallel.
+//
 // Dispatch a functor templated on (LA, LB) for a runtime class index (l_A >= l_B).
 template <template <int, int> class K, typename... Args>
 cudaError_t dispatch_class(int cls, Args &&...args)

@@ -10,6 +10,15 @@
 
 namespace qmmm {
 
+template <int LA, int LB>
+struct VgradF32 {
+    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                           int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
+                           int nsm, cudaStream_t st);
+};
+
+#ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
+
 constexpr int GFOLD = 16;
 
 template <int LA, int LB>
@@ -228,30 +237,32 @@ inline unsigned boys32_bytes_g()
 }
 
 template <int LA, int LB>
-struct VgradF32 {
-    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, cudaStream_t st)
-    {
-        const unsigned tb = boys32_bytes_g();
-        const size_t per = 2 * sizeof(float4) + 4 * sizeof(double);
-        const size_t smem = (size_t)(ch_end - ch_begin) * per + tb;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(CHUNK_GRAD * per + tb));
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        const int ntile = (pp_end - pp_begin + 31) / 32;
-        int grid = (ntile + 7) / 8;
-        if (grid > nsm) grid = nsm;
-        if (grid < 1) return cudaSuccess;
-        k_vgrad_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, dm, gqm,
-                                                     gchg, err);
-        return cudaGetLastError();
+cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                  int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
+                                  int nsm, cudaStream_t st)
+{
+    const unsigned tb = boys32_bytes_g();
+    const size_t per = 2 * sizeof(float4) + 4 * sizeof(double);
+    const size_t smem = (size_t)(ch_end - ch_begin) * per + tb;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(CHUNK_GRAD * per + tb));
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
-};
+    const int ntile = (pp_end - pp_begin + 31) / 32;
+    int grid = (ntile + 7) / 8;
+    if (grid > nsm) grid = nsm;
+    if (grid < 1) return cudaSuccess;
+    k_vgrad_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, dm, gqm,
+                                                 gchg, err);
+    return cudaGetLastError();
+}
+
+template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
+
+#else  // the dispatcher
 
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
@@ -261,5 +272,7 @@ cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int
     return dispatch_class<VgradF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
                                     st);
 }
+
+#endif
 
 }  // namespace qmmm

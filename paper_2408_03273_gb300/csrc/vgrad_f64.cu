@@ -16,6 +16,15 @@
 namespace qmmm {
 
 template <int LA, int LB>
+struct VgradF64 {
+    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                           int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
+                           int nsm, cudaStream_t st);
+};
+
+#ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
+
+template <int LA, int LB>
 __global__ void __launch_bounds__(256, 1)
 k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
             const double *__restrict__ boys, const double *__restrict__ dm, double *__restrict__ gqm,
@@ -170,28 +179,30 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
 }
 
 template <int LA, int LB>
-struct VgradF64 {
-    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, cudaStream_t st)
-    {
-        const size_t smem = (size_t)(ch_end - ch_begin) * (sizeof(double4_32a) + 4 * sizeof(double));
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(CHUNK_GRAD * (sizeof(double4_32a) + 4 * sizeof(double))));
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        const int ntile = (pp_end - pp_begin + 31) / 32;
-        int grid = (ntile + 7) / 8;
-        if (grid > nsm) grid = nsm;
-        if (grid < 1) return cudaSuccess;
-        k_vgrad_f64<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm,
-                                                     gchg, err);
-        return cudaGetLastError();
+cudaError_t VgradF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                  int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
+                                  int nsm, cudaStream_t st)
+{
+    const size_t smem = (size_t)(ch_end - ch_begin) * (sizeof(double4_32a) + 4 * sizeof(double));
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(CHUNK_GRAD * (sizeof(double4_32a) + 4 * sizeof(double))));
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
-};
+    const int ntile = (pp_end - pp_begin + 31) / 32;
+    int grid = (ntile + 7) / 8;
+    if (grid > nsm) grid = nsm;
+    if (grid < 1) return cudaSuccess;
+    k_vgrad_f64<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm,
+                                                 gchg, err);
+    return cudaGetLastError();
+}
+
+template struct VgradF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
+
+#else  // the dispatcher
 
 cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
@@ -201,5 +212,7 @@ cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int
     return dispatch_class<VgradF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
                                     st);
 }
+
+#endif
 
 }  // namespace qmmm

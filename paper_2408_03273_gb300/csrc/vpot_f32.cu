@@ -13,6 +13,14 @@
 
 namespace qmmm {
 
+template <int LA, int LB>
+struct VpotF32 {
+    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                           int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st);
+};
+
+#ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
+
 constexpr int FOLD = 16;
 
 template <int LA, int LB>
@@ -131,27 +139,29 @@ inline unsigned boys32_bytes()
 }
 
 template <int LA, int LB>
-struct VpotF32 {
-    static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st)
-    {
-        const unsigned tb = boys32_bytes();
-        const size_t smem = (size_t)(ch_end - ch_begin) * 2 * sizeof(float4) + tb;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(CHUNK_F32 * 2 * sizeof(float4) + tb));
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        const int ntile = (pp_end - pp_begin + 31) / 32;
-        int grid = (ntile + 7) / 8;
-        if (grid > nsm) grid = nsm;
-        if (grid < 1) return cudaSuccess;
-        k_vpot_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, V, err);
-        return cudaGetLastError();
+cudaError_t VpotF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                 int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st)
+{
+    const unsigned tb = boys32_bytes();
+    const size_t smem = (size_t)(ch_end - ch_begin) * 2 * sizeof(float4) + tb;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(CHUNK_F32 * 2 * sizeof(float4) + tb));
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
-};
+    const int ntile = (pp_end - pp_begin + 31) / 32;
+    int grid = (ntile + 7) / 8;
+    if (grid > nsm) grid = nsm;
+    if (grid < 1) return cudaSuccess;
+    k_vpot_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, V, err);
+    return cudaGetLastError();
+}
+
+template struct VpotF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
+
+#else  // the dispatcher
 
 cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                             int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm,
@@ -160,5 +170,7 @@ cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int 
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
 }
+
+#endif
 
 }  // namespace qmmm
