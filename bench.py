@@ -191,6 +191,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-autotune", action="store_true", help="run the class sweeps with the flop-model schedule")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -216,6 +217,19 @@ def main():
     stream = torch.cuda.current_stream()
     h.set_stream(stream)
     info = h.info
+    tuning = {}
+
+    def tune(hh):
+        # one-time plan step outside the timed region: block shape and SM split per angular class
+        if args.no_autotune:
+            return
+        hh.autotune()
+        for k in range(4):
+            t = hh.tuning(k)
+            if t["tuned"]:
+                tuning[q.SWEEP_KINDS[k]] = {"threads": t["threads"], "share": t["share"]}
+
+    tune(h)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
     qm_d, mm_d, q_d, dm_d = t(s.atom_xyz), t(s.mm_xyz), t(s.mm_q), t(s.dm)
     nao, natm, nmm = s.nao, s.natm, s.nmm
@@ -296,6 +310,7 @@ def main():
         E64 = h.energy(dm_d).clone()
         hm = q.Handle(s, precision=q.QMMM_MIXED)
         hm.set_stream(stream)
+        tune(hm)
         ms_m, rec_m = timed(hm, args.steps, args.warmup)
         Em = hm.energy(dm_d)
         fro = float(torch.linalg.norm(V_d - V64) / torch.linalg.norm(V64))
@@ -342,7 +357,11 @@ def main():
            "config": {"workload": describe(s, info), "precision": args.precision,
                       "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "units_per_step": units_per_step},
+                      "units_per_step": units_per_step,
+                      "prim_pairs_per_class": dict(zip(["ss", "ps", "pp", "ds", "dp", "dd", "fs", "fp", "fd", "ff"],
+                                                       info["n_prim_pairs_class"])),
+                      "sweep_schedule": ("flop-model SM split, 256-thread blocks" if args.no_autotune else
+                                         {"autotuned": tuning})},
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
            "e2e": {"value": world * units_per_step / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}

@@ -154,6 +154,73 @@ int qmmm_get_potential(qmmm_handle *h, double *v);
  * Returns the number of values written (2). */
 int qmmm_last_timing(const qmmm_handle *h, double *out);
 
+/* Autotuner (the paper has no counterpart: its integrals come from a library).  The region-I
+ * sweeps run one kernel per angular class (l_A, l_B), all classes at once on their own streams,
+ * each with a cap on its grid -- its share of the SMs -- and a block shape.  By default the
+ * shares follow a flop model of each class's work and every class uses 256-thread blocks.
+ * qmmm_autotune times each class kernel alone on this handle's geometry, in each block shape
+ * it has (256 threads, or a wider block where registers allow: more pair tiles per CTA on the
+ * same staged charges), keeps the faster shape, sets each class's share in proportion to its
+ * measured SM-time so that the classes finish together, and keeps the tuned configuration only
+ * if the concurrent sweep is faster than the untuned one.
+ *   flags: QMMM_TUNE_V and/or QMMM_TUNE_FORCES select the V and adjoint sweeps (0 = both);
+ *   QMMM_TUNE_BOTH_PRECISIONS tunes the FP64 and the mixed kernels, else the current precision.
+ * Needs a geometry (qmmm_create / qmmm_set_positions).  It works in scratch buffers with a zero
+ * density: results of earlier calls stay valid, and results of later calls are unchanged apart
+ * from the order of floating-point atomic additions.  It synchronises the handle's stream and
+ * takes of the order of 20 sweep launches per tuned kernel.  The tuning is kept until
+ * qmmm_set_positions changes region I's size by more than a quarter, when it resets to the model. */
+enum { QMMM_TUNE_V = 1, QMMM_TUNE_FORCES = 2, QMMM_TUNE_BOTH_PRECISIONS = 4 };
+int qmmm_autotune(qmmm_handle *h, int flags);
+
+/* The sweep configuration in use for one kernel kind (0 V FP64, 1 V mixed, 2 adjoint FP64,
+ * 3 adjoint mixed), per angular class in the order (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) (3,0)
+ * (3,1) (3,2) (3,3): threads[10] per block, share[10] = grid cap (SMs; 0 for an empty class),
+ * ms[10] = the class's measured time alone at that share (0 if not measured), wide[10] = the
+ * class's wide block size (0: it has only 256-thread blocks).  Any array may be NULL.  Returns 1
+ * if the kind was tuned, 0 if it runs the model configuration, <0 on error. */
+int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, double *ms, int *wide);
+
+/* Install a sweep configuration (e.g. one saved from qmmm_get_tuning on an earlier run of the
+ * same system): threads[10] per class must be 256 or that class's wide block size (the values
+ * qmmm_get_tuning can report); weight[10] (NULL = the flop model) is each class's SM-time per
+ * primitive pair, in any common unit, from which the SM shares follow.  QMMM_ERR_ARG if a block
+ * size is not available for its class or a weight is not positive. */
+int qmmm_set_tuning(qmmm_handle *h, int kind, const int *threads, const double *weight);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batches of independent systems (MD frames or sampling replicas of uneven sizes).  The paper
+ * runs one system per process; this groups F handles (each from qmmm_create, each with its own
+ * geometry, basis and charges) so that one call evaluates, for every frame, V (Eq. 9), the
+ * energy E[4] as qmmm_energy, and the gradient as qmmm_forces, at that frame's density.
+ *
+ * qmmm_batch_run records the whole batch once into a CUDA graph -- every frame on its own stream,
+ * its angular-class sweeps on that frame's class streams, so small frames fill the SMs that
+ * large ones leave free -- and from then on launches the graph: one launch per call, no host
+ * work per kernel.  Before recording it runs the batch once through the plain calls (which
+ * sizes every buffer and sets every kernel attribute); the graph is recorded again when a frame's
+ * region-I size, precision, sweep configuration or any array pointer differs from the recorded
+ * one.  Positions change through qmmm_set_positions on the frame's handle between runs.
+ *
+ * qmmm_batch_create: frames[nframes] (borrowed: they must outlive the batch and must not be used
+ * on their own while the batch runs), stream = cudaStream_t as void* (NULL: the batch creates its
+ * own stream, since the legacy stream cannot be recorded).
+ * qmmm_batch_run: per frame f, DEVICE pointers dm[f] (nao_f^2, input), V[f] (nao_f^2),
+ * E[f] (4 doubles), dE_dRqm[f] (natm_f*3), dE_dRmm[f] (nmm_f*3), dE_dq[f] (nmm_f); each of the
+ * output pointer arrays may be NULL (that output is not written) and so may single entries.
+ * Host memory is rejected (QMMM_ERR_ARG): a recorded graph cannot copy to pageable memory.  The
+ * call returns after the graph has finished and every frame's device error flag is checked.
+ * qmmm_batch_timing: ms[0] = the last run (graph launch to last frame done), ms[1 + f] = the time
+ * at which frame f's outputs were complete, measured from the same start; returns nframes + 1. */
+typedef struct qmmm_batch qmmm_batch;
+int qmmm_batch_create(qmmm_handle *const *frames, int nframes, void *stream, qmmm_batch **out);
+int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, double *const *E,
+                   double *const *dE_dRqm, double *const *dE_dRmm, double *const *dE_dq);
+int qmmm_batch_timing(const qmmm_batch *b, double *ms);
+/* Number of graph recordings so far (1 after the first run when nothing changes). */
+int qmmm_batch_captures(const qmmm_batch *b);
+void qmmm_batch_destroy(qmmm_batch *b);
+
 void qmmm_destroy(qmmm_handle *h);
 const char *qmmm_strerror(int code);
 const char *qmmm_last_error(void);

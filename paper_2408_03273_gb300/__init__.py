@@ -16,8 +16,20 @@ from ._lib import (  # noqa: F401
     EXPORTS,
     QMMM_FP64,
     QMMM_MIXED,
+    QMMM_TUNE_BOTH_PRECISIONS,
+    QMMM_TUNE_FORCES,
+    QMMM_TUNE_V,
+    SWEEP_KINDS,
     QMMMError,
     load,
+    qmmm_batch_captures,
+    qmmm_batch_create,
+    qmmm_batch_destroy,
+    qmmm_batch_run,
+    qmmm_batch_timing,
+    qmmm_autotune,
+    qmmm_get_tuning,
+    qmmm_set_tuning,
     library_path,
     qmmm_create,
     qmmm_destroy,
@@ -36,4 +48,4 @@ from ._lib import (  # noqa: F401
     qmmm_strerror,
     qmmm_vpot,
 )
-from .handle import Handle, QMMMEnergy  # noqa: F401
+from .handle import Batch, Handle, QMMMEnergy  # noqa: F401

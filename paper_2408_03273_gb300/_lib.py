@@ -59,7 +59,8 @@ _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
-           "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
+           "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
+           "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
 
 def library_path() -> str:
@@ -91,6 +92,15 @@ def load(build_if_needed: bool = True):
         "qmmm_nao": (c_int, [c_void_p]),
         "qmmm_get_potential": (c_int, [c_void_p, c_void_p]),
         "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
+        "qmmm_autotune": (c_int, [c_void_p, c_int]),
+        "qmmm_get_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_double), P(c_int)]),
+        "qmmm_set_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_double)]),
+        "qmmm_batch_create": (c_int, [P(c_void_p), c_int, c_void_p, P(c_void_p)]),
+        "qmmm_batch_run": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p),
+                                   P(c_void_p)]),
+        "qmmm_batch_timing": (c_int, [c_void_p, P(c_double)]),
+        "qmmm_batch_captures": (c_int, [c_void_p]),
+        "qmmm_batch_destroy": (None, [c_void_p]),
         "qmmm_destroy": (None, [c_void_p]),
         "qmmm_strerror": (ctypes.c_char_p, [c_int]),
         "qmmm_last_error": (ctypes.c_char_p, []),
@@ -253,6 +263,66 @@ def qmmm_last_timing(h):
     out = (c_double * 2)()
     load().qmmm_last_timing(h, out)
     return float(out[0]), float(out[1])
+
+
+QMMM_TUNE_V, QMMM_TUNE_FORCES, QMMM_TUNE_BOTH_PRECISIONS = 1, 2, 4
+SWEEP_KINDS = ("vpot_f64", "vpot_mixed", "vgrad_f64", "vgrad_mixed")
+CLASSES = ((0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2), (3, 0), (3, 1), (3, 2), (3, 3))
+
+
+def qmmm_autotune(h, flags=0):
+    _check(load().qmmm_autotune(h, int(flags)), "qmmm_autotune")
+
+
+def qmmm_get_tuning(h, kind):
+    """Sweep configuration of one kind (index into SWEEP_KINDS): tuned flag and, per angular class,
+    threads per block, SM share, the measured time alone (ms) and the wide block size (0: none)."""
+    th, sh, ms, wd = (c_int * 10)(), (c_int * 10)(), (c_double * 10)(), (c_int * 10)()
+    rc = load().qmmm_get_tuning(h, int(kind), th, sh, ms, wd)
+    _check(min(rc, 0), "qmmm_get_tuning")
+    return {"tuned": bool(rc), "threads": list(th), "share": list(sh), "ms": list(ms), "wide": list(wd)}
+
+
+def qmmm_set_tuning(h, kind, threads, weight=None):
+    th = (c_int * 10)(*[int(t) for t in threads])
+    w = (c_double * 10)(*[float(x) for x in weight]) if weight is not None else None
+    _check(load().qmmm_set_tuning(h, int(kind), th, w), "qmmm_set_tuning")
+
+
+def qmmm_batch_create(handles, stream=None):
+    arr = (c_void_p * len(handles))(*handles)
+    out = c_void_p()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(load().qmmm_batch_create(arr, len(handles), st, ctypes.byref(out)), "qmmm_batch_create")
+    return out.value
+
+
+def _ptr_array(xs, n):
+    if xs is None:
+        return None
+    return (c_void_p * n)(*[_ptr(x) for x in xs])
+
+
+def qmmm_batch_run(b, dm, V=None, E=None, dE_dRqm=None, dE_dRmm=None, dE_dq=None):
+    """dm and each output: a list with one DEVICE tensor (float64, contiguous) per frame, or None."""
+    n = len(dm)
+    _check(load().qmmm_batch_run(b, _ptr_array(dm, n), _ptr_array(V, n), _ptr_array(E, n), _ptr_array(dE_dRqm, n),
+                                 _ptr_array(dE_dRmm, n), _ptr_array(dE_dq, n)), "qmmm_batch_run")
+
+
+def qmmm_batch_timing(b, nframes):
+    out = (c_double * (nframes + 1))()
+    load().qmmm_batch_timing(b, out)
+    return float(out[0]), [float(x) for x in out[1:]]
+
+
+def qmmm_batch_captures(b):
+    return int(load().qmmm_batch_captures(b))
+
+
+def qmmm_batch_destroy(b):
+    if b:
+        load().qmmm_batch_destroy(b)
 
 
 def qmmm_destroy(h):

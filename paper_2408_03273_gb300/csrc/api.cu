@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "pp_tile.cuh"
 #include "qmmm_internal.h"
 
 using namespace qmmm;
@@ -149,9 +150,17 @@ struct qmmm_handle {
     std::vector<int> cls_off_I;
     bool V_valid = false;
     float t_sweep = 0.f, t_other = 0.f;
+    bool quiet = false;  // inside a batch graph capture: no host synchronisation, no timing events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t side[NCLASS] = {};   // one stream per angular class (concurrent class sweeps)
     cudaEvent_t fork = nullptr, join[NCLASS] = {};
+    // region-I sweep configuration per kernel kind (SweepKind) and angular class: SM-time weight
+    // per primitive pair (flop model, or measured by qmmm_autotune), block variant, measured time
+    double cls_cost[SW_NKIND][NCLASS] = {};
+    int cls_variant[SW_NKIND][NCLASS] = {};
+    double cls_ms[SW_NKIND][NCLASS] = {};
+    int tuned_mask = 0, tuned_nI = 0;
+    DBuf<double> tune_V, tune_dm, tune_gqm, tune_gchg;  // autotuner scratch
     EwaldBuf ew;
     int nblk_mm = 1;
 
@@ -251,6 +260,8 @@ namespace {
 
 constexpr int NPART = 256;
 
+void reset_tuning(qmmm_handle *h, int kind);
+
 int check_device_errors(qmmm_handle *h)
 {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -261,6 +272,27 @@ int check_device_errors(qmmm_handle *h)
         CUDA_TRY(cudaMemset(h->err.p, 0, sizeof(int)));
         if (e & DEVERR_TIMEOUT) return fail(QMMM_ERR_TIMEOUT, "a bounded device wait ran out");
         return fail(QMMM_ERR_CUDA, "device bounds check failed");
+    }
+    return QMMM_OK;
+}
+
+// Timing mark k of the current call (skipped while a batch graph is being captured).
+cudaError_t mark(qmmm_handle *h, int k) { return h->quiet ? cudaSuccess : cudaEventRecord(h->ev[k], h->stream); }
+
+// End of a call: wait for the device, check its error flag and read the `nmarks` timing marks
+// (3: sweep = mark 0..1, rest = 1..2; 2: everything = 0..1).  Inside a batch capture nothing
+// waits: the batch checks every frame after the graph has run.
+int finish(qmmm_handle *h, int nmarks)
+{
+    if (h->quiet) return QMMM_OK;
+    const int rc = check_device_errors(h);
+    if (rc) return rc;
+    if (nmarks == 3) {
+        cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+    } else if (nmarks == 2) {
+        h->t_sweep = 0.f;
+        cudaEventElapsedTime(&h->t_other, h->ev[0], h->ev[1]);
     }
     return QMMM_OK;
 }
@@ -325,6 +357,9 @@ int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, co
         CUDA_TRY(cudaMemcpyAsync(cnt.data() + 1, h->cls_count.p, h->ncls * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         h->nI = cnt[0];
+        // a tuned sweep configuration holds while region I keeps roughly its size
+        if (h->tuned_mask && 4 * (long long)std::abs(h->nI - h->tuned_nI) > h->tuned_nI)
+            for (int k = 0; k < SW_NKIND; ++k) reset_tuning(h, k);
         h->cls_off_I.assign(h->ncls + 1, 0);
         for (int c = 0; c < h->ncls; ++c) h->cls_off_I[c + 1] = h->cls_off_I[c] + cnt[1 + c];
         if (h->cls_off_I[h->ncls] != h->nI) return fail(QMMM_ERR_CUDA, "region-I class counts inconsistent");
@@ -346,13 +381,18 @@ int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, co
     return check_device_errors(h);
 }
 
-int chunk_size(const qmmm_handle *h, bool grad)
+bool kind_is_grad(int kind) { return kind == SW_VGRAD_F64 || kind == SW_VGRAD_F32; }
+bool kind_is_mixed(int kind) { return kind == SW_VPOT_F32 || kind == SW_VGRAD_F32; }
+
+// Region-I charges per sweep launch (what one block stages into shared memory).
+int chunk_for_kind(int kind)
 {
-    if (grad) return CHUNK_GRAD;
-    return h->precision == QMMM_MIXED ? CHUNK_F32 : CHUNK_F64;
+    if (kind_is_grad(kind)) return CHUNK_GRAD;
+    return kind_is_mixed(kind) ? CHUNK_F32 : CHUNK_F64;
 }
 
-// Work per (primitive pair, charge) of a class with L = l_A + l_B, for splitting the SMs.
+// Work per (primitive pair, charge) of a class with L = l_A + l_B: the flop model that splits the
+// SMs between the concurrent class sweeps until qmmm_autotune measures the real costs.
 double class_weight(int L, bool grad)
 {
     auto c4 = [](int n) { return n >= 4 ? (double)n * (n - 1) * (n - 2) * (n - 3) / 24.0 : 0.0; };
@@ -360,30 +400,200 @@ double class_weight(int L, bool grad)
     return grad ? 75 + 3 * L + 2 * c4(L + 5) + 14 * c3(L + 3) : 40 + 3 * L + 2 * c4(L + 4) + 2 * c3(L + 3);
 }
 
-// Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
-// forked from and joined back into the handle's stream, with a grid cap proportional to its
-// share of the work (so small classes do not leave most SMs idle while they run alone).
-template <typename F>
-int run_classes(qmmm_handle *h, bool grad, F launch)
+int sweep_kind(const qmmm_handle *h, bool grad)
 {
-    static const int Lc[NCLASS] = {0, 1, 2, 2, 3, 4, 3, 4, 5, 6};
-    double w[NCLASS], W = 0.0;
+    const bool mixed = h->precision == QMMM_MIXED;
+    return grad ? (mixed ? SW_VGRAD_F32 : SW_VGRAD_F64) : (mixed ? SW_VPOT_F32 : SW_VPOT_F64);
+}
+
+void reset_tuning(qmmm_handle *h, int kind)
+{
     for (int c = 0; c < NCLASS; ++c) {
-        w[c] = (double)(h->class_off[c + 1] - h->class_off[c]) * class_weight(Lc[c], grad);
-        W += w[c];
+        h->cls_cost[kind][c] = class_weight(la_of_class(c) + lb_of_class(c), kind_is_grad(kind));
+        h->cls_variant[kind][c] = 0;
+        h->cls_ms[kind][c] = 0.0;
     }
-    if (W <= 0.0) return QMMM_OK;
+    h->tuned_mask &= ~(1 << kind);
+}
+
+int variant_threads(int kind, int cls, int variant)
+{
+    const int w = sweep_wide_threads(kind, cls);
+    return (variant == 1 && w > 0) ? w : 256;
+}
+
+// Grid caps of the concurrent class sweeps: shares of the SMs in proportion to each class's
+// SM-time (primitive pairs x cost), but never more blocks than the class has warps' worth of
+// 32-pair tiles for; what a capped class cannot use goes to the others.  Returns false when no
+// class has work.
+bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share)
+{
+    double w[NCLASS], s[NCLASS];
+    int cap[NCLASS];
+    bool open[NCLASS];
+    int nopen = 0;
+    for (int c = 0; c < NCLASS; ++c) {
+        const int npp = h->class_off[c + 1] - h->class_off[c];
+        share[c] = 0;
+        open[c] = npp > 0;
+        if (!open[c]) continue;
+        const int nwarp = variant_threads(kind, c, variant[c]) / 32;
+        cap[c] = std::max(1, ((npp + 31) / 32 + nwarp - 1) / nwarp);
+        w[c] = npp * std::max(h->cls_cost[kind][c], 1e-30);
+        ++nopen;
+    }
+    if (!nopen) return false;
+    double left = h->nsm;
+    for (bool again = true; again;) {
+        again = false;
+        double W = 0.0;
+        for (int c = 0; c < NCLASS; ++c)
+            if (open[c]) W += w[c];
+        for (int c = 0; c < NCLASS; ++c) {
+            if (!open[c]) continue;
+            s[c] = W > 0.0 ? left * w[c] / W : 0.0;
+            if (s[c] >= cap[c]) {  // capped: fix it and share the rest again
+                share[c] = cap[c];
+                left -= cap[c];
+                open[c] = false;
+                again = true;
+                break;
+            }
+        }
+    }
+    for (int c = 0; c < NCLASS; ++c)
+        if (open[c]) share[c] = std::min(cap[c], std::max(1, (int)std::lround(s[c])));
+    return true;
+}
+
+// Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
+// forked from and joined back into the handle's stream, its grid capped at its share of the SMs
+// (so small classes do not leave most SMs idle while they run alone).
+template <typename F>
+int run_classes(qmmm_handle *h, int kind, F launch)
+{
+    int share[NCLASS];
+    if (!split_sms(h, kind, h->cls_variant[kind], share)) return QMMM_OK;
     CUDA_TRY(cudaEventRecord(h->fork, h->stream));
     for (int c = 0; c < NCLASS; ++c) {
         const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
         if (p1 <= p0) continue;
-        const int share = std::max(1, (int)std::lround(h->nsm * w[c] / W));
         CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
-        CUDA_TRY(launch(c, p0, p1, share, h->side[c]));
+        CUDA_TRY(launch(c, p0, p1, share[c], h->cls_variant[kind][c], h->side[c]));
         CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
     }
     for (int c = 0; c < NCLASS; ++c)
         if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join[c], 0));
+    return QMMM_OK;
+}
+
+// One class sweep of the given kind over region-I charges [c0, c1).
+cudaError_t launch_sweep(const qmmm_handle *h, int kind, int cls, int p0, int p1, int c0, int c1, int share,
+                         int variant, const double *ddm, double *V, double *gqm, double *gchg, cudaStream_t cs)
+{
+    const BasisDev b = h->basis();
+    const RegionDev r = h->region();
+    switch (kind) {
+    case SW_VPOT_F64:
+        return launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, V, h->err.p, share, variant, cs);
+    case SW_VPOT_F32:
+        return launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, V, h->err.p, share, variant, cs);
+    case SW_VGRAD_F64:
+        return launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, gqm, gchg, h->err.p, share, variant,
+                                cs);
+    case SW_VGRAD_F32:
+        return launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, gqm, gchg, h->err.p, share, variant,
+                                cs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Charges per autotuner timing run: the class kernels sweep every staged charge per pair, so
+// their times scale with the count; a few hundred keep tuning short and the ratios intact.
+constexpr int TUNE_CHARGES = 512;
+
+// Best of three timed runs after a warm-up, on the handle's stream.
+template <typename F>
+int time_best(qmmm_handle *h, cudaEvent_t e0, cudaEvent_t e1, F run, float *ms)
+{
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        CUDA_TRY(cudaEventRecord(e0, h->stream));
+        const int rc = run();
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(e1, h->stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) best = std::min(best, t);
+    }
+    *ms = best;
+    return check_device_errors(h);
+}
+
+// The class sweeps of one kind, alone (cls >= 0) or all concurrently (cls < 0), over the first
+// charges of region I, in the autotuner's scratch buffers.
+int tune_launch(qmmm_handle *h, int kind, int cls, int share, int variant)
+{
+    const int c1 = std::min(h->nI, std::min(chunk_for_kind(kind), TUNE_CHARGES));
+    auto one = [&](int c, int p0, int p1, int s, int v, cudaStream_t cs) {
+        return launch_sweep(h, kind, c, p0, p1, 0, c1, s, v, h->tune_dm.p, h->tune_V.p, h->tune_gqm.p, h->tune_gchg.p,
+                            cs);
+    };
+    if (cls < 0) return run_classes(h, kind, one);
+    CUDA_TRY(one(cls, h->class_off[cls], h->class_off[cls + 1], share, variant, h->stream));
+    return QMMM_OK;
+}
+
+// Tune one sweep kind: two rounds of timing every class alone, in each block variant, at its
+// current share; the SM-time (time x blocks) per primitive pair becomes the class's cost, which
+// sets the next shares.  The result is kept only if the concurrent sweep beats the model's.
+int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
+{
+    reset_tuning(h, kind);
+    int share[NCLASS];
+    if (!split_sms(h, kind, h->cls_variant[kind], share)) return QMMM_OK;
+    int rc;
+    float t_model = 0.f, t_tuned = 0.f;
+    if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, -1, 0, 0); }, &t_model))) return rc;
+    double ms[NCLASS] = {};
+    for (int round = 0; round < 2; ++round) {
+        split_sms(h, kind, h->cls_variant[kind], share);
+        double cost[NCLASS];
+        int var[NCLASS];
+        for (int c = 0; c < NCLASS; ++c) {
+            cost[c] = h->cls_cost[kind][c];
+            var[c] = h->cls_variant[kind][c];
+            const int npp = h->class_off[c + 1] - h->class_off[c];
+            if (npp <= 0) continue;
+            double best = 1e300;
+            const int nvar = sweep_wide_threads(kind, c) > 0 ? 2 : 1;
+            for (int v = 0; v < nvar; ++v) {
+                float t = 0.f;
+                if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, c, share[c], v); }, &t))) return rc;
+                const int nwarp = variant_threads(kind, c, v) / 32;
+                const int blocks = std::min(share[c], ((npp + 31) / 32 + nwarp - 1) / nwarp);
+                const double smt = (double)t * blocks;
+                if (smt < best) {
+                    best = smt;
+                    var[c] = v;
+                    ms[c] = t;
+                }
+            }
+            cost[c] = best / npp;
+        }
+        for (int c = 0; c < NCLASS; ++c) {
+            h->cls_cost[kind][c] = cost[c];
+            h->cls_variant[kind][c] = var[c];
+        }
+    }
+    if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, -1, 0, 0); }, &t_tuned))) return rc;
+    if (t_tuned < t_model) {
+        for (int c = 0; c < NCLASS; ++c) h->cls_ms[kind][c] = ms[c];
+        h->tuned_mask |= 1 << kind;
+    } else {
+        reset_tuning(h, kind);
+    }
     return QMMM_OK;
 }
 
@@ -686,11 +896,12 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         // Ewald buffers
         EwaldDev e = h->ewald();
         const int nd = ewald_dense_size(e);
-        h->ew.sf_nslice = ewald_sf_nslice(e, h->nsm);
+        h->ew.sf_nslice = ewald_sf_nslice(e, h->nsm, false);
+        h->ew.sf_nslice_df = ewald_sf_nslice(e, h->nsm, true);
         h->ew.real_nslice = ewald_real_nslice(e, h->nsm);
         if ((rc = h->gfac.ensure(nd)) || (rc = h->S.ensure(nd)) || (rc = h->A.ensure(nd)) || (rc = h->Az.ensure(nd)) ||
             (rc = h->Adf.ensure(nd)) || (rc = h->Azdf.ensure(nd)) ||
-            (rc = h->Spart.ensure((size_t)nd * h->ew.sf_nslice)) ||
+            (rc = h->Spart.ensure((size_t)nd * std::max(h->ew.sf_nslice, h->ew.sf_nslice_df))) ||
             (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
             return rc;
         h->ew.gfac = h->gfac.p;
@@ -711,6 +922,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
             CUDA_TRY(cudaEventCreateWithFlags(&h->join[c], cudaEventDisableTiming));
         }
     }
+    for (int k = 0; k < SW_NKIND; ++k) reset_tuning(h, k);
     // initial geometry
     std::vector<double> qm0 = h->qm_xyz;
     int rc = run_positions(h, qm0.data(), nmm ? ux.data() : nullptr, nmm ? uq.data() : nullptr);
@@ -748,29 +960,23 @@ int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
     int rc;
     if ((rc = h->V.ensure((size_t)h->nao * h->nao))) return rc;
     CUDA_TRY(cudaMemsetAsync(h->V.p, 0, (size_t)h->nao * h->nao * sizeof(double), st));
-    const BasisDev b = h->basis();
-    const RegionDev r = h->region();
-    const int ch = chunk_size(h, false);
-    CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    const int kind = sweep_kind(h, false), ch = chunk_for_kind(kind);
+    CUDA_TRY(mark(h, 0));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
-        rc = run_classes(h, false, [&](int cls, int p0, int p1, int share, cudaStream_t cs) {
-            return h->precision == QMMM_MIXED
-                       ? launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, h->V.p, h->err.p, share, cs)
-                       : launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, h->V.p, h->err.p, share, cs);
+        rc = run_classes(h, kind, [&](int cls, int p0, int p1, int share, int variant, cudaStream_t cs) {
+            return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nullptr, h->V.p, nullptr, nullptr, cs);
         });
         if (rc) return rc;
     }
-    CUDA_TRY(cudaEventRecord(h->ev[1], st));
+    CUDA_TRY(mark(h, 1));
     CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
                            nullptr, 0, st));
     CUDA_TRY(launch_sum(h->Epart.p, enucmm_nblk(h->nI), h->out4.p + 4, st));
     if ((rc = copy_out(h, Vout, h->V.p, (size_t)h->nao * h->nao))) return rc;
     if ((rc = copy_out(h, E_nuc_mm, h->out4.p + 4, 1))) return rc;
-    CUDA_TRY(cudaEventRecord(h->ev[2], st));
-    if ((rc = check_device_errors(h))) return rc;
-    cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+    CUDA_TRY(mark(h, 2));
+    if ((rc = finish(h, 3))) return rc;
     h->V_valid = true;
     return QMMM_OK;
 }
@@ -796,7 +1002,7 @@ int qmmm_ewald(qmmm_handle *h, const double *dmat, double *E_II, double *multipo
     int rc;
     const double *ddm;
     const size_t n2 = (size_t)h->nao * h->nao;
-    CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    CUDA_TRY(mark(h, 0));
     if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
     double *Fd = nullptr;
     if (F_II) {
@@ -810,10 +1016,8 @@ int qmmm_ewald(qmmm_handle *h, const double *dmat, double *E_II, double *multipo
     if ((rc = copy_out(h, E_II, h->out4.p + 3, 1))) return rc;
     if ((rc = copy_out(h, multipoles, h->mult.p, 10 * (size_t)h->natm))) return rc;
     if (F_II && (rc = copy_out(h, F_II, h->F.p, n2))) return rc;
-    CUDA_TRY(cudaEventRecord(h->ev[1], st));
-    if ((rc = check_device_errors(h))) return rc;
-    h->t_sweep = 0.f;
-    cudaEventElapsedTime(&h->t_other, h->ev[0], h->ev[1]);
+    CUDA_TRY(mark(h, 1));
+    if ((rc = finish(h, 2))) return rc;
     return QMMM_OK;
 }
 
@@ -830,7 +1034,7 @@ int qmmm_energy(qmmm_handle *h, const double *dmat, double *E)
     CUDA_TRY(launch_energy_terms(ddm, h->V.p, h->nao, 1, h->mult.p, h->phi.p, h->natm, h->Epart.p,
                                  enucmm_nblk(h->nI), h->partials.p, NPART, h->out4.p, st));
     if ((rc = copy_out(h, E, h->out4.p, 4))) return rc;
-    return check_device_errors(h);
+    return finish(h, 0);
 }
 
 int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_dRmm, double *dE_dq)
@@ -848,22 +1052,16 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
     // multipoles and the Pulay term
     if ((rc = compute_multipoles(h, ddm, nullptr, MOM_PULAY))) return rc;
     // region-I adjoint sweep
-    const BasisDev b = h->basis();
-    const RegionDev r = h->region();
-    const int ch = chunk_size(h, true);
-    CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    const int kind = sweep_kind(h, true), ch = chunk_for_kind(kind);
+    CUDA_TRY(mark(h, 0));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
-        rc = run_classes(h, true, [&](int cls, int p0, int p1, int share, cudaStream_t cs) {
-            return h->precision == QMMM_MIXED
-                       ? launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
-                                          share, cs)
-                       : launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, h->gqm.p, h->gchg.p, h->err.p,
-                                          share, cs);
+        rc = run_classes(h, kind, [&](int cls, int p0, int p1, int share, int variant, cudaStream_t cs) {
+            return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, ddm, nullptr, h->gqm.p, h->gchg.p, cs);
         });
         if (rc) return rc;
     }
-    CUDA_TRY(cudaEventRecord(h->ev[1], st));
+    CUDA_TRY(mark(h, 1));
     // nuclear-MM region I, multipolar Ewald (MM side + QM tensor part), scatter to MM atoms
     CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, h->gqm.p,
                            h->gchg.p, 1, st));
@@ -882,10 +1080,8 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
         if ((rc = copy_out(h, dE_dRmm, h->dR_out.p, 3 * (size_t)h->nmm))) return rc;
         if ((rc = copy_out(h, dE_dq, h->dq_out.p, (size_t)h->nmm))) return rc;
     }
-    CUDA_TRY(cudaEventRecord(h->ev[2], st));
-    if ((rc = check_device_errors(h))) return rc;
-    cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+    CUDA_TRY(mark(h, 2));
+    if ((rc = finish(h, 3))) return rc;
     return QMMM_OK;
 }
 
@@ -920,6 +1116,79 @@ int qmmm_get_potential(qmmm_handle *h, double *v)
     return check_device_errors(h);
 }
 
+int qmmm_autotune(qmmm_handle *h, int flags)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    if (flags & ~(QMMM_TUNE_V | QMMM_TUNE_FORCES | QMMM_TUNE_BOTH_PRECISIONS))
+        return fail(QMMM_ERR_ARG, "unknown autotune flags");
+    int which = flags & (QMMM_TUNE_V | QMMM_TUNE_FORCES);
+    if (!which) which = QMMM_TUNE_V | QMMM_TUNE_FORCES;
+    int kinds[SW_NKIND], nk = 0;
+    for (int k = 0; k < SW_NKIND; ++k) {
+        const bool grad = kind_is_grad(k), mixed = kind_is_mixed(k);
+        if (!(which & (grad ? QMMM_TUNE_FORCES : QMMM_TUNE_V))) continue;
+        if (!(flags & QMMM_TUNE_BOTH_PRECISIONS) && mixed != (h->precision == QMMM_MIXED)) continue;
+        kinds[nk++] = k;
+    }
+    if (h->nI == 0 || h->n_pp == 0) return QMMM_OK;
+    const size_t n2 = (size_t)h->nao * h->nao;
+    const int nch = std::min(h->nI, TUNE_CHARGES);
+    int rc;
+    if ((rc = h->tune_V.ensure(n2)) || (rc = h->tune_dm.ensure(n2)) || (rc = h->tune_gqm.ensure(3 * (size_t)h->natm)) ||
+        (rc = h->tune_gchg.ensure(4 * (size_t)nch)))
+        return rc;
+    // a zero density: the sweeps' work does not depend on its values
+    CUDA_TRY(cudaMemsetAsync(h->tune_dm.p, 0, n2 * sizeof(double), h->stream));
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    CUDA_TRY(cudaEventCreate(&e[0]));
+    if (cudaEventCreate(&e[1]) != cudaSuccess) {
+        cudaEventDestroy(e[0]);
+        return fail(QMMM_ERR_CUDA, "cudaEventCreate");
+    }
+    for (int i = 0; i < nk && !rc; ++i) rc = tune_kind(h, kinds[i], e[0], e[1]);
+    cudaEventDestroy(e[0]);
+    cudaEventDestroy(e[1]);
+    if (rc) return rc;
+    h->tuned_nI = h->nI;
+    return QMMM_OK;
+}
+
+int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, double *ms, int *wide)
+{
+    if (!h || kind < 0 || kind >= SW_NKIND) return fail(QMMM_ERR_ARG, "null handle or unknown sweep kind");
+    int sh[NCLASS];
+    if (!split_sms(h, kind, h->cls_variant[kind], sh))
+        for (int c = 0; c < NCLASS; ++c) sh[c] = 0;
+    for (int c = 0; c < NCLASS; ++c) {
+        if (threads) threads[c] = variant_threads(kind, c, h->cls_variant[kind][c]);
+        if (share) share[c] = sh[c];
+        if (ms) ms[c] = h->cls_ms[kind][c];
+        if (wide) wide[c] = sweep_wide_threads(kind, c);
+    }
+    return (h->tuned_mask >> kind) & 1;
+}
+
+int qmmm_set_tuning(qmmm_handle *h, int kind, const int *threads, const double *weight)
+{
+    if (!h || kind < 0 || kind >= SW_NKIND || !threads) return fail(QMMM_ERR_ARG, "null argument or unknown kind");
+    int var[NCLASS];
+    for (int c = 0; c < NCLASS; ++c) {
+        const int w = sweep_wide_threads(kind, c);
+        if (threads[c] == 256) var[c] = 0;
+        else if (w > 0 && threads[c] == w) var[c] = 1;
+        else return fail(QMMM_ERR_ARG, "block size " + std::to_string(threads[c]) + " not available for class " +
+                                           std::to_string(c));
+        if (weight && !(weight[c] > 0.0)) return fail(QMMM_ERR_ARG, "weights must be positive");
+    }
+    reset_tuning(h, kind);
+    for (int c = 0; c < NCLASS; ++c) {
+        h->cls_variant[kind][c] = var[c];
+        if (weight) h->cls_cost[kind][c] = weight[c];
+    }
+    h->tuned_nI = h->nI;
+    return QMMM_OK;
+}
+
 int qmmm_last_timing(const qmmm_handle *h, double *out)
 {
     if (!h || !out) return fail(QMMM_ERR_ARG, "null argument");
@@ -929,5 +1198,207 @@ int qmmm_last_timing(const qmmm_handle *h, double *out)
 }
 
 void qmmm_destroy(qmmm_handle *h) { delete h; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batches of frames: one CUDA graph over every frame's V, energy and gradient
+// ---------------------------------------------------------------------------------------------
+struct qmmm_batch {
+    std::vector<qmmm_handle *> f;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;        // created here: the legacy stream cannot be captured
+    std::vector<cudaStream_t> fst;  // one stream per frame
+    std::vector<cudaEvent_t> done;  // frame f complete (recorded by the graph, for timing)
+    std::vector<cudaEvent_t> join;  // frame f joins the batch stream
+    cudaEvent_t start = nullptr, fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> key;  // what the graph was recorded for
+    int captures = 0;
+    std::vector<double> ms;  // last run: total, then per frame
+    ~qmmm_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t e : done)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : join)
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t s : fst)
+            if (s) cudaStreamDestroy(s);
+        if (start) cudaEventDestroy(start);
+        if (fork) cudaEventDestroy(fork);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+// Everything a recorded batch graph depends on: per frame its region-I size, precision, sweep
+// configuration and the arrays it reads and writes.
+std::vector<long long> batch_key(const qmmm_batch *b, const double *const *dm, double *const *V, double *const *E,
+                                 double *const *gq, double *const *gm, double *const *gc)
+{
+    std::vector<long long> k;
+    auto ptr = [](const void *p) { return (long long)(uintptr_t)p; };
+    for (size_t i = 0; i < b->f.size(); ++i) {
+        const qmmm_handle *h = b->f[i];
+        k.push_back(h->nI);
+        k.push_back(h->precision);
+        for (int kind = 0; kind < SW_NKIND; ++kind)
+            for (int c = 0; c < NCLASS; ++c) {
+                long long bits;
+                std::memcpy(&bits, &h->cls_cost[kind][c], sizeof(bits));
+                k.push_back(bits);
+                k.push_back(h->cls_variant[kind][c]);
+            }
+        k.push_back(ptr(dm[i]));
+        k.push_back(ptr(V ? V[i] : nullptr));
+        k.push_back(ptr(E ? E[i] : nullptr));
+        k.push_back(ptr(gq ? gq[i] : nullptr));
+        k.push_back(ptr(gm ? gm[i] : nullptr));
+        k.push_back(ptr(gc ? gc[i] : nullptr));
+    }
+    return k;
+}
+
+// One frame's work through the public calls, on the handle's current stream.
+int batch_frame(qmmm_handle *h, const double *dm, double *V, double *E, double *gq, double *gm, double *gc)
+{
+    int rc;
+    if ((rc = qmmm_vpot(h, V, nullptr))) return rc;
+    if (E && (rc = qmmm_energy(h, dm, E))) return rc;
+    return qmmm_forces(h, dm, gq, gm, gc);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmmm_batch_create(qmmm_handle *const *frames, int nframes, void *stream, qmmm_batch **out)
+{
+    if (!out || !frames || nframes <= 0) return fail(QMMM_ERR_ARG, "null argument or no frames");
+    *out = nullptr;
+    std::unique_ptr<qmmm_batch> b(new qmmm_batch());
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    for (int i = 0; i < nframes; ++i) {
+        if (!frames[i]) return fail(QMMM_ERR_ARG, "null frame handle");
+        for (int j = 0; j < i; ++j)
+            if (frames[j] == frames[i]) return fail(QMMM_ERR_ARG, "a handle appears twice in the batch");
+        b->f.push_back(frames[i]);
+    }
+    b->fst.assign(nframes, nullptr);
+    b->done.assign(nframes, nullptr);
+    b->join.assign(nframes, nullptr);
+    CUDA_TRY(cudaEventCreate(&b->start));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    for (int i = 0; i < nframes; ++i) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->fst[i], cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreate(&b->done[i]));
+        CUDA_TRY(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+    }
+    b->ms.assign(nframes + 1, 0.0);
+    *out = b.release();
+    return QMMM_OK;
+}
+
+int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, double *const *E,
+                   double *const *dE_dRqm, double *const *dE_dRmm, double *const *dE_dq)
+{
+    if (!b || !dm) return fail(QMMM_ERR_ARG, "null batch or density array");
+    const int n = (int)b->f.size();
+    auto at = [](double *const *a, int i) { return a ? a[i] : nullptr; };
+    for (int i = 0; i < n; ++i) {
+        if (!dm[i] || !is_device_ptr(dm[i])) return fail(QMMM_ERR_ARG, "every density must be device memory");
+        const void *o[5] = {at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i)};
+        for (const void *p : o)
+            if (p && !is_device_ptr(p)) return fail(QMMM_ERR_ARG, "batch outputs must be device memory");
+    }
+    std::vector<cudaStream_t> own(n);
+    for (int i = 0; i < n; ++i) own[i] = b->f[i]->stream;
+    auto restore = [&] {
+        for (int i = 0; i < n; ++i) {
+            b->f[i]->stream = own[i];
+            b->f[i]->quiet = false;
+        }
+    };
+    int rc = QMMM_OK;
+    std::vector<long long> key = batch_key(b, dm, V, E, dE_dRqm, dE_dRmm, dE_dq);
+    if (!b->exec || key != b->key) {
+        // plain pass: sizes every buffer and sets every kernel attribute before recording
+        for (int i = 0; i < n && !rc; ++i) {
+            b->f[i]->stream = b->fst[i];
+            rc = batch_frame(b->f[i], dm[i], at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
+        }
+        if (rc) {
+            restore();
+            return rc;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->start, b->stream, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+        for (int i = 0; i < n && e == cudaSuccess && !rc; ++i) {
+            qmmm_handle *h = b->f[i];
+            if ((e = cudaStreamWaitEvent(b->fst[i], b->fork, 0)) != cudaSuccess) break;
+            h->quiet = true;
+            rc = batch_frame(h, dm[i], at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
+            h->quiet = false;
+            if (rc) break;
+            if ((e = cudaEventRecordWithFlags(b->done[i], b->fst[i], cudaEventRecordExternal)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(b->join[i], b->fst[i])) != cudaSuccess) break;
+            e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+        }
+        // always end the capture, so the stream leaves capture mode even after a failure
+        const cudaError_t e_end = cudaStreamEndCapture(b->stream, &graph);
+        restore();
+        if (rc || e != cudaSuccess || e_end != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (rc) return rc;
+            return fail(QMMM_ERR_CUDA, std::string("batch graph capture: ") +
+                                           cudaGetErrorString(e != cudaSuccess ? e : e_end));
+        }
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return fail(QMMM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+        b->key = key;
+        ++b->captures;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, b->start, b->done[i]));
+        b->ms[1 + i] = t;
+        total = std::max(total, (double)t);
+        if ((rc = check_device_errors(b->f[i]))) return rc;
+        b->f[i]->V_valid = true;
+    }
+    b->ms[0] = total;
+    return QMMM_OK;
+}
+
+int qmmm_batch_timing(const qmmm_batch *b, double *ms)
+{
+    if (!b || !ms) return fail(QMMM_ERR_ARG, "null argument");
+    for (size_t i = 0; i < b->ms.size(); ++i) ms[i] = b->ms[i];
+    return (int)b->ms.size();
+}
+
+int qmmm_batch_captures(const qmmm_batch *b) { return b ? b->captures : fail(QMMM_ERR_ARG, "null batch"); }
+
+void qmmm_batch_destroy(qmmm_batch *b) { delete b; }
 
 }  // extern "C"

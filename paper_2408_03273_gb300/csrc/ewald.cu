@@ -301,7 +301,8 @@ __global__ void __launch_bounds__(256) k_structure_factor(EwaldDev e, double2 *p
     double2 *pz = py + tile * NY;                            // [tile][NZP]
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = item < NL * NZC;
-    const int line = active ? item / NZC : 0, zc = active ? item % NZC : 0;
+    // z chunk outermost: the threads of a warp share zc, so their z-phase reads are broadcasts
+    const int line = active ? item % NL : 0, zc = active ? item / NL : 0;
     const int nx = line / NY, iy = line % NY, iz0 = zc * SF_NZ;
     double2 acc[SF_NZ];
 #pragma unroll
@@ -365,17 +366,18 @@ __global__ void __launch_bounds__(256) k_structure_factor(EwaldDev e, double2 *p
 // multiply-add of about 48 FP32 operations instead of 4 FP64 FMAs (~47-bit accuracy per term).
 __device__ __forceinline__ void phase_row_df(float4 *dst, double frac, int nmax, double scale)
 {
+    // start and step in FP64 (one sincospi), the recurrence itself in double-float arithmetic
     double s, c;
     sincospi(2.0 * frac, &s, &c);
-    const double2 e1 = make_double2(c, s);
-    double2 z = make_double2(1.0, 0.0);
+    const c2 e1{f2_from(c), f2_from(s)};
+    c2 z{f2_from(scale), f2{0.f, 0.f}};
     for (int n = 0; n <= nmax; ++n) {
-        dst[n] = c2_pack(scale * z.x, scale * z.y);
-        z = cmul(z, e1);
+        dst[n] = make_float4(z.re.h, z.re.l, z.im.h, z.im.l);
+        z = c2_mul(z, e1);
     }
 }
 
-__global__ void __launch_bounds__(256) k_structure_factor_df(EwaldDev e, double2 *partial, int tile)
+__global__ void __launch_bounds__(256, 3) k_structure_factor_df(EwaldDev e, double2 *partial, int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
@@ -388,7 +390,8 @@ __global__ void __launch_bounds__(256) k_structure_factor_df(EwaldDev e, double2
     float4 *pz = py + tile * NY;                          // [tile][NZP]
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = item < NL * NZC;
-    const int line = active ? item / NZC : 0, zc = active ? item % NZC : 0;
+    // z chunk outermost: the threads of a warp share zc, so their z-phase reads are broadcasts
+    const int line = active ? item % NL : 0, zc = active ? item / NL : 0;
     const int nx = line / NY, iy = line % NY, iz0 = zc * SF_NZ;
     float acc[SF_NZ][4];
 #pragma unroll
@@ -531,14 +534,13 @@ static size_t sf_smem(const EwaldDev &e, int *tile_out)
 
 // Charge slices of the structure factor: the grid (line blocks x slices) is sized to one full
 // wave of resident blocks, so no partial last wave leaves most SMs idle.
-int ewald_sf_nslice(const EwaldDev &e, int nsm)
+int ewald_sf_nslice(const EwaldDev &e, int nsm, bool df)
 {
     const size_t smem = sf_smem(e, nullptr);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_structure_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *fn = df ? (const void *)k_structure_factor_df : (const void *)k_structure_factor;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_structure_factor, 256, smem) != cudaSuccess ||
-        per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -626,14 +628,15 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
                 return err;
             a = smem;
         }
-        dim3 grid((sf_items(e) + 255) / 256, w.sf_nslice);
+        const int nslice = df ? w.sf_nslice_df : w.sf_nslice;
+        dim3 grid((sf_items(e) + 255) / 256, nslice);
         if (df)
             k_structure_factor_df<<<grid, 256, smem, st>>>(e, w.Spart, tile);
         else
             k_structure_factor<<<grid, 256, smem, st>>>(e, w.Spart, tile);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         const int n = ewald_dense_size(e);
-        k_sum_slices<<<(n + 255) / 256, 256, 0, st>>>(w.Spart, w.sf_nslice, n, w.S);
+        k_sum_slices<<<(n + 255) / 256, 256, 0, st>>>(w.Spart, nslice, n, w.S);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     // reciprocal part at the QM sites into phi (temporarily), then the final combination
@@ -888,14 +891,14 @@ __global__ void __launch_bounds__(MMR_THREADS) k_mm_recip_df(EwaldDev e, const f
     sincospi(-2.0 * fy, &s, &c);
     const c2 ey1{f2_from(c), f2_from(s)};
     sincospi(-2.0 * fz, &s, &c);
-    const double2 ez1 = make_double2(c, s);
+    const c2 ez1{f2_from(c), f2_from(s)};
     sincospi(2.0 * ky * fy, &s, &c);
     const c2 ey0{f2_from(c), f2_from(s)};
     sincospi(2.0 * kz * fz, &s, &c);
-    double2 pz = make_double2(c, s);
+    c2 pz{f2_from(c), f2_from(s)};
     for (int iz = 0; iz < NZ; ++iz) {
-        zs[(size_t)iz * MMR_THREADS + t] = c2_pack(pz.x, pz.y);
-        pz = cmul(pz, ez1);
+        zs[(size_t)iz * MMR_THREADS + t] = make_float4(pz.re.h, pz.re.l, pz.im.h, pz.im.l);
+        pz = c2_mul(pz, ez1);
     }
     __syncthreads();
     f2 pot{0.f, 0.f}, f1{0.f, 0.f}, f2z{0.f, 0.f};
@@ -908,15 +911,28 @@ __global__ void __launch_bounds__(MMR_THREADS) k_mm_recip_df(EwaldDev e, const f
             if (nx > 0 || iy >= ky) {
                 const float4 *Ar = A + ((size_t)nx * NY + iy) * NZ;
                 const float4 *Azr = Az + ((size_t)nx * NY + iy) * NZ;
+                // two independent accumulator sets (even / odd n_z) for instruction-level parallelism
                 float B[4] = {0.f, 0.f, 0.f, 0.f}, Bz[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int iz = 0; iz < NZ; ++iz) {
-                    const c2 z = c2_from(zs[(size_t)iz * MMR_THREADS + t]);
-                    c2_mac(B, c2_from(__ldg(Ar + iz)), z);
-                    c2_mac(Bz, c2_from(__ldg(Azr + iz)), z);
+                float C[4] = {0.f, 0.f, 0.f, 0.f}, Cz[4] = {0.f, 0.f, 0.f, 0.f};
+                int iz = 0;
+                for (; iz + 1 < NZ; iz += 2) {
+                    const c2 z0 = c2_from(zs[(size_t)iz * MMR_THREADS + t]);
+                    const c2 z1 = c2_from(zs[(size_t)(iz + 1) * MMR_THREADS + t]);
+                    c2_mac(B, c2_from(__ldg(Ar + iz)), z0);
+                    c2_mac(C, c2_from(__ldg(Ar + iz + 1)), z1);
+                    c2_mac(Bz, c2_from(__ldg(Azr + iz)), z0);
+                    c2_mac(Cz, c2_from(__ldg(Azr + iz + 1)), z1);
+                }
+                if (iz < NZ) {
+                    const c2 z0 = c2_from(zs[(size_t)iz * MMR_THREADS + t]);
+                    c2_mac(B, c2_from(__ldg(Ar + iz)), z0);
+                    c2_mac(Bz, c2_from(__ldg(Azr + iz)), z0);
                 }
                 const c2 pxy = c2_mul(px, py);
-                const c2 b{f2_add(f2{B[0], 0.f}, f2{B[1], 0.f}), f2_add(f2{B[2], 0.f}, f2{B[3], 0.f})};
-                const f2 bzr = f2_add(f2{Bz[0], 0.f}, f2{Bz[1], 0.f}), bzi = f2_add(f2{Bz[2], 0.f}, f2{Bz[3], 0.f});
+                const c2 b{f2_add(f2_add(f2{B[0], 0.f}, f2{B[1], 0.f}), f2_add(f2{C[0], 0.f}, f2{C[1], 0.f})),
+                           f2_add(f2_add(f2{B[2], 0.f}, f2{B[3], 0.f}), f2_add(f2{C[2], 0.f}, f2{C[3], 0.f}))};
+                const f2 bzr = f2_add(f2_add(f2{Bz[0], 0.f}, f2{Bz[1], 0.f}), f2_add(f2{Cz[0], 0.f}, f2{Cz[1], 0.f}));
+                const f2 bzi = f2_add(f2_add(f2{Bz[2], 0.f}, f2{Bz[3], 0.f}), f2_add(f2{Cz[2], 0.f}, f2{Cz[3], 0.f}));
                 const c2 pr = c2_mul(pxy, b);
                 const f2 imz = f2_add(f2_mul(pxy.re, bzi), f2_mul(pxy.im, bzr));
                 pot = f2_add(pot, pr.re);
@@ -1001,14 +1017,18 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
 // ---------------------------------------------------------------------------------------------
 // region-I nuclear-MM term  sum_j Z_j q_C erf(r/sigma_C)/r  (1/r for point charges)
 // ---------------------------------------------------------------------------------------------
-int enucmm_nblk(int nI) { return nI > 0 ? (nI + 255) / 256 : 1; }
+// Block = 32 charges x 8 warps; warp w takes the QM atoms j = w, w + 8, ...  Per-charge values
+// are summed over the 8 warps in shared memory in a fixed order, so E and dE/dq are reproducible.
+constexpr int ENUC_CH = 32, ENUC_WARPS = 8;
+int enucmm_nblk(int nI) { return nI > 0 ? (nI + ENUC_CH - 1) / ENUC_CH : 1; }
 
-__global__ void __launch_bounds__(256) k_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI,
-                                                const int *rI_idx, int nI, const double *mm_beta, double *Epart,
-                                                double *gqm, double *gchg, int want_grad)
+__global__ void __launch_bounds__(ENUC_CH * ENUC_WARPS)
+k_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI, const int *rI_idx, int nI,
+         const double *mm_beta, double *Epart, double *gqm, double *gchg, int want_grad)
 {
-    __shared__ double ws[8];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double red[5][ENUC_WARPS][ENUC_CH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * ENUC_CH + lane;
     const bool act = k < nI;
     double4_32a c;
     c.x = c.y = c.z = c.w = 0.0;
@@ -1018,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_enucmm(const double *qm_xyz, const doub
         beta = mm_beta[rI_idx[k]];
     }
     double E = 0.0, dq = 0.0, dC[3] = {0.0, 0.0, 0.0};
-    for (int j = 0; j < natm; ++j) {
+    for (int j = warp; j < natm; j += ENUC_WARPS) {
         double g[3] = {0.0, 0.0, 0.0};
         if (act) {
             const double x = qm_xyz[3 * j] - c.x, y = qm_xyz[3 * j + 1] - c.y, z = qm_xyz[3 * j + 2] - c.z;
@@ -1042,23 +1062,29 @@ __global__ void __launch_bounds__(256) k_enucmm(const double *qm_xyz, const doub
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
                 const double v = warp_sum(g[x]);
-                if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(gqm + 3 * j + x, v);
+                if (lane == 0 && v != 0.0) atomicAdd(gqm + 3 * j + x, v);
             }
         }
     }
-    if (want_grad && act) {
-        gchg[4 * (size_t)k + 0] += dC[0];
-        gchg[4 * (size_t)k + 1] += dC[1];
-        gchg[4 * (size_t)k + 2] += dC[2];
-        gchg[4 * (size_t)k + 3] += dq;
-    }
-    E = warp_sum(E);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = E;
+    red[0][warp][lane] = E;
+    red[1][warp][lane] = dq;
+    red[2][warp][lane] = dC[0];
+    red[3][warp][lane] = dC[1];
+    red[4][warp][lane] = dC[2];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        Epart[blockIdx.x] = t;
+    if (warp == 0) {
+        double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < ENUC_WARPS; ++w)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) t[v] += red[v][w][lane];
+        if (want_grad && act) {
+            gchg[4 * (size_t)k + 0] += t[2];
+            gchg[4 * (size_t)k + 1] += t[3];
+            gchg[4 * (size_t)k + 2] += t[4];
+            gchg[4 * (size_t)k + 3] += t[1];
+        }
+        const double e = warp_sum(t[0]);
+        if (lane == 0) Epart[blockIdx.x] = e;
     }
 }
 
@@ -1066,7 +1092,8 @@ cudaError_t launch_enucmm(const double *qm_xyz, const double *Z, int natm, const
                           int nI, const double *mm_beta, double *Epart, double *gqm, double *gchg, int want_grad,
                           cudaStream_t st)
 {
-    k_enucmm<<<enucmm_nblk(nI), 256, 0, st>>>(qm_xyz, Z, natm, rI, rI_idx, nI, mm_beta, Epart, gqm, gchg, want_grad);
+    k_enucmm<<<enucmm_nblk(nI), ENUC_CH * ENUC_WARPS, 0, st>>>(qm_xyz, Z, natm, rI, rI_idx, nI, mm_beta, Epart, gqm,
+                                                               gchg, want_grad);
     return cudaGetLastError();
 }
 

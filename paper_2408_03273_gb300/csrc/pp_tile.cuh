@@ -59,6 +59,27 @@ __host__ __device__ constexpr int la_of_class(int c)
 __host__ __device__ constexpr int lb_of_class(int c) { return c - la_of_class(c) * (la_of_class(c) + 1) / 2; }
 static_assert(la_of_class(class_of(3, 2)) == 3 && lb_of_class(class_of(3, 2)) == 2, "class index inverse");
 
+// The four region-I sweep kernels.
+enum SweepKind { SW_VPOT_F64 = 0, SW_VPOT_F32 = 1, SW_VGRAD_F64 = 2, SW_VGRAD_F32 = 3, SW_NKIND = 4 };
+
+// Threads per block of the wide variant of a sweep kernel (0: none).  All warps of a block share
+// one staged chunk of charges, and that chunk's shared memory allows one block per SM, so the
+// block size sets the warps per SM.  A block of NT threads launched with __launch_bounds__(NT, 1)
+// may use 65536 / NT registers per thread, rounded down to a multiple of 8; NT is the widest block
+// whose cap stays at or above the kernel's register count at 256 threads, so the wide variant
+// holds more warps per SM without spilling.  Classes at 255 registers have no wide variant.
+__host__ __device__ constexpr int sweep_wide_threads(int kind, int cls)
+{
+    // class order: (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) (3,0) (3,1) (3,2) (3,3)
+    constexpr int T[SW_NKIND][10] = {
+        {1024, 640, 512, 640, 384, 384, 512, 0, 0, 0},  // vpot_f64 : 64 87 105 96 150 158 120 regs
+        {896, 768, 512, 512, 384, 0, 384, 0, 0, 0},     // vpot_f32 : 68 80 106 102 154 - 136
+        {640, 512, 0, 0, 0, 0, 0, 0, 0, 0},             // vgrad_f64: 93 117
+        {768, 640, 384, 384, 0, 0, 0, 0, 0, 0},         // vgrad_f32: 80 96 168 148
+    };
+    return (kind >= 0 && kind < SW_NKIND && cls >= 0 && cls < 10) ? T[kind][cls] : 0;
+}
+
 // Class-split compilation.  A sweep source (vpot_*.cu, vgrad_*.cu) is compiled once per angular
 // class with -DQMMM_SPLIT_CLASS=<class index>, which defines that class's kernel and explicitly
 // instantiates its launcher, and once without, which compiles only the runtime dispatcher below;

@@ -44,18 +44,21 @@ struct RegionDev {
 struct qmmm_handle_impl;
 
 // launchers (defined in the .cu files); all return a cudaError_t of the last launch
+// Region-I sweeps.  `nsm` caps the grid (the class's share of the SMs); `variant` picks the block
+// shape: 0 = 256 threads, 1 = the class's wide block (sweep_wide_threads), where one exists.
 cudaError_t launch_vpot_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
-                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm,
+                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
                             cudaStream_t st);
 cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
-                            int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm,
+                            int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
                             cudaStream_t st);
 cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
-                             double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, cudaStream_t st);
+                             double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, int variant,
+                             cudaStream_t st);
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, cudaStream_t st);
+                             double *gchg, int *err, int nsm, int variant, cudaStream_t st);
 
 // moments / multipoles / Fock / Pulay (mode bits below)
 enum { MOM_MULT = 1, MOM_FOCK = 2, MOM_PULAY = 4 };
@@ -91,7 +94,8 @@ struct EwaldBuf {
     double *gfac = nullptr;      // dense (kx+1)(2ky+1)(2kz+1): 2 g(G) on the half space, else 0
     double2 *S = nullptr;        // dense MM structure factor
     double2 *Spart = nullptr;    // per-slice partial structure factors
-    int sf_nslice = 1;
+    int sf_nslice = 1;     // charge slices of the FP64 structure-factor grid
+    int sf_nslice_df = 1;  // the same for the double-float kernel
     double *preal = nullptr;     // natm * real_nslice * 20
     int real_nslice = 1;
     double *pr1 = nullptr;       // natm * 20
@@ -102,7 +106,7 @@ struct EwaldBuf {
     double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
 };
 int ewald_dense_size(const EwaldDev &e);
-int ewald_sf_nslice(const EwaldDev &e, int nsm);
+int ewald_sf_nslice(const EwaldDev &e, int nsm, bool df);
 int ewald_real_nslice(const EwaldDev &e, int nsm);
 cudaError_t launch_gfac(const EwaldDev &e, double *gfac, cudaStream_t st);
 // v_j,c (natm*20) at the current geometry

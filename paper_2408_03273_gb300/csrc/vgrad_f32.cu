@@ -14,15 +14,16 @@ template <int LA, int LB>
 struct VgradF32 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                            int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, cudaStream_t st);
+                           int nsm, int variant,
+                           cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
 constexpr int GFOLD = 16;
 
-template <int LA, int LB>
-__global__ void __launch_bounds__(256, 1)
+template <int LA, int LB, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
             const float *__restrict__ boys_g, unsigned boys_bytes, const double *__restrict__ dm,
             double *__restrict__ gqm, double *__restrict__ gchg, int *err)
@@ -236,28 +237,41 @@ inline unsigned boys32_bytes_g()
     return (unsigned)(((BOYS_NROW_F * BOYS_NCOL_F + 3) / 4) * 4 * sizeof(float));
 }
 
-template <int LA, int LB>
-cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                                  int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                                  int nsm, cudaStream_t st)
+template <int LA, int LB, int NT>
+static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                             int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
+                             int nsm, cudaStream_t st)
 {
     const unsigned tb = boys32_bytes_g();
     const size_t per = 2 * sizeof(float4) + 4 * sizeof(double);
     const size_t smem = (size_t)(ch_end - ch_begin) * per + tb;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(CHUNK_GRAD * per + tb));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntile = (pp_end - pp_begin + 31) / 32;
-    int grid = (ntile + 7) / 8;
+    int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vgrad_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, dm, gqm,
+    k_vgrad_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, dm, gqm,
                                                  gchg, err);
     return cudaGetLastError();
+}
+
+template <int LA, int LB>
+cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                  int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
+                                  int nsm, int variant,
+                                  cudaStream_t st)
+{
+    constexpr int W = sweep_wide_threads(SW_VGRAD_F32, class_of(LA, LB));
+    if constexpr (W > 0)
+        if (variant == 1)
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
 }
 
 template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -266,11 +280,11 @@ template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_C
 
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, cudaStream_t st)
+                             double *gchg, int *err, int nsm, int variant, cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VgradF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                    st);
+                                    variant, st);
 }
 
 #endif

@@ -19,13 +19,14 @@ template <int LA, int LB>
 struct VgradF64 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                            int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, cudaStream_t st);
+                           int nsm, int variant,
+                           cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
-template <int LA, int LB>
-__global__ void __launch_bounds__(256, 1)
+template <int LA, int LB, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
             const double *__restrict__ boys, const double *__restrict__ dm, double *__restrict__ gqm,
             double *__restrict__ gchg, int *err)
@@ -178,26 +179,39 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     }
 }
 
-template <int LA, int LB>
-cudaError_t VgradF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                                  int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
-                                  int nsm, cudaStream_t st)
+template <int LA, int LB, int NT>
+static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                             int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
+                             int nsm, cudaStream_t st)
 {
     const size_t smem = (size_t)(ch_end - ch_begin) * (sizeof(double4_32a) + 4 * sizeof(double));
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(CHUNK_GRAD * (sizeof(double4_32a) + 4 * sizeof(double))));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntile = (pp_end - pp_begin + 31) / 32;
-    int grid = (ntile + 7) / 8;
+    int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vgrad_f64<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm,
+    k_vgrad_f64<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm,
                                                  gchg, err);
     return cudaGetLastError();
+}
+
+template <int LA, int LB>
+cudaError_t VgradF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                  int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
+                                  int nsm, int variant,
+                                  cudaStream_t st)
+{
+    constexpr int W = sweep_wide_threads(SW_VGRAD_F64, class_of(LA, LB));
+    if constexpr (W > 0)
+        if (variant == 1)
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
 }
 
 template struct VgradF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -206,11 +220,11 @@ template struct VgradF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_C
 
 cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, cudaStream_t st)
+                             double *gchg, int *err, int nsm, int variant, cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VgradF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                    st);
+                                    variant, st);
 }
 
 #endif

@@ -16,15 +16,16 @@ namespace qmmm {
 template <int LA, int LB>
 struct VpotF32 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st);
+                           int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
+                           cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
 constexpr int FOLD = 16;
 
-template <int LA, int LB>
-__global__ void __launch_bounds__(256, 1)
+template <int LA, int LB, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
            const float *__restrict__ boys_g, unsigned boys_bytes, double *__restrict__ V, int *err)
 {
@@ -138,25 +139,37 @@ inline unsigned boys32_bytes()
     return (unsigned)(((BOYS_NROW_F * BOYS_NCOL_F + 3) / 4) * 4 * sizeof(float));
 }
 
-template <int LA, int LB>
-cudaError_t VpotF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                                 int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st)
+template <int LA, int LB, int NT>
+static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                             int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st)
 {
     const unsigned tb = boys32_bytes();
     const size_t smem = (size_t)(ch_end - ch_begin) * 2 * sizeof(float4) + tb;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(CHUNK_F32 * 2 * sizeof(float4) + tb));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntile = (pp_end - pp_begin + 31) / 32;
-    int grid = (ntile + 7) / 8;
+    int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vpot_f32<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, V, err);
+    k_vpot_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, V, err);
     return cudaGetLastError();
+}
+
+template <int LA, int LB>
+cudaError_t VpotF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                 int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
+                                 cudaStream_t st)
+{
+    constexpr int W = sweep_wide_threads(SW_VPOT_F32, class_of(LA, LB));
+    if constexpr (W > 0)
+        if (variant == 1)
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
 }
 
 template struct VpotF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -164,11 +177,11 @@ template struct VpotF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CL
 #else  // the dispatcher
 
 cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
-                            int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm,
+                            int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
                             cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
-    return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+    return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant, st);
 }
 
 #endif

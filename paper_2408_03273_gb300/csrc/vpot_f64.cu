@@ -19,13 +19,14 @@ namespace qmmm {
 template <int LA, int LB>
 struct VpotF64 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const double *boys, double *V, int *err, int nsm, cudaStream_t st);
+                           int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
+                           cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
-template <int LA, int LB>
-__global__ void __launch_bounds__(256, 1)
+template <int LA, int LB, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_vpot_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
            const double *__restrict__ boys, double *__restrict__ V, int *err)
 {
@@ -106,24 +107,36 @@ k_vpot_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
     }
 }
 
-template <int LA, int LB>
-cudaError_t VpotF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                                 int ch_end, const double *boys, double *V, int *err, int nsm, cudaStream_t st)
+template <int LA, int LB, int NT>
+static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                             int ch_end, const double *boys, double *V, int *err, int nsm, cudaStream_t st)
 {
     const size_t smem = (size_t)(ch_end - ch_begin) * sizeof(double4_32a);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_vpot_f64<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_vpot_f64<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(CHUNK_F64 * sizeof(double4_32a)));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntile = (pp_end - pp_begin + 31) / 32;
-    int grid = (ntile + 7) / 8;
+    int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vpot_f64<LA, LB><<<grid, 256, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err);
+    k_vpot_f64<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err);
     return cudaGetLastError();
+}
+
+template <int LA, int LB>
+cudaError_t VpotF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                                 int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
+                                 cudaStream_t st)
+{
+    constexpr int W = sweep_wide_threads(SW_VPOT_F64, class_of(LA, LB));
+    if constexpr (W > 0)
+        if (variant == 1)
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
 }
 
 template struct VpotF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -131,11 +144,11 @@ template struct VpotF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CL
 #else  // the dispatcher
 
 cudaError_t launch_vpot_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
-                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm,
+                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
                             cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
-    return dispatch_class<VpotF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+    return dispatch_class<VpotF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant, st);
 }
 
 #endif

@@ -49,6 +49,18 @@ class Handle:
     def potential(self, like=None):
         return L.qmmm_get_potential(self.h, like=like)
 
+    def autotune(self, flags: int = 0):
+        """Time the region-I class sweeps on this geometry and keep the fastest block shapes and SM
+        split (flags: QMMM_TUNE_V / QMMM_TUNE_FORCES / QMMM_TUNE_BOTH_PRECISIONS; 0 = V and forces
+        at the current precision)."""
+        L.qmmm_autotune(self.h, flags)
+
+    def tuning(self, kind: int):
+        return L.qmmm_get_tuning(self.h, kind)
+
+    def set_tuning(self, kind: int, threads, weight=None):
+        L.qmmm_set_tuning(self.h, kind, threads, weight)
+
     def last_timing(self):
         return L.qmmm_last_timing(self.h)
 
@@ -56,6 +68,36 @@ class Handle:
         if self.h:
             L.qmmm_destroy(self.h)
             self.h = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several frames (Handles) evaluated together through one recorded CUDA graph: per frame V,
+    E[4] and the gradient at that frame's density (see qmmm_batch_run)."""
+
+    def __init__(self, handles, stream=None):
+        self.handles = list(handles)  # kept alive: the batch borrows the library handles
+        self.b = L.qmmm_batch_create([h.h for h in self.handles], stream)
+
+    def run(self, dm, V=None, E=None, dE_dRqm=None, dE_dRmm=None, dE_dq=None):
+        L.qmmm_batch_run(self.b, dm, V, E, dE_dRqm, dE_dRmm, dE_dq)
+
+    def timing(self):
+        """(ms of the last run, [ms at which each frame finished])."""
+        return L.qmmm_batch_timing(self.b, len(self.handles))
+
+    def captures(self):
+        return L.qmmm_batch_captures(self.b)
+
+    def close(self):
+        if self.b:
+            L.qmmm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):  # pragma: no cover - interpreter shutdown order
         try:

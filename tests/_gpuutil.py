@@ -34,11 +34,14 @@ def grad_err(got, ref, key, mixed):
     return float(np.max(np.abs(np.asarray(got) - ref[key]))) / max(scale, 1e-300)
 
 
-def gpu_all(s, precision=0, screen_tol=-1.0):
-    """Run the whole path through the C ABI on host arrays; returns a dict like the oracle's."""
+def gpu_all(s, precision=0, screen_tol=-1.0, setup=None):
+    """Run the whole path through the C ABI on host arrays; returns a dict like the oracle's.
+    setup(handle), if given, runs right after the handle is created (e.g. a sweep configuration)."""
     import paper_2408_03273_gb300 as q
     h = q.Handle(s, precision=precision, screen_tol=screen_tol)
     try:
+        if setup is not None:
+            setup(h)
         V, En = h.vpot()
         E = h.energy(s.dm)
         EII, M, F = h.ewald(s.dm, want_F=True)
