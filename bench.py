@@ -13,7 +13,8 @@ Default workload: 60 QM atoms (600 shells, 1560 AOs), 59463 MM charges (TIP3P wa
 box, cutoff 12 A, alpha 0.3 A^-1, kmax 16 (synthetic, seeded).  Inputs are smaller than L2 so the
 L2 is flushed (256 MiB write) before every timed step, outside the timed interval.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c1|c2|c4]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c1|c2|c4|c5]
+(c5: 64 uneven frames through the batch API, one CUDA graph, against a loop of FP64 calls)
 N > 1 runs replicas (one per GPU, launched by torch.distributed.run): the path does not shard.
 """
 from __future__ import annotations
@@ -181,13 +182,111 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, q, torch, dev):
+    """Frames workload: 64 uneven frames (QM water clusters of 20-120 atoms, 20k-120k MM charges at
+    water density), mixed-precision V + energy + gradient per frame through one recorded CUDA
+    graph (qmmm_batch_run), against a loop of plain FP64 calls over the same frames."""
+    import workloads
+    frames = workloads.config5_frames(args.frames)
+    n = len(frames)
+    hs = [q.Handle(s, precision=q.QMMM_MIXED) for s in frames]
+    # tune the largest frame; its measured class weights and block shapes serve every frame
+    work = [h.info["n_prim_pairs"] * h.info["n_region1"] for h in hs]
+    big = int(np.argmax(work))
+    if not args.no_autotune:
+        hs[big].autotune()
+        for k in (1, 3):
+            t = hs[big].tuning(k)
+            for i, h in enumerate(hs):
+                if i != big:
+                    h.set_tuning(k, t["threads"], t["weight"])
+    units = [h.info["n_shell_pairs"] * h.info["n_region1"] for h in hs]
+    total_units = int(sum(units))
+    dm = [torch.as_tensor(np.ascontiguousarray(s.dm), device=dev) for s in frames]
+    z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=dev)  # noqa: E731
+    V = [z(s.nao, s.nao) for s in frames]
+    E = [z(4) for _ in frames]
+    gq = [z(s.natm, 3) for s in frames]
+    gm = [z(s.nmm, 3) for s in frames]
+    gc = [z(s.nmm) for s in frames]
+    stream = torch.cuda.Stream()
+    b = q.Batch(hs, stream)
+    for _ in range(args.warmup):
+        b.run(dm, V, E, gq, gm, gc)
+    runs, lat = [], []
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(args.steps):
+            b.run(dm, V, E, gq, gm, gc)
+            tot, per = b.timing()
+            runs.append(tot)
+            lat += per
+    ms = float(np.mean(runs))
+    captures = b.captures()
+    b.close()
+
+    # the same frames through a loop of plain calls (one call at a time, synchronised per call)
+    def plain_loop(prec, keep=False):
+        out = []
+        hh = [q.Handle(s, precision=prec) for s in frames] if prec != q.QMMM_MIXED else hs
+        for h in hh:
+            h.set_stream(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, h in enumerate(hh):
+            Vp, _ = h.vpot(like=dm[i])
+            Ep = h.energy(dm[i])
+            g = h.forces(dm[i])
+            if keep:
+                out.append((Vp, Ep, g))
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) * 1e3
+        if prec != q.QMMM_MIXED:
+            for h in hh:
+                h.close()
+        return t, out
+
+    ms_mixed_loop, _ = plain_loop(q.QMMM_MIXED)
+    ms_f64_loop, ref = plain_loop(q.QMMM_FP64, keep=True)
+    # errors of the batched mixed results against the FP64 loop
+    fro = max(float(torch.linalg.norm(V[i] - ref[i][0]) / torch.linalg.norm(ref[i][0])) for i in range(n))
+    gerr = 0.0
+    for i in range(n):
+        for a_, r_ in ((gq[i], ref[i][2][0]), (gm[i], ref[i][2][1]), (gc[i], ref[i][2][2])):
+            gerr = max(gerr, float((a_ - r_).abs().max() / r_.abs().max()))
+    eerr = max(float(abs(E[i][0] - ref[i][1][0]) / (ref[i][1][1].abs() + ref[i][1][2].abs() + ref[i][1][3].abs()))
+               for i in range(n))
+    for h in hs:
+        h.close()
+    lat = np.asarray(lat)
+    value = total_units / (ms * 1e-3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic (seeded TIP3P water boxes + QM water clusters per frame)",
+           "config": {"workload": f"frames_c5: {n} frames, QM {min(s.natm for s in frames)}-"
+                                  f"{max(s.natm for s in frames)} atoms, {min(s.nmm for s in frames)}-"
+                                  f"{max(s.nmm for s in frames)} MM charges, cutoff 12 A, alpha 0.3 A^-1",
+                      "precision": "mixed", "units_per_step": total_units,
+                      "l2": "inputs of all frames exceed L2 (129 MB)",
+                      "graph": f"one CUDA graph per batch ({captures} recording(s))",
+                      "sweep_schedule": "autotuned on the largest frame" if not args.no_autotune else "flop model"},
+           "batched": {"ms_per_batch": ms, "frame_latency_ms_p50": float(np.percentile(lat, 50)),
+                       "frame_latency_ms_p99": float(np.percentile(lat, 99)),
+                       "fp64_loop_ms": ms_f64_loop, "fp64_loop_value": total_units / (ms_f64_loop * 1e-3),
+                       "speedup_vs_fp64_loop": ms_f64_loop / ms, "mixed_loop_ms": ms_mixed_loop,
+                       "rel_fro_err_V_max_frame": fro, "max_rel_err_forces": gerr, "max_rel_err_E": eerr},
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4", "c5"])
+    ap.add_argument("--frames", type=int, default=64, help="frames of the c5 (batched) workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
@@ -210,6 +309,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     args.warmup = max(3, args.warmup)
+    if args.config == "c5":
+        return run_batched(args, q, torch, dev)
 
     s = make_system(args.config)
     prec = q.QMMM_MIXED if args.precision == "mixed" else q.QMMM_FP64

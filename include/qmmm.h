@@ -177,9 +177,13 @@ int qmmm_autotune(qmmm_handle *h, int flags);
  * 3 adjoint mixed), per angular class in the order (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) (3,0)
  * (3,1) (3,2) (3,3): threads[10] per block, share[10] = grid cap (SMs; 0 for an empty class),
  * ms[10] = the class's measured time alone at that share (0 if not measured), wide[10] = the
- * class's wide block size (0: it has only 256-thread blocks).  Any array may be NULL.  Returns 1
- * if the kind was tuned, 0 if it runs the model configuration, <0 on error. */
-int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, double *ms, int *wide);
+ * class's wide block size (0: it has only 256-thread blocks), weight[10] = the SM-time per
+ * primitive pair that sets the shares (ms x blocks / pairs when tuned, the flop model if not;
+ * qmmm_set_tuning accepts it back, e.g. to share one frame's tuning with similar frames).  Any
+ * array may be NULL.  Returns 1 if the kind was tuned, 0 if it runs the model configuration, <0
+ * on error. */
+int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, double *ms, int *wide,
+                    double *weight);
 
 /* Install a sweep configuration (e.g. one saved from qmmm_get_tuning on an earlier run of the
  * same system): threads[10] per class must be 256 or that class's wide block size (the values

@@ -93,7 +93,7 @@ def load(build_if_needed: bool = True):
         "qmmm_get_potential": (c_int, [c_void_p, c_void_p]),
         "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
         "qmmm_autotune": (c_int, [c_void_p, c_int]),
-        "qmmm_get_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_double), P(c_int)]),
+        "qmmm_get_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_double), P(c_int), P(c_double)]),
         "qmmm_set_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_double)]),
         "qmmm_batch_create": (c_int, [P(c_void_p), c_int, c_void_p, P(c_void_p)]),
         "qmmm_batch_run": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p),
@@ -276,11 +276,13 @@ def qmmm_autotune(h, flags=0):
 
 def qmmm_get_tuning(h, kind):
     """Sweep configuration of one kind (index into SWEEP_KINDS): tuned flag and, per angular class,
-    threads per block, SM share, the measured time alone (ms) and the wide block size (0: none)."""
-    th, sh, ms, wd = (c_int * 10)(), (c_int * 10)(), (c_double * 10)(), (c_int * 10)()
-    rc = load().qmmm_get_tuning(h, int(kind), th, sh, ms, wd)
+    threads per block, SM share, the measured time alone (ms), the wide block size (0: none) and the
+    SM-time weight per primitive pair (accepted back by qmmm_set_tuning)."""
+    th, sh, ms, wd, wt = (c_int * 10)(), (c_int * 10)(), (c_double * 10)(), (c_int * 10)(), (c_double * 10)()
+    rc = load().qmmm_get_tuning(h, int(kind), th, sh, ms, wd, wt)
     _check(min(rc, 0), "qmmm_get_tuning")
-    return {"tuned": bool(rc), "threads": list(th), "share": list(sh), "ms": list(ms), "wide": list(wd)}
+    return {"tuned": bool(rc), "threads": list(th), "share": list(sh), "ms": list(ms), "wide": list(wd),
+            "weight": list(wt)}
 
 
 def qmmm_set_tuning(h, kind, threads, weight=None):

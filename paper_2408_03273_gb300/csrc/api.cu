@@ -174,6 +174,7 @@ struct qmmm_handle {
     DBuf<double> dcls_kappa, gfac, preal, pr1, sums, phi, boys64, V, dm, F, mult, mult_init, gqm, gchg, dq_int,
         dR_int, dq_out, dR_out, Epart, partials, out4;
     DBuf<float> boys32;
+    DBuf<double> centre_d;  // [3] QM centre for the kernels
     DBuf<double2> S, Spart, A, Az;
     DBuf<float4> Adf, Azdf;
     DBuf<int> err;
@@ -204,7 +205,7 @@ struct qmmm_handle {
         r.cls_kappa = dcls_kappa.p;
         r.ncls = ncls;
         r.n = nI;
-        for (int x = 0; x < 3; ++x) r.centre[x] = centre[x];
+        r.centre = centre_d.p;
         return r;
     }
     EwaldDev ewald() const
@@ -336,6 +337,11 @@ int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, co
         double c = 0.0;
         for (int j = 0; j < h->natm; ++j) c += h->qm_xyz[3 * j + x];
         h->centre[x] = c / h->natm;
+    }
+    {
+        int rc;
+        if ((rc = h->centre_d.ensure(3))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(h->centre_d.p, h->centre, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     // MM positions/charges: user order -> internal order
     if (h->nmm > 0 && (mm_xyz || mm_q)) {
@@ -1153,7 +1159,8 @@ int qmmm_autotune(qmmm_handle *h, int flags)
     return QMMM_OK;
 }
 
-int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, double *ms, int *wide)
+int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, double *ms, int *wide,
+                    double *weight)
 {
     if (!h || kind < 0 || kind >= SW_NKIND) return fail(QMMM_ERR_ARG, "null handle or unknown sweep kind");
     int sh[NCLASS];
@@ -1164,6 +1171,7 @@ int qmmm_get_tuning(const qmmm_handle *h, int kind, int *threads, int *share, do
         if (share) share[c] = sh[c];
         if (ms) ms[c] = h->cls_ms[kind][c];
         if (wide) wide[c] = sweep_wide_threads(kind, c);
+        if (weight) weight[c] = h->cls_cost[kind][c];
     }
     return (h->tuned_mask >> kind) & 1;
 }

@@ -38,7 +38,8 @@ struct RegionDev {
     const double *cls_kappa;    // [ncls] exponent 1/sigma^2 (<= 0: point charge)
     int ncls;
     int n;
-    double centre[3];
+    const double *centre;       // [3] the QM centre, in device memory (read at run time, so a
+                                // recorded graph sees the current geometry)
 };
 
 struct qmmm_handle_impl;

@@ -4,6 +4,21 @@ import numpy as np
 # tolerances: the FP64 path against the FP64 oracle, and the mixed-precision path
 TOL_FP64 = 1e-10
 TOL_MIXED = 1e-6
+# Mixed path, V element by element (relative to max |V|).  The mixed V is held to TOL_MIXED in
+# the relative Frobenius norm; single elements are not: every per-charge term is an FP32 number,
+# and the terms of a region-I sum cancel 20-40 fold (neutral waters), so rounding each term once
+# to FP32 already leaves 2-5e-7 of max |V| in the s-s elements (CPU emulation with exact F_0), and
+# the Hermite recursion adds a small factor for f functions.
+TOL_MIXED_ELEM = 3e-6
+
+
+def check_V(got, ref, precision):
+    """V parity: FP64 element by element; mixed in the Frobenius norm plus the element bound."""
+    if precision == 0:
+        assert rel_max(got, ref) < TOL_FP64
+    else:
+        assert rel_fro(got, ref) < TOL_MIXED
+        assert rel_max(got, ref) < TOL_MIXED_ELEM
 
 
 def rel_max(got, ref):

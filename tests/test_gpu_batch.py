@@ -1,0 +1,107 @@
+"""Batches of frames through one recorded CUDA graph (qmmm_batch_*): every frame's V, energy and
+gradient against the same handle's plain calls, graph replay without re-recording, a position
+update between runs, and the argument checks."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _frames():
+    return [workloads.small_system(seed=120 + i, n_atoms=2 + i, lmax=2, nprim=(1, 3), n_waters=10 + 6 * i)
+            for i in range(3)]
+
+
+def _plain(h, s, dm):
+    V, _ = h.vpot()
+    E = h.energy(dm)
+    gq, gm, gc = h.forces(dm)
+    return {"V": V, "E": np.asarray(E), "gq": gq, "gm": gm, "gc": gc}
+
+
+def _dev_outputs(torch, frames):
+    dev = torch.device("cuda")
+    z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=dev)  # noqa: E731
+    return ([z(s.nao, s.nao) for s in frames], [z(4) for s in frames], [z(s.natm, 3) for s in frames],
+            [z(s.nmm, 3) for s in frames], [z(s.nmm) for s in frames])
+
+
+def _close(a, b, tol):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b))) <= tol * max(float(np.max(np.abs(b))), 1e-300)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_plain_calls_and_replays(precision):
+    torch = pytest.importorskip("torch")
+    import paper_2408_03273_gb300 as q
+    frames = _frames()
+    hs = [q.Handle(s, precision=precision) for s in frames]
+    try:
+        ref = [_plain(h, s, s.dm) for h, s in zip(hs, frames)]
+        dev = torch.device("cuda")
+        dm = [torch.as_tensor(s.dm, device=dev) for s in frames]
+        V, E, gq, gm, gc = _dev_outputs(torch, frames)
+        b = q.Batch(hs)
+        try:
+            tol = 1e-12 if precision == 0 else 1e-7  # same kernels; only atomic addition order differs
+            for rep in range(2):
+                b.run(dm, V, E, gq, gm, gc)
+                assert b.captures() == 1
+                for i in range(len(frames)):
+                    assert _close(V[i].cpu(), ref[i]["V"], tol), (rep, i)
+                    assert _close(E[i].cpu(), ref[i]["E"], tol), (rep, i)
+                    for k, out in (("gq", gq), ("gm", gm), ("gc", gc)):
+                        assert _close(out[i].cpu(), ref[i][k], tol), (rep, i, k)
+            total, per = b.timing()
+            assert total > 0 and len(per) == len(frames) and max(per) == pytest.approx(total)
+            # new positions for frame 0 (a small shift keeps its region-I size): the graph replays
+            s0 = frames[0]
+            qm = s0.atom_xyz + 0.01
+            n_before = hs[0].info["n_region1"]
+            hs[0].set_positions(qm, s0.mm_xyz)
+            same_size = hs[0].info["n_region1"] == n_before
+            b.run(dm, V, E, gq, gm, gc)
+            h_ref = q.Handle(s0, precision=precision)
+            try:
+                h_ref.set_positions(qm, s0.mm_xyz)
+                r0 = _plain(h_ref, s0, s0.dm)
+            finally:
+                h_ref.close()
+            assert b.captures() == (1 if same_size else 2)
+            assert _close(V[0].cpu(), r0["V"], tol)
+            assert _close(gq[0].cpu(), r0["gq"], tol)
+            # a different output array is a different graph
+            V2 = [v.clone() for v in V]
+            b.run(dm, V2, E, gq, gm, gc)
+            assert b.captures() == (2 if same_size else 3)
+            assert _close(V2[0].cpu(), r0["V"], tol)
+        finally:
+            b.close()
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_batch_rejects_host_memory():
+    torch = pytest.importorskip("torch")
+    import paper_2408_03273_gb300 as q
+    frames = _frames()[:2]
+    hs = [q.Handle(s) for s in frames]
+    try:
+        b = q.Batch(hs)
+        try:
+            with pytest.raises(q.QMMMError):
+                b.run([s.dm for s in frames])  # host densities
+            dm = [torch.as_tensor(s.dm, device="cuda") for s in frames]
+            with pytest.raises(q.QMMMError):
+                b.run(dm, V=[np.zeros((s.nao, s.nao)) for s in frames])  # host outputs
+        finally:
+            b.close()
+        with pytest.raises(q.QMMMError):
+            q.Batch([hs[0], hs[0]])  # a handle twice
+    finally:
+        for h in hs:
+            h.close()
