@@ -783,175 +783,235 @@ __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *
 }
 
 // dq_i += sum_G Re[A(G) exp(-iG.R_i)],  dR_i += q_i sum_G G Im[A(G) exp(-iG.R_i)].
-// One thread per MM charge.  exp(-iG.R) = X(n_x) Y(n_y) Z(n_z): each thread keeps its Z row in
-// shared memory (structure of arrays, so a warp reads consecutive words), and for every
-// (n_x, n_y) line forms the two complex sums B = sum_nz A Z and Bz = sum_nz Az Z (8 FMA per G),
-// then applies X(n_x) Y(n_y) once per line.  X and Y advance by recurrence.
-constexpr int MMR_THREADS = 128;
+// exp(-iG.R) = X(n_x) Y(n_y) Z(n_z).  A block takes 32 MM charges (one per lane) and its 8 warps
+// share the half-space (n_x, n_y) lines round-robin: for each line a warp stages the line's A and
+// Az rows in shared memory, forms B = sum_nz A Z and Bz = sum_nz Az Z per lane (Z rows of the
+// block's charges in shared memory, one row per lane), then applies X(n_x) Y(n_y) from per-charge
+// phase tables.  The 8 warps' partial sums are added in a fixed order at the end.  Small blocks
+// (32 charges) make a grid of many waves, so the last one leaves little of the GPU idle.
+constexpr int MMR_CH = 32, MMR_WARPS = 8, MMR_SEG = 8;
 
-__global__ void __launch_bounds__(MMR_THREADS) k_mm_recip(EwaldDev e, const double2 *__restrict__ A,
-                                                          const double2 *__restrict__ Az, double *dq, double *dR)
+// shared memory of one block: phase tables Z[NZ][32], X[NX][32], Y[NY][32] (16 B entries), the
+// per-warp A/Az line buffers [8][2][NZ] (16 B) and the reduction area [8 values][8 warps][32]
+// (4 B, double-float) / [4][8][32] (8 B, FP64) -- 8 KiB either way.
+size_t mm_recip_smem(const EwaldDev &e)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
-    const int NY = 2 * ky + 1, NZ = 2 * kz + 1;
-    double *zre = reinterpret_cast<double *>(smem_raw);   // [NZ][MMR_THREADS]
-    double *zim = zre + (size_t)NZ * MMR_THREADS;          // [NZ][MMR_THREADS]
-    const int t = threadIdx.x;
-    const int i = blockIdx.x * blockDim.x + t;
-    const bool act = i < e.nmm;
-    const int ii = act ? i : 0;
-    const double fx = e.mm_xyz[3 * ii] / e.box[0], fy = e.mm_xyz[3 * ii + 1] / e.box[1],
-                 fz = e.mm_xyz[3 * ii + 2] / e.box[2];
-    double s, c;
-    sincospi(-2.0 * fx, &s, &c);
-    const double2 ex1 = make_double2(c, s);
-    sincospi(-2.0 * fy, &s, &c);
-    const double2 ey1 = make_double2(c, s);
-    sincospi(-2.0 * fz, &s, &c);
-    const double2 ez1 = make_double2(c, s);
-    sincospi(2.0 * ky * fy, &s, &c);
-    const double2 ey0 = make_double2(c, s);   // n_y = -ky
-    sincospi(2.0 * kz * fz, &s, &c);
-    double2 pz = make_double2(c, s);          // n_z = -kz
-    for (int iz = 0; iz < NZ; ++iz) {
-        zre[(size_t)iz * MMR_THREADS + t] = pz.x;
-        zim[(size_t)iz * MMR_THREADS + t] = pz.y;
-        pz = cmul(pz, ez1);
-    }
-    double pot = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
-    double2 px = make_double2(1.0, 0.0);
-    for (int nx = 0; nx <= kx; ++nx) {
-        double2 py = ey0;
-        const double Gx = TWO_PI * nx / e.box[0];
-        for (int iy = 0; iy < NY; ++iy) {
-            // lines with n_x = 0 and n_y < 0 lie outside the half space (their A is zero)
-            if (nx > 0 || iy >= ky) {
-                const double2 *Ar = A + ((size_t)nx * NY + iy) * NZ;
-                const double2 *Azr = Az + ((size_t)nx * NY + iy) * NZ;
-                double br = 0.0, bi = 0.0, bzr = 0.0, bzi = 0.0;
-                for (int iz = 0; iz < NZ; ++iz) {
-                    const double2 a = __ldg(Ar + iz), az = __ldg(Azr + iz);
-                    const double pr = zre[(size_t)iz * MMR_THREADS + t], pi = zim[(size_t)iz * MMR_THREADS + t];
-                    br = fma(a.x, pr, br);
-                    br = fma(-a.y, pi, br);
-                    bi = fma(a.x, pi, bi);
-                    bi = fma(a.y, pr, bi);
-                    bzr = fma(az.x, pr, bzr);
-                    bzr = fma(-az.y, pi, bzr);
-                    bzi = fma(az.x, pi, bzi);
-                    bzi = fma(az.y, pr, bzi);
-                }
-                const double2 pxy = cmul(px, py);
-                const double re = pxy.x * br - pxy.y * bi;
-                const double im = pxy.x * bi + pxy.y * br;
-                const double imz = pxy.x * bzi + pxy.y * bzr;
-                const double Gy = TWO_PI * (iy - ky) / e.box[1];
-                pot += re;
-                f0 += Gx * im;
-                f1 += Gy * im;
-                f2 += imz;
-            }
-            py = cmul(py, ey1);
-        }
-        px = cmul(px, ex1);
-    }
-    if (!act) return;
-    const double q = e.mm_q[i];
-    dq[i] += pot;
-    dR[3 * i] += q * f0;
-    dR[3 * i + 1] += q * f1;
-    dR[3 * i + 2] += q * f2;
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    return (size_t)(NZ + NX + NY) * MMR_CH * 16 + (size_t)MMR_WARPS * 2 * NZ * 16 + 8 * MMR_WARPS * MMR_CH * 4;
 }
 
-// Double-float variant of k_mm_recip (mixed-precision path): Z rows, A and Az as FP32 (hi, lo)
-// pairs; the two complex dot products per line are error-free multiply-adds, the per-line
-// combination and the X, Y recurrences run in double-float arithmetic.
-__global__ void __launch_bounds__(MMR_THREADS) k_mm_recip_df(EwaldDev e, const float4 *__restrict__ A,
-                                                             const float4 *__restrict__ Az, double *dq, double *dR)
+// line index -> (n_x, row of n_y): n_x = 0 keeps n_y >= 0 (the half space), n_x > 0 all n_y
+__device__ __forceinline__ void mm_line(int L, int ky, int NY, int &nx, int &iy)
+{
+    if (L <= ky) {
+        nx = 0;
+        iy = ky + L;
+    } else {
+        const int r = L - ky - 1;
+        nx = 1 + r / NY;
+        iy = r % NY;
+    }
+}
+
+__global__ void __launch_bounds__(MMR_CH *MMR_WARPS, 2) k_mm_recip(EwaldDev e, const double2 *__restrict__ A,
+                                                                 const double2 *__restrict__ Az, double *dq,
+                                                                 double *dR)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float2 gyt[2 * 56 + 1];
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
-    const int NY = 2 * ky + 1, NZ = 2 * kz + 1;
-    float4 *zs = reinterpret_cast<float4 *>(smem_raw);  // [NZ][MMR_THREADS]
-    const int t = threadIdx.x;
-    for (int iy = t; iy < NY; iy += blockDim.x) {
-        const f2 g = f2_from(TWO_PI * (iy - ky) / e.box[1]);
-        gyt[iy] = make_float2(g.h, g.l);
-    }
-    const int i = blockIdx.x * blockDim.x + t;
+    const int NX = kx + 1, NY = 2 * ky + 1, NZ = 2 * kz + 1;
+    double2 *zs = reinterpret_cast<double2 *>(smem_raw);  // [NZ][32]
+    double2 *xs = zs + NZ * MMR_CH;                        // [NX][32]
+    double2 *ys = xs + NX * MMR_CH;                        // [NY][32]
+    double2 *wab = ys + NY * MMR_CH;                       // [8][2][NZ]
+    double *red = reinterpret_cast<double *>(wab + MMR_WARPS * 2 * NZ);  // [4][8][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * MMR_CH + lane;
     const bool act = i < e.nmm;
     const int ii = act ? i : 0;
-    const double fx = e.mm_xyz[3 * ii] / e.box[0], fy = e.mm_xyz[3 * ii + 1] / e.box[1],
-                 fz = e.mm_xyz[3 * ii + 2] / e.box[2];
-    double s, c;
-    sincospi(-2.0 * fx, &s, &c);
-    const c2 ex1{f2_from(c), f2_from(s)};
-    sincospi(-2.0 * fy, &s, &c);
-    const c2 ey1{f2_from(c), f2_from(s)};
-    sincospi(-2.0 * fz, &s, &c);
-    const c2 ez1{f2_from(c), f2_from(s)};
-    sincospi(2.0 * ky * fy, &s, &c);
-    const c2 ey0{f2_from(c), f2_from(s)};
-    sincospi(2.0 * kz * fz, &s, &c);
-    c2 pz{f2_from(c), f2_from(s)};
-    for (int iz = 0; iz < NZ; ++iz) {
-        zs[(size_t)iz * MMR_THREADS + t] = make_float4(pz.re.h, pz.re.l, pz.im.h, pz.im.l);
-        pz = c2_mul(pz, ez1);
+    // fractional coordinates
+    const double u0 = e.mm_xyz[3 * ii] / e.box[0], u1 = e.mm_xyz[3 * ii + 1] / e.box[1],
+                 u2 = e.mm_xyz[3 * ii + 2] / e.box[2];
+    // phase rows in segments of 8 (one sincospi each, then the recurrence), segments over warps
+    {
+        const int sx = (NX + MMR_SEG - 1) / MMR_SEG, sy = (NY + MMR_SEG - 1) / MMR_SEG,
+                  sz = (NZ + MMR_SEG - 1) / MMR_SEG;
+        for (int sg = warp; sg < sx + sy + sz; sg += MMR_WARPS) {
+            const int d = sg < sx ? 0 : sg < sx + sy ? 1 : 2;
+            const int s = sg - (d == 0 ? 0 : d == 1 ? sx : sx + sy);
+            const int len = d == 0 ? NX : d == 1 ? NY : NZ, off = d == 0 ? 0 : d == 1 ? ky : kz;
+            const double fd = d == 0 ? u0 : d == 1 ? u1 : u2;
+            double2 *row = d == 0 ? xs : d == 1 ? ys : zs;
+            double sn, cs;
+            sincospi(-2.0 * fd, &sn, &cs);
+            const double2 step = make_double2(cs, sn);
+            const int n0 = s * MMR_SEG;
+            sincospi(-2.0 * (n0 - off) * fd, &sn, &cs);
+            double2 p = make_double2(cs, sn);
+            for (int n = n0; n < min(len, n0 + MMR_SEG); ++n) {
+                row[n * MMR_CH + lane] = p;
+                p = cmul(p, step);
+            }
+        }
     }
     __syncthreads();
-    f2 pot{0.f, 0.f}, f1{0.f, 0.f}, f2z{0.f, 0.f};
-    double f0 = 0.0;
-    c2 px{f2{1.f, 0.f}, f2{0.f, 0.f}};
-    for (int nx = 0; nx <= kx; ++nx) {
-        c2 py = ey0;
-        f2 sim{0.f, 0.f};
-        for (int iy = 0; iy < NY; ++iy) {
-            if (nx > 0 || iy >= ky) {
-                const float4 *Ar = A + ((size_t)nx * NY + iy) * NZ;
-                const float4 *Azr = Az + ((size_t)nx * NY + iy) * NZ;
-                // two independent accumulator sets (even / odd n_z) for instruction-level parallelism
-                float B[4] = {0.f, 0.f, 0.f, 0.f}, Bz[4] = {0.f, 0.f, 0.f, 0.f};
-                float C[4] = {0.f, 0.f, 0.f, 0.f}, Cz[4] = {0.f, 0.f, 0.f, 0.f};
-                int iz = 0;
-                for (; iz + 1 < NZ; iz += 2) {
-                    const c2 z0 = c2_from(zs[(size_t)iz * MMR_THREADS + t]);
-                    const c2 z1 = c2_from(zs[(size_t)(iz + 1) * MMR_THREADS + t]);
-                    c2_mac(B, c2_from(__ldg(Ar + iz)), z0);
-                    c2_mac(C, c2_from(__ldg(Ar + iz + 1)), z1);
-                    c2_mac(Bz, c2_from(__ldg(Azr + iz)), z0);
-                    c2_mac(Cz, c2_from(__ldg(Azr + iz + 1)), z1);
-                }
-                if (iz < NZ) {
-                    const c2 z0 = c2_from(zs[(size_t)iz * MMR_THREADS + t]);
-                    c2_mac(B, c2_from(__ldg(Ar + iz)), z0);
-                    c2_mac(Bz, c2_from(__ldg(Azr + iz)), z0);
-                }
-                const c2 pxy = c2_mul(px, py);
-                const c2 b{f2_add(f2_add(f2{B[0], 0.f}, f2{B[1], 0.f}), f2_add(f2{C[0], 0.f}, f2{C[1], 0.f})),
-                           f2_add(f2_add(f2{B[2], 0.f}, f2{B[3], 0.f}), f2_add(f2{C[2], 0.f}, f2{C[3], 0.f}))};
-                const f2 bzr = f2_add(f2_add(f2{Bz[0], 0.f}, f2{Bz[1], 0.f}), f2_add(f2{Cz[0], 0.f}, f2{Cz[1], 0.f}));
-                const f2 bzi = f2_add(f2_add(f2{Bz[2], 0.f}, f2{Bz[3], 0.f}), f2_add(f2{Cz[2], 0.f}, f2{Cz[3], 0.f}));
-                const c2 pr = c2_mul(pxy, b);
-                const f2 imz = f2_add(f2_mul(pxy.re, bzi), f2_mul(pxy.im, bzr));
-                pot = f2_add(pot, pr.re);
-                sim = f2_add(sim, pr.im);
-                const float2 gy = gyt[iy];
-                f1 = f2_add(f1, f2_mul(f2{gy.x, gy.y}, pr.im));
-                f2z = f2_add(f2z, imz);
-            }
-            py = c2_mul(py, ey1);
+    double pot = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    double2 *wa = wab + warp * 2 * NZ, *waz = wa + NZ;
+    const int nlines = kx * NY + ky + 1;
+    for (int L = warp; L < nlines; L += MMR_WARPS) {
+        int nx, iy;
+        mm_line(L, ky, NY, nx, iy);
+        const size_t base = ((size_t)nx * NY + iy) * NZ;
+        __syncwarp();
+        for (int k = lane; k < NZ; k += 32) {
+            wa[k] = __ldg(A + base + k);
+            waz[k] = __ldg(Az + base + k);
         }
-        f0 += TWO_PI * nx / e.box[0] * f2_to(sim);
-        px = c2_mul(px, ex1);
+        __syncwarp();
+        double br = 0.0, bi = 0.0, bzr = 0.0, bzi = 0.0;
+        for (int iz = 0; iz < NZ; ++iz) {
+            const double2 a = wa[iz], az = waz[iz], z = zs[iz * MMR_CH + lane];
+            br = fma(a.x, z.x, br);
+            br = fma(-a.y, z.y, br);
+            bi = fma(a.x, z.y, bi);
+            bi = fma(a.y, z.x, bi);
+            bzr = fma(az.x, z.x, bzr);
+            bzr = fma(-az.y, z.y, bzr);
+            bzi = fma(az.x, z.y, bzi);
+            bzi = fma(az.y, z.x, bzi);
+        }
+        const double2 pxy = cmul(xs[nx * MMR_CH + lane], ys[iy * MMR_CH + lane]);
+        const double re = pxy.x * br - pxy.y * bi;
+        const double im = pxy.x * bi + pxy.y * br;
+        pot += re;
+        fx += TWO_PI * nx / e.box[0] * im;
+        fy += TWO_PI * (iy - ky) / e.box[1] * im;
+        fz += pxy.x * bzi + pxy.y * bzr;
     }
-    if (!act) return;
-    const double q = e.mm_q[i];
-    dq[i] += f2_to(pot);
-    dR[3 * i] += q * f0;
-    dR[3 * i + 1] += q * f2_to(f1);
-    dR[3 * i + 2] += q * f2_to(f2z);
+    red[(0 * MMR_WARPS + warp) * MMR_CH + lane] = pot;
+    red[(1 * MMR_WARPS + warp) * MMR_CH + lane] = fx;
+    red[(2 * MMR_WARPS + warp) * MMR_CH + lane] = fy;
+    red[(3 * MMR_WARPS + warp) * MMR_CH + lane] = fz;
+    __syncthreads();
+    if (warp == 0 && act) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < MMR_WARPS; ++w)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) t[v] += red[(v * MMR_WARPS + w) * MMR_CH + lane];
+        const double q = e.mm_q[i];
+        dq[i] += t[0];
+        dR[3 * i] += q * t[1];
+        dR[3 * i + 1] += q * t[2];
+        dR[3 * i + 2] += q * t[3];
+    }
+}
+
+// Double-float variant (mixed-precision path): A, Az and the phase tables as FP32 (hi, lo)
+// pairs; the dot products along n_z are error-free multiply-adds, the per-line combination runs
+// in double-float arithmetic, and the phase rows start from one FP64 sincospi per segment.
+__global__ void __launch_bounds__(MMR_CH *MMR_WARPS, 3) k_mm_recip_df(EwaldDev e, const float4 *__restrict__ A,
+                                                                    const float4 *__restrict__ Az, double *dq,
+                                                                    double *dR)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NX = kx + 1, NY = 2 * ky + 1, NZ = 2 * kz + 1;
+    float4 *zs = reinterpret_cast<float4 *>(smem_raw);  // [NZ][32]
+    float4 *xs = zs + NZ * MMR_CH;                       // [NX][32]
+    float4 *ys = xs + NX * MMR_CH;                       // [NY][32]
+    float4 *wab = ys + NY * MMR_CH;                      // [8][2][NZ]
+    float *red = reinterpret_cast<float *>(wab + MMR_WARPS * 2 * NZ);  // [8][8][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * MMR_CH + lane;
+    const bool act = i < e.nmm;
+    const int ii = act ? i : 0;
+    // fractional coordinates
+    const double u0 = e.mm_xyz[3 * ii] / e.box[0], u1 = e.mm_xyz[3 * ii + 1] / e.box[1],
+                 u2 = e.mm_xyz[3 * ii + 2] / e.box[2];
+    {
+        const int sx = (NX + MMR_SEG - 1) / MMR_SEG, sy = (NY + MMR_SEG - 1) / MMR_SEG,
+                  sz = (NZ + MMR_SEG - 1) / MMR_SEG;
+        for (int sg = warp; sg < sx + sy + sz; sg += MMR_WARPS) {
+            const int d = sg < sx ? 0 : sg < sx + sy ? 1 : 2;
+            const int s = sg - (d == 0 ? 0 : d == 1 ? sx : sx + sy);
+            const int len = d == 0 ? NX : d == 1 ? NY : NZ, off = d == 0 ? 0 : d == 1 ? ky : kz;
+            const double fd = d == 0 ? u0 : d == 1 ? u1 : u2;
+            float4 *row = d == 0 ? xs : d == 1 ? ys : zs;
+            double sn, cs;
+            sincospi(-2.0 * fd, &sn, &cs);
+            const c2 step{f2_from(cs), f2_from(sn)};
+            const int n0 = s * MMR_SEG;
+            sincospi(-2.0 * (n0 - off) * fd, &sn, &cs);
+            c2 p{f2_from(cs), f2_from(sn)};
+            for (int n = n0; n < min(len, n0 + MMR_SEG); ++n) {
+                row[n * MMR_CH + lane] = make_float4(p.re.h, p.re.l, p.im.h, p.im.l);
+                p = c2_mul(p, step);
+            }
+        }
+    }
+    __syncthreads();
+    f2 pot{0.f, 0.f}, fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f};
+    float4 *wa = wab + warp * 2 * NZ, *waz = wa + NZ;
+    const f2 gx1 = f2_from(TWO_PI / e.box[0]), gy1 = f2_from(TWO_PI / e.box[1]);
+    const int nlines = kx * NY + ky + 1;
+    for (int L = warp; L < nlines; L += MMR_WARPS) {
+        int nx, iy;
+        mm_line(L, ky, NY, nx, iy);
+        const size_t base = ((size_t)nx * NY + iy) * NZ;
+        __syncwarp();
+        for (int k = lane; k < NZ; k += 32) {
+            wa[k] = __ldg(A + base + k);
+            waz[k] = __ldg(Az + base + k);
+        }
+        __syncwarp();
+        // two independent accumulator sets (even / odd n_z) for instruction-level parallelism
+        float B[4] = {0.f, 0.f, 0.f, 0.f}, Bz[4] = {0.f, 0.f, 0.f, 0.f};
+        float C[4] = {0.f, 0.f, 0.f, 0.f}, Cz[4] = {0.f, 0.f, 0.f, 0.f};
+        int iz = 0;
+        for (; iz + 1 < NZ; iz += 2) {
+            const c2 z0 = c2_from(zs[iz * MMR_CH + lane]), z1 = c2_from(zs[(iz + 1) * MMR_CH + lane]);
+            c2_mac(B, c2_from(wa[iz]), z0);
+            c2_mac(C, c2_from(wa[iz + 1]), z1);
+            c2_mac(Bz, c2_from(waz[iz]), z0);
+            c2_mac(Cz, c2_from(waz[iz + 1]), z1);
+        }
+        if (iz < NZ) {
+            const c2 z0 = c2_from(zs[iz * MMR_CH + lane]);
+            c2_mac(B, c2_from(wa[iz]), z0);
+            c2_mac(Bz, c2_from(waz[iz]), z0);
+        }
+        const c2 pxy = c2_mul(c2_from(xs[nx * MMR_CH + lane]), c2_from(ys[iy * MMR_CH + lane]));
+        const c2 b{f2_add(f2_add(f2{B[0], 0.f}, f2{B[1], 0.f}), f2_add(f2{C[0], 0.f}, f2{C[1], 0.f})),
+                   f2_add(f2_add(f2{B[2], 0.f}, f2{B[3], 0.f}), f2_add(f2{C[2], 0.f}, f2{C[3], 0.f}))};
+        const f2 bzr = f2_add(f2_add(f2{Bz[0], 0.f}, f2{Bz[1], 0.f}), f2_add(f2{Cz[0], 0.f}, f2{Cz[1], 0.f}));
+        const f2 bzi = f2_add(f2_add(f2{Bz[2], 0.f}, f2{Bz[3], 0.f}), f2_add(f2{Cz[2], 0.f}, f2{Cz[3], 0.f}));
+        const c2 pr = c2_mul(pxy, b);
+        pot = f2_add(pot, pr.re);
+        // G_x = (2 pi / L_x) n_x and G_y = (2 pi / L_y) n_y: small integers times a double-float
+        fx = f2_add(fx, f2_mul(f2_mul(gx1, f2{(float)nx, 0.f}), pr.im));
+        fy = f2_add(fy, f2_mul(f2_mul(gy1, f2{(float)(iy - ky), 0.f}), pr.im));
+        fz = f2_add(fz, f2_add(f2_mul(pxy.re, bzi), f2_mul(pxy.im, bzr)));
+    }
+    const f2 vals[4] = {pot, fx, fy, fz};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        red[((2 * v) * MMR_WARPS + warp) * MMR_CH + lane] = vals[v].h;
+        red[((2 * v + 1) * MMR_WARPS + warp) * MMR_CH + lane] = vals[v].l;
+    }
+    __syncthreads();
+    if (warp == 0 && act) {
+        f2 t[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int w = 0; w < MMR_WARPS; ++w)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                t[v] = f2_add(t[v], f2{red[((2 * v) * MMR_WARPS + w) * MMR_CH + lane],
+                                       red[((2 * v + 1) * MMR_WARPS + w) * MMR_CH + lane]});
+        const double q = e.mm_q[i];
+        dq[i] += f2_to(t[0]);
+        dR[3 * i] += q * f2_to(t[1]);
+        dR[3 * i + 1] += q * f2_to(t[2]);
+        dR[3 * i + 2] += q * f2_to(t[3]);
+    }
 }
 
 __global__ void k_mm_background(EwaldDev e, const double *sums, double *dq)
@@ -992,7 +1052,7 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
         k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A, w.Az, df ? w.Adf : nullptr,
                                                          df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        const size_t smem = (size_t)2 * (2 * e.kmax[2] + 1) * MMR_THREADS * sizeof(double);  // = NZ float4 per thread
+        const size_t smem = mm_recip_smem(e);
         static size_t attr = 0, attr_df = 0;
         size_t &a = df ? attr_df : attr;
         if (smem > 48 * 1024 && smem > a) {
@@ -1001,11 +1061,11 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
                 return err;
             a = smem;
         }
-        const int nb = (e.nmm + MMR_THREADS - 1) / MMR_THREADS;
+        const int nb = (e.nmm + MMR_CH - 1) / MMR_CH;
         if (df)
-            k_mm_recip_df<<<nb, MMR_THREADS, smem, st>>>(e, w.Adf, w.Azdf, dq_int, dR_int);
+            k_mm_recip_df<<<nb, MMR_CH * MMR_WARPS, smem, st>>>(e, w.Adf, w.Azdf, dq_int, dR_int);
         else
-            k_mm_recip<<<nb, MMR_THREADS, smem, st>>>(e, w.A, w.Az, dq_int, dR_int);
+            k_mm_recip<<<nb, MMR_CH * MMR_WARPS, smem, st>>>(e, w.A, w.Az, dq_int, dR_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         k_mm_background<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, w.sums, dq_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -1,0 +1,67 @@
+"""Large active site with f shells (150 QM atoms, 1500 shells, 5100 AOs, ~200000 MM charges in an
+86 A box, kmax 24): sampled V blocks of every angular class up to (f, f) against the oracle, the
+mixed path against FP64, and invariants of the full gradient.  (The oracle's charge derivatives
+take minutes at this size; the active-site workload and the small systems cover them.)"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _gpuutil import TOL_FP64, TOL_MIXED, TOL_MIXED_ELEM, gpu_all, rel_fro, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return workloads.config4_large_site()
+
+
+@pytest.fixture(scope="module")
+def c4_gpu(c4):
+    return {p: gpu_all(c4, precision=p) for p in (0, 1)}
+
+
+def test_config4_counts(c4, c4_gpu):
+    info = c4_gpu[0]["info"]
+    assert info["nao"] == 5100 and info["nshell"] == 1500
+    assert info["n_region1"] == len(oracle.region1(c4)[0])
+    assert info["n_gvec"] == (49 ** 3 - 1) // 2
+    assert all(n > 0 for n in info["n_prim_pairs_class"])  # every class up to (f, f) is present
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config4_sampled_V_blocks(c4, c4_gpu, precision):
+    s = c4
+    rng = np.random.default_rng(41)
+    off = np.concatenate([[0], np.cumsum([(l + 1) * (l + 2) // 2 for l in s.shell_l])])
+    pairs = []
+    for la in range(4):
+        for lb in range(la + 1):
+            A = np.flatnonzero(s.shell_l == la)
+            B = np.flatnonzero(s.shell_l == lb)
+            for _ in range(3):
+                pairs.append((int(rng.choice(A)), int(rng.choice(B))))
+    V = c4_gpu[precision]["V"]
+    Vref = oracle.vpot(s, pairs=pairs)
+    got = np.concatenate([V[off[a]:off[a + 1], off[b]:off[b + 1]].ravel() for a, b in pairs])
+    ref = np.concatenate([Vref[off[a]:off[a + 1], off[b]:off[b + 1]].ravel() for a, b in pairs])
+    tol = TOL_FP64 if precision == 0 else TOL_MIXED_ELEM
+    assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(V))
+
+
+def test_config4_mixed_vs_fp64(c4_gpu):
+    assert rel_fro(c4_gpu[1]["V"], c4_gpu[0]["V"]) < TOL_MIXED
+    for k in ("dE_dRqm", "dE_dRmm", "dE_dq"):
+        assert rel_max(c4_gpu[1][k], c4_gpu[0][k]) < TOL_MIXED, k
+    sc = abs(c4_gpu[0]["E_I_elec"]) + abs(c4_gpu[0]["E_nuc_mm"]) + abs(c4_gpu[0]["E_II"])
+    assert abs(c4_gpu[1]["E"] - c4_gpu[0]["E"]) < TOL_MIXED * sc
+
+
+def test_config4_invariants(c4, c4_gpu):
+    for p in (0, 1):
+        g = c4_gpu[p]
+        tot = g["dE_dRqm"].sum(0) + g["dE_dRmm"].sum(0)
+        assert np.max(np.abs(tot)) < (1e-9 if p == 0 else 1e-6) * np.max(np.abs(g["dE_dRqm"]))
+        sc = abs(g["E_I_elec"]) + abs(g["E_nuc_mm"]) + abs(g["E_II"])
+        assert abs(np.dot(c4.mm_q, g["dE_dq"]) - g["E"]) < (1e-11 if p == 0 else 1e-6) * sc
