@@ -60,6 +60,10 @@ def flops_adjoint(L):
 
 CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la(la+1)/2 + lb
 
+# DRAM bytes (read + write) of one adjoint sweep (all class kernels of one launch round), from
+# the ncu capture summarised in profiles/vgrad_traffic_c2.md; None where not captured.
+SWEEP_TRAFFIC = {("c2", "fp64"): 25_316_608, ("c2", "mixed"): 21_309_184}
+
 
 def sweep_flops(info, adjoint):
     f = flops_adjoint if adjoint else flops_forward
@@ -391,7 +395,9 @@ def main():
     peak = FP64_PEAK_TFLOPS if prec == q.QMMM_FP64 else FP32_PEAK_TFLOPS
     roof = {"kernel": "vgrad (region-I adjoint sweep)" if dom_adj else "vpot (region-I sweep)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel_ms": t_g if dom_adj else t_v, "other_sweep_ms": t_v if dom_adj else t_g,
+            "traffic": SWEEP_TRAFFIC.get((args.config, args.precision)) if dom_adj else None,
+            "traffic_note": "DRAM bytes per adjoint sweep (all angular-class kernels), ncu capture",
+            "kernel_ms": t_g if dom_adj else t_v, "other_sweep_ms": t_v if dom_adj else t_g,
             "peak_note": ("FP64 plain-ALU peak from the unit counts at 2070 MHz (152 SMs x 2 DFMA/clk)"
                           if prec == q.QMMM_FP64 else "FP32 plain-ALU peak at 2070 MHz (152 SMs x 128 FFMA/clk)"),
             "flops_per_launch": fl}
@@ -427,7 +433,8 @@ def main():
                  "rel_fro_err_V": fro, "max_rel_err_forces": gerr,
                  "rel_err_E": float(abs(Em[0] - E64[0]) / escale),
                  "roofline": {"bound": "alu", "achieved": ach_m, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": ach_m / FP32_PEAK_TFLOPS}}
+                              "frac": ach_m / FP32_PEAK_TFLOPS,
+                              "traffic": SWEEP_TRAFFIC.get((args.config, "mixed")) if t_gm >= t_vm else None}}
         hm.close()
 
     # end to end: host (pinned) inputs and outputs, copies inside the timed interval

@@ -889,14 +889,35 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         for (int j = 0; j < natm; ++j) minit[10 * j] = h->Z[j];
         CUDA_TRY(cudaMemcpy(h->mult_init.p, minit.data(), minit.size() * sizeof(double), cudaMemcpyHostToDevice));
         // Boys tables
-        std::vector<double> t64;
-        boys_table(BOYS_NROW_D, BOYS_NCOL_D, BOYS_STEP, t64);
+        std::vector<double> raw, t64((size_t)BOYS_MAXM * BOYS_NROW_D * BOYS_ROW_D);
+        boys_table(BOYS_NROW_D, BOYS_NCOL_D, BOYS_STEP, raw);
+        // one table per order M: F_{M+j}(T_k) / j!, j = 0..6, then e^{-T_k}
+        for (int M = 0; M < BOYS_MAXM; ++M)
+            for (int k = 0; k < BOYS_NROW_D; ++k) {
+                double *row = &t64[((size_t)M * BOYS_NROW_D + k) * BOYS_ROW_D];
+                double fact = 1.0;
+                for (int j = 0; j < BOYS_TAYLOR_D; ++j) {
+                    if (j > 0) fact *= j;
+                    row[j] = raw[(size_t)k * BOYS_NCOL_D + M + j] / fact;
+                }
+                row[BOYS_ROW_D - 1] = raw[(size_t)k * BOYS_NCOL_D + BOYS_NCOL_D - 1];
+            }
         if ((rc = h->boys64.ensure(t64.size()))) return rc;
         CUDA_TRY(cudaMemcpy(h->boys64.p, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
         std::vector<double> t32d;
         boys_table(BOYS_NROW_F, BOYS_NCOL_F, BOYS_STEP, t32d);
-        std::vector<float> t32((t32d.size() + 3) / 4 * 4, 0.0f);
-        for (size_t k = 0; k < t32d.size(); ++k) t32[k] = (float)t32d[k];
+        // one table per order M: F_{M+j}(T_k) / j!, j = 0..4, then e^{-T_k}
+        std::vector<float> t32((size_t)BOYS_MAXM * BOYS_TAB_F, 0.0f);
+        for (int M = 0; M < BOYS_MAXM; ++M)
+            for (int k = 0; k < BOYS_NROW_F; ++k) {
+                float *row = &t32[(size_t)M * BOYS_TAB_F + (size_t)k * BOYS_ROW_F];
+                double fact = 1.0;
+                for (int j = 0; j < BOYS_TAYLOR_F; ++j) {
+                    if (j > 0) fact *= j;
+                    row[j] = (float)(t32d[(size_t)k * BOYS_NCOL_F + M + j] / fact);
+                }
+                row[BOYS_TAYLOR_F] = (float)t32d[(size_t)k * BOYS_NCOL_F + BOYS_NCOL_F - 1];
+            }
         if ((rc = h->boys32.ensure(t32.size()))) return rc;
         CUDA_TRY(cudaMemcpy(h->boys32.p, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
         // Ewald buffers

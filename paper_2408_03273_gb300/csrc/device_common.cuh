@@ -28,14 +28,21 @@ constexpr double HALF_SQRT_PI = 0.88622692545275801365;
 // Boys tables (rows T_k = k * step; columns m = 0..NCOL-2, last column e^{-T_k})
 constexpr double BOYS_STEP = 0.1;
 constexpr double BOYS_INV_STEP = 10.0;
-constexpr double BOYS_TMAX_D = 36.0;          // FP64 table range; above: asymptotic branch
-constexpr int BOYS_NROW_D = 361;
-constexpr int BOYS_NCOL_D = 17;               // orders 0..15 + exp column (padded row stride)
+constexpr double BOYS_TMAX_D = 60.0;          // FP64 table range; above: asymptotic branch, where
+                                              // e^{-T} < 1e-26 is below FP64 resolution of F_m, m <= 8
+constexpr int BOYS_NROW_D = 601;
+constexpr int BOYS_NCOL_D = 17;               // host table: orders 0..15 + exp column
 constexpr int BOYS_TAYLOR_D = 7;              // terms of the FP64 Taylor expansion
+constexpr int BOYS_ROW_D = 8;                 // device row for order M: F_{M+j}(T_k) / j!, j = 0..6,
+                                              // then e^{-T_k} (64 B: four aligned double2 loads)
 constexpr float BOYS_TMAX_F = 20.0f;          // FP32 table range
 constexpr int BOYS_NROW_F = 201;
-constexpr int BOYS_NCOL_F = 17;               // orders 0..15 + exp column, odd stride (banks)
+constexpr int BOYS_NCOL_F = 17;               // host table: orders 0..15 + exp column
 constexpr int BOYS_TAYLOR_F = 5;
+constexpr int BOYS_ROW_F = 7;                 // device row for order M: F_{M+j}(T_k) / j!, j = 0..4,
+                                              // e^{-T_k}, pad (odd stride: lanes on different rows
+                                              // read different banks)
+constexpr int BOYS_TAB_F = (BOYS_NROW_F * BOYS_ROW_F + 3) / 4 * 4;  // floats per order (16-byte multiple)
 constexpr int BOYS_MAXM = 8;                  // highest order any kernel asks for
 
 // ------------------------------------------------------------------------------------------
@@ -75,27 +82,31 @@ __host__ __device__ constexpr int class_of(int la, int lb) { return la * (la + 1
 // ------------------------------------------------------------------------------------------
 // Boys function
 // ------------------------------------------------------------------------------------------
+// F_m(T), m = 0..M.  tab holds one table per order M (BOYS_NROW_D rows of BOYS_ROW_D): for
+// T < BOYS_TMAX_D a 7-term Taylor expansion about the nearest T_k with the 1/j! folded into the
+// table (Horner with one FMA per term), then the stable downward recursion; above, F_0 from its
+// asymptotic form and the upward recursion, which is exact there up to e^{-T}.
 template <int M>
 __device__ __forceinline__ void boys_f64(double T, double (&F)[M + 1], const double *__restrict__ tab)
 {
     if (T < BOYS_TMAX_D) {
         const int k = __double2int_rn(T * BOYS_INV_STEP);
         const double x = (double)k * BOYS_STEP - T;  // -(T - T_k)
-        const double *row = tab + k * BOYS_NCOL_D;
-        // sum_{j<7} F_{M+j}(T_k) x^j / j!  (Horner)
-        double f = __ldg(row + M + 6);
-        f = __ldg(row + M + 5) + f * x * (1.0 / 6.0);
-        f = __ldg(row + M + 4) + f * x * (1.0 / 5.0);
-        f = __ldg(row + M + 3) + f * x * (1.0 / 4.0);
-        f = __ldg(row + M + 2) + f * x * (1.0 / 3.0);
-        f = __ldg(row + M + 1) + f * x * 0.5;
-        f = __ldg(row + M) + f * x;
+        const double2 *row =
+            reinterpret_cast<const double2 *>(tab + ((size_t)M * BOYS_NROW_D + k) * BOYS_ROW_D);
+        const double2 c01 = __ldg(row), c23 = __ldg(row + 1), c45 = __ldg(row + 2), c6e = __ldg(row + 3);
+        double f = fma(c6e.x, x, c45.y);
+        f = fma(f, x, c45.x);
+        f = fma(f, x, c23.y);
+        f = fma(f, x, c23.x);
+        f = fma(f, x, c01.y);
+        f = fma(f, x, c01.x);
         F[M] = f;
         if (M > 0) {
             // e^{-T} = e^{-T_k} e^{x}, |x| <= 0.05: 8-term Taylor of e^x
             double ex = 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0 + x * (1.0 / 24.0 + x * (1.0 / 120.0 +
                         x * (1.0 / 720.0 + x * (1.0 / 5040.0)))))));
-            const double e = __ldg(row + BOYS_NCOL_D - 1) * ex;
+            const double e = c6e.y * ex;
             const double T2 = 2.0 * T;
 #pragma unroll
             for (int m = M; m > 0; --m) F[m - 1] = (T2 * F[m] + e) * (1.0 / (2 * m - 1));
@@ -104,10 +115,9 @@ __device__ __forceinline__ void boys_f64(double T, double (&F)[M + 1], const dou
         const double rs = rsqrt(T);
         F[0] = HALF_SQRT_PI * rs;
         if (M > 0) {
-            const double e = (T < 60.0) ? exp(-T) : 0.0;
             const double inv2T = 0.5 * rs * rs;
 #pragma unroll
-            for (int m = 0; m < M; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * inv2T;
+            for (int m = 0; m < M; ++m) F[m + 1] = ((2 * m + 1) * inv2T) * F[m];
         }
     }
 }
@@ -131,6 +141,7 @@ __device__ __forceinline__ void boys_arg_f32(float rho, float X, float Y, float 
     Tl = fmaf(rho, s2, -Th) + rho * lo;
 }
 
+// tab: the order-M FP32 table (BOYS_NROW_F rows of BOYS_ROW_F), staged in shared memory.
 template <int M>
 __device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float *__restrict__ tab /* smem */,
                                          float Tlo = 0.0f)
@@ -138,12 +149,11 @@ __device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float
     if (T < BOYS_TMAX_F) {
         const int k = __float2int_rn(T * 10.0f);
         const float x = ((float)k * 0.1f - T) - Tlo;
-        const float *row = tab + k * BOYS_NCOL_F;
-        float f = row[M + 4];
-        f = row[M + 3] + f * x * 0.25f;
-        f = row[M + 2] + f * x * (1.0f / 3.0f);
-        f = row[M + 1] + f * x * 0.5f;
-        f = row[M] + f * x;
+        const float *row = tab + k * BOYS_ROW_F;  // the order-M table: 1/j! folded in
+        float f = fmaf(row[4], x, row[3]);
+        f = fmaf(f, x, row[2]);
+        f = fmaf(f, x, row[1]);
+        f = fmaf(f, x, row[0]);
         F[M] = f;
         if (M > 0) {
             const float e = __expf(-T);

@@ -671,16 +671,41 @@ __device__ __forceinline__ void contract_pot_field(const double *M, const double
     }
 }
 
-__global__ void __launch_bounds__(256) k_mm_real(EwaldDev e, const double *mult, double *dq, double *dR)
+// Blocks of 32 MM charges (one per lane) x 8 warps; warp w takes the QM atoms j = w, w + 8, ...
+// and the 8 partial sums per charge are added in a fixed order (as in the nuclear-MM kernel), so
+// small N_MM still fills the GPU and the result is reproducible.
+constexpr int MMQ_CH = 32, MMQ_WARPS = 8;
+
+// per-charge reduction over the 8 warps: red[4][8][32]; returns the sums in lane order on warp 0
+__device__ __forceinline__ void mmq_reduce(double (&red)[4][MMQ_WARPS][MMQ_CH], double pot, const double (&fld)[3],
+                                           double (&out)[4])
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= e.nmm) return;
-    const double q = e.mm_q[i], beta = e.mm_beta[i];
-    const double xi = e.mm_xyz[3 * i], yi = e.mm_xyz[3 * i + 1], zi = e.mm_xyz[3 * i + 2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    red[0][warp][lane] = pot;
+    red[1][warp][lane] = fld[0];
+    red[2][warp][lane] = fld[1];
+    red[3][warp][lane] = fld[2];
+    __syncthreads();
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    if (warp == 0)
+        for (int w = 0; w < MMQ_WARPS; ++w)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) out[v] += red[v][w][lane];
+}
+
+__global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_real(EwaldDev e, const double *mult, double *dq, double *dR)
+{
+    __shared__ double red[4][MMQ_WARPS][MMQ_CH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * MMQ_CH + lane;
+    const bool act = i < e.nmm;
+    const int ii = act ? i : 0;
+    const double beta = e.mm_beta[ii];
+    const double xi = e.mm_xyz[3 * ii], yi = e.mm_xyz[3 * ii + 1], zi = e.mm_xyz[3 * ii + 2];
     const double rc2 = e.ewald_rc * e.ewald_rc;
     const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
     double pot = 0.0, fld[3] = {0.0, 0.0, 0.0}, T[20];
-    for (int j = 0; j < e.natm; ++j) {
+    for (int j = warp; act && j < e.natm; j += MMQ_WARPS) {
         const double dx0 = __ldg(e.qm_xyz + 3 * j) - xi, dy0 = __ldg(e.qm_xyz + 3 * j + 1) - yi,
                      dz0 = __ldg(e.qm_xyz + 3 * j + 2) - zi;
         const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
@@ -711,21 +736,30 @@ __global__ void __launch_bounds__(256) k_mm_real(EwaldDev e, const double *mult,
                     }
                 }
     }
-    dq[i] += pot;
-    dR[3 * i] += -q * fld[0];
-    dR[3 * i + 1] += -q * fld[1];
-    dR[3 * i + 2] += -q * fld[2];
+    double t[4];
+    mmq_reduce(red, pot, fld, t);
+    if (warp == 0 && act) {
+        const double q = e.mm_q[i];
+        dq[i] += t[0];
+        dR[3 * i] += -q * t[1];
+        dR[3 * i + 1] += -q * t[2];
+        dR[3 * i + 2] += -q * t[3];
+    }
 }
 
 // minus the point tensors over region I, per region-I image (gchg += : [dC_x, dC_y, dC_z, dq])
-__global__ void __launch_bounds__(256) k_mm_region1(EwaldDev e, const double4_32a *rI, int nI, const double *mult,
-                                                     double *gchg)
+__global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_region1(EwaldDev e, const double4_32a *rI, int nI,
+                                                                   const double *mult, double *gchg)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nI) return;
-    const double4_32a c = rI[k];
+    __shared__ double red[4][MMQ_WARPS][MMQ_CH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * MMQ_CH + lane;
+    const bool act = k < nI;
+    double4_32a c;
+    c.x = c.y = c.z = c.w = 0.0;
+    if (act) c = rI[k];
     double pot = 0.0, fld[3] = {0.0, 0.0, 0.0}, T[20];
-    for (int j = 0; j < e.natm; ++j) {
+    for (int j = warp; act && j < e.natm; j += MMQ_WARPS) {
         const double x = __ldg(e.qm_xyz + 3 * j) - c.x, y = __ldg(e.qm_xyz + 3 * j + 1) - c.y,
                      z = __ldg(e.qm_xyz + 3 * j + 2) - c.z;
         double f, g1, g2, g3, p, fl[3], Mj[10];
@@ -736,10 +770,14 @@ __global__ void __launch_bounds__(256) k_mm_region1(EwaldDev e, const double4_32
         contract_pot_field(Mj, T, p, fl);
         pot += p; fld[0] += fl[0]; fld[1] += fl[1]; fld[2] += fl[2];
     }
-    gchg[4 * (size_t)k + 0] += c.w * fld[0];
-    gchg[4 * (size_t)k + 1] += c.w * fld[1];
-    gchg[4 * (size_t)k + 2] += c.w * fld[2];
-    gchg[4 * (size_t)k + 3] -= pot;
+    double t[4];
+    mmq_reduce(red, pot, fld, t);
+    if (warp == 0 && act) {
+        gchg[4 * (size_t)k + 0] += c.w * t[1];
+        gchg[4 * (size_t)k + 1] += c.w * t[2];
+        gchg[4 * (size_t)k + 2] += c.w * t[3];
+        gchg[4 * (size_t)k + 3] -= t[0];
+    }
 }
 
 // A(G) = 2 g(G) sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G) on the dense box, and
@@ -1040,11 +1078,11 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
     cudaError_t err;
     if ((err = launch_sum_strided(mult, e.natm, 10, w.sums + 1, st)) != cudaSuccess) return err;
     if (e.nmm > 0) {
-        k_mm_real<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, mult, dq_int, dR_int);
+        k_mm_real<<<(e.nmm + MMQ_CH - 1) / MMQ_CH, MMQ_CH * MMQ_WARPS, 0, st>>>(e, mult, dq_int, dR_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (nI > 0) {
-        k_mm_region1<<<(nI + 255) / 256, 256, 0, st>>>(e, rI, nI, mult, gchg);
+        k_mm_region1<<<(nI + MMQ_CH - 1) / MMQ_CH, MMQ_CH * MMQ_WARPS, 0, st>>>(e, rI, nI, mult, gchg);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (e.nmm > 0) {

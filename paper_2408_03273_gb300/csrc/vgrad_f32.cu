@@ -232,10 +232,8 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     }
 }
 
-inline unsigned boys32_bytes_g()
-{
-    return (unsigned)(((BOYS_NROW_F * BOYS_NCOL_F + 3) / 4) * 4 * sizeof(float));
-}
+// bytes of one order's FP32 Boys table (what a block stages)
+inline unsigned boys32_bytes_g() { return (unsigned)(BOYS_TAB_F * sizeof(float)); }
 
 template <int LA, int LB, int NT>
 static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
@@ -256,8 +254,9 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vgrad_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, dm, gqm,
-                                                 gchg, err);
+    k_vgrad_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
+                                                    boys + (size_t)(LA + LB + 1) * BOYS_TAB_F, tb, dm, gqm,
+                                                    gchg, err);
     return cudaGetLastError();
 }
 

@@ -134,10 +134,8 @@ k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
     }
 }
 
-inline unsigned boys32_bytes()
-{
-    return (unsigned)(((BOYS_NROW_F * BOYS_NCOL_F + 3) / 4) * 4 * sizeof(float));
-}
+// bytes of one order's FP32 Boys table (what a block stages)
+inline unsigned boys32_bytes() { return (unsigned)(BOYS_TAB_F * sizeof(float)); }
 
 template <int LA, int LB, int NT>
 static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
@@ -156,7 +154,8 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vpot_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, tb, V, err);
+    k_vpot_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
+                                                   boys + (size_t)(LA + LB) * BOYS_TAB_F, tb, V, err);
     return cudaGetLastError();
 }
 
