@@ -59,6 +59,7 @@ def lib():
                 "oracle_vgrad": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, i, dp, dp, dp, i, dp, i, ip, dp, dp, dp]),
                 "oracle_enucmm": (d, [i, dp, dp, i, dp, dp, dp, dp, dp, dp]),
                 "oracle_multipoles": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, dp, i, dp, dp]),
+                "oracle_octupoles": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, i, dp, dp]),
                 "oracle_fock_ii": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp]),
                 "oracle_pulay": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp, dp]),
                 "oracle_tensor": (None, [i, d, dp, dp]),
@@ -187,6 +188,38 @@ def multipoles(s, dm=None) -> np.ndarray:
     out = np.zeros((s.natm, 10))
     lib().oracle_multipoles(*b.args(), s.natm, _dp(_d(s.atom_xyz)), _dp(_d(s.atom_Z)), s.nao, _dp(dm), _dp(out))
     return out
+
+
+def octupoles(s, dm=None) -> np.ndarray:
+    """Mulliken octupoles Omega_j (SI, Multipolar Ewald): natm x 10 (xxx, xxy, xxz, xyy, xyz, xzz,
+    yyy, yyz, yzz, zzz)."""
+    b = _Basis(s)
+    dm = _d(s.dm if dm is None else dm)
+    out = np.zeros((s.natm, 10))
+    lib().oracle_octupoles(*b.args(), s.natm, _dp(_d(s.atom_xyz)), s.nao, _dp(dm), _dp(out))
+    return out
+
+
+# multiplicity of each unique component of a symmetric rank-3 tensor in the full contraction
+MULT3 = np.array([1, 3, 3, 3, 6, 3, 1, 3, 3, 1], dtype=np.float64)
+
+
+def octupole_error(s, radii, dm=None) -> np.ndarray:
+    """Octupole error estimate of the multipole truncation (Sec. "Error Control", the charge-octupole
+    sum over region II): for each region-I radius R, sum_j sum_abc Omega_j,abc v_j,abc(R), with
+    v_j,abc(R) the third Taylor components (T_abc = 1/6 d^3) of the region-II potential at atom j
+    when region I is the sphere of radius R (periodic, as the l <= 2 terms; the Ewald real-space
+    cutoff stays the system's).  Region II is recomputed from scratch for every R."""
+    Om = octupoles(s, dm)
+    out = []
+    km = _i(s.kmax)
+    for R in radii:
+        phi = np.zeros((s.natm, 20))
+        lib().oracle_ewald_phi(s.natm, _dp(_d(s.atom_xyz)), s.nmm, _dp(_d(s.mm_xyz)), _dp(_d(s.mm_q)),
+                               _dp(_d(s.mm_sigma)), _dp(_d(s.box)), float(R), float(ewald_rc(s)),
+                               float(s.ewald_alpha), _ip(km), EW_ALL, _dp(phi))
+        out.append(float(np.sum(MULT3[None, :] * Om * phi[:, 10:20])))
+    return np.array(out)
 
 
 def ewald_phi(s, mode: int = EW_ALL) -> np.ndarray:

@@ -466,6 +466,48 @@ void oracle_multipoles(int nshell, const int *shell_atom, const int *shell_l, co
     free(blk); free(aoff);
 }
 
+/* Mulliken octupoles (SI, Multipolar Ewald, fourth definition):
+ *   Omega_k,abc = - sum_{mu in k, nu} dm[nu,mu] <mu|(r-R_k)_a (r-R_k)_b (r-R_k)_c|nu>
+ * for the 10 unique components xxx, xxy, xxz, xyy, xyz, xzz, yyy, yyz, yzz, zzz; out[natm*10].
+ * The moments are products of three 1-D Obara-Saika overlaps with the (x-K)^e factor, e <= 3. */
+static const int OPX3[10][3] = {{3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1},
+                                {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
+
+void oracle_octupoles(int nshell, const int *shell_atom, const int *shell_l, const int *shell_nprim,
+                      const int *shell_off, const double *exps, const double *ncoef, int natm,
+                      const double *qm_xyz, int nao, const double *dm, double *out)
+{
+    int *aoff = (int *)malloc(sizeof(int) * nshell);
+    ao_offsets(nshell, shell_l, aoff);
+    for (int c = 0; c < 10 * natm; c++) out[c] = 0.0;
+    static double Sx[LMAXT + 2][LMAXT + 2][4], Sy[LMAXT + 2][LMAXT + 2][4], Sz[LMAXT + 2][LMAXT + 2][4];
+    for (int sA = 0; sA < nshell; sA++)
+        for (int sB = 0; sB < nshell; sB++) {
+            const int k = shell_atom[sA], la = shell_l[sA], lb = shell_l[sB];
+            const double *A = qm_xyz + 3 * k, *B = qm_xyz + 3 * shell_atom[sB];
+            int ca[36][3], cb[36][3];
+            cart_comp(la, ca);
+            cart_comp(lb, cb);
+            for (int ka = 0; ka < shell_nprim[sA]; ka++)
+                for (int kb = 0; kb < shell_nprim[sB]; kb++) {
+                    const double a = exps[shell_off[sA] + ka], b = exps[shell_off[sB] + kb];
+                    const double cc = ncoef[shell_off[sA] + ka] * ncoef[shell_off[sB] + kb];
+                    os_overlap1d(la, lb, 3, a, A[0], b, B[0], A[0], Sx);
+                    os_overlap1d(la, lb, 3, a, A[1], b, B[1], A[1], Sy);
+                    os_overlap1d(la, lb, 3, a, A[2], b, B[2], A[2], Sz);
+                    for (int i = 0; i < ncart(la); i++)
+                        for (int j = 0; j < ncart(lb); j++) {
+                            const double g = dm[(long)(aoff[sB] + j) * nao + aoff[sA] + i];
+                            for (int op = 0; op < 10; op++)
+                                out[10 * k + op] -= g * cc * Sx[ca[i][0]][cb[j][0]][OPX3[op][0]] *
+                                                    Sy[ca[i][1]][cb[j][1]][OPX3[op][1]] *
+                                                    Sz[ca[i][2]][cb[j][2]][OPX3[op][2]];
+                        }
+                }
+        }
+    free(aoff);
+}
+
 /* weight of the 10 stored components in a full (a,b) contraction: off-diagonal theta counts twice */
 static const double W10[10] = {1, 1, 1, 1, 1, 2, 2, 1, 2, 1};
 

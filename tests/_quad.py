@@ -68,10 +68,13 @@ def moment_quad(la, lb, a, A, b, B, K, op):
 OPS = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
 
 
-def ao_moments(s, ncoef):
+OPS3 = [(3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1), (0, 1, 2), (0, 0, 3)]
+
+
+def ao_moments(s, ncoef, ops=OPS):
     """AO-basis moment matrices O[op][mu,nu] = <mu|(r-R_{atom(mu)})^op|nu> by quadrature."""
     off = np.concatenate([[0], np.cumsum([(l + 1) * (l + 2) // 2 for l in s.shell_l])])
-    out = np.zeros((10, s.nao, s.nao))
+    out = np.zeros((len(ops), s.nao, s.nao))
     for sa in range(s.nshell):
         for sb in range(s.nshell):
             A = s.atom_xyz[s.shell_atom[sa]]
@@ -81,7 +84,7 @@ def ao_moments(s, ncoef):
                 for kb in range(s.shell_nprim[sb]):
                     pa, pb = s.shell_prim_offset[sa] + ka, s.shell_prim_offset[sb] + kb
                     cc = ncoef[pa] * ncoef[pb]
-                    for k, op in enumerate(OPS):
+                    for k, op in enumerate(ops):
                         out[k, off[sa]:off[sa + 1], off[sb]:off[sb + 1]] += cc * moment_quad(
                             la, lb, s.prim_exp[pa], A, s.prim_exp[pb], B, A, op)
     return out
