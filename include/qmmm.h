@@ -154,6 +154,26 @@ int qmmm_get_potential(qmmm_handle *h, double *v);
  * Returns the number of values written (2). */
 int qmmm_last_timing(const qmmm_handle *h, double *out);
 
+/* Octupole error estimate of the multipole truncation (Sec. "Error Control"): the leading error
+ * of keeping region-II interactions to quadrupole order is the charge-octupole interaction
+ *   Err(R) = sum_{i in II} sum_j sum_abc Omega_j,abc q_i T_ji,abc,
+ * Omega_j the Mulliken octupoles (SI, fourth multipole definition) at density dm.  The sum over
+ * region II is taken in the same periodic (Ewald) form as the l <= 2 terms: Err(R) = sum_j
+ * Omega_j : v_j^(3)(R), with v^(3) the third Taylor components of the region-II potential (T_abc =
+ * 1/6 d^3) when region I is the sphere of radius R about the QM centre; the Ewald real-space cutoff
+ * stays the handle's.  err[k] = Err(r_lo + k dr), k = 0..n-1 (1 <= n <= 65536, dr > 0, bohr),
+ * obtained from the handle's current region-II potential by moving the images between radius R
+ * and the handle's cutoff.  octupoles[natm*10] (NULL: not returned) in the order xxx, xxy, xxz,
+ * xyy, xyz, xzz, yyy, yyz, yzz, zzz.  dm[nao*nao], err, octupoles: host or device memory. */
+int qmmm_octupole_error(qmmm_handle *h, const double *dm, double r_lo, double dr, int n, double *err,
+                        double *octupoles);
+
+/* On-the-fly region-I radius (same section): the smallest R_k = r_lo + k dr, k < n, with
+ * |Err(R_k)| < eps; *rcut = R_k (or -1 if none), *err_at = Err(R_k) (nullable).  The handle's own
+ * cutoff is not changed: create a handle with the new radius to use it. */
+int qmmm_rcut_search(qmmm_handle *h, const double *dm, double r_lo, double dr, int n, double eps, double *rcut,
+                     double *err_at);
+
 /* Autotuner (the paper has no counterpart: its integrals come from a library).  The region-I
  * sweeps run one kernel per angular class (l_A, l_B), all classes at once on their own streams,
  * each with a cap on its grid -- its share of the SMs -- and a block shape.  By default the

@@ -42,6 +42,8 @@ from ._lib import (  # noqa: F401
     qmmm_last_timing,
     qmmm_nao,
     qmmm_nuclear_mm_energy_static,
+    qmmm_octupole_error,
+    qmmm_rcut_search,
     qmmm_set_positions,
     qmmm_set_precision,
     qmmm_set_stream,

@@ -59,7 +59,7 @@ _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
-           "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
+           "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
            "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
 
@@ -92,6 +92,9 @@ def load(build_if_needed: bool = True):
         "qmmm_nao": (c_int, [c_void_p]),
         "qmmm_get_potential": (c_int, [c_void_p, c_void_p]),
         "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
+        "qmmm_octupole_error": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p]),
+        "qmmm_rcut_search": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, P(c_double),
+                                     P(c_double)]),
         "qmmm_autotune": (c_int, [c_void_p, c_int]),
         "qmmm_get_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_double), P(c_int), P(c_double)]),
         "qmmm_set_tuning": (c_int, [c_void_p, c_int, P(c_int), P(c_double)]),
@@ -263,6 +266,25 @@ def qmmm_last_timing(h):
     out = (c_double * 2)()
     load().qmmm_last_timing(h, out)
     return float(out[0]), float(out[1])
+
+
+def qmmm_octupole_error(h, dm, r_lo, dr, n, err=None, octupoles=None, want_octupoles=False):
+    """Err(R_k), R_k = r_lo + k dr (bohr), and optionally the Mulliken octupoles (natm x 10)."""
+    info = qmmm_get_info(h)
+    err = _out(err, (int(n),), dm)
+    if want_octupoles:
+        octupoles = _out(octupoles, (info["natm"], 10), dm)
+    _check(load().qmmm_octupole_error(h, _ptr(dm), float(r_lo), float(dr), int(n), _ptr(err), _ptr(octupoles)),
+           "qmmm_octupole_error")
+    return (err, octupoles) if want_octupoles else err
+
+
+def qmmm_rcut_search(h, dm, r_lo, dr, n, eps):
+    """(smallest R_k with |Err| < eps or -1, Err there)."""
+    r, e = c_double(), c_double()
+    _check(load().qmmm_rcut_search(h, _ptr(dm), float(r_lo), float(dr), int(n), float(eps), ctypes.byref(r),
+                                   ctypes.byref(e)), "qmmm_rcut_search")
+    return r.value, e.value
 
 
 QMMM_TUNE_V, QMMM_TUNE_FORCES, QMMM_TUNE_BOTH_PRECISIONS = 1, 2, 4

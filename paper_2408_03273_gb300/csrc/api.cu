@@ -161,6 +161,7 @@ struct qmmm_handle {
     double cls_ms[SW_NKIND][NCLASS] = {};
     int tuned_mask = 0, tuned_nI = 0;
     DBuf<double> tune_V, tune_dm, tune_gqm, tune_gchg;  // autotuner scratch
+    DBuf<double> oct, oct_bins, oct_err;                  // octupole error estimate
     EwaldBuf ew;
     int nblk_mm = 1;
 
@@ -1141,6 +1142,50 @@ int qmmm_get_potential(qmmm_handle *h, double *v)
     int rc;
     if ((rc = copy_out(h, v, h->phi.p, 20 * (size_t)h->natm))) return rc;
     return check_device_errors(h);
+}
+
+int qmmm_octupole_error(qmmm_handle *h, const double *dmat, double r_lo, double dr, int n, double *err,
+                        double *octupoles)
+{
+    if (!h || !dmat || !err) return fail(QMMM_ERR_ARG, "null argument");
+    if (n < 1 || n > 65536 || !(dr > 0.0) || !(r_lo >= 0.0))
+        return fail(QMMM_ERR_ARG, "need 1 <= n <= 65536, dr > 0, r_lo >= 0");
+    cudaStream_t st = h->stream;
+    int rc;
+    const double *ddm;
+    const size_t n2 = (size_t)h->nao * h->nao;
+    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    if ((rc = h->oct.ensure(10 * (size_t)h->natm)) || (rc = h->oct_bins.ensure((size_t)n + 1)) ||
+        (rc = h->oct_err.ensure((size_t)n)))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(h->oct.p, 0, 10 * (size_t)h->natm * sizeof(double), st));
+    const BasisDev b = h->basis();
+    for (int cls = 0; cls < NCLASS; ++cls) {
+        const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
+        if (p1 > p0) CUDA_TRY(launch_octupoles(b, cls, p0, p1, ddm, h->oct.p, st));
+    }
+    CUDA_TRY(launch_octupole_error(h->ewald(), h->oct.p, h->phi.p, r_lo, dr, n, h->oct_bins.p, h->oct_err.p, st));
+    if ((rc = copy_out(h, err, h->oct_err.p, (size_t)n))) return rc;
+    if ((rc = copy_out(h, octupoles, h->oct.p, 10 * (size_t)h->natm))) return rc;
+    return finish(h, 0);
+}
+
+int qmmm_rcut_search(qmmm_handle *h, const double *dm, double r_lo, double dr, int n, double eps, double *rcut,
+                     double *err_at)
+{
+    if (!rcut || !(eps > 0.0)) return fail(QMMM_ERR_ARG, "null output or eps <= 0");
+    std::vector<double> err(std::max(n, 1));
+    const int rc = qmmm_octupole_error(h, dm, r_lo, dr, n, err.data(), nullptr);
+    if (rc) return rc;
+    *rcut = -1.0;
+    if (err_at) *err_at = 0.0;
+    for (int k = 0; k < n; ++k)
+        if (std::fabs(err[k]) < eps) {
+            *rcut = r_lo + k * dr;
+            if (err_at) *err_at = err[k];
+            break;
+        }
+    return QMMM_OK;
 }
 
 int qmmm_autotune(qmmm_handle *h, int flags)

@@ -1195,6 +1195,96 @@ cudaError_t launch_enucmm(const double *qm_xyz, const double *Z, int natm, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Octupole error estimate of the multipole truncation (Sec. "Error Control")
+//   Err(R) = sum_j sum_abc Omega_j,abc v_j,abc(R),
+// v_j,abc(R) the third Taylor components of the region-II potential with region I of radius R.
+// From the handle's v (region I of radius rc) it follows for any R by moving the images between
+// the two spheres:  Err(R) = E0 + F(rc) - F(R),  F(R) = sum over images with r_min <= d < R of
+//   e_i = q_i sum_j Omega_j : (T_ji - [r_ji < 9 sigma_i] T-hat_ji)   (third-order parts),
+// d = |image - centre|, since an image entering region I adds -q T (the region-I subtraction) and
+// drops -q T-hat (the Gaussian correction of region II).
+// ---------------------------------------------------------------------------------------------
+__constant__ double c_mult3[10] = {1, 3, 3, 3, 6, 3, 1, 3, 3, 1};  // multiplicity of each unique component
+
+// bins[k], k < nbin - 1: images with r_lo + k dr <= d < r_lo + (k + 1) dr;  bins[nbin - 1]: images
+// with r_min <= d < r_lo;  bins[nbin]: images with r_min <= d < rc.  e.rcut must be r_max.
+__global__ void __launch_bounds__(256) k_oct_shell(EwaldDev e, const double *oct, double r_min, double r_lo,
+                                                   double dr, int nbin, double rc, double *bins)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= e.nmm) return;
+    const double q = e.mm_q[i], beta = e.mm_beta[i];
+    const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
+    region1_images(e, i, [&](double px, double py, double pz, int) {
+        const double cx = px - e.centre[0], cy = py - e.centre[1], cz = pz - e.centre[2];
+        const double d = sqrt(cx * cx + cy * cy + cz * cz);
+        if (d < r_min) return;
+        double ei = 0.0, T[20], Th[20];
+        for (int j = 0; j < e.natm; ++j) {
+            const double x = __ldg(e.qm_xyz + 3 * j) - px, y = __ldg(e.qm_xyz + 3 * j + 1) - py,
+                         z = __ldg(e.qm_xyz + 3 * j + 2) - pz;
+            const double r2 = x * x + y * y + z * z;
+            double f, g1, g2, g3;
+            point_radial(r2, f, g1, g2, g3);
+            radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+            if (r2 < rhat2) {
+                screened_radial(r2, beta, f, g1, g2, g3);
+                radial_tensor(f, g1, g2, g3, x, y, z, Th, 3);
+#pragma unroll
+                for (int c = 10; c < 20; ++c) T[c] -= Th[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 10; ++c) ei += c_mult3[c] * __ldg(oct + 10 * j + c) * T[10 + c];
+        }
+        ei *= q;
+        if (d < r_lo) atomicAdd(bins + nbin - 1, ei);
+        else {
+            const int k = (int)floor((d - r_lo) / dr);
+            if (k < nbin - 1) atomicAdd(bins + k, ei);
+        }
+        if (d < rc) atomicAdd(bins + nbin, ei);
+    });
+}
+
+// E0 = sum_j Omega_j : v_j(rc) and err[k] = E0 + F(rc) - F(R_k); one block
+__global__ void k_oct_finish(const double *oct, const double *phi, int natm, const double *bins, int nbin,
+                             double *err)
+{
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < 10 * natm; t += blockDim.x) s += c_mult3[t % 10] * oct[t] * phi[20 * (t / 10) + 10 + t % 10];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e0 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) e0 += ws[w];
+        double F = bins[nbin - 1];  // F(r_lo)
+        for (int k = 0; k < nbin; ++k) {
+            err[k] = e0 + bins[nbin] - F;
+            if (k < nbin - 1) F += bins[k];
+        }
+    }
+}
+
+cudaError_t launch_octupole_error(const EwaldDev &e0, const double *oct, const double *phi, double r_lo, double dr,
+                                  int n, double *bins, double *err, cudaStream_t st)
+{
+    EwaldDev e = e0;
+    const double rc = e0.rcut, r_hi = r_lo + (n - 1) * dr;
+    const double r_min = fmin(r_lo, rc);
+    e.rcut = fmax(r_hi, rc);  // candidate images: r_min <= d < r_max
+    cudaError_t err_ = cudaMemsetAsync(bins, 0, (n + 1) * sizeof(double), st);
+    if (err_ != cudaSuccess) return err_;
+    if (e.nmm > 0) {
+        k_oct_shell<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, oct, r_min, r_lo, dr, n, rc, bins);
+        if ((err_ = cudaGetLastError()) != cudaSuccess) return err_;
+    }
+    k_oct_finish<<<1, 256, 0, st>>>(oct, phi, e.natm, bins, n, err);
+    return cudaGetLastError();
+}
+
 __global__ void k_scatter_region(const int *rI_idx, int nI, const double *gchg, double *dq, double *dR)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;

@@ -145,6 +145,107 @@ k_moments(BasisDev bd, int pp_begin, int pp_end, const double *__restrict__ dm, 
     }
 }
 
+// Mulliken octupoles (SI, fourth multipole definition):
+//   Omega_k,abc = - sum_{mu in k, nu} gamma_{nu mu} <mu|(r-R_k)_a (r-R_k)_b (r-R_k)_c|nu>.
+// Third 1-D moment about K from the Hermite expansion:
+//   M^3 = (X^3 + 3hX, 3X^2 + 3h, 6X, 6), h = 1/(2p), X = P - K.
+__constant__ int c_o3x[10] = {3, 2, 2, 1, 1, 1, 0, 0, 0, 0};
+__constant__ int c_o3y[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+__constant__ int c_o3z[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(128)
+k_octupoles(BasisDev bd, int pp_begin, int pp_end, const double *__restrict__ dm, double *__restrict__ oct)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB);
+    const int lane = threadIdx.x & 31;
+    const int i = pp_begin + (blockIdx.x * blockDim.x + threadIdx.x);
+    if (pp_begin + (int)((blockIdx.x * blockDim.x + (threadIdx.x & ~31))) >= pp_end) return;  // whole warp out
+    const PPLane pl = load_pp(bd, i, pp_end);
+    const bool mirror = pl.sp.shA != pl.sp.shB;
+    // 1-D moments of order 0 and 3 about A and B, per direction (orders 1, 2 are not needed)
+    double SA[3][LA + 1][LB + 1][4], SB[3][LA + 1][LB + 1][4];
+    {
+        double E[LA + 1][LB + 1][LA + LB + 1];
+        const double h = 0.5 * pl.ip;
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            hermite_E<LA, LB, double>(E, pl.P[d] - pl.A[d], pl.P[d] - pl.B[d], h);
+            const double XA = pl.P[d] - pl.A[d], XB = pl.P[d] - pl.B[d];
+#pragma unroll
+            for (int a = 0; a <= LA; ++a)
+#pragma unroll
+                for (int b = 0; b <= LB; ++b) {
+                    // E^{ab}_t vanishes for t > a + b; the array holds t <= LA + LB only
+                    const double e0 = E[a][b][0];
+                    double e1 = 0.0, e2 = 0.0, e3 = 0.0;
+                    if constexpr (LA + LB >= 1) e1 = (a + b >= 1) ? E[a][b][1] : 0.0;
+                    if constexpr (LA + LB >= 2) e2 = (a + b >= 2) ? E[a][b][2] : 0.0;
+                    if constexpr (LA + LB >= 3) e3 = (a + b >= 3) ? E[a][b][3] : 0.0;
+                    SA[d][a][b][0] = e0;
+                    SA[d][a][b][1] = XA * e0 + e1;
+                    SA[d][a][b][2] = (XA * XA + h) * e0 + 2.0 * XA * e1 + 2.0 * e2;
+                    SA[d][a][b][3] = (XA * XA + 3.0 * h) * XA * e0 + 3.0 * (XA * XA + h) * e1 + 6.0 * XA * e2 + 6.0 * e3;
+                    SB[d][a][b][0] = e0;
+                    SB[d][a][b][1] = XB * e0 + e1;
+                    SB[d][a][b][2] = (XB * XB + h) * e0 + 2.0 * XB * e1 + 2.0 * e2;
+                    SB[d][a][b][3] = (XB * XB + 3.0 * h) * XB * e0 + 3.0 * (XB * XB + h) * e1 + 6.0 * XB * e2 + 6.0 * e3;
+                }
+        }
+    }
+    const double spp = PI * pl.ip;
+    const double coef = pl.active ? pl.cab * spp * sqrt(spp) : 0.0;
+    bool take[5], head;
+    seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
+    double mA[10], mB[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) mA[k] = mB[k] = 0.0;
+#pragma unroll 1
+    for (int ia = 0; ia < NA; ++ia) {
+#pragma unroll 1
+        for (int ib = 0; ib < NB; ++ib) {
+            const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+            const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+            const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
+            const double g_ba = pl.active ? dm[c * bd.nao + r] : 0.0;
+            const double g_ab = pl.active ? dm[r * bd.nao + c] : 0.0;
+#pragma unroll
+            for (int op = 0; op < 10; ++op) {
+                const int ox = c_o3x[op], oy = c_o3y[op], oz = c_o3z[op];
+                mA[op] -= g_ba * SA[0][ax][bx][ox] * SA[1][ay][by][oy] * SA[2][az][bz][oz];
+                mB[op] -= g_ab * SB[0][ax][bx][ox] * SB[1][ay][by][oy] * SB[2][az][bz][oz];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const double va = seg_reduce(coef * mA[k], take);
+        const double vb = seg_reduce(mirror ? coef * mB[k] : 0.0, take);
+        if (head && pl.active) {
+            atomicAdd(oct + 10 * pl.atomA + k, va);
+            if (mirror) atomicAdd(oct + 10 * pl.atomB + k, vb);
+        }
+    }
+}
+
+template <int LA, int LB>
+struct Octupoles {
+    static cudaError_t run(const BasisDev &bd, int pp_begin, int pp_end, const double *dm, double *oct,
+                           cudaStream_t st)
+    {
+        const int grid = (pp_end - pp_begin + 127) / 128;
+        k_octupoles<LA, LB><<<grid, 128, 0, st>>>(bd, pp_begin, pp_end, dm, oct);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_octupoles(const BasisDev &b, int cls, int pp_begin, int pp_end, const double *dm, double *oct,
+                             cudaStream_t st)
+{
+    if (pp_end <= pp_begin) return cudaSuccess;
+    return dispatch_class<Octupoles>(cls, b, pp_begin, pp_end, dm, oct, st);
+}
+
 template <int LA, int LB>
 struct Moments {
     static cudaError_t run(const BasisDev &bd, int pp_begin, int pp_end, const double *dm, const double *phi,

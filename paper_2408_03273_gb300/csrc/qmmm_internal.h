@@ -63,6 +63,9 @@ cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int
 
 // moments / multipoles / Fock / Pulay (mode bits below)
 enum { MOM_MULT = 1, MOM_FOCK = 2, MOM_PULAY = 4 };
+// Mulliken octupoles: oct[natm*10] -= (accumulated; the caller zeroes it)
+cudaError_t launch_octupoles(const BasisDev &b, int cls, int pp_begin, int pp_end, const double *dm, double *oct,
+                             cudaStream_t st);
 cudaError_t launch_moments(const BasisDev &b, int cls, int pp_begin, int pp_end, const double *dm,
                            const double *phi /* natm*20 */, double *mult /* natm*10 */, double *F,
                            double *gqm, int mode, cudaStream_t st);
@@ -85,6 +88,9 @@ struct EwaldDev {
     int nG;
     int kmax[3];
 };
+// Octupole error estimate: err[k] for region-I radii r_lo + k dr, k < n (bins: n + 1 doubles)
+cudaError_t launch_octupole_error(const EwaldDev &e, const double *oct, const double *phi, double r_lo, double dr,
+                                  int n, double *bins, double *err, cudaStream_t st);
 cudaError_t launch_region1_count(const EwaldDev &e, int *blk_count, int *cls_count, int nblk, cudaStream_t st);
 cudaError_t launch_region1_fill(const EwaldDev &e, const int *blk_off, double4_32a *chg, float4 *hi, float4 *lo,
                                 int *idx, int nblk, cudaStream_t st);

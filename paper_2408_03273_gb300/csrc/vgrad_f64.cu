@@ -151,10 +151,25 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                 const double q = ch.w;
                 sdx += q * dx; sdy += q * dy; sdz += q * dz;
                 sex += q * ex; sey += q * ey; sez += q * ez;
-                // per-charge: dE/dq_C += -e0, dE/dC += q e
-                double v0 = warp_sum(-e0), v1 = warp_sum(q * ex), v2 = warp_sum(q * ey), v3 = warp_sum(q * ez);
-                const double mine = lane == 0 ? v1 : lane == 1 ? v2 : lane == 2 ? v3 : v0;
-                if (lane < 4) atomicAdd(acc + 4 * j + lane, mine);
+                // per-charge sums over the 32 primitive pairs of (dE/dC_x, dE/dC_y, dE/dC_z, dE/dq) =
+                // (q e_x, q e_y, q e_z, -e0): halve the four values twice (each lane keeps one
+                // component summed over 4 lanes), then a 3-step butterfly; lane 8c ends with
+                // component c.  6 FP64 additions instead of 4 full warp sums (20).
+                {
+                    const double v0 = q * ex, v1 = q * ey, v2 = q * ez, v3 = -e0;
+                    const bool up = lane & 16;
+                    double k0 = up ? v2 : v0, k1 = up ? v3 : v1;
+                    const double s0 = up ? v0 : v2, s1 = up ? v1 : v3;
+                    k0 += __shfl_xor_sync(FULL, s0, 16);
+                    k1 += __shfl_xor_sync(FULL, s1, 16);
+                    const bool up8 = lane & 8;
+                    double k = up8 ? k1 : k0;
+                    k += __shfl_xor_sync(FULL, up8 ? k0 : k1, 8);
+                    k += __shfl_xor_sync(FULL, k, 4);
+                    k += __shfl_xor_sync(FULL, k, 2);
+                    k += __shfl_xor_sync(FULL, k, 1);
+                    if ((lane & 7) == 0) atomicAdd(acc + 4 * j + (((lane >> 4) << 1) | ((lane >> 3) & 1)), k);
+                }
             }
         }
         // dE/dA = -(sd + a/p se), dE/dB = sd - b/p se

@@ -49,6 +49,12 @@ class Handle:
     def potential(self, like=None):
         return L.qmmm_get_potential(self.h, like=like)
 
+    def octupole_error(self, dm, r_lo, dr, n, want_octupoles=False):
+        return L.qmmm_octupole_error(self.h, dm, r_lo, dr, n, want_octupoles=want_octupoles)
+
+    def rcut_search(self, dm, r_lo, dr, n, eps):
+        return L.qmmm_rcut_search(self.h, dm, r_lo, dr, n, eps)
+
     def autotune(self, flags: int = 0):
         """Time the region-I class sweeps on this geometry and keep the fastest block shapes and SM
         split (flags: QMMM_TUNE_V / QMMM_TUNE_FORCES / QMMM_TUNE_BOTH_PRECISIONS; 0 = V and forces
