@@ -494,6 +494,24 @@ int run_classes(qmmm_handle *h, int kind, F launch)
     return QMMM_OK;
 }
 
+// One kernel per non-empty angular class, all classes concurrently on the class streams (forked
+// from and joined back into the handle's stream), each with its full grid.
+template <typename F>
+int fork_classes(qmmm_handle *h, F launch)
+{
+    CUDA_TRY(cudaEventRecord(h->fork, h->stream));
+    for (int c = 0; c < NCLASS; ++c) {
+        const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
+        if (p1 <= p0) continue;
+        CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
+        CUDA_TRY(launch(c, p0, p1, h->side[c]));
+        CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
+    }
+    for (int c = 0; c < NCLASS; ++c)
+        if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join[c], 0));
+    return QMMM_OK;
+}
+
 // One class sweep of the given kind over region-I charges [c0, c1).
 cudaError_t launch_sweep(const qmmm_handle *h, int kind, int cls, int p0, int p1, int c0, int c1, int share,
                          int variant, const double *ddm, double *V, double *gqm, double *gchg, cudaStream_t cs)
@@ -1015,12 +1033,10 @@ static int compute_multipoles(qmmm_handle *h, const double *ddm, double *F, int 
     CUDA_TRY(cudaMemcpyAsync(h->mult.p, h->mult_init.p, 10 * (size_t)h->natm * sizeof(double), cudaMemcpyDeviceToDevice, st));
     const BasisDev b = h->basis();
     const int mode = MOM_MULT | (F ? MOM_FOCK : 0) | extra_mode;
-    for (int cls = 0; cls < NCLASS; ++cls) {
-        const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
-        if (p1 <= p0) continue;
-        CUDA_TRY(launch_moments(b, cls, p0, p1, ddm, h->phi.p, h->mult.p, F, h->gqm.p, mode, st));
-    }
-    return QMMM_OK;
+    // the classes are small kernels (one lane per primitive pair): run them concurrently
+    return fork_classes(h, [&](int cls, int p0, int p1, cudaStream_t cs) {
+        return launch_moments(b, cls, p0, p1, ddm, h->phi.p, h->mult.p, F, h->gqm.p, mode, cs);
+    });
 }
 
 int qmmm_ewald(qmmm_handle *h, const double *dmat, double *E_II, double *multipoles, double *F_II)
@@ -1160,10 +1176,10 @@ int qmmm_octupole_error(qmmm_handle *h, const double *dmat, double r_lo, double 
         return rc;
     CUDA_TRY(cudaMemsetAsync(h->oct.p, 0, 10 * (size_t)h->natm * sizeof(double), st));
     const BasisDev b = h->basis();
-    for (int cls = 0; cls < NCLASS; ++cls) {
-        const int p0 = h->class_off[cls], p1 = h->class_off[cls + 1];
-        if (p1 > p0) CUDA_TRY(launch_octupoles(b, cls, p0, p1, ddm, h->oct.p, st));
-    }
+    if ((rc = fork_classes(h, [&](int cls, int p0, int p1, cudaStream_t cs) {
+             return launch_octupoles(b, cls, p0, p1, ddm, h->oct.p, cs);
+         })))
+        return rc;
     CUDA_TRY(launch_octupole_error(h->ewald(), h->oct.p, h->phi.p, r_lo, dr, n, h->oct_bins.p, h->oct_err.p, st));
     if ((rc = copy_out(h, err, h->oct_err.p, (size_t)n))) return rc;
     if ((rc = copy_out(h, octupoles, h->oct.p, 10 * (size_t)h->natm))) return rc;
