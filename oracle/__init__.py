@@ -60,6 +60,7 @@ def lib():
                 "oracle_enucmm": (d, [i, dp, dp, i, dp, dp, dp, dp, dp, dp]),
                 "oracle_multipoles": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, dp, i, dp, dp]),
                 "oracle_octupoles": (None, [i, ip, ip, ip, ip, dp, dp, i, dp, i, dp, dp]),
+                "oracle_qmqm": (None, [i, dp, dp, dp, d, d, ip, dp, dp, dp]),
                 "oracle_fock_ii": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp]),
                 "oracle_pulay": (None, [i, ip, ip, ip, ip, dp, dp, dp, dp, i, i, dp, dp]),
                 "oracle_tensor": (None, [i, d, dp, dp]),
@@ -220,6 +221,35 @@ def octupole_error(s, radii, dm=None) -> np.ndarray:
                                float(s.ewald_alpha), _ip(km), EW_ALL, _dp(phi))
         out.append(float(np.sum(MULT3[None, :] * Om * phi[:, 10:20])))
     return np.array(out)
+
+
+def qmqm(s, M=None, alpha=None, kmax=None, ewald_rcut=None):
+    """QM-QM periodic-image multipole energy (Eq. 5, in the Ewald form of Eq. 6) for multipoles M
+    (natm x 10; default: the Mulliken multipoles of s): (E, u, grad) with u = dE/dM per stored
+    component / W10 (natm x 10) and grad = dE/dR_QM at fixed multipoles (natm x 3).  alpha, kmax
+    and ewald_rcut default to the system's."""
+    M = _d(multipoles(s) if M is None else M)
+    E = np.zeros(1)
+    u = np.zeros((s.natm, 10))
+    g = np.zeros((s.natm, 3))
+    km = _i(s.kmax if kmax is None else kmax)
+    lib().oracle_qmqm(s.natm, _dp(_d(s.atom_xyz)), _dp(M), _dp(_d(s.box)),
+                      float(ewald_rc(s) if ewald_rcut is None else ewald_rcut),
+                      float(s.ewald_alpha if alpha is None else alpha), _ip(km), _dp(E), _dp(u), _dp(g))
+    return float(E[0]), u, g
+
+
+def qm_images(s, dm=None, **conv):
+    """QM-QM periodic-image term at density dm (Eq. 5 / Eq. 6): E, its gradient dE/dR_QM at fixed
+    density (image tensors at fixed multipoles plus the multipoles' dependence on the basis
+    positions, the Pulay term of Eq. 15 with the image potential u) and its Fock matrix
+    dE/dgamma (Eqs. 11-14 with u in place of the MM potential).  conv: alpha, kmax, ewald_rcut."""
+    dm = _d(s.dm if dm is None else dm)
+    M = multipoles(s, dm)
+    E, u, g = qmqm(s, M, **conv)
+    b = _Basis(s)
+    lib().oracle_pulay(*b.args(), _dp(_d(s.atom_xyz)), _dp(_d(u)), 10, s.nao, _dp(dm), _dp(g))
+    return {"E": E, "dE_dRqm": g, "F": fock_ii(s, u), "u": u, "M": M}
 
 
 def ewald_phi(s, mode: int = EW_ALL) -> np.ndarray:

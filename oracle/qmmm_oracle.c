@@ -923,6 +923,131 @@ void oracle_ewald_mm(int natm, const double *qm_xyz, const double *M, int nmm, c
 
 /* Tensor part of dE/dR_QM: dE/dR_j,x = sum_c W_c M_j,c d_x phi_j,c with d_x phi_0 = phi_x,
  * d_x phi_a = 2 phi_ax, d_x phi_ab = 3 phi_abx (phi from oracle_ewald_phi).  Accumulates. */
+/* QM-QM periodic-image multipole energy (Eq. 5 and its Ewald form in Eq. 6, readings in the test
+ * file): with the image tensor P_ji = sum_{L != 0} T(R_j - R_i + L), evaluated as the Ewald sum
+ * (erfc real space over images within ewald_rc, reciprocal sum over the kmax cube, self terms
+ * -2 kappa/sqrt(pi) and +(2/3) kappa^3/sqrt(pi) delta_ab for i = j) minus the L = 0 point tensor
+ * for i != j, and the pair energy
+ *   e(j,i) = Q_j Q_i P + 2 mu_j.Q_i P_a + 2 theta_j:Q_i P_ab - 2 mu_j mu_i : P_ab,
+ * E = 1/2 sum_{j,i} e(j,i) - pi/(2 V kappa^2) (sum_j Q_j)^2.  Outputs: E[0]; u[natm*10], the
+ * derivative of E with respect to each stored multipole component divided by its weight W10 (the
+ * potential that plays the role of phi for the Fock and Pulay terms); grad[natm*3], dE/dR at fixed
+ * multipoles.  M[natm*10] in the stored order (Q, mu xyz, theta xx xy xz yy yz zz). */
+void oracle_qmqm(int natm, const double *qm_xyz, const double *M, const double *box, double ewald_rc, double kappa,
+                 const int *kmax, double *E, double *u, double *grad)
+{
+    const double V = box[0] * box[1] * box[2], sp = sqrt(OR_PI);
+    static const int P2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    int mrc[3];
+    ew_images(box, ewald_rc, mrc);
+    double etot = 0.0, qsum = 0.0;
+    memset(u, 0, sizeof(double) * natm * 10);
+    memset(grad, 0, sizeof(double) * natm * 3);
+    for (int j = 0; j < natm; j++) qsum += M[10 * j];
+    for (int j = 0; j < natm; j++)
+        for (int i = 0; i < natm; i++) {
+            double P[20], T[20];
+            memset(P, 0, sizeof(P));
+            double d0[3];
+            for (int x = 0; x < 3; x++) d0[x] = qm_xyz[3 * j + x] - qm_xyz[3 * i + x];
+            /* real space: erfc-screened tensors over images within the Ewald cutoff */
+            for (int nx = -mrc[0]; nx <= mrc[0]; nx++)
+                for (int ny = -mrc[1]; ny <= mrc[1]; ny++)
+                    for (int nz = -mrc[2]; nz <= mrc[2]; nz++) {
+                        if (i == j && nx == 0 && ny == 0 && nz == 0) continue;
+                        double d[3] = {d0[0] - nx * box[0], d0[1] - ny * box[1], d0[2] - nz * box[2]};
+                        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= ewald_rc * ewald_rc) continue;
+                        oracle_tensor(1, kappa, d, T);
+                        for (int k = 0; k < 20; k++) P[k] += T[k];
+                    }
+            /* reciprocal space: T = f, f_a, 1/2 f_ab, 1/6 f_abc of (4 pi / V) sum g(G) cos(G.d) */
+            for (int nx = -kmax[0]; nx <= kmax[0]; nx++)
+                for (int ny = -kmax[1]; ny <= kmax[1]; ny++)
+                    for (int nz = -kmax[2]; nz <= kmax[2]; nz++) {
+                        if (nx == 0 && ny == 0 && nz == 0) continue;
+                        double G[3] = {2.0 * OR_PI * nx / box[0], 2.0 * OR_PI * ny / box[1], 2.0 * OR_PI * nz / box[2]};
+                        double G2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+                        double g = 4.0 * OR_PI / V * exp(-G2 / (4.0 * kappa * kappa)) / G2;
+                        double ph = G[0] * d0[0] + G[1] * d0[1] + G[2] * d0[2], cs = cos(ph), sn = sin(ph);
+                        P[0] += g * cs;
+                        for (int a = 0; a < 3; a++) P[1 + a] -= g * G[a] * sn;
+                        for (int k = 0; k < 6; k++) P[4 + k] -= 0.5 * g * G[P2[k][0]] * G[P2[k][1]] * cs;
+                        static const int P3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                                                      {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+                        for (int k = 0; k < 10; k++)
+                            P[10 + k] += g * G[P3[k][0]] * G[P3[k][1]] * G[P3[k][2]] * sn / 6.0;
+                    }
+            if (i == j) {
+                /* self terms: Taylor coefficients of -erf(kappa r)/r at r = 0 */
+                P[0] += -2.0 * kappa / sp;
+                P[4] += 2.0 / 3.0 * kappa * kappa * kappa / sp;
+                P[7] += 2.0 / 3.0 * kappa * kappa * kappa / sp;
+                P[9] += 2.0 / 3.0 * kappa * kappa * kappa / sp;
+            } else {
+                /* the reference-cell pair is the QM calculation's: remove its point interaction */
+                oracle_tensor(0, 0.0, d0, T);
+                for (int k = 0; k < 20; k++) P[k] -= T[k];
+            }
+            /* full symmetric 3x3 views of P_ab and theta, 3x3x3 of P_abc */
+            double Pab[3][3], thj[3][3], Pabc[3][3][3];
+            for (int k = 0; k < 6; k++) {
+                int a = P2[k][0], b = P2[k][1];
+                Pab[a][b] = Pab[b][a] = P[4 + k];
+                thj[a][b] = thj[b][a] = M[10 * j + 4 + k];
+            }
+            {
+                static const int P3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                                              {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+                for (int k = 0; k < 10; k++) {
+                    int a = P3[k][0], b = P3[k][1], c = P3[k][2];
+                    Pabc[a][b][c] = Pabc[a][c][b] = Pabc[b][a][c] = Pabc[b][c][a] = Pabc[c][a][b] = Pabc[c][b][a] = P[10 + k];
+                }
+            }
+            const double Qj = M[10 * j], Qi = M[10 * i];
+            const double *mj = M + 10 * j + 1, *mi = M + 10 * i + 1;
+            double e = Qj * Qi * P[0];
+            for (int a = 0; a < 3; a++) e += 2.0 * mj[a] * Qi * P[1 + a];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) e += 2.0 * thj[a][b] * Qi * Pab[a][b] - 2.0 * mj[a] * mi[b] * Pab[a][b];
+            etot += 0.5 * e;
+            /* conjugate potentials: 1/2 de/dM_j (first slot) and 1/2 de/dM_i (second slot) */
+            u[10 * j] += 0.5 * Qi * P[0];
+            for (int a = 0; a < 3; a++) {
+                double t = 2.0 * Qi * P[1 + a];
+                for (int b = 0; b < 3; b++) t -= 2.0 * mi[b] * Pab[a][b];
+                u[10 * j + 1 + a] += 0.5 * t;
+            }
+            for (int k = 0; k < 6; k++) u[10 * j + 4 + k] += 0.5 * 2.0 * Qi * P[4 + k];
+            {
+                double t = Qj * P[0];
+                for (int a = 0; a < 3; a++) t += 2.0 * mj[a] * P[1 + a];
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++) t += 2.0 * thj[a][b] * Pab[a][b];
+                u[10 * i] += 0.5 * t;
+                for (int b = 0; b < 3; b++) {
+                    double s2 = 0.0;
+                    for (int a = 0; a < 3; a++) s2 -= 2.0 * mj[a] * Pab[a][b];
+                    u[10 * i + 1 + b] += 0.5 * s2;
+                }
+            }
+            /* gradient at fixed multipoles: d/dd of e, d = R_j - R_i (i = j terms do not move) */
+            if (i != j)
+                for (int c = 0; c < 3; c++) {
+                    double g = Qj * Qi * P[1 + c];
+                    for (int a = 0; a < 3; a++) g += 2.0 * mj[a] * Qi * 2.0 * Pab[a][c];
+                    for (int a = 0; a < 3; a++)
+                        for (int b = 0; b < 3; b++)
+                            g += 2.0 * thj[a][b] * Qi * 3.0 * Pabc[a][b][c] - 2.0 * mj[a] * mi[b] * 3.0 * Pabc[a][b][c];
+                    grad[3 * j + c] += 0.5 * g;
+                    grad[3 * i + c] -= 0.5 * g;
+                }
+        }
+    /* neutralising background for a charged QM cell */
+    etot += -OR_PI / (2.0 * V * kappa * kappa) * qsum * qsum;
+    for (int j = 0; j < natm; j++) u[10 * j] += -OR_PI / (V * kappa * kappa) * qsum;
+    E[0] = etot;
+}
+
 void oracle_tensor_grad_qm(int natm, const double *M, const double *phi, double *dRqm)
 {
     static const int I2[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
