@@ -154,6 +154,18 @@ int qmmm_get_potential(qmmm_handle *h, double *v);
  * Returns the number of values written (2). */
 int qmmm_last_timing(const qmmm_handle *h, double *out);
 
+/* QM-QM periodic images (Eq. 5, summed by Ewald as in Eq. 6): the interaction of the QM
+ * Mulliken multipoles at density dm with all their periodic images, minus the reference-cell
+ * pairs (the QM calculation's own), with the tin-foil boundary and, for a charged QM cell, the
+ * neutralising background -pi/(2 V kappa^2) (sum Q)^2:
+ *   E = 1/2 sum_{j,i} sum_{L != 0} [Q_j Q_i T + 2 mu_j.Q_i T_a + 2 theta_j:Q_i T_ab - 2 mu_j mu_i:T_ab]
+ * at R_j - R_i + L (readings: the dipole-charge and quadrupole-charge weights 2 and the
+ * dipole-dipole sign follow from the lattice energy of point multipoles; Eq. 5 prints 1, 1, +2).
+ * E[1]; dE_dRqm[natm*3], its gradient at fixed density (image tensors and the Pulay term of the
+ * moving basis); F[nao*nao], dE/dgamma (nullable).  Not part of E from qmmm_energy: add it when the
+ * QM cell's images are to be included.  Arrays: host or device memory. */
+int qmmm_qm_images(qmmm_handle *h, const double *dm, double *E, double *dE_dRqm, double *F);
+
 /* Octupole error estimate of the multipole truncation (Sec. "Error Control"): the leading error
  * of keeping region-II interactions to quadrupole order is the charge-octupole interaction
  *   Err(R) = sum_{i in II} sum_j sum_abc Omega_j,abc q_i T_ji,abc,

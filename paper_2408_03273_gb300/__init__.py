@@ -43,6 +43,7 @@ from ._lib import (  # noqa: F401
     qmmm_nao,
     qmmm_nuclear_mm_energy_static,
     qmmm_octupole_error,
+    qmmm_qm_images,
     qmmm_rcut_search,
     qmmm_set_positions,
     qmmm_set_precision,

@@ -59,7 +59,7 @@ _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
-           "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
+           "qmmm_qm_images", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
            "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
 
@@ -92,6 +92,7 @@ def load(build_if_needed: bool = True):
         "qmmm_nao": (c_int, [c_void_p]),
         "qmmm_get_potential": (c_int, [c_void_p, c_void_p]),
         "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
+        "qmmm_qm_images": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "qmmm_octupole_error": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p]),
         "qmmm_rcut_search": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, P(c_double),
                                      P(c_double)]),
@@ -266,6 +267,16 @@ def qmmm_last_timing(h):
     out = (c_double * 2)()
     load().qmmm_last_timing(h, out)
     return float(out[0]), float(out[1])
+
+
+def qmmm_qm_images(h, dm, want_F=False):
+    """QM-QM periodic-image energy, its gradient dE/dR_QM and (optionally) its Fock matrix."""
+    info = qmmm_get_info(h)
+    E = _out(None, (1,), dm)
+    g = _out(None, (info["natm"], 3), dm)
+    F = _out(None, (info["nao"], info["nao"]), dm) if want_F else None
+    _check(load().qmmm_qm_images(h, _ptr(dm), _ptr(E), _ptr(g), _ptr(F)), "qmmm_qm_images")
+    return E, g, F
 
 
 def qmmm_octupole_error(h, dm, r_lo, dr, n, err=None, octupoles=None, want_octupoles=False):

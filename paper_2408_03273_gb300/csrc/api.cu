@@ -162,6 +162,7 @@ struct qmmm_handle {
     int tuned_mask = 0, tuned_nI = 0;
     DBuf<double> tune_V, tune_dm, tune_gqm, tune_gchg;  // autotuner scratch
     DBuf<double> oct, oct_bins, oct_err;                  // octupole error estimate
+    DBuf<double> qmq_P, qmq_u, qmq_g, qmq_E, qmq_F;       // QM-QM periodic images
     EwaldBuf ew;
     int nblk_mm = 1;
 
@@ -1158,6 +1159,40 @@ int qmmm_get_potential(qmmm_handle *h, double *v)
     int rc;
     if ((rc = copy_out(h, v, h->phi.p, 20 * (size_t)h->natm))) return rc;
     return check_device_errors(h);
+}
+
+int qmmm_qm_images(qmmm_handle *h, const double *dmat, double *E, double *dE_dRqm, double *F)
+{
+    if (!h || !dmat) return fail(QMMM_ERR_ARG, "null handle or density");
+    cudaStream_t st = h->stream;
+    int rc;
+    const double *ddm;
+    const size_t n2 = (size_t)h->nao * h->nao, na = (size_t)h->natm;
+    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    if ((rc = h->qmq_P.ensure(na * na * 20)) || (rc = h->qmq_u.ensure(na * 20)) || (rc = h->qmq_g.ensure(na * 3)) ||
+        (rc = h->qmq_E.ensure(1)))
+        return rc;
+    double *Fd = nullptr;
+    if (F) {
+        if ((rc = h->qmq_F.ensure(n2))) return rc;
+        CUDA_TRY(cudaMemsetAsync(h->qmq_F.p, 0, n2 * sizeof(double), st));
+        Fd = h->qmq_F.p;
+    }
+    // Mulliken multipoles at this density, then the image tensors, energy, potentials, gradient
+    if ((rc = compute_multipoles(h, ddm, nullptr, 0))) return rc;
+    CUDA_TRY(launch_qm_images(h->ewald(), h->gfac.p, h->mult.p, h->qmq_P.p, h->qmq_E.p, h->qmq_u.p, h->qmq_g.p, st));
+    // the multipoles move with the basis (Pulay) and depend on gamma (Fock): the moment kernels
+    // with the image potential in place of the MM one
+    const BasisDev b = h->basis();
+    const int mode = MOM_PULAY | (Fd ? MOM_FOCK : 0);
+    if ((rc = fork_classes(h, [&](int cls, int p0, int p1, cudaStream_t cs) {
+             return launch_moments(b, cls, p0, p1, ddm, h->qmq_u.p, h->mult.p, Fd, h->qmq_g.p, mode, cs);
+         })))
+        return rc;
+    if ((rc = copy_out(h, E, h->qmq_E.p, 1))) return rc;
+    if ((rc = copy_out(h, dE_dRqm, h->qmq_g.p, 3 * na))) return rc;
+    if (F && (rc = copy_out(h, F, h->qmq_F.p, n2))) return rc;
+    return finish(h, 0);
 }
 
 int qmmm_octupole_error(qmmm_handle *h, const double *dmat, double r_lo, double dr, int n, double *err,

@@ -1285,6 +1285,205 @@ cudaError_t launch_octupole_error(const EwaldDev &e0, const double *oct, const d
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// QM-QM periodic images (Eq. 5 in the Ewald form of Eq. 6)
+//   P_ji = sum_{L != 0} T(R_j - R_i + L) (20 Taylor components), by Ewald: erfc real space over
+//   images within the Ewald cutoff, reciprocal sum over the half space (2 g(G) weights), self
+//   terms -2 kappa/sqrt(pi) and +(2/3) kappa^3/sqrt(pi) delta_ab for i = j, minus the L = 0 point
+//   tensor for i != j (the reference-cell pair belongs to the QM calculation).
+//   E = 1/2 sum_{j,i} [Q_j Q_i P + 2 mu_j.Q_i P_a + 2 theta_j:Q_i P_ab - 2 mu_j mu_i : P_ab]
+//       - pi/(2 V kappa^2) (sum Q)^2.
+// ---------------------------------------------------------------------------------------------
+__constant__ int c_p2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+__constant__ int c_p3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                                {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+
+// one block per ordered pair (i = blockIdx.x, j = blockIdx.y); P[(j*natm + i)*20 + c]
+__global__ void __launch_bounds__(128) k_qmqm_pairs(EwaldDev e, const double *gfac, double *P)
+{
+    __shared__ double scratch[4 * 20];
+    const int i = blockIdx.x, j = blockIdx.y;
+    const double d0[3] = {e.qm_xyz[3 * j] - e.qm_xyz[3 * i], e.qm_xyz[3 * j + 1] - e.qm_xyz[3 * i + 1],
+                          e.qm_xyz[3 * j + 2] - e.qm_xyz[3 * i + 2]};
+    double acc[20];
+#pragma unroll
+    for (int c = 0; c < 20; ++c) acc[c] = 0.0;
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double w = gfac[k];
+        if (w == 0.0) continue;
+        const double G[3] = {TWO_PI * (k / (NY * NZ)) / e.box[0], TWO_PI * ((k / NZ) % NY - ky) / e.box[1],
+                             TWO_PI * (k % NZ - kz) / e.box[2]};
+        double sn, cs;
+        sincos(G[0] * d0[0] + G[1] * d0[1] + G[2] * d0[2], &sn, &cs);
+        acc[0] += w * cs;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[1 + a] -= w * G[a] * sn;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[4 + c] -= 0.5 * w * G[c_p2[c][0]] * G[c_p2[c][1]] * cs;
+#pragma unroll
+        for (int c = 0; c < 10; ++c)
+            acc[10 + c] += w * G[c_p3[c][0]] * G[c_p3[c][1]] * G[c_p3[c][2]] * sn * (1.0 / 6.0);
+    }
+    if (threadIdx.x == 0) {
+        double T[20];
+        const double rc2 = e.ewald_rc * e.ewald_rc;
+        double n0[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) n0[x] = rint(d0[x] / e.box[x]);
+        for (int a = -e.img[0] - 1; a <= e.img[0] + 1; ++a)
+            for (int b = -e.img[1] - 1; b <= e.img[1] + 1; ++b)
+                for (int c = -e.img[2] - 1; c <= e.img[2] + 1; ++c) {
+                    const double L[3] = {(n0[0] + a) * e.box[0], (n0[1] + b) * e.box[1], (n0[2] + c) * e.box[2]};
+                    if (i == j && L[0] == 0.0 && L[1] == 0.0 && L[2] == 0.0) continue;
+                    const double x = d0[0] - L[0], y = d0[1] - L[1], z = d0[2] - L[2];
+                    const double r2 = x * x + y * y + z * z;
+                    if (r2 >= rc2) continue;
+                    double f, g1, g2, g3;
+                    screened_radial(r2, e.alpha, f, g1, g2, g3);
+                    radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+#pragma unroll
+                    for (int k = 0; k < 20; ++k) acc[k] += T[k];
+                }
+        if (i == j) {
+            const double k1 = 2.0 * e.alpha / 1.7724538509055160273, k3 = k1 * e.alpha * e.alpha / 3.0;
+            acc[0] -= k1;
+            acc[4] += k3;
+            acc[7] += k3;
+            acc[9] += k3;
+        } else {
+            double f, g1, g2, g3;
+            point_radial(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2], f, g1, g2, g3);
+            radial_tensor(f, g1, g2, g3, d0[0], d0[1], d0[2], T, 3);
+#pragma unroll
+            for (int k = 0; k < 20; ++k) acc[k] -= T[k];
+        }
+    }
+    block_reduce_store<20>(acc, P + ((size_t)j * gridDim.x + i) * 20, scratch);
+}
+
+// Energy, image potentials u (dE/dM per stored component / W10, 20-stride like phi) and the
+// gradient at fixed multipoles, from the pair tensors.  One block; each atom's sums in a fixed order.
+__global__ void k_qmqm_contract(int natm, const double *P, const double *M, double bg, double *E, double *u20,
+                                double *grad)
+{
+    __shared__ double ws[32];
+    double esum = 0.0;
+    for (int k = threadIdx.x; k < natm; k += blockDim.x) {
+        double uk[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, gk[3] = {0.0, 0.0, 0.0};
+        for (int o = 0; o < natm; ++o) {
+            // (j, i) = (k, o): first slot is k
+            for (int pass = 0; pass < 2; ++pass) {
+                const int j = pass == 0 ? k : o, i = pass == 0 ? o : k;
+                const double *p = P + ((size_t)j * natm + i) * 20;
+                double Pab[3][3], thj[3][3];
+                for (int c = 0; c < 6; ++c) {
+                    const int a = c_p2[c][0], b = c_p2[c][1];
+                    Pab[a][b] = Pab[b][a] = p[4 + c];
+                    thj[a][b] = thj[b][a] = M[10 * j + 4 + c];
+                }
+                const double Qj = M[10 * j], Qi = M[10 * i];
+                const double *mj = M + 10 * j + 1, *mi = M + 10 * i + 1;
+                if (pass == 0) {
+                    // the pair energy, counted once per ordered pair
+                    double e2 = Qj * Qi * p[0];
+                    for (int a = 0; a < 3; ++a) e2 += 2.0 * mj[a] * Qi * p[1 + a];
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            e2 += 2.0 * thj[a][b] * Qi * Pab[a][b] - 2.0 * mj[a] * mi[b] * Pab[a][b];
+                    esum += 0.5 * e2;
+                    // k in the first slot
+                    uk[0] += 0.5 * Qi * p[0];
+                    for (int a = 0; a < 3; ++a) {
+                        double t = 2.0 * Qi * p[1 + a];
+                        for (int b = 0; b < 3; ++b) t -= 2.0 * mi[b] * Pab[a][b];
+                        uk[1 + a] += 0.5 * t;
+                    }
+                    for (int c = 0; c < 6; ++c) uk[4 + c] += Qi * p[4 + c];
+                    // gradient: d/dR_j of e(j, i) with R_i fixed, for i != j
+                    if (i != j)
+                        for (int c = 0; c < 3; ++c) {
+                            double g = Qj * Qi * p[1 + c];
+                            for (int a = 0; a < 3; ++a) g += 4.0 * mj[a] * Qi * Pab[a][c];
+                            for (int a = 0; a < 3; ++a)
+                                for (int b = 0; b < 3; ++b) {
+                                    // P_abc from the 10 stored components
+                                    int s3[3] = {a, b, c};
+                                    // sort the three indices
+                                    if (s3[0] > s3[1]) { int t = s3[0]; s3[0] = s3[1]; s3[1] = t; }
+                                    if (s3[1] > s3[2]) { int t = s3[1]; s3[1] = s3[2]; s3[2] = t; }
+                                    if (s3[0] > s3[1]) { int t = s3[0]; s3[0] = s3[1]; s3[1] = t; }
+                                    int idx = 0;
+                                    for (int q = 0; q < 10; ++q)
+                                        if (c_p3[q][0] == s3[0] && c_p3[q][1] == s3[1] && c_p3[q][2] == s3[2]) idx = q;
+                                    g += (6.0 * thj[a][b] * Qi - 6.0 * mj[a] * mi[b]) * p[10 + idx];
+                                }
+                            gk[c] += 0.5 * g;
+                        }
+                } else {
+                    // k in the second slot of e(j = o, i = k)
+                    double t = Qj * p[0];
+                    for (int a = 0; a < 3; ++a) t += 2.0 * mj[a] * p[1 + a];
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) t += 2.0 * thj[a][b] * Pab[a][b];
+                    uk[0] += 0.5 * t;
+                    for (int b = 0; b < 3; ++b) {
+                        double s2 = 0.0;
+                        for (int a = 0; a < 3; ++a) s2 -= 2.0 * mj[a] * Pab[a][b];
+                        uk[1 + b] += 0.5 * s2;
+                    }
+                    // gradient: d/dR_i of e(j, i) = -d/dd
+                    if (i != j)
+                        for (int c = 0; c < 3; ++c) {
+                            double g = Qj * Qi * p[1 + c];
+                            for (int a = 0; a < 3; ++a) g += 4.0 * mj[a] * Qi * Pab[a][c];
+                            for (int a = 0; a < 3; ++a)
+                                for (int b = 0; b < 3; ++b) {
+                                    int s3[3] = {a, b, c};
+                                    if (s3[0] > s3[1]) { int t2 = s3[0]; s3[0] = s3[1]; s3[1] = t2; }
+                                    if (s3[1] > s3[2]) { int t2 = s3[1]; s3[1] = s3[2]; s3[2] = t2; }
+                                    if (s3[0] > s3[1]) { int t2 = s3[0]; s3[0] = s3[1]; s3[1] = t2; }
+                                    int idx = 0;
+                                    for (int q = 0; q < 10; ++q)
+                                        if (c_p3[q][0] == s3[0] && c_p3[q][1] == s3[1] && c_p3[q][2] == s3[2]) idx = q;
+                                    g += (6.0 * thj[a][b] * Qi - 6.0 * mj[a] * mi[b]) * p[10 + idx];
+                                }
+                            gk[c] -= 0.5 * g;
+                        }
+                }
+            }
+        }
+        double qsum = 0.0;
+        for (int o = 0; o < natm; ++o) qsum += M[10 * o];
+        uk[0] += 2.0 * bg * qsum;
+        for (int c = 0; c < 10; ++c) u20[20 * k + c] = uk[c];
+        for (int c = 10; c < 20; ++c) u20[20 * k + c] = 0.0;
+        for (int c = 0; c < 3; ++c) grad[3 * k + c] = gk[c];
+    }
+    esum = warp_sum(esum);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = esum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0, qsum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        for (int o = 0; o < natm; ++o) qsum += M[10 * o];
+        E[0] = t + bg * qsum * qsum;
+    }
+}
+
+cudaError_t launch_qm_images(const EwaldDev &e, const double *gfac, const double *mult, double *P, double *E,
+                             double *u20, double *grad, cudaStream_t st)
+{
+    if (e.natm <= 0) return cudaSuccess;
+    k_qmqm_pairs<<<dim3(e.natm, e.natm), 128, 0, st>>>(e, gfac, P);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const double V = e.box[0] * e.box[1] * e.box[2];
+    k_qmqm_contract<<<1, 256, 0, st>>>(e.natm, P, mult, -PI / (2.0 * V * e.alpha * e.alpha), E, u20, grad);
+    return cudaGetLastError();
+}
+
 __global__ void k_scatter_region(const int *rI_idx, int nI, const double *gchg, double *dq, double *dR)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;

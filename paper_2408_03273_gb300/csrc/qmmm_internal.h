@@ -91,6 +91,10 @@ struct EwaldDev {
 // Octupole error estimate: err[k] for region-I radii r_lo + k dr, k < n (bins: n + 1 doubles)
 cudaError_t launch_octupole_error(const EwaldDev &e, const double *oct, const double *phi, double r_lo, double dr,
                                   int n, double *bins, double *err, cudaStream_t st);
+// QM-QM periodic images: pair tensors P[natm*natm*20] (scratch), energy E[1], image potentials
+// u20[natm*20] (components 10..19 zero), gradient at fixed multipoles grad[natm*3]
+cudaError_t launch_qm_images(const EwaldDev &e, const double *gfac, const double *mult, double *P, double *E,
+                             double *u20, double *grad, cudaStream_t st);
 cudaError_t launch_region1_count(const EwaldDev &e, int *blk_count, int *cls_count, int nblk, cudaStream_t st);
 cudaError_t launch_region1_fill(const EwaldDev &e, const int *blk_off, double4_32a *chg, float4 *hi, float4 *lo,
                                 int *idx, int nblk, cudaStream_t st);

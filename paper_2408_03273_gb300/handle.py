@@ -49,6 +49,9 @@ class Handle:
     def potential(self, like=None):
         return L.qmmm_get_potential(self.h, like=like)
 
+    def qm_images(self, dm, want_F=False):
+        return L.qmmm_qm_images(self.h, dm, want_F=want_F)
+
     def octupole_error(self, dm, r_lo, dr, n, want_octupoles=False):
         return L.qmmm_octupole_error(self.h, dm, r_lo, dr, n, want_octupoles=want_octupoles)
 
