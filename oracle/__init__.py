@@ -252,6 +252,21 @@ def qm_images(s, dm=None, **conv):
     return {"E": E, "dE_dRqm": g, "F": fock_ii(s, u), "u": u, "M": M}
 
 
+def aspc_coefficients(K: int) -> np.ndarray:
+    """Predictor weights of the always-stable predictor-corrector density extrapolation used for
+    the MD runs (Sec. "Common Setup", from K+1 previous steps; Kolafa's closed form):
+      B_j = (-1)^(j+1) j C(2K+2, K+1-j) / C(2K, K),  j = 1..K+1,
+    so that gamma_pred(t) = sum_j B_j gamma(t - j)."""
+    from math import comb
+    return np.array([(-1) ** (j + 1) * j * comb(2 * K + 2, K + 1 - j) / comb(2 * K, K) for j in range(1, K + 2)])
+
+
+def aspc_predict(history) -> np.ndarray:
+    """history[j-1] = gamma(t - j), most recent first."""
+    B = aspc_coefficients(len(history) - 1)
+    return sum(b * np.asarray(h, dtype=np.float64) for b, h in zip(B, history))
+
+
 def ewald_phi(s, mode: int = EW_ALL) -> np.ndarray:
     """Generalised potential (20 components) at each QM atom from all MM charges."""
     out = np.zeros((s.natm, 20))
