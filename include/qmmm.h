@@ -166,6 +166,14 @@ int qmmm_last_timing(const qmmm_handle *h, double *out);
  * QM cell's images are to be included.  Arrays: host or device memory. */
 int qmmm_qm_images(qmmm_handle *h, const double *dm, double *E, double *dE_dRqm, double *F);
 
+/* Density predictor for MD (Sec. "Common Setup": the always-stable predictor-corrector of the
+ * one-particle density matrix from the K+1 preceding steps, used as the SCF guess and to set
+ * region I on the fly):  out = sum_{j=1}^{K+1} B_j hist[j-1],
+ *   B_j = (-1)^(j+1) j C(2K+2, K+1-j) / C(2K, K),  K = nhist - 1, 1 <= nhist <= 9
+ * (nhist = 4 as in the paper: B = 2.8, -2.8, 1.2, -0.2).  hist[0] is the most recent density.
+ * hist[*] and out: DEVICE arrays of n doubles; queued on `stream`, returns without waiting. */
+int qmmm_aspc_predict(int nhist, const double *const *hist, size_t n, double *out, void *stream);
+
 /* Octupole error estimate of the multipole truncation (Sec. "Error Control"): the leading error
  * of keeping region-II interactions to quadrupole order is the charge-octupole interaction
  *   Err(R) = sum_{i in II} sum_j sum_abc Omega_j,abc q_i T_ji,abc,

@@ -27,6 +27,7 @@ from ._lib import (  # noqa: F401
     qmmm_batch_destroy,
     qmmm_batch_run,
     qmmm_batch_timing,
+    qmmm_aspc_predict,
     qmmm_autotune,
     qmmm_get_tuning,
     qmmm_set_tuning,

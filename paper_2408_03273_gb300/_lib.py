@@ -59,7 +59,7 @@ _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
-           "qmmm_qm_images", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
+           "qmmm_qm_images", "qmmm_aspc_predict", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
            "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
 
@@ -93,6 +93,7 @@ def load(build_if_needed: bool = True):
         "qmmm_get_potential": (c_int, [c_void_p, c_void_p]),
         "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
         "qmmm_qm_images": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "qmmm_aspc_predict": (c_int, [c_int, P(c_void_p), ctypes.c_size_t, c_void_p, c_void_p]),
         "qmmm_octupole_error": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p]),
         "qmmm_rcut_search": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, P(c_double),
                                      P(c_double)]),
@@ -267,6 +268,16 @@ def qmmm_last_timing(h):
     out = (c_double * 2)()
     load().qmmm_last_timing(h, out)
     return float(out[0]), float(out[1])
+
+
+def qmmm_aspc_predict(history, out=None, stream=None):
+    """ASPC-predicted density from device tensors history[0] (most recent) .. history[K]."""
+    n = history[0].numel()
+    out = history[0].new_empty(history[0].shape) if out is None else out
+    arr = (c_void_p * len(history))(*[_ptr(x) for x in history])
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(load().qmmm_aspc_predict(len(history), arr, n, _ptr(out), st), "qmmm_aspc_predict")
+    return out
 
 
 def qmmm_qm_images(h, dm, want_F=False):

@@ -3,6 +3,9 @@
 // E_QM-MM = sum gamma V (region-I electronic, Eq. 9) + E_nuc_mm + E_II, with
 // E_II = sum_j sum_c w_c M_j,c v_j,c (Eq. 6 QM-MM lines + Eq. 10); every sum here runs in a fixed
 // order so repeated calls give identical bits.
+#include <algorithm>
+#include <string>
+
 #include "device_common.cuh"
 #include "qmmm_internal.h"
 
@@ -114,4 +117,70 @@ cudaError_t launch_unpermute(const double *dq_int, const double *dR_int, const i
     return cudaGetLastError();
 }
 
+// ASPC density predictor: out = sum_j B_j hist_j (the weights come from the host)
+struct AspcArgs {
+    const double *h[9];
+    double B[9];
+    int m;
+};
+
+__global__ void k_aspc(AspcArgs a, size_t n, double *out)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < a.m; ++j) s += a.B[j] * a.h[j][k];
+        out[k] = s;
+    }
+}
+
 }  // namespace qmmm
+
+namespace {
+bool dev_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" int qmmm_aspc_predict(int nhist, const double *const *hist, size_t n, double *out, void *stream)
+{
+    if (nhist < 1 || nhist > 9 || !hist || !out) {
+        qmmm::set_last_error("need 1 <= nhist <= 9 and non-null arrays");
+        return QMMM_ERR_ARG;
+    }
+    qmmm::AspcArgs a;
+    a.m = nhist;
+    const int K = nhist - 1;
+    auto comb = [](int N, int k) {
+        if (k < 0 || k > N) return 0.0;
+        double c = 1.0;
+        for (int t = 1; t <= k; ++t) c = c * (N - k + t) / t;
+        return c;
+    };
+    for (int j = 1; j <= nhist; ++j) {
+        if (!hist[j - 1] || !dev_ptr(hist[j - 1])) {
+            qmmm::set_last_error("history arrays must be device memory");
+            return QMMM_ERR_ARG;
+        }
+        a.h[j - 1] = hist[j - 1];
+        a.B[j - 1] = ((j % 2) ? 1.0 : -1.0) * j * comb(2 * K + 2, K + 1 - j) / comb(2 * K, K);
+    }
+    if (!dev_ptr(out)) {
+        qmmm::set_last_error("output must be device memory");
+        return QMMM_ERR_ARG;
+    }
+    if (n == 0) return QMMM_OK;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    qmmm::k_aspc<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a, n, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        qmmm::set_last_error(std::string("k_aspc: ") + cudaGetErrorString(e));
+        return QMMM_ERR_CUDA;
+    }
+    return QMMM_OK;
+}
