@@ -163,6 +163,7 @@ struct qmmm_handle {
     DBuf<double> tune_V, tune_dm, tune_gqm, tune_gchg;  // autotuner scratch
     DBuf<double> oct, oct_bins, oct_err;                  // octupole error estimate
     DBuf<double> qmq_P, qmq_u, qmq_g, qmq_E, qmq_F;       // QM-QM periodic images
+    DBuf<double> Vslices;                                 // per-slice partial V (small systems)
     EwaldBuf ew;
     int nblk_mm = 1;
 
@@ -478,7 +479,7 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share)
 // forked from and joined back into the handle's stream, its grid capped at its share of the SMs
 // (so small classes do not leave most SMs idle while they run alone).
 template <typename F>
-int run_classes(qmmm_handle *h, int kind, F launch)
+int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1)
 {
     int share[NCLASS];
     if (!split_sms(h, kind, h->cls_variant[kind], share)) return QMMM_OK;
@@ -487,7 +488,7 @@ int run_classes(qmmm_handle *h, int kind, F launch)
         const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
         if (p1 <= p0) continue;
         CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
-        CUDA_TRY(launch(c, p0, p1, share[c], h->cls_variant[kind][c], h->side[c]));
+        CUDA_TRY(launch(c, p0, p1, share[c], h->cls_variant[kind][c], nslice, h->side[c]));
         CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
     }
     for (int c = 0; c < NCLASS; ++c)
@@ -513,23 +514,41 @@ int fork_classes(qmmm_handle *h, F launch)
     return QMMM_OK;
 }
 
-// One class sweep of the given kind over region-I charges [c0, c1).
+// Charge slices of a sweep: when the classes together ask for fewer than half the SMs (a small
+// QM region: few 32-pair tiles), the charge chunk is split over up to 8 block rows so that the
+// work spreads over more SMs (at least 64 charges per slice).
+int sweep_slices(const qmmm_handle *h, int kind, int nch)
+{
+    int share[NCLASS];
+    if (!split_sms(h, kind, h->cls_variant[kind], share)) return 1;
+    int blocks = 0;
+    for (int c = 0; c < NCLASS; ++c) blocks += share[c];
+    int ns = blocks > 0 ? h->nsm / blocks : 1;
+    ns = std::min(ns, std::min(8, nch / 64));
+    return std::max(ns, 1);
+}
+
+// One class sweep of the given kind over region-I charges [c0, c1), split into nslice block rows;
+// V kernels write slice s into V + s * vstride.
 cudaError_t launch_sweep(const qmmm_handle *h, int kind, int cls, int p0, int p1, int c0, int c1, int share,
-                         int variant, const double *ddm, double *V, double *gqm, double *gchg, cudaStream_t cs)
+                         int variant, int nslice, size_t vstride, const double *ddm, double *V, double *gqm,
+                         double *gchg, cudaStream_t cs)
 {
     const BasisDev b = h->basis();
     const RegionDev r = h->region();
     switch (kind) {
     case SW_VPOT_F64:
-        return launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, V, h->err.p, share, variant, cs);
+        return launch_vpot_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, V, h->err.p, share, variant, nslice, vstride,
+                               cs);
     case SW_VPOT_F32:
-        return launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, V, h->err.p, share, variant, cs);
+        return launch_vpot_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, V, h->err.p, share, variant, nslice, vstride,
+                               cs);
     case SW_VGRAD_F64:
         return launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, gqm, gchg, h->err.p, share, variant,
-                                cs);
+                                nslice, cs);
     case SW_VGRAD_F32:
         return launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, gqm, gchg, h->err.p, share, variant,
-                                cs);
+                                nslice, cs);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -562,12 +581,12 @@ int time_best(qmmm_handle *h, cudaEvent_t e0, cudaEvent_t e1, F run, float *ms)
 int tune_launch(qmmm_handle *h, int kind, int cls, int share, int variant)
 {
     const int c1 = std::min(h->nI, std::min(chunk_for_kind(kind), TUNE_CHARGES));
-    auto one = [&](int c, int p0, int p1, int s, int v, cudaStream_t cs) {
-        return launch_sweep(h, kind, c, p0, p1, 0, c1, s, v, h->tune_dm.p, h->tune_V.p, h->tune_gqm.p, h->tune_gchg.p,
-                            cs);
+    auto one = [&](int c, int p0, int p1, int s, int v, int ns, cudaStream_t cs) {
+        return launch_sweep(h, kind, c, p0, p1, 0, c1, s, v, ns, 0, h->tune_dm.p, h->tune_V.p, h->tune_gqm.p,
+                            h->tune_gchg.p, cs);
     };
     if (cls < 0) return run_classes(h, kind, one);
-    CUDA_TRY(one(cls, h->class_off[cls], h->class_off[cls + 1], share, variant, h->stream));
+    CUDA_TRY(one(cls, h->class_off[cls], h->class_off[cls + 1], share, variant, 1, h->stream));
     return QMMM_OK;
 }
 
@@ -1008,14 +1027,27 @@ int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
     if ((rc = h->V.ensure((size_t)h->nao * h->nao))) return rc;
     CUDA_TRY(cudaMemsetAsync(h->V.p, 0, (size_t)h->nao * h->nao * sizeof(double), st));
     const int kind = sweep_kind(h, false), ch = chunk_for_kind(kind);
+    const size_t n2 = (size_t)h->nao * h->nao;
+    const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
+    double *Vdst = h->V.p;
+    if (ns > 1) {  // per-slice partial V, summed in a fixed order afterwards
+        if ((rc = h->Vslices.ensure((size_t)ns * n2))) return rc;
+        CUDA_TRY(cudaMemsetAsync(h->Vslices.p, 0, (size_t)ns * n2 * sizeof(double), st));
+        Vdst = h->Vslices.p;
+    }
     CUDA_TRY(mark(h, 0));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
-        rc = run_classes(h, kind, [&](int cls, int p0, int p1, int share, int variant, cudaStream_t cs) {
-            return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nullptr, h->V.p, nullptr, nullptr, cs);
-        });
+        rc = run_classes(
+            h, kind,
+            [&](int cls, int p0, int p1, int share, int variant, int nsl, cudaStream_t cs) {
+                return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, nsl > 1 ? n2 : 0, nullptr, Vdst,
+                                    nullptr, nullptr, cs);
+            },
+            ns);
         if (rc) return rc;
     }
+    if (ns > 1) CUDA_TRY(launch_sum_slices_d(h->Vslices.p, ns, n2, h->V.p, st));
     CUDA_TRY(mark(h, 1));
     CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
                            nullptr, 0, st));
@@ -1098,12 +1130,17 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
     if ((rc = compute_multipoles(h, ddm, nullptr, MOM_PULAY))) return rc;
     // region-I adjoint sweep
     const int kind = sweep_kind(h, true), ch = chunk_for_kind(kind);
+    const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
     CUDA_TRY(mark(h, 0));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
-        rc = run_classes(h, kind, [&](int cls, int p0, int p1, int share, int variant, cudaStream_t cs) {
-            return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, ddm, nullptr, h->gqm.p, h->gchg.p, cs);
-        });
+        rc = run_classes(
+            h, kind,
+            [&](int cls, int p0, int p1, int share, int variant, int nsl, cudaStream_t cs) {
+                return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, 0, ddm, nullptr, h->gqm.p,
+                                    h->gchg.p, cs);
+            },
+            ns);
         if (rc) return rc;
     }
     CUDA_TRY(mark(h, 1));

@@ -117,6 +117,23 @@ cudaError_t launch_unpermute(const double *dq_int, const double *dR_int, const i
     return cudaGetLastError();
 }
 
+__global__ void k_sum_slices_d(const double *src, int nslice, size_t n, double *dst)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int sl = 0; sl < nslice; ++sl) s += src[(size_t)sl * n + k];
+        dst[k] = s;
+    }
+}
+
+cudaError_t launch_sum_slices_d(const double *src, int nslice, size_t n, double *dst, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 8192);
+    k_sum_slices_d<<<grid, 256, 0, st>>>(src, nslice, n, dst);
+    return cudaGetLastError();
+}
+
 // ASPC density predictor: out = sum_j B_j hist_j (the weights come from the host)
 struct AspcArgs {
     const double *h[9];

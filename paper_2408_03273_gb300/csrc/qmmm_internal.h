@@ -46,20 +46,24 @@ struct qmmm_handle_impl;
 
 // launchers (defined in the .cu files); all return a cudaError_t of the last launch
 // Region-I sweeps.  `nsm` caps the grid (the class's share of the SMs); `variant` picks the block
-// shape: 0 = 256 threads, 1 = the class's wide block (sweep_wide_threads), where one exists.
+// shape: 0 = 256 threads, 1 = the class's wide block (sweep_wide_threads), where one exists;
+// `nslice` splits the charge chunk over that many block rows (small systems), the V kernels then
+// writing slice s into V + s * vstride.
+// dst[k] = sum_s src[s*n + k], s < nslice, in order (the V slices)
+cudaError_t launch_sum_slices_d(const double *src, int nslice, size_t n, double *dst, cudaStream_t st);
 cudaError_t launch_vpot_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                             int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
-                            cudaStream_t st);
+                            int nslice, size_t vstride, cudaStream_t st);
 cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                             int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
-                            cudaStream_t st);
+                            int nslice, size_t vstride, cudaStream_t st);
 cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
-                             double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, int variant,
+                             double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, int variant, int nslice,
                              cudaStream_t st);
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, int variant, cudaStream_t st);
+                             double *gchg, int *err, int nsm, int variant, int nslice, cudaStream_t st);
 
 // moments / multipoles / Fock / Pulay (mode bits below)
 enum { MOM_MULT = 1, MOM_FOCK = 2, MOM_PULAY = 4 };

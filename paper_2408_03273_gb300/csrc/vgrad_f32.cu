@@ -14,7 +14,7 @@ template <int LA, int LB>
 struct VgradF32 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                            int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, int variant,
+                           int nsm, int variant, int nslice,
                            cudaStream_t st);
 };
 
@@ -31,6 +31,13 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1), NA = ncart(LA), NB = ncart(LB);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    {
+        // this block row's slice of the charge chunk (gridDim.y > 1 spreads small systems over more SMs)
+        const int per = (ch_end - ch_begin + (int)gridDim.y - 1) / (int)gridDim.y;
+        ch_begin += (int)blockIdx.y * per;
+        ch_end = min(ch_end, ch_begin + per);
+    }
+    if (ch_begin >= ch_end) return;
     const int nch = ch_end - ch_begin;
     float4 *chi = reinterpret_cast<float4 *>(smem_raw);
     float4 *clo = chi + nch;
@@ -238,11 +245,12 @@ inline unsigned boys32_bytes_g() { return (unsigned)(BOYS_TAB_F * sizeof(float))
 template <int LA, int LB, int NT>
 static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                              int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                             int nsm, cudaStream_t st)
+                             int nsm, int nslice, cudaStream_t st)
 {
     const unsigned tb = boys32_bytes_g();
     const size_t per = 2 * sizeof(float4) + 4 * sizeof(double);
-    const size_t smem = (size_t)(ch_end - ch_begin) * per + tb;
+    const int nper = (ch_end - ch_begin + nslice - 1) / nslice;  // charges per slice
+    const size_t smem = (size_t)nper * per + tb;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -254,23 +262,26 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vgrad_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
-                                                    boys + (size_t)(LA + LB + 1) * BOYS_TAB_F, tb, dm, gqm,
-                                                    gchg, err);
+    k_vgrad_f32<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
+                                                                  boys + (size_t)(LA + LB + 1) * BOYS_TAB_F, tb,
+                                                                  dm, gqm, gchg, err);
     return cudaGetLastError();
 }
 
 template <int LA, int LB>
 cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                                  int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                                  int nsm, int variant,
+                                  int ch_end, const float *boys, const double *dm, double *gqm, double *gchg,
+                                  int *err,
+                                  int nsm, int variant, int nslice,
                                   cudaStream_t st)
 {
     constexpr int W = sweep_wide_threads(SW_VGRAD_F32, class_of(LA, LB));
     if constexpr (W > 0)
         if (variant == 1)
-            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
-    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                        nslice, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                  nslice, st);
 }
 
 template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -279,11 +290,11 @@ template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_C
 
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, int variant, cudaStream_t st)
+                             double *gchg, int *err, int nsm, int variant, int nslice, cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VgradF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                    variant, st);
+                                    variant, nslice, st);
 }
 
 #endif

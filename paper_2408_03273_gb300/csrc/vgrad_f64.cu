@@ -19,7 +19,7 @@ template <int LA, int LB>
 struct VgradF64 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                            int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, int variant,
+                           int nsm, int variant, int nslice,
                            cudaStream_t st);
 };
 
@@ -34,6 +34,13 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1), NA = ncart(LA), NB = ncart(LB);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    {
+        // this block row's slice of the charge chunk (gridDim.y > 1 spreads small systems over more SMs)
+        const int per = (ch_end - ch_begin + (int)gridDim.y - 1) / (int)gridDim.y;
+        ch_begin += (int)blockIdx.y * per;
+        ch_end = min(ch_end, ch_begin + per);
+    }
+    if (ch_begin >= ch_end) return;
     const int nch = ch_end - ch_begin;
     double4_32a *chg = reinterpret_cast<double4_32a *>(smem_raw);
     double *acc = reinterpret_cast<double *>(smem_raw + (size_t)nch * sizeof(double4_32a));
@@ -197,9 +204,10 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
 template <int LA, int LB, int NT>
 static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                              int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
-                             int nsm, cudaStream_t st)
+                             int nsm, int nslice, cudaStream_t st)
 {
-    const size_t smem = (size_t)(ch_end - ch_begin) * (sizeof(double4_32a) + 4 * sizeof(double));
+    const int nper = (ch_end - ch_begin + nslice - 1) / nslice;  // charges per slice
+    const size_t smem = (size_t)nper * (sizeof(double4_32a) + 4 * sizeof(double));
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -211,22 +219,25 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vgrad_f64<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm,
-                                                 gchg, err);
+    k_vgrad_f64<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys,
+                                                                  dm, gqm, gchg, err);
     return cudaGetLastError();
 }
 
 template <int LA, int LB>
 cudaError_t VgradF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                                  int ch_end, const double *boys, const double *dm, double *gqm, double *gchg, int *err,
-                                  int nsm, int variant,
+                                  int ch_end, const double *boys, const double *dm, double *gqm, double *gchg,
+                                  int *err,
+                                  int nsm, int variant, int nslice,
                                   cudaStream_t st)
 {
     constexpr int W = sweep_wide_threads(SW_VGRAD_F64, class_of(LA, LB));
     if constexpr (W > 0)
         if (variant == 1)
-            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
-    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm, st);
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                        nslice, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                  nslice, st);
 }
 
 template struct VgradF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -235,11 +246,11 @@ template struct VgradF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_C
 
 cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, int variant, cudaStream_t st)
+                             double *gchg, int *err, int nsm, int variant, int nslice, cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VgradF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                    variant, st);
+                                    variant, nslice, st);
 }
 
 #endif

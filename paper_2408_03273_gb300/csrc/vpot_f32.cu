@@ -16,7 +16,8 @@ namespace qmmm {
 template <int LA, int LB>
 struct VpotF32 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
+                           int ch_end, const float *boys, double *V, int *err, int nsm, int variant, int nslice,
+                           size_t vstride,
                            cudaStream_t st);
 };
 
@@ -27,11 +28,19 @@ constexpr int FOLD = 16;
 template <int LA, int LB, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
-           const float *__restrict__ boys_g, unsigned boys_bytes, double *__restrict__ V, int *err)
+           const float *__restrict__ boys_g, unsigned boys_bytes, double *__restrict__ V, size_t vstride, int *err)
 {
+    V += (size_t)blockIdx.y * vstride;  // per-slice partial V when the charges are split
     constexpr int L = LA + LB, NH = nherm(L), NA = ncart(LA), NB = ncart(LB);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    {
+        // this block row's slice of the charge chunk (gridDim.y > 1 spreads small systems over more SMs)
+        const int per = (ch_end - ch_begin + (int)gridDim.y - 1) / (int)gridDim.y;
+        ch_begin += (int)blockIdx.y * per;
+        ch_end = min(ch_end, ch_begin + per);
+    }
+    if (ch_begin >= ch_end) return;
     const int nch = ch_end - ch_begin;
     float4 *chi = reinterpret_cast<float4 *>(smem_raw);
     float4 *clo = chi + nch;
@@ -139,10 +148,12 @@ inline unsigned boys32_bytes() { return (unsigned)(BOYS_TAB_F * sizeof(float)); 
 
 template <int LA, int LB, int NT>
 static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                             int ch_end, const float *boys, double *V, int *err, int nsm, cudaStream_t st)
+                             int ch_end, const float *boys, double *V, int *err, int nsm, int nslice,
+                             size_t vstride, cudaStream_t st)
 {
     const unsigned tb = boys32_bytes();
-    const size_t smem = (size_t)(ch_end - ch_begin) * 2 * sizeof(float4) + tb;
+    const int per = (ch_end - ch_begin + nslice - 1) / nslice;
+    const size_t smem = (size_t)per * 2 * sizeof(float4) + tb;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -154,21 +165,24 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vpot_f32<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
-                                                   boys + (size_t)(LA + LB) * BOYS_TAB_F, tb, V, err);
+    k_vpot_f32<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
+                                                                 boys + (size_t)(LA + LB) * BOYS_TAB_F, tb, V,
+                                                                 vstride, err);
     return cudaGetLastError();
 }
 
 template <int LA, int LB>
 cudaError_t VpotF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                                  int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
+                                 int nslice, size_t vstride,
                                  cudaStream_t st)
 {
     constexpr int W = sweep_wide_threads(SW_VPOT_F32, class_of(LA, LB));
     if constexpr (W > 0)
         if (variant == 1)
-            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
-    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, nslice,
+                                        vstride, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, nslice, vstride, st);
 }
 
 template struct VpotF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -177,10 +191,12 @@ template struct VpotF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CL
 
 cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                             int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
+                            int nslice, size_t vstride,
                             cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
-    return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant, st);
+    return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant,
+                                   nslice, vstride, st);
 }
 
 #endif

@@ -19,7 +19,8 @@ namespace qmmm {
 template <int LA, int LB>
 struct VpotF64 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                           int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
+                           int ch_end, const double *boys, double *V, int *err, int nsm, int variant, int nslice,
+                           size_t vstride,
                            cudaStream_t st);
 };
 
@@ -28,12 +29,20 @@ struct VpotF64 {
 template <int LA, int LB, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_vpot_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
-           const double *__restrict__ boys, double *__restrict__ V, int *err)
+           const double *__restrict__ boys, double *__restrict__ V, size_t vstride, int *err)
 {
+    V += (size_t)blockIdx.y * vstride;  // per-slice partial V when the charges are split
     constexpr int L = LA + LB, NH = nherm(L), NA = ncart(LA), NB = ncart(LB);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     double4_32a *chg = reinterpret_cast<double4_32a *>(smem_raw);
+    {
+        // this block row's slice of the charge chunk (gridDim.y > 1 spreads small systems over more SMs)
+        const int per = (ch_end - ch_begin + (int)gridDim.y - 1) / (int)gridDim.y;
+        ch_begin += (int)blockIdx.y * per;
+        ch_end = min(ch_end, ch_begin + per);
+    }
+    if (ch_begin >= ch_end) return;
     const int nch = ch_end - ch_begin;
     if (!stage_to_smem(chg, rg.chg + ch_begin, (unsigned)(nch * sizeof(double4_32a)), &bar, err)) return;
 
@@ -109,9 +118,11 @@ k_vpot_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
 
 template <int LA, int LB, int NT>
 static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                             int ch_end, const double *boys, double *V, int *err, int nsm, cudaStream_t st)
+                             int ch_end, const double *boys, double *V, int *err, int nsm, int nslice,
+                             size_t vstride, cudaStream_t st)
 {
-    const size_t smem = (size_t)(ch_end - ch_begin) * sizeof(double4_32a);
+    const int per = (ch_end - ch_begin + nslice - 1) / nslice;
+    const size_t smem = (size_t)per * sizeof(double4_32a);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_vpot_f64<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -123,20 +134,23 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vpot_f64<LA, LB, NT><<<grid, NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err);
+    k_vpot_f64<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys,
+                                                                 V, vstride, err);
     return cudaGetLastError();
 }
 
 template <int LA, int LB>
 cudaError_t VpotF64<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                                  int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
+                                 int nslice, size_t vstride,
                                  cudaStream_t st)
 {
     constexpr int W = sweep_wide_threads(SW_VPOT_F64, class_of(LA, LB));
     if constexpr (W > 0)
         if (variant == 1)
-            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
-    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, st);
+            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, nslice,
+                                        vstride, st);
+    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, nslice, vstride, st);
 }
 
 template struct VpotF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -144,11 +158,13 @@ template struct VpotF64<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CL
 #else  // the dispatcher
 
 cudaError_t launch_vpot_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
-                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm, int variant,
+                            int ch_begin, int ch_end, const double *boys, double *V, int *err, int nsm,
+                            int variant, int nslice, size_t vstride,
                             cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
-    return dispatch_class<VpotF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant, st);
+    return dispatch_class<VpotF64>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant,
+                                   nslice, vstride, st);
 }
 
 #endif
