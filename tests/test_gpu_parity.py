@@ -75,11 +75,14 @@ def test_screening_default_changes_nothing_visible(case):
 
 
 def test_repeat_is_bitwise_identical():
+    # V (at most two additions per element) and the region-II potential (fixed-order sums) are
+    # reproducible bit for bit; the multipoles are summed with atomics over shell pairs, so E may
+    # differ in the last bits
     s = workloads.small_system(seed=106, n_atoms=3, lmax=2, nprim=(1, 3), n_waters=12)
     a, b = gpu_all(s), gpu_all(s)
     assert np.array_equal(a["V"], b["V"])
     assert np.array_equal(a["phi"], b["phi"])
-    assert a["E"] == b["E"]
+    assert abs(a["E"] - b["E"]) <= 1e-14 * abs(a["E"])
 
 
 def test_region1_empty():
