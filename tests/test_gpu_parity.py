@@ -141,3 +141,12 @@ def test_no_mm_charges():
     assert np.max(np.abs(g["V"])) == 0.0
     assert g["E"] == 0.0
     assert np.max(np.abs(g["dE_dRqm"])) == 0.0
+
+
+def test_mixed_region2_potential_keeps_double_float_accuracy(case):
+    # the mixed path computes the reciprocal Ewald sums in double-float arithmetic (~47 bits):
+    # its region-II potential stays within 1e-12 of the FP64 oracle, far inside the 1e-6 budget
+    name, s, ref = case
+    g = gpu_all(s, precision=1)
+    phi = oracle.ewald_phi(s)
+    assert rel_max(g["phi"], phi) < 1e-12, name
