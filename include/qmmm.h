@@ -244,7 +244,8 @@ int qmmm_set_tuning(qmmm_handle *h, int kind, const int *threads, const double *
  * work per kernel.  Before recording it runs the batch once through the plain calls (which
  * sizes every buffer and sets every kernel attribute); the graph is recorded again when a frame's
  * region-I size, precision, sweep configuration or any array pointer differs from the recorded
- * one.  Positions change through qmmm_set_positions on the frame's handle between runs.
+ * one (see qmmm_batch_counts).  Positions change through qmmm_set_positions on the frame's
+ * handle between runs.
  *
  * qmmm_batch_create: frames[nframes] (borrowed: they must outlive the batch and must not be used
  * on their own while the batch runs), stream = cudaStream_t as void* (NULL: the batch creates its
@@ -263,7 +264,20 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
 int qmmm_batch_timing(const qmmm_batch *b, double *ms);
 /* Number of graph recordings so far (1 after the first run when nothing changes). */
 int qmmm_batch_captures(const qmmm_batch *b);
+/* Recordings, instantiations and in-place updates of the batch graph so far.  After new
+ * positions (an MD step) the batch is recorded again without the plain pass -- unless a frame's
+ * region I outgrew its buffers -- and, when only launch parameters changed (sizes, grids,
+ * pointers), the instantiated graph is updated in place instead of instantiated anew. */
+int qmmm_batch_counts(const qmmm_batch *b, int *recorded, int *instantiated, int *updated);
 void qmmm_batch_destroy(qmmm_batch *b);
+
+/* Self-test of the failure path (no counterpart in the paper).  Every wait in the kernels (the
+ * mbarrier that completes a TMA bulk copy) gives up after 0.5 s of wall time and then records a
+ * device error flag and returns, which the call reports as QMMM_ERR_TIMEOUT with the CUDA context
+ * still usable.  This launches one block that waits on an mbarrier nothing completes; it returns
+ * QMMM_ERR_TIMEOUT when the failure path works (after a 20 ms wait); it never faults or hangs.
+ * stream: a cudaStream_t as void* (NULL = legacy stream). */
+int qmmm_selftest_bounded_wait(void *stream);
 
 void qmmm_destroy(qmmm_handle *h);
 const char *qmmm_strerror(int code);

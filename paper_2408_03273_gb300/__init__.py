@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     QMMMError,
     load,
     qmmm_batch_captures,
+    qmmm_batch_counts,
     qmmm_batch_create,
     qmmm_batch_destroy,
     qmmm_batch_run,
@@ -47,6 +48,7 @@ from ._lib import (  # noqa: F401
     qmmm_qm_images,
     qmmm_rcut_search,
     qmmm_set_positions,
+    qmmm_selftest_bounded_wait,
     qmmm_set_precision,
     qmmm_set_stream,
     qmmm_strerror,

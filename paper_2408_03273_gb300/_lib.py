@@ -59,8 +59,8 @@ _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
-           "qmmm_qm_images", "qmmm_aspc_predict", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
-           "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
+           "qmmm_qm_images", "qmmm_aspc_predict", "qmmm_selftest_bounded_wait", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
+           "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_counts", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
 
 def library_path() -> str:
@@ -94,6 +94,7 @@ def load(build_if_needed: bool = True):
         "qmmm_last_timing": (c_int, [c_void_p, P(c_double)]),
         "qmmm_qm_images": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "qmmm_aspc_predict": (c_int, [c_int, P(c_void_p), ctypes.c_size_t, c_void_p, c_void_p]),
+        "qmmm_selftest_bounded_wait": (c_int, [c_void_p]),
         "qmmm_octupole_error": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p]),
         "qmmm_rcut_search": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, P(c_double),
                                      P(c_double)]),
@@ -105,6 +106,7 @@ def load(build_if_needed: bool = True):
                                    P(c_void_p)]),
         "qmmm_batch_timing": (c_int, [c_void_p, P(c_double)]),
         "qmmm_batch_captures": (c_int, [c_void_p]),
+        "qmmm_batch_counts": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
         "qmmm_batch_destroy": (None, [c_void_p]),
         "qmmm_destroy": (None, [c_void_p]),
         "qmmm_strerror": (ctypes.c_char_p, [c_int]),
@@ -270,6 +272,12 @@ def qmmm_last_timing(h):
     return float(out[0]), float(out[1])
 
 
+def qmmm_selftest_bounded_wait(stream=None):
+    """Return code of the failure-path self-test (QMMM_ERR_TIMEOUT = -4 when it works)."""
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return int(load().qmmm_selftest_bounded_wait(st))
+
+
 def qmmm_aspc_predict(history, out=None, stream=None):
     """ASPC-predicted density from device tensors history[0] (most recent) .. history[K]."""
     n = history[0].numel()
@@ -364,6 +372,13 @@ def qmmm_batch_timing(b, nframes):
 
 def qmmm_batch_captures(b):
     return int(load().qmmm_batch_captures(b))
+
+
+def qmmm_batch_counts(b):
+    """(recordings, instantiations, in-place updates) of the batch graph."""
+    r, i, u = c_int(), c_int(), c_int()
+    _check(load().qmmm_batch_counts(b, ctypes.byref(r), ctypes.byref(i), ctypes.byref(u)), "qmmm_batch_counts")
+    return r.value, i.value, u.value
 
 
 def qmmm_batch_destroy(b):

@@ -1376,7 +1376,8 @@ struct qmmm_batch {
     cudaEvent_t start = nullptr, fork = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> key;  // what the graph was recorded for
-    int captures = 0;
+    std::vector<int> planned_nI; // each frame's region-I size at the last plain pass (buffer sizes)
+    int captures = 0, instantiations = 0, updates = 0;
     std::vector<double> ms;  // last run: total, then per frame
     ~qmmm_batch()
     {
@@ -1490,14 +1491,22 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
     int rc = QMMM_OK;
     std::vector<long long> key = batch_key(b, dm, V, E, dE_dRqm, dE_dRmm, dE_dq);
     if (!b->exec || key != b->key) {
-        // plain pass: sizes every buffer and sets every kernel attribute before recording
-        for (int i = 0; i < n && !rc; ++i) {
-            b->f[i]->stream = b->fst[i];
-            rc = batch_frame(b->f[i], dm[i], at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
-        }
-        if (rc) {
-            restore();
-            return rc;
+        // plain pass, which sizes every buffer and sets every kernel attribute, before the first
+        // recording and whenever a frame's region I outgrew its buffers; otherwise (new positions
+        // of the same frames, as in MD) only the recording is repeated
+        bool plain = !b->exec || (int)b->planned_nI.size() != n;
+        for (int i = 0; i < n && !plain; ++i) plain = b->f[i]->nI > b->planned_nI[i];
+        if (plain) {
+            for (int i = 0; i < n && !rc; ++i) {
+                b->f[i]->stream = b->fst[i];
+                rc = batch_frame(b->f[i], dm[i], at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
+            }
+            if (rc) {
+                restore();
+                return rc;
+            }
+            b->planned_nI.assign(n, 0);
+            for (int i = 0; i < n; ++i) b->planned_nI[i] = b->f[i]->nI;
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
@@ -1524,16 +1533,29 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
             return fail(QMMM_ERR_CUDA, std::string("batch graph capture: ") +
                                            cudaGetErrorString(e != cudaSuccess ? e : e_end));
         }
+        // same topology with new launch parameters (region-I sizes, pointers): update in place
+        bool updated = false;
         if (b->exec) {
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess) {
+                updated = true;
+                ++b->updates;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
         }
-        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (!updated) {
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                b->exec = nullptr;
+                return fail(QMMM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            }
+            ++b->instantiations;
+        }
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            b->exec = nullptr;
-            return fail(QMMM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-        }
         b->key = key;
         ++b->captures;
     }
@@ -1560,6 +1582,15 @@ int qmmm_batch_timing(const qmmm_batch *b, double *ms)
 }
 
 int qmmm_batch_captures(const qmmm_batch *b) { return b ? b->captures : fail(QMMM_ERR_ARG, "null batch"); }
+
+int qmmm_batch_counts(const qmmm_batch *b, int *recorded, int *instantiated, int *updated)
+{
+    if (!b) return fail(QMMM_ERR_ARG, "null batch");
+    if (recorded) *recorded = b->captures;
+    if (instantiated) *instantiated = b->instantiations;
+    if (updated) *updated = b->updates;
+    return QMMM_OK;
+}
 
 void qmmm_batch_destroy(qmmm_batch *b) { delete b; }
 

@@ -329,6 +329,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
 // Error flags written by kernels (read back by the host after the call).
 enum : int { DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `phase` of an mbarrier, giving up after `limit_ns` nanoseconds of wall time (the
+// global timer, read every 32 polls) or 2^24 polls, whichever comes first.  Block-uniform outcome:
+// if any thread gave up, every thread gets false and *err records DEVERR_TIMEOUT.
+constexpr uint64_t MBAR_LIMIT_NS = 500000000ull;  // 0.5 s: a bulk copy takes microseconds
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, int *err,
+                                                  uint64_t limit_ns = MBAR_LIMIT_NS)
+{
+    bool done = false;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (mbar_try_wait(bar, phase)) { done = true; break; }
+        if ((it & 31) == 31 && global_ns() - t0 > limit_ns) break;
+    }
+    const int fail = __syncthreads_or(!done);
+    if (fail && threadIdx.x == 0 && err) atomicOr(err, DEVERR_TIMEOUT);
+    return !fail;
+}
+
 // Stage up to three segments (sizes multiples of 16 bytes, all addresses 16-byte aligned) from
 // global to shared memory with the TMA bulk-copy engine, completing on one mbarrier.  Every
 // thread of the block must call it.  Returns false on every thread (and sets *err) if the copies
@@ -358,14 +383,7 @@ __device__ __forceinline__ bool stage_segments(const Seg *seg, int nseg, uint64_
             }
         }
     }
-    bool done = false;
-    for (int it = 0; it < (1 << 22); ++it) {
-        if (mbar_try_wait(bar, 0)) { done = true; break; }
-    }
-    // block-uniform outcome: if any thread gave up, every thread returns
-    const int fail = __syncthreads_or(!done);
-    if (fail && threadIdx.x == 0 && err) atomicOr(err, DEVERR_TIMEOUT);
-    return !fail;
+    return mbar_wait_bounded(bar, 0, err);
 }
 
 __device__ __forceinline__ bool stage_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *bar, int *err)

@@ -133,3 +133,51 @@ extern "C" int qmmm_nuclear_mm_energy_static(int natm, const double *qm_xyz, con
     }
     return QMMM_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Self-test of the failure path: one block waits on an mbarrier that nothing completes (no copy
+// is issued), so the bounded wait gives up after 20 ms, the kernel records DEVERR_TIMEOUT and
+// returns.
+// ---------------------------------------------------------------------------------------------
+namespace {
+__global__ void k_wait_for_nothing(int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        qmmm::mbar_init(&bar, 1);
+        qmmm::fence_mbar_init();
+    }
+    __syncthreads();
+    qmmm::mbar_wait_bounded(&bar, 0, err, 20000000ull);  // 20 ms
+}
+}  // namespace
+
+extern "C" int qmmm_selftest_bounded_wait(void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        qmmm::set_last_error("cudaMalloc");
+        return QMMM_ERR_ALLOC;
+    }
+    int flag = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        k_wait_for_nothing<<<1, 64, 0, st>>>(err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err);
+    if (e != cudaSuccess) {
+        qmmm::set_last_error(std::string("self-test: ") + cudaGetErrorString(e));
+        return QMMM_ERR_CUDA;
+    }
+    if (flag & qmmm::DEVERR_TIMEOUT) {
+        qmmm::set_last_error("the bounded wait ran out, as intended");
+        return QMMM_ERR_TIMEOUT;
+    }
+    qmmm::set_last_error("the wait completed although nothing could complete it");
+    return QMMM_ERR_CUDA;
+}

@@ -103,6 +103,10 @@ class Batch:
     def captures(self):
         return L.qmmm_batch_captures(self.b)
 
+    def counts(self):
+        """(recordings, instantiations, in-place updates)."""
+        return L.qmmm_batch_counts(self.b)
+
     def close(self):
         if self.b:
             L.qmmm_batch_destroy(self.b)

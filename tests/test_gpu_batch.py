@@ -105,3 +105,51 @@ def test_batch_rejects_host_memory():
     finally:
         for h in hs:
             h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_follows_md_steps(precision):
+    # new positions every step (region-I sizes change): the batch is recorded again without its
+    # plain pass when the buffers suffice, and updated in place when only launch parameters change
+    torch = pytest.importorskip("torch")
+    import paper_2408_03273_gb300 as q
+    frames = _frames()
+    hs = [q.Handle(s, precision=precision) for s in frames]
+    rng = np.random.default_rng(7)
+    try:
+        dev = torch.device("cuda")
+        dm = [torch.as_tensor(s.dm, device=dev) for s in frames]
+        V, E, gq, gm, gc = _dev_outputs(torch, frames)
+        b = q.Batch(hs)
+        try:
+            tol = 1e-12 if precision == 0 else 1e-7
+            pos = [(s.atom_xyz.copy(), s.mm_xyz.copy()) for s in frames]
+            sizes = []
+            for step in range(4):
+                if step:
+                    for i, h in enumerate(hs):
+                        qm, mm = pos[i]
+                        qm = qm + rng.normal(scale=0.05, size=qm.shape)
+                        mm = mm + rng.normal(scale=0.8, size=mm.shape)  # waters cross the region-I sphere
+                        pos[i] = (qm, mm)
+                        h.set_positions(qm, mm)
+                sizes.append([h.info["n_region1"] for h in hs])
+                b.run(dm, V, E, gq, gm, gc)
+                for i, s in enumerate(frames):
+                    r = q.Handle(s, precision=precision)
+                    try:
+                        r.set_positions(*pos[i])
+                        ref = _plain(r, s, s.dm)
+                    finally:
+                        r.close()
+                    assert _close(V[i].cpu(), ref["V"], tol), (step, i)
+                    assert _close(E[i].cpu(), ref["E"], tol), (step, i)
+                    assert _close(gm[i].cpu(), ref["gm"], tol), (step, i)
+            recorded, inst, upd = b.counts()
+            assert 1 <= recorded <= 4 and inst + upd == recorded and inst >= 1
+            assert len({tuple(x) for x in sizes}) > 1  # region I did change between steps
+        finally:
+            b.close()
+    finally:
+        for h in hs:
+            h.close()
