@@ -295,6 +295,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-autotune", action="store_true", help="run the class sweeps with the flop-model schedule")
+    ap.add_argument("--recip", default="auto", choices=["auto", "cuda", "tensor"],
+                    help="structure factor of the reciprocal sum: auto (tensor cores for the mixed path), CUDA "
+                         "cores, or tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -323,6 +326,26 @@ def main():
     h.set_stream(stream)
     info = h.info
     tuning = {}
+
+    RECIP = {"auto": q.QMMM_RECIP_AUTO, "cuda": q.QMMM_RECIP_CUDA_CORES, "tensor": q.QMMM_RECIP_TENSOR}[args.recip]
+    RECIP_NAME = {q.QMMM_RECIP_CUDA_CORES: "CUDA cores", q.QMMM_RECIP_TENSOR: "tensor cores (exact BF16 digit planes)"}
+
+    def recip_in_effect(precision):
+        if RECIP != q.QMMM_RECIP_AUTO:
+            return RECIP_NAME[RECIP]
+        return RECIP_NAME[q.QMMM_RECIP_TENSOR if precision == q.QMMM_MIXED else q.QMMM_RECIP_CUDA_CORES]
+
+    def positions_ms(hh, n=10):
+        # set_positions alone (region I and the region-II potential, i.e. the structure factor)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n)]
+        for k in range(n):
+            ev[2 * k].record(stream)
+            q.qmmm_set_positions(hh.h, qm_d, mm_d, q_d)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.median([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n)]))
+
+    h.set_recip_method(RECIP)
 
     def tune(hh):
         # one-time plan step outside the timed region: block shape and SM split per angular class
@@ -417,6 +440,7 @@ def main():
         E64 = h.energy(dm_d).clone()
         hm = q.Handle(s, precision=q.QMMM_MIXED)
         hm.set_stream(stream)
+        hm.set_recip_method(RECIP)
         tune(hm)
         ms_m, rec_m = timed(hm, args.steps, args.warmup)
         Em = hm.energy(dm_d)
@@ -435,6 +459,15 @@ def main():
                  "roofline": {"bound": "alu", "achieved": ach_m, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": ach_m / FP32_PEAK_TFLOPS,
                               "traffic": SWEEP_TRAFFIC.get((args.config, "mixed")) if t_gm >= t_vm else None}}
+        # the region-II potential by each structure-factor method (set_positions alone)
+        pos = {}
+        for name, m in (("cuda_cores", q.QMMM_RECIP_CUDA_CORES), ("tensor_cores", q.QMMM_RECIP_TENSOR)):
+            hm.set_recip_method(m)
+            positions_ms(hm, 3)
+            pos[name] = positions_ms(hm)
+        hm.set_recip_method(RECIP)
+        mixed["structure_factor"] = recip_in_effect(q.QMMM_MIXED)
+        mixed["set_positions_ms"] = pos
         hm.close()
 
     # end to end: host (pinned) inputs and outputs, copies inside the timed interval
@@ -463,6 +496,7 @@ def main():
            "vs_baseline": None, "dtype": "f64" if prec == q.QMMM_FP64 else "f32+f64",
            "data": "synthetic (seeded TIP3P water box + random active-site QM region and basis)",
            "config": {"workload": describe(s, info), "precision": args.precision,
+                      "structure_factor": recip_in_effect(prec),
                       "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "units_per_step": units_per_step,

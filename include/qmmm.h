@@ -117,6 +117,21 @@ int qmmm_set_stream(qmmm_handle *h, void *stream);
  * FP64). */
 int qmmm_set_precision(qmmm_handle *h, int precision);
 
+/* Method of the MM structure factor S(G) = sum_i q_i exp(iG.R_i) in the reciprocal Ewald sum
+ * (SI, "Multipolar Ewald", long-range part), used for the region-II potential at the QM atoms:
+ *   QMMM_RECIP_CUDA_CORES: FP64 (double-float for QMMM_MIXED) on the CUDA cores;
+ *   QMMM_RECIP_TENSOR: S as a product of two matrices on the BF16 tensor cores, each operand
+ *     split exactly into seven digit planes (a leading one and six of 7 bits) with exact FP32
+ *     accumulation of the leading levels (about 2^-45 of max|q| per term: FP64-class);
+ *   QMMM_RECIP_AUTO [default]: the tensor cores for QMMM_MIXED, the CUDA cores for QMMM_FP64.
+ * The tensor-core scratch is allocated the first time the method is in effect: 16 N_MM
+ * (kx + 2 ky + 2 kz + 3) bytes of fixed-point phases, the B-operand digit planes (about 1 KB per
+ * charge at kmax 16) and the partial sums of each block of 512 charges (about 2 KB per charge).
+ * Recomputes the region-II potential at the current geometry if the method in effect changes.
+ * QMMM_ERR_ARG for another value. */
+enum { QMMM_RECIP_CUDA_CORES = 0, QMMM_RECIP_TENSOR = 1, QMMM_RECIP_AUTO = 2 };
+int qmmm_set_recip_method(qmmm_handle *h, int method);
+
 /* New geometry (MD step): qm_xyz[natm*3], mm_xyz[nmm*3] (bohr), mm_q[nmm] (NULL keeps the
  * charges).  Rebuilds region I and the gamma-independent region-II potential v (20 Taylor
  * components per QM atom, Eq. 6 QM-MM lines + Eq. 10). */

@@ -50,6 +50,10 @@ from ._lib import (  # noqa: F401
     qmmm_set_positions,
     qmmm_selftest_bounded_wait,
     qmmm_set_precision,
+    qmmm_set_recip_method,
+    QMMM_RECIP_CUDA_CORES,
+    QMMM_RECIP_TENSOR,
+    QMMM_RECIP_AUTO,
     qmmm_set_stream,
     qmmm_strerror,
     qmmm_vpot,

@@ -57,7 +57,7 @@ class QMMMError(RuntimeError):
 
 _L = None
 
-EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
+EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_recip_method", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
            "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
            "qmmm_qm_images", "qmmm_aspc_predict", "qmmm_selftest_bounded_wait", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
            "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_counts", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
@@ -83,6 +83,7 @@ def load(build_if_needed: bool = True):
                                 P(c_double), c_double, c_double, P(QmmmOptions), P(c_void_p)]),
         "qmmm_set_stream": (c_int, [c_void_p, c_void_p]),
         "qmmm_set_precision": (c_int, [c_void_p, c_int]),
+        "qmmm_set_recip_method": (c_int, [c_void_p, c_int]),
         "qmmm_set_positions": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
         "qmmm_vpot": (c_int, [c_void_p, c_void_p, c_void_p]),
         "qmmm_ewald": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -205,6 +206,13 @@ def qmmm_set_stream(h, stream):
 
 def qmmm_set_precision(h, precision):
     _check(load().qmmm_set_precision(h, int(precision)), "qmmm_set_precision")
+
+
+QMMM_RECIP_CUDA_CORES, QMMM_RECIP_TENSOR, QMMM_RECIP_AUTO = 0, 1, 2
+
+
+def qmmm_set_recip_method(h, method):
+    _check(load().qmmm_set_recip_method(h, int(method)), "qmmm_set_recip_method")
 
 
 def qmmm_set_positions(h, qm_xyz, mm_xyz, mm_q=None):

@@ -133,6 +133,7 @@ struct qmmm_handle {
     cudaStream_t stream = nullptr;
     int natm = 0, nshell = 0, nprim = 0, nmm = 0, nao = 0;
     int precision = QMMM_FP64;
+    int recip_mode = QMMM_RECIP_AUTO;  // structure-factor method requested (see select_recip)
     double box[3] = {0, 0, 0}, cutoff = 0, alpha = 0, ewald_rc = 0;
     int kmax[3] = {0, 0, 0};
     double screen_tol = 1e-14;
@@ -181,6 +182,10 @@ struct qmmm_handle {
     DBuf<double2> S, Spart, A, Az;
     DBuf<float4> Adf, Azdf;
     DBuf<int> err;
+    DBuf<int4> tc_phase;  // tensor-core structure factor scratch (allocated on first use)
+    DBuf<uint32_t> tc_bpl;
+    DBuf<int> tc_part;
+    DBuf<double> tc_bmax;
 
     BasisDev basis() const
     {
@@ -256,6 +261,7 @@ struct qmmm_handle {
         mult_init.release(); gqm.release(); gchg.release(); dq_int.release(); dR_int.release();
         dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
         boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); err.release();
+        tc_phase.release(); tc_bpl.release(); tc_part.release(); tc_bmax.release();
         Adf.release(); Azdf.release();
     }
 };
@@ -322,6 +328,29 @@ int copy_out(qmmm_handle *h, double *dst, const double *src, size_t n)
     return QMMM_OK;
 }
 
+// The structure-factor method in effect (QMMM_RECIP_AUTO: tensor cores for the mixed path, FP64
+// on the CUDA cores otherwise); allocates the tensor-core scratch the first time it is needed.
+int select_recip(qmmm_handle *h)
+{
+    int m = h->recip_mode;
+    if (m == QMMM_RECIP_AUTO) m = h->precision == QMMM_MIXED ? QMMM_RECIP_TENSOR : QMMM_RECIP_CUDA_CORES;
+    if (m == QMMM_RECIP_TENSOR && !h->tc_part.p) {
+        const TcShape &sh = h->ew.tcs;
+        int rc;
+        if ((rc = h->tc_phase.ensure(sh.phase_rows)) || (rc = h->tc_bpl.ensure(sh.bplane_words)) ||
+            (rc = h->tc_part.ensure(sh.part_ints)) || (rc = h->tc_bmax.ensure(sh.nbmax)))
+            return rc;
+        // the padding beyond the last charge is copied but never used; keep it defined
+        CUDA_TRY(cudaMemset(h->tc_phase.p, 0, sh.phase_rows * sizeof(int4)));
+        h->ew.tcb.phase = h->tc_phase.p;
+        h->ew.tcb.bpl = h->tc_bpl.p;
+        h->ew.tcb.part = h->tc_part.p;
+        h->ew.tcb.bmax = h->tc_bmax.p;
+    }
+    h->ew.recip = m;
+    return QMMM_OK;
+}
+
 int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, const double *mm_q)
 {
     cudaStream_t st = h->stream;
@@ -385,6 +414,10 @@ int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, co
         h->cls_off_I.assign(h->ncls + 1, 0);
     }
     // region-II potential at the QM sites
+    {
+        int rc = select_recip(h);
+        if (rc) return rc;
+    }
     CUDA_TRY(launch_ewald_phi(e, h->rI.p, h->nI, h->ew, h->phi.p, h->precision == QMMM_MIXED, st));
     h->V_valid = false;
     return check_device_errors(h);
@@ -980,6 +1013,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.Adf = h->Adf.p;
         h->ew.Azdf = h->Azdf.p;
         h->ew.sums = h->sums.p;
+        h->ew.err = h->err.p;
+        tc_sf_shape(e, h->ew.tcs);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
@@ -1011,6 +1046,22 @@ int qmmm_set_precision(qmmm_handle *h, int precision)
     if (precision != h->precision) h->V_valid = false;
     h->precision = precision;
     return QMMM_OK;
+}
+
+int qmmm_set_recip_method(qmmm_handle *h, int method)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    if (method != QMMM_RECIP_CUDA_CORES && method != QMMM_RECIP_TENSOR && method != QMMM_RECIP_AUTO)
+        return fail(QMMM_ERR_ARG, "bad method");
+    const int before = h->ew.recip;
+    h->recip_mode = method;
+    int rc = select_recip(h);
+    if (rc) return rc;
+    if (h->ew.recip == before) return QMMM_OK;
+    // the region-II potential at the current geometry, by the selected method
+    CUDA_TRY(launch_ewald_phi(h->ewald(), h->rI.p, h->nI, h->ew, h->phi.p, h->precision == QMMM_MIXED, h->stream));
+    h->V_valid = false;
+    return check_device_errors(h);
 }
 
 int qmmm_set_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, const double *mm_q)

@@ -617,7 +617,9 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
     k_phi_region1<<<e.natm, 256, 0, st>>>(e, rI, nI, w.pr1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // structure factor
-    {
+    if (w.recip == 1) {
+        if ((err = launch_structure_factor_tc(e, w.tcs, w.tcb, w.S, w.err, st)) != cudaSuccess) return err;
+    } else {
         int tile = 1;
         const size_t smem = sf_smem(e, &tile);
         static size_t attr = 0, attr_df = 0;

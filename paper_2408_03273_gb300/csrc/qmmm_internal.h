@@ -104,6 +104,26 @@ cudaError_t launch_region1_fill(const EwaldDev &e, const int *blk_off, double4_3
                                 int *idx, int nblk, cudaStream_t st);
 cudaError_t launch_scan_blocks(int *blk_count, int nblk, cudaStream_t st);
 
+// Tensor-core structure factor (recip_tc.cu): tile shape and scratch.
+struct TcShape {
+    int NL = 0, mtiles = 0, ntiles = 0, ntr = 0, nkb = 0;  // lines, line tiles, N tiles (rows each), charge blocks
+    int nbmax = 0;           // blocks of the max|q| reduction
+    size_t part_ints = 0;    // per-CTA accumulator partials, int32 words
+    size_t phase_rows = 0;   // fixed-point phase entries (int4: re hi/lo, im hi/lo), whole charge blocks
+    size_t bplane_words = 0; // digit planes of the B operand (32-bit words), in shared-memory layout
+    bool staged = false;     // phase rows of each chunk staged in shared memory by TMA bulk copies
+};
+struct TcBuf {
+    int4 *phase = nullptr;      // qX [npad][NX], Y [npad][NY], Z [npad][NZ] (2^61 fixed point, split)
+    uint32_t *bpl = nullptr;    // B digit planes per (charge block, chunk, N tile)
+    int *part = nullptr;
+    double *bmax = nullptr;     // per-block max |q|
+};
+void tc_sf_shape(const EwaldDev &e, TcShape &sh);
+// S (dense, as the FP64 kernel writes it) by BF16 tensor-core products of exact digit planes
+cudaError_t launch_structure_factor_tc(const EwaldDev &e, const TcShape &sh, const TcBuf &b, double2 *S, int *err,
+                                       cudaStream_t st);
+
 // Scratch of the Ewald kernels (device buffers owned by the handle).
 struct EwaldBuf {
     double *gfac = nullptr;      // dense (kx+1)(2ky+1)(2kz+1): 2 g(G) on the half space, else 0
@@ -119,6 +139,10 @@ struct EwaldBuf {
     float4 *Adf = nullptr;       // A and Az as double-float (re.h, re.l, im.h, im.l), mixed path
     float4 *Azdf = nullptr;
     double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
+    int recip = 0;               // structure factor: 0 CUDA cores (FP64 / double-float), 1 tensor cores
+    TcShape tcs;
+    TcBuf tcb;
+    int *err = nullptr;          // device error word of the handle
 };
 int ewald_dense_size(const EwaldDev &e);
 int ewald_sf_nslice(const EwaldDev &e, int nsm, bool df);

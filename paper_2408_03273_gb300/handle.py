@@ -30,6 +30,11 @@ class Handle:
         L.qmmm_set_precision(self.h, precision)
         self.info = L.qmmm_get_info(self.h)
 
+    def set_recip_method(self, method: int):
+        """QMMM_RECIP_CUDA_CORES, QMMM_RECIP_TENSOR (structure factor on the tensor cores) or
+        QMMM_RECIP_AUTO (tensor cores for the mixed path)."""
+        L.qmmm_set_recip_method(self.h, method)
+
     def set_positions(self, qm_xyz, mm_xyz, mm_q=None):
         L.qmmm_set_positions(self.h, qm_xyz, mm_xyz, mm_q)
         self.info = L.qmmm_get_info(self.h)
