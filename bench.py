@@ -296,8 +296,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-autotune", action="store_true", help="run the class sweeps with the flop-model schedule")
     ap.add_argument("--recip", default="auto", choices=["auto", "cuda", "tensor"],
-                    help="structure factor of the reciprocal sum: auto (tensor cores for the mixed path), CUDA "
-                         "cores, or tensor cores")
+                    help="reciprocal Ewald sums: auto (= tensor), CUDA cores, or tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -328,12 +327,11 @@ def main():
     tuning = {}
 
     RECIP = {"auto": q.QMMM_RECIP_AUTO, "cuda": q.QMMM_RECIP_CUDA_CORES, "tensor": q.QMMM_RECIP_TENSOR}[args.recip]
-    RECIP_NAME = {q.QMMM_RECIP_CUDA_CORES: "CUDA cores", q.QMMM_RECIP_TENSOR: "tensor cores (exact BF16 digit planes)"}
+    RECIP_NAME = {q.QMMM_RECIP_CUDA_CORES: "CUDA cores (FP64; double-float on the mixed path)",
+                  q.QMMM_RECIP_TENSOR: "tensor cores (BF16 products of exact 7-bit digit planes, FP64 class)"}
 
     def recip_in_effect(precision):
-        if RECIP != q.QMMM_RECIP_AUTO:
-            return RECIP_NAME[RECIP]
-        return RECIP_NAME[q.QMMM_RECIP_TENSOR if precision == q.QMMM_MIXED else q.QMMM_RECIP_CUDA_CORES]
+        return RECIP_NAME[q.QMMM_RECIP_TENSOR if RECIP == q.QMMM_RECIP_AUTO else RECIP]
 
     def positions_ms(hh, n=10):
         # set_positions alone (region I and the region-II potential, i.e. the structure factor)
@@ -431,6 +429,10 @@ def main():
     ch_f = math.ceil(nI / (4096)) if nI else 0
     ch_g = math.ceil(nI / 2560) if nI else 0
     per_step = (11 + 1) + (ncls * ch_f + 2) + (ncls + 1) + (ncls + ncls * ch_g + 1 + 7 + 1 + 1)
+    if RECIP != q.QMMM_RECIP_CUDA_CORES:
+        # structure factor: 5 kernels instead of 2; MM-side sum: phases, scales and, per N tile
+        # (2 for FP64, 1 on the mixed path), B planes + MMA kernel, instead of 1
+        per_step += 3 + (5 if prec == q.QMMM_FP64 else 3)
     launches = per_step * args.steps
 
     # mixed precision beside FP64 (same GPU, same inputs), with its error against FP64
@@ -466,7 +468,7 @@ def main():
             positions_ms(hm, 3)
             pos[name] = positions_ms(hm)
         hm.set_recip_method(RECIP)
-        mixed["structure_factor"] = recip_in_effect(q.QMMM_MIXED)
+        mixed["reciprocal_sums"] = recip_in_effect(q.QMMM_MIXED)
         mixed["set_positions_ms"] = pos
         hm.close()
 
@@ -496,7 +498,7 @@ def main():
            "vs_baseline": None, "dtype": "f64" if prec == q.QMMM_FP64 else "f32+f64",
            "data": "synthetic (seeded TIP3P water box + random active-site QM region and basis)",
            "config": {"workload": describe(s, info), "precision": args.precision,
-                      "structure_factor": recip_in_effect(prec),
+                      "reciprocal_sums": recip_in_effect(prec),
                       "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "units_per_step": units_per_step,

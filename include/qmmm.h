@@ -117,16 +117,20 @@ int qmmm_set_stream(qmmm_handle *h, void *stream);
  * FP64). */
 int qmmm_set_precision(qmmm_handle *h, int precision);
 
-/* Method of the MM structure factor S(G) = sum_i q_i exp(iG.R_i) in the reciprocal Ewald sum
- * (SI, "Multipolar Ewald", long-range part), used for the region-II potential at the QM atoms:
+/* Method of the two reciprocal Ewald sums (SI, "Multipolar Ewald", long-range part): the MM
+ * structure factor S(G) = sum_i q_i exp(iG.R_i) behind the region-II potential at the QM atoms,
+ * and the MM-side sum of the adjoint (dE/dq_i, dE/dR_i from the QM multipoles):
  *   QMMM_RECIP_CUDA_CORES: FP64 (double-float for QMMM_MIXED) on the CUDA cores;
- *   QMMM_RECIP_TENSOR: S as a product of two matrices on the BF16 tensor cores, each operand
- *     split exactly into seven digit planes (a leading one and six of 7 bits) with exact FP32
- *     accumulation of the leading levels (about 2^-45 of max|q| per term: FP64-class);
- *   QMMM_RECIP_AUTO [default]: the tensor cores for QMMM_MIXED, the CUDA cores for QMMM_FP64.
- * The tensor-core scratch is allocated the first time the method is in effect: 16 N_MM
- * (kx + 2 ky + 2 kz + 3) bytes of fixed-point phases, the B-operand digit planes (about 1 KB per
- * charge at kmax 16) and the partial sums of each block of 512 charges (about 2 KB per charge).
+ *   QMMM_RECIP_TENSOR: each sum as a product of two matrices on the BF16 tensor cores, every
+ *     operand split exactly into seven digit planes (a leading one and six of 7 bits, 48-bit
+ *     fixed point) with exact FP32 accumulation of the leading digit levels: FP64 class (about
+ *     1e-12 relative on the region-II potential and the MM gradients).  The mixed path keeps
+ *     three exact levels in the MM-side sum instead of four (about 1e-9 relative; one N tile);
+ *     the MM-side sum stays on the CUDA cores when 2 kz + 1 < 8;
+ *   QMMM_RECIP_AUTO [default]: QMMM_RECIP_TENSOR.
+ * The tensor-core scratch is allocated the first time the method is in effect: fixed-point
+ * phase rows (16 (kx + 4 ky + 4 kz + 5) bytes per charge), the B-operand digit planes and the
+ * structure factor's partial sums (about 3 KB per charge at kmax 16 in all).
  * Recomputes the region-II potential at the current geometry if the method in effect changes.
  * QMMM_ERR_ARG for another value. */
 enum { QMMM_RECIP_CUDA_CORES = 0, QMMM_RECIP_TENSOR = 1, QMMM_RECIP_AUTO = 2 };

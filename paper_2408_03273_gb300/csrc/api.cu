@@ -186,6 +186,9 @@ struct qmmm_handle {
     DBuf<uint32_t> tc_bpl;
     DBuf<int> tc_part;
     DBuf<double> tc_bmax;
+    DBuf<int4> mmr_phase;  // tensor-core MM-side reciprocal sum scratch
+    DBuf<uint32_t> mmr_bpl;
+    DBuf<double> mmr_cscale;
 
     BasisDev basis() const
     {
@@ -262,6 +265,7 @@ struct qmmm_handle {
         dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
         boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); err.release();
         tc_phase.release(); tc_bpl.release(); tc_part.release(); tc_bmax.release();
+        mmr_phase.release(); mmr_bpl.release(); mmr_cscale.release();
         Adf.release(); Azdf.release();
     }
 };
@@ -328,12 +332,12 @@ int copy_out(qmmm_handle *h, double *dst, const double *src, size_t n)
     return QMMM_OK;
 }
 
-// The structure-factor method in effect (QMMM_RECIP_AUTO: tensor cores for the mixed path, FP64
-// on the CUDA cores otherwise); allocates the tensor-core scratch the first time it is needed.
+// The reciprocal-sum method in effect (QMMM_RECIP_AUTO: the tensor cores); allocates the
+// tensor-core scratch the first time it is needed.
 int select_recip(qmmm_handle *h)
 {
     int m = h->recip_mode;
-    if (m == QMMM_RECIP_AUTO) m = h->precision == QMMM_MIXED ? QMMM_RECIP_TENSOR : QMMM_RECIP_CUDA_CORES;
+    if (m == QMMM_RECIP_AUTO) m = QMMM_RECIP_TENSOR;
     if (m == QMMM_RECIP_TENSOR && !h->tc_part.p) {
         const TcShape &sh = h->ew.tcs;
         int rc;
@@ -346,6 +350,18 @@ int select_recip(qmmm_handle *h)
         h->ew.tcb.bpl = h->tc_bpl.p;
         h->ew.tcb.part = h->tc_part.p;
         h->ew.tcb.bmax = h->tc_bmax.p;
+        const MmrShape &m0 = h->ew.mms[0], &m1 = h->ew.mms[1];
+        if (m0.supported || m1.supported) {
+            if ((rc = h->mmr_phase.ensure(m0.phase_rows)) ||
+                (rc = h->mmr_bpl.ensure(std::max(m0.bplane_words, m1.bplane_words))) ||
+                (rc = h->mmr_cscale.ensure(3 * (h->kmax[0] + 1))))
+                return rc;
+            // the rows of padding charges are copied but never used; keep them defined
+            CUDA_TRY(cudaMemset(h->mmr_phase.p, 0, m0.phase_rows * sizeof(int4)));
+            h->ew.mmb.phase = h->mmr_phase.p;
+            h->ew.mmb.bpl = h->mmr_bpl.p;
+            h->ew.mmb.cscale = h->mmr_cscale.p;
+        }
     }
     h->ew.recip = m;
     return QMMM_OK;
@@ -1015,6 +1031,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sums = h->sums.p;
         h->ew.err = h->err.p;
         tc_sf_shape(e, h->ew.tcs);
+        tc_mmr_shape(e, 5, h->ew.mms[0]);
+        tc_mmr_shape(e, 4, h->ew.mms[1]);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));

@@ -1092,6 +1092,15 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
         k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A, w.Az, df ? w.Adf : nullptr,
                                                          df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        const MmrShape &ms = w.mms[df ? 1 : 0];
+        if (w.recip == 1 && ms.supported) {
+            if ((err = launch_mm_recip_tc(e, ms, w.mmb, w.A, w.Az, dq_int, dR_int, w.err, st)) != cudaSuccess)
+                return err;
+            k_mm_background<<<(e.nmm + 255) / 256, 256, 0, st>>>(e, w.sums, dq_int);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            k_qm_tensor_grad<<<(e.natm + 63) / 64, 64, 0, st>>>(e.natm, mult, phi, gqm);
+            return cudaGetLastError();
+        }
         const size_t smem = mm_recip_smem(e);
         static size_t attr = 0, attr_df = 0;
         size_t &a = df ? attr_df : attr;

@@ -1,0 +1,449 @@
+// mmrecip_tc.cu -- the MM side of the reciprocal Ewald sum (SI, "Multipolar Ewald", long-range
+// part, differentiated for the adjoint) on the tensor cores:
+//
+//   dE/dq_i += sum_G Re[A(G) e^{-iG.R_i}],   dE/dR_i += q_i sum_G G Im[A(G) e^{-iG.R_i}]
+//
+// over the half space of the kmax cube, with A(G) = 2 g(G) sum_j e^{iG.R_j} (Q_j + i G.mu_j
+// - 1/2 G.theta_j.G) from the QM multipoles and the separable phase e^{-iG.R} = X(n_x) Y(n_y) Z(n_z).
+// Over K = (n_y, n_z) the sum is a product of two matrices followed by a short contraction:
+//
+//   T_k[i, n_x] = sum_{n_y, n_z} C_k[n_x, n_y, n_z] Y_i(n_y) Z_i(n_z),   C_0 = A, C_1 = G_y A, C_2 = G_z A,
+//   dE/dq_i = Re sum X_i T_0,  f_x = sum G_x Im(X_i T_0),  f_y = sum Im(X_i T_1),  f_z = sum Im(X_i T_2).
+//
+// A operand (M = 128 charges x K): the outer products Y_i(n_y) Z_i(n_z), digitised on chip from
+// fixed-point phase rows staged by TMA; B operand (N = 112 rows (k, n_x, re/im) x K): C_k divided
+// by a power of two per (k, n_x) so that |C| <= 1, digitised once per call into the shared-memory
+// layout.  Digits as for the structure factor (tc_digits.cuh): 28 plane pairs per K-step into
+// FP32 accumulators in tensor memory, five (levels 0..3 kept apart, 4..6 merged: FP64 class; the
+// three channels then take two N tiles) or four (levels 0..2 apart, 3..6 merged: about 2^-35 of
+// the largest row coefficient, for the mixed-precision path, one N tile).  Level 0
+// is exact for any input while 4096 x 2 N_y N_z < 2^24 (kmax <= 20) and beyond that unless the
+// row-normalised coefficients, which decay as exp(-G^2/4 alpha^2), sum to more than 2^11 in
+// magnitude; levels 1 and 2 are sums of random-sign digit products, typically 2^17 or less.  The epilogue
+// (one thread per charge) combines the levels exactly in 64-bit integers, applies the row scales
+// and contracts with X_i(n_x) in FP64.
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "qmmm_internal.h"
+#include "tc_common.cuh"
+#include "tc_digits.cuh"
+
+namespace qmmm {
+
+namespace {
+using namespace tcd;
+constexpr int MM = 128;                 // charges per tile (MMA M)
+constexpr int NRMAX = 128;              // N rows (channel k, n_x, re/im) of one tile, a multiple of 16
+constexpr int KC = 16;                  // K entries per chunk: 8 (n_y, n_z) pairs x re/im
+constexpr int PCH = KC / 2;             // pairs per chunk
+constexpr int NSTGMAX = 3;              // pipeline depth (2 when three stages do not fit)
+constexpr int NACCMAX = 5;              // accumulators: levels 0 .. nacc-2 exact, the rest merged
+constexpr int NPROD = 16;               // producer warps
+constexpr int NTHR = (NPROD + 2) * 32;  // + MMA warp + loader warp
+constexpr uint32_t CMK = 128;                    // byte step between core matrices along K
+constexpr uint32_t CMN = (KC / 8) * 128;         // byte step between 8-row groups
+constexpr uint32_t APL = MM * KC * 2;            // A plane bytes per chunk
+constexpr uint32_t ROWB = MM * 16;               // one staged phase row (128 charges, int4)
+constexpr uint32_t PBUF = (2 + PCH) * ROWB;      // Y rows n_y0, n_y0 + 1 and one Z row per pair
+constexpr size_t SMEM_MAX = 232448;
+__host__ __device__ inline uint32_t mmr_bpl(int nr) { return (uint32_t)nr * KC * 2; }  // B plane bytes
+__host__ __device__ inline uint32_t mmr_stage(int nr) { return ND * (APL + mmr_bpl(nr)); }
+__host__ inline size_t mmr_smem(int nr, int nstg) { return nstg * (size_t)(mmr_stage(nr) + PBUF) + 256; }
+
+struct MmrArgs {
+    const int4 *Yt, *Zt;   // [NY][npad], [NZ][npad] split 2^61 fixed point, e^{-2 pi i n u}
+    const uint32_t *bpl;   // B planes per chunk (ND * BPL bytes)
+    const double *cscale;  // [3][NX] power-of-two row scales
+    const double *mm_xyz, *mm_q;
+    double *dq, *dR;
+    int *err;
+    int nmm, npad, NX, NY, NZ, npair, nchunk;
+    int nr, kfirst, nk, nstg;  // N rows of this tile, its channels [kfirst, kfirst + nk), stages
+    int nacc;                  // accumulators (4 or 5)
+    double box0;
+};
+}  // namespace
+
+// grid (mtiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set ch % nstg
+__global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int NSTG = a.nstg, NR = a.nr;
+    const uint32_t BPL = mmr_bpl(NR), STG = mmr_stage(NR);
+    unsigned char *pbuf0 = sm + NSTG * STG;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pbuf0 + NSTG * PBUF);
+    uint64_t *full = bars, *bfull = bars + NSTGMAX, *pfull = bars + 2 * NSTGMAX, *empty = bars + 3 * NSTGMAX;
+    uint64_t *done = bars + 4 * NSTGMAX;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * MM;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NSTGMAX; ++k) {
+            mbar_init(&full[k], NPROD);
+            mbar_init(&bfull[k], 1);
+            mbar_init(&pfull[k], 1);
+            mbar_init(&empty[k], 1);
+        }
+        mbar_init(done, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == NPROD) {
+        tc::tmem_alloc(tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    auto give_up = [&]() {
+        *abort = 1;
+        atomicOr(a.err, DEVERR_TIMEOUT);
+    };
+
+    if (warp < NPROD) {
+        // ---------------- producers: A planes, 128 charges x 8 pairs per chunk ----------------
+        // groups of 8 charges x 4 pairs (32 distinct banks), two per warp
+        constexpr int AJ = 2;
+        int e_m[AJ], e_j[AJ];
+        uint32_t e_off[AJ];
+#pragma unroll
+        for (int j = 0; j < AJ; ++j) {
+            const int combo = warp * AJ + j, rg = combo >> 1, cg = combo & 1;
+            e_m[j] = rg * 8 + (lane >> 2);
+            e_j[j] = cg * 4 + (lane & 3);
+            e_off[j] = rg * CMN + cg * CMK + (lane >> 2) * 16 + (lane & 3) * 4;
+        }
+        for (int ch = 0; ch < a.nchunk; ++ch) {
+            const int st = ch % NSTG, u = ch / NSTG;
+            if (ch >= NSTG && !tc::mbar_wait_thread(&empty[st], (u - 1) & 1, abort)) {
+                give_up();
+                break;
+            }
+            if (!tc::mbar_wait_thread(&pfull[st], u & 1, abort)) {
+                give_up();
+                break;
+            }
+            unsigned char *sA = sm + st * STG;
+            const int4 *Ys = reinterpret_cast<const int4 *>(pbuf0 + st * PBUF), *Zs = Ys + 2 * MM;
+            const int p0 = ch * PCH, iy0 = p0 / a.NZ;
+#pragma unroll
+            for (int j = 0; j < AJ; ++j) {
+                const int m = e_m[j], jp = e_j[j], p = p0 + jp;
+                if (m0 + m < a.nmm && p < a.npair) {
+                    long long re, im;  // 2^60 scale
+                    cmul61(Ys[(p / a.NZ - iy0) * MM + m], Zs[jp * MM + m], re, im);
+                    const Planes pr = planes(fixw(re, 12)), pi = planes(fixw(im, 12));
+#pragma unroll
+                    for (int s = 0; s < ND; ++s)
+                        *reinterpret_cast<uint32_t *>(sA + s * APL + e_off[j]) = pack_bf16(pr.p[s], pi.p[s]);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < ND; ++s) *reinterpret_cast<uint32_t *>(sA + s * APL + e_off[j]) = 0u;
+                }
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&full[st]);
+        }
+    } else if (warp == NPROD) {
+        if (lane == 0) {
+            // ---------------- MMA issue: 28 plane pairs per chunk ----------------
+            const uint32_t idesc = tc::idesc_bf16_f32(MM, NR);
+            for (int ch = 0; ch < a.nchunk; ++ch) {
+                const int st = ch % NSTG, u = ch / NSTG;
+                if (!tc::mbar_wait_thread(&full[st], u & 1, abort) || !tc::mbar_wait_thread(&bfull[st], u & 1, abort)) {
+                    give_up();
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t sA = smem_addr(sm + st * STG), sB = sA + ND * APL;
+#pragma unroll
+                for (int s = 0; s < ND; ++s)
+#pragma unroll
+                    for (int t = 0; t < ND - s; ++t) {
+                        const int acc = s + t < a.nacc - 1 ? s + t : a.nacc - 1;
+                        const uint32_t first = (ch == 0 && s == 0 && t == acc);
+                        const uint64_t ad = tc::smem_desc(sA + s * APL, CMK, CMN);
+                        const uint64_t bd = tc::smem_desc(sB + t * BPL, CMK, CMN);
+                        tc::mma_bf16(tbase + acc * NR, ad, bd, idesc, first ? 0u : 1u);
+                    }
+                tc::commit(&empty[st]);
+            }
+            tc::commit(done);
+        }
+    } else if (lane == 0) {
+        // ---------------- loader: phase rows and B planes of chunk ch ----------------
+        int issued = 0, pissued = 0;
+        for (int ch = 0; ch < a.nchunk; ++ch) {
+            const int st = ch % NSTG, u = ch / NSTG;
+            if (ch >= NSTG && !tc::mbar_wait_thread(&full[st], (u - 1) & 1, abort)) {
+                give_up();
+                break;
+            }
+            const int p0 = ch * PCH, iy0 = p0 / a.NZ, iy1 = min(iy0 + 1, a.NY - 1);
+            const int nvalid = min(PCH, a.npair - p0);
+            unsigned char *dst = pbuf0 + st * PBUF;
+            mbar_arrive_expect_tx(&pfull[st], (2 + nvalid) * ROWB);
+            bulk_g2s(dst, a.Yt + (size_t)iy0 * a.npad + m0, ROWB, &pfull[st]);
+            bulk_g2s(dst + ROWB, a.Yt + (size_t)iy1 * a.npad + m0, ROWB, &pfull[st]);
+            for (int j = 0; j < nvalid; ++j) {
+                const int iz = (p0 + j) % a.NZ;
+                bulk_g2s(dst + (2 + j) * ROWB, a.Zt + (size_t)iz * a.npad + m0, ROWB, &pfull[st]);
+            }
+            pissued = ch + 1;
+            if (ch >= NSTG && !tc::mbar_wait_thread(&empty[st], (u - 1) & 1, abort)) {
+                give_up();
+                break;
+            }
+            mbar_arrive_expect_tx(&bfull[st], ND * BPL);
+            bulk_g2s(sm + st * STG + ND * APL, a.bpl + (size_t)ch * (ND * BPL / 4), ND * BPL, &bfull[st]);
+            issued = ch + 1;
+        }
+        for (int ch = issued > NSTG ? issued - NSTG : 0; ch < issued; ++ch)
+            tc::mbar_wait_thread(&bfull[ch % NSTG], (ch / NSTG) & 1, abort);
+        for (int ch = pissued > NSTG ? pissued - NSTG : 0; ch < pissued; ++ch)
+            tc::mbar_wait_thread(&pfull[ch % NSTG], (ch / NSTG) & 1, abort);
+    }
+
+    // ---------------- epilogue: one thread per charge (warps 0..3) ----------------
+    if (warp < 4) {
+        if (!tc::mbar_wait_thread(done, 0, abort)) {
+            give_up();
+        } else {
+            tc::fence_after_sync();
+            const int row = 32 * warp + lane, i = m0 + row;
+            const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
+            const bool act = i < a.nmm;
+            double sn, cs;
+            sincospi(-2.0 * (act ? a.mm_xyz[3 * i] : 0.0) / a.box0, &sn, &cs);
+            double xr = 1.0, xi = 0.0;
+            double pot = 0.0;
+            double f[3] = {0.0, 0.0, 0.0};  // sum_nx Im(X T_k) (channel 0 weighted by G_x)
+            for (int nx = 0; nx < a.NX; ++nx) {
+                const double gx = 6.283185307179586476925 * nx / a.box0;
+                for (int kl = 0; kl < a.nk; ++kl) {
+                    const int k = a.kfirst + kl, col = 2 * (kl * a.NX + nx);
+                    uint32_t v[NACCMAX][2];
+#pragma unroll
+                    for (int acc = 0; acc < NACCMAX; ++acc) {
+                        v[acc][0] = v[acc][1] = 0u;
+                        if (acc < a.nacc)
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                                         : "=r"(v[acc][0]), "=r"(v[acc][1])
+                                         : "r"(tl + acc * NR + col)
+                                         : "memory");
+                    }
+                    tc::tmem_wait_ld();
+                    double t2[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        // exact levels 0 .. nacc-2 in units of 2^-21, then the merged rest
+                        long long ex = 0;
+#pragma unroll
+                        for (int l = 0; l < NACCMAX - 1; ++l)
+                            if (l < a.nacc - 1)
+                                ex += __float2ll_rn(__uint_as_float(v[l][r]) * (float)(1 << (7 * l))) << (21 - 7 * l);
+                        t2[r] = fma((double)ex, 0x1p-21, (double)__uint_as_float(v[a.nacc - 1][r]));
+                    }
+                    const double sc = __ldg(a.cscale + k * a.NX + nx) * 0x1p-12;
+                    const double tr = t2[0] * sc, ti = t2[1] * sc;
+                    if (k == 0) pot += xr * tr - xi * ti;
+                    f[k] += (k == 0 ? gx : 1.0) * (xr * ti + xi * tr);
+                }
+                const double nr = xr * cs - xi * sn;
+                xi = xr * sn + xi * cs;
+                xr = nr;
+            }
+            if (act) {
+                // each channel belongs to exactly one N tile: no two CTAs write the same output
+                const double q = a.mm_q[i];
+                if (a.kfirst == 0) a.dq[i] += pot;
+                for (int kl = 0; kl < a.nk; ++kl) a.dR[3 * i + a.kfirst + kl] += q * f[a.kfirst + kl];
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == NPROD) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, 512);
+    }
+}
+
+// Y_i(n_y) = e^{-2 pi i n_y u_y}, Z_i(n_z) = e^{-2 pi i n_z u_z} in rows over the charges:
+// Yt[iy][i], Zt[iz][i] (index iy = n_y + ky), split 2^61 fixed point.  One thread per (axis,
+// charge): the start and the step from FP64 sincospi, the recurrence in fixed point.
+__global__ void k_mmr_phases(EwaldDev e, int npad, int4 *Yt, int4 *Zt)
+{
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= 2ll * e.nmm) return;
+    const int d = 1 + (int)(item / e.nmm), i = (int)(item - (long long)(d - 1) * e.nmm);
+    const int k = e.kmax[d], len = 2 * k + 1;
+    int4 *col = (d == 1 ? Yt : Zt) + i;
+    const double u = e.mm_xyz[3 * i + d] / e.box[d];
+    double sn, cs;
+    sincospi(-2.0 * u, &sn, &cs);
+    const long long sr = fix61(cs), si = fix61(sn);
+    sincospi(2.0 * (double)k * u, &sn, &cs);  // index 0 is n = -k
+    long long pr = fix61(cs), pi = fix61(sn);
+    for (int n = 0; n < len; ++n) {
+        col[(size_t)n * npad] = split61(pr, pi);
+        const long long nr = (mul61(pr, sr) - mul61(pi, si)) * 2;
+        const long long ni = (mul61(pr, si) + mul61(pi, sr)) * 2;
+        pr = nr;
+        pi = ni;
+    }
+}
+
+// channel k of the B operand at dense index (n_x, iy, iz): C_0 = A, C_1 = G_y A, C_2 = A_z
+__device__ __forceinline__ double2 mmr_channel(const double2 *A, const double2 *Az, int k, size_t idx, double gy)
+{
+    if (k == 2) return Az[idx];
+    const double2 c = A[idx];
+    return k == 1 ? make_double2(gy * c.x, gy * c.y) : c;
+}
+
+// cscale[k NX + n_x] = 2^e >= max over (n_y, n_z) of |Re C_k|, |Im C_k| (1 where C_k vanishes);
+// one block per (k, n_x)
+__global__ void __launch_bounds__(256) k_mmr_scale(EwaldDev e, const double2 *A, const double2 *Az, double *cscale)
+{
+    __shared__ double ws[8];
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    const int k = blockIdx.x / NX, nx = blockIdx.x % NX;
+    double m = 0.0;
+    for (int t = threadIdx.x; t < NY * NZ; t += 256) {
+        const int iy = t / NZ;
+        const double gy = 6.283185307179586476925 * (iy - e.kmax[1]) / e.box[1];
+        const double2 c = mmr_channel(A, Az, k, (size_t)nx * NY * NZ + t, gy);
+        m = fmax(m, fmax(fabs(c.x), fabs(c.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < 8; ++w) r = fmax(r, ws[w]);
+        int ex = 0;
+        if (r > 0.0) frexp(r, &ex);
+        cscale[blockIdx.x] = r > 0.0 ? ldexp(1.0, ex) : 1.0;
+    }
+}
+
+// B planes of one N tile (channels [kfirst, kfirst + nk)), per chunk of 8 (n_y, n_z) pairs, in the
+// shared-memory layout: row (k, n_x, 0) holds (Re C, -Im C), row (k, n_x, 1) holds (Im C, Re C)
+// of C_k / cscale.  A warp writes 8 rows x 4 pairs: 128 contiguous bytes of each plane.
+__global__ void k_mmr_bplanes(EwaldDev e, const double2 *A, const double2 *Az, const double *cscale, int kfirst,
+                              int nk, int nr, int nchunk, uint32_t *bpl)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = (long long)nr * PCH;  // (row, pair) items of one chunk
+    if (t >= per * nchunk) return;
+    const int ch = (int)(t / per), it = (int)(t - (long long)ch * per);
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    const int lane = it & 31, grp = it >> 5;
+    const int j = (grp & 1) * 4 + (lane & 3), n = (grp >> 1) * 8 + (lane >> 2);
+    const int p = ch * PCH + j;
+    long long w0 = BAL, w1 = BAL;
+    if (n < 2 * nk * NX && p < NY * NZ) {
+        const int kl = n / (2 * NX), nx = (n % (2 * NX)) >> 1, r = n & 1, k = kfirst + kl;
+        const int iy = p / NZ, iz = p - iy * NZ;
+        const double gy = 6.283185307179586476925 * (iy - e.kmax[1]) / e.box[1];
+        const double2 c = mmr_channel(A, Az, k, ((size_t)nx * NY + iy) * NZ + iz, gy);
+        const double sc = 1.0 / cscale[k * NX + nx];  // a power of two: exact
+        const double re = c.x * sc, im = c.y * sc;
+        w0 += __double2ll_rn((r ? im : re) * 0x1p48);
+        w1 += __double2ll_rn((r ? re : -im) * 0x1p48);
+    }
+    const Planes p0 = planes(w0), p1 = planes(w1);
+    const uint32_t words = mmr_bpl(nr) / 4;
+    uint32_t *dst = bpl + (size_t)ch * ND * words + ((n >> 3) * CMN + (j >> 2) * CMK + (n & 7) * 16 + (j & 3) * 4) / 4;
+#pragma unroll
+    for (int s = 0; s < ND; ++s) dst[(size_t)s * words] = pack_bf16(p0.p[s], p1.p[s]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+// nacc = 5: levels 0..3 exact (channels split over N tiles so that 5 accumulators fit in 512
+// columns); nacc = 4: levels 0..2 exact and one tile where possible
+void tc_mmr_shape(const EwaldDev &e, int nacc, MmrShape &sh)
+{
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    sh.nacc = nacc;
+    sh.mtiles = (e.nmm + MM - 1) / MM;
+    sh.npad = sh.mtiles * MM;
+    sh.npair = NY * NZ;
+    sh.nchunk = (sh.npair + PCH - 1) / PCH;
+    const int maxr = std::min(NRMAX, 512 / nacc / 16 * 16);  // N rows that fit nacc accumulators
+    int cpt = 3;  // channels per N tile: 2 cpt NX rows
+    while (cpt > 1 && 2 * cpt * NX > maxr) --cpt;
+    sh.cpt = cpt;
+    sh.ntiles = (3 + cpt - 1) / cpt;
+    sh.nr = (2 * cpt * NX + 15) / 16 * 16;
+    sh.supported = sh.nr <= maxr && NZ >= PCH;  // a chunk of 8 pairs spans at most two n_y rows
+    sh.nstg = mmr_smem(sh.nr, 3) <= SMEM_MAX ? 3 : 2;
+    sh.phase_rows = (size_t)(NY + NZ) * sh.npad;
+    sh.bplane_words = (size_t)sh.ntiles * sh.nchunk * ND * mmr_bpl(sh.nr) / 4;
+}
+
+cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,
+                               const double2 *Az, double *dq, double *dR, int *err, cudaStream_t st)
+{
+    if (e.nmm == 0) return cudaSuccess;
+    cudaError_t rc;
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    int4 *Yt = b.phase, *Zt = Yt + (size_t)NY * sh.npad;
+    k_mmr_phases<<<(unsigned)((2ll * e.nmm + 255) / 256), 256, 0, st>>>(e, sh.npad, Yt, Zt);
+    if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+    k_mmr_scale<<<3 * NX, 256, 0, st>>>(e, A, Az, b.cscale);
+    if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+    const size_t smem = mmr_smem(sh.nr, sh.nstg);
+    static size_t attr = 0;
+    if (smem > attr) {
+        if ((rc = cudaFuncSetAttribute(k_mm_recip_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return rc;
+        attr = smem;
+    }
+    const size_t tile_words = (size_t)sh.nchunk * ND * mmr_bpl(sh.nr) / 4;
+    for (int tl = 0; tl < sh.ntiles; ++tl) {
+        const int kfirst = tl * sh.cpt, nk = std::min(sh.cpt, 3 - kfirst);
+        uint32_t *bpl = b.bpl + tl * tile_words;
+        const long long n = (long long)sh.nr * PCH * sh.nchunk;
+        k_mmr_bplanes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr, sh.nchunk,
+                                                                    bpl);
+        if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+        MmrArgs a;
+        a.Yt = Yt;
+        a.Zt = Zt;
+        a.bpl = bpl;
+        a.cscale = b.cscale;
+        a.mm_xyz = e.mm_xyz;
+        a.mm_q = e.mm_q;
+        a.dq = dq;
+        a.dR = dR;
+        a.err = err;
+        a.nmm = e.nmm;
+        a.npad = sh.npad;
+        a.NX = NX;
+        a.NY = NY;
+        a.NZ = NZ;
+        a.npair = sh.npair;
+        a.nchunk = sh.nchunk;
+        a.nr = sh.nr;
+        a.kfirst = kfirst;
+        a.nk = nk;
+        a.nstg = sh.nstg;
+        a.nacc = sh.nacc;
+        a.box0 = e.box[0];
+        k_mm_recip_tc<<<sh.mtiles, NTHR, smem, st>>>(a);
+        if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qmmm

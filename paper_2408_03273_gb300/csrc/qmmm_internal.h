@@ -124,6 +124,26 @@ void tc_sf_shape(const EwaldDev &e, TcShape &sh);
 cudaError_t launch_structure_factor_tc(const EwaldDev &e, const TcShape &sh, const TcBuf &b, double2 *S, int *err,
                                        cudaStream_t st);
 
+// Tensor-core MM-side reciprocal sum (mmrecip_tc.cu): tiling and scratch.
+struct MmrShape {
+    int mtiles = 0, npad = 0, npair = 0, nchunk = 0;  // charge tiles (128), padded charges, (n_y, n_z) pairs, chunks of 8
+    int cpt = 3, ntiles = 1, nr = 0, nstg = 3;        // channels per N tile, N tiles, N rows, stages
+    int nacc = 4;                                     // accumulators (exact levels + 1)
+    bool supported = false;                           // kx small enough for one channel per tile
+    size_t phase_rows = 0;                            // Y and Z phase rows (int4)
+    size_t bplane_words = 0;                          // B digit planes of all N tiles (32-bit words)
+};
+struct MmrBuf {
+    int4 *phase = nullptr;     // Yt [NY][npad], Zt [NZ][npad]
+    uint32_t *bpl = nullptr;   // B planes per N tile and chunk
+    double *cscale = nullptr;  // [3][NX] power-of-two row scales
+};
+void tc_mmr_shape(const EwaldDev &e, int nacc, MmrShape &sh);
+// dq[i] += sum_G Re[A e^{-iG.R_i}], dR[i] += q_i sum_G G Im[A e^{-iG.R_i}] (internal order), from the
+// dense A and A_z = G_z A of k_multipole_sf, on the BF16 tensor cores (exact digit planes)
+cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,
+                               const double2 *Az, double *dq, double *dR, int *err, cudaStream_t st);
+
 // Scratch of the Ewald kernels (device buffers owned by the handle).
 struct EwaldBuf {
     double *gfac = nullptr;      // dense (kx+1)(2ky+1)(2kz+1): 2 g(G) on the half space, else 0
@@ -139,9 +159,11 @@ struct EwaldBuf {
     float4 *Adf = nullptr;       // A and Az as double-float (re.h, re.l, im.h, im.l), mixed path
     float4 *Azdf = nullptr;
     double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
-    int recip = 0;               // structure factor: 0 CUDA cores (FP64 / double-float), 1 tensor cores
+    int recip = 0;               // reciprocal sums: 0 CUDA cores (FP64 / double-float), 1 tensor cores
     TcShape tcs;
     TcBuf tcb;
+    MmrShape mms[2];             // MM-side sum: [0] FP64 class (5 accumulators), [1] mixed path (4)
+    MmrBuf mmb;
     int *err = nullptr;          // device error word of the handle
 };
 int ewald_dense_size(const EwaldDev &e);

@@ -33,12 +33,14 @@
 #include "device_common.cuh"
 #include "qmmm_internal.h"
 #include "tc_common.cuh"
+#include "tc_digits.cuh"
 
 namespace qmmm {
 
 namespace {
+using namespace tcd;
 constexpr int TCM = 128;               // lines per tile (MMA M)
-constexpr int TCND = 7;                // digit planes
+constexpr int TCND = tcd::ND;           // digit planes
 constexpr int TCKC = 32;               // K entries per chunk (16 charges x re/im): two MMA K-steps
 constexpr int TCCH = TCKC / 2;         // charges per chunk
 constexpr int TCNCH = 32;              // chunks per charge block
@@ -50,7 +52,6 @@ constexpr int TCTHREADS = (TCPROD + 2) * 32;  // + the MMA warp + the loader war
 constexpr uint32_t A_PLANE = TCM * TCKC * 2;  // bytes per A digit plane of a chunk
 constexpr uint32_t CM_K = 128;                // byte step between core matrices along K
 constexpr uint32_t CM_MN = (TCKC / 8) * 128;  // byte step between 8-row groups
-constexpr double FIX61 = 2305843009213693952.0;  // 2^61
 constexpr size_t TC_SMEM_MAX = 232448;           // 227 KB per CTA
 constexpr int BMAX_CH = 4096;                    // charges per block of the max |q| reduction
 
@@ -62,64 +63,6 @@ __host__ __device__ inline uint32_t tc_pbuf_bytes(int nrow) { return (uint32_t)T
 __host__ inline size_t tc_smem_bytes(int ntr, int nrow, bool staged)
 {
     return NSTAGE * ((size_t)tc_stage_bytes(ntr) + (staged ? (size_t)tc_pbuf_bytes(nrow) : 0)) + 256;
-}
-
-// Balanced digits: w = v + 64 sum_{k<6} 2^7k; plane 0 = w >> 42 (|.| <= 64), plane s >= 1 =
-// (((w >> 7 (6 - s)) & 127) - 64) 2^-7s in [-64, 63] 2^-7s, so sum_s p_s = 2^-42 v exactly and the
-// digit products have random signs (their sums do not drift).  Each plane is exact in BF16.
-constexpr long long BAL = 64ll * (((1ll << 42) - 1) / 127);
-struct Planes { float p[TCND]; };
-__device__ __forceinline__ Planes planes(long long w)
-{
-    Planes r;
-    const uint32_t lo = (uint32_t)w, hi = (uint32_t)((unsigned long long)w >> 32);
-    r.p[0] = (float)((int)hi >> 10);
-    uint32_t u[TCND - 1];  // u[k] = bits [7k, 7k + 7) of w (higher bits masked below)
-    u[0] = lo;
-    u[1] = lo >> 7;
-    u[2] = lo >> 14;
-    u[3] = lo >> 21;
-    u[4] = __funnelshift_r(lo, hi, 28);
-    u[5] = hi >> 3;
-#pragma unroll
-    for (int s = 1; s < TCND; ++s) {
-        const uint32_t mag = (uint32_t)(127 + 23 - 7 * s) << 23;  // 2^(23-7s): mantissa LSB 2^-7s
-        r.p[s] = __uint_as_float(mag | (u[TCND - 1 - s] & 127u)) - __uint_as_float(mag | 64u);
-    }
-    return r;
-}
-// (lo, hi) as BF16 (exact values) in one 32-bit word, lo at the lower K index
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
-}
-
-// 2^61 fixed point split into 32-bit halves: x = h 2^31 + l, l in [0, 2^31), |h| <= 2^30; an int4
-// holds (re h, re l, im h, im l)
-__device__ __forceinline__ int4 split61(long long re, long long im)
-{
-    return make_int4((int)(re >> 31), (int)(re & 0x7fffffff), (int)(im >> 31), (int)(im & 0x7fffffff));
-}
-__device__ __forceinline__ long long join61(int h, int l) { return (long long)h * 2147483648ll + l; }
-// (x y) / 2^62 for 2^61 values, within 1 unit: the low x low term is dropped
-__device__ __forceinline__ long long mul61(long long x, long long y)
-{
-    const int xh = (int)(x >> 31), xl = (int)(x & 0x7fffffff), yh = (int)(y >> 31), yl = (int)(y & 0x7fffffff);
-    return (long long)xh * yh + (((long long)xh * yl + (long long)xl * yh) >> 31);
-}
-// complex product of two split 2^61 values at 2^60 scale, within 2 units (six 32 x 32 -> 64
-// products and four for the cross terms)
-__device__ __forceinline__ void cmul61(const int4 x, const int4 y, long long &re, long long &im)
-{
-    const long long mr = (long long)x.x * y.y + (long long)x.y * y.x - (long long)x.z * y.w - (long long)x.w * y.z;
-    const long long mi = (long long)x.x * y.w + (long long)x.y * y.z + (long long)x.z * y.y + (long long)x.w * y.x;
-    re = (long long)x.x * y.x - (long long)x.z * y.z + (mr >> 31);
-    im = (long long)x.x * y.z + (long long)x.z * y.x + (mi >> 31);
-}
-// balanced-digit input w of a value v at 2^(48 + shift) scale: rounded to 2^-48, offset by BAL
-__device__ __forceinline__ long long fixw(long long v, int shift)
-{
-    return (v + (1ll << (shift - 1)) + (BAL << shift)) >> shift;
 }
 
 struct TcSfArgs {
@@ -436,7 +379,6 @@ __global__ void __launch_bounds__(256) k_absmax(const double *q, int n, double *
 // fixed-point phase rows: qx = (q_i / max|q|) X_i(n_x), py = Y_i(n_y), pz = Z_i(n_z), split 2^61;
 // one thread per (axis, charge): the start and the step from FP64 sincospi, the recurrence in
 // 2^61 fixed point (each step rounds within 2^-60; at most 2 kmax + 1 steps)
-__device__ __forceinline__ long long fix61(double v) { return __double2ll_rn(v * FIX61); }
 __global__ void k_tc_phases(EwaldDev e, const double *bmax, int nbmax, int4 *qx, int4 *py, int4 *pz)
 {
     const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;

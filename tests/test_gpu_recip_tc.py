@@ -1,7 +1,9 @@
-"""Structure factor on the tensor cores (QMMM_RECIP_TENSOR): BF16 products of exact 6-bit digit
-planes with exact FP32 accumulation of the leading levels.  The region-II potential and everything
-downstream against the oracle, on shapes that exercise the tiling: ragged line tiles (128 lines),
-one and several blocks of 512 charges, one and two N tiles (2 (2 kz + 1) > 80 rows)."""
+"""Reciprocal sums on the tensor cores (QMMM_RECIP_TENSOR): the structure factor at the QM atoms
+and the MM-side sum of the adjoint, as BF16 products of exact 7-bit digit planes with exact FP32
+accumulation of the leading levels.  The region-II potential, energies and gradients against the
+oracle, on shapes that exercise the tiling: ragged line tiles (128 lines), one and several blocks
+of 512 charges, one and two N tiles of the structure factor (2 (2 kz + 1) > 80 rows), ragged
+charge tiles of the MM-side sum, and its fallback for short n_z rows."""
 import numpy as np
 import pytest
 
@@ -16,8 +18,11 @@ CASES = {
     "tiny": dict(seed=41, n_waters=12, kmax=(5, 5, 5)),
     # two N tiles (86 rows)
     "two_ntiles": dict(seed=42, n_waters=12, kmax=(4, 4, 21)),
-    # 1200 charges: three charge blocks, the last one ragged; 3 line tiles
+    # 1200 charges: three charge blocks, the last one ragged; 3 line tiles; 10 charge tiles of
+    # the MM-side sum, the last one ragged
     "three_blocks": dict(seed=43, n_waters=400, box_A=24.0, kmax=(9, 9, 6)),
+    # 2 (2 kz + 1) < 8: the MM-side sum stays on the CUDA cores (a chunk would span three n_y rows)
+    "small_kz": dict(seed=44, n_waters=12, kmax=(5, 5, 3)),
 }
 
 
@@ -29,6 +34,11 @@ def _system(name):
 def _tc(h):
     import paper_2408_03273_gb300 as q
     h.set_recip_method(q.QMMM_RECIP_TENSOR)
+
+
+def _cuda_cores(h):
+    import paper_2408_03273_gb300 as q
+    h.set_recip_method(q.QMMM_RECIP_CUDA_CORES)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -53,7 +63,7 @@ def test_tensor_core_matches_cuda_core_reciprocal_part(name):
     # the parity tolerance, measured against the size of the reciprocal part alone
     s = _system(name)
     lr = oracle.ewald_phi(s, oracle.EW_LR)
-    a = gpu_all(s, precision=0)["phi"]
+    a = gpu_all(s, precision=0, setup=_cuda_cores)["phi"]
     b = gpu_all(s, precision=0, setup=_tc)["phi"]
     assert np.max(np.abs(a - b)) < 1e-11 * np.max(np.abs(lr))
 
@@ -69,32 +79,62 @@ def test_tensor_core_water_workload():
 def test_switching_methods_recomputes_potential():
     import paper_2408_03273_gb300 as q
     s = _system("three_blocks")
-    h = q.Handle(s)
+    h = q.Handle(s)  # QMMM_RECIP_AUTO: the tensor cores
     try:
         p0 = h.potential()
         h.set_recip_method(q.QMMM_RECIP_TENSOR)
-        p1 = h.potential()
+        assert np.array_equal(h.potential(), p0)
         h.set_recip_method(q.QMMM_RECIP_CUDA_CORES)
         p2 = h.potential()
-        assert np.array_equal(p0, p2)
-        assert rel_max(p1, p0) < 1e-12
+        assert not np.array_equal(p2, p0)
+        assert rel_max(p2, p0) < 1e-12
+        h.set_recip_method(q.QMMM_RECIP_AUTO)
+        assert np.array_equal(h.potential(), p0)
         with pytest.raises(q.QMMMError):
             h.set_recip_method(7)
     finally:
         h.close()
 
 
-def test_auto_selects_tensor_cores_for_the_mixed_path():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_auto_is_the_tensor_core_method(precision):
     import paper_2408_03273_gb300 as q
     s = _system("three_blocks")
-    h = q.Handle(s, precision=q.QMMM_MIXED)  # QMMM_RECIP_AUTO
+    h = q.Handle(s, precision=precision)  # QMMM_RECIP_AUTO
     try:
         p_auto = h.potential()
         h.set_recip_method(q.QMMM_RECIP_TENSOR)
         assert np.array_equal(h.potential(), p_auto)
-        h.set_recip_method(q.QMMM_RECIP_CUDA_CORES)  # double-float on the CUDA cores
-        p_df = h.potential()
-        assert not np.array_equal(p_df, p_auto)
-        assert rel_max(p_df, p_auto) < 1e-11
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-8)])
+def test_tensor_core_mm_side_matches_cuda_cores(name, precision, tol):
+    # the two methods differ only in the reciprocal sums: dE/dq and dE/dR_MM agree to well below
+    # the parity tolerance, measured against the size of the reciprocal part alone.  FP64: five
+    # accumulators (digit levels 0..3 exact); mixed path: four (levels 3..6 merged in FP32)
+    s = _system(name)
+    dq_lr, dR_lr = oracle.ewald_mm(s, oracle.multipoles(s), oracle.EW_LR)
+    # same precision on both sides (the mixed region-I sweeps differ from FP64 by far more)
+    a = gpu_all(s, precision=precision, setup=_cuda_cores)
+    b = gpu_all(s, precision=precision, setup=_tc)
+    assert np.max(np.abs(a["dE_dq"] - b["dE_dq"])) < tol * np.max(np.abs(dq_lr))
+    assert np.max(np.abs(a["dE_dRmm"] - b["dE_dRmm"])) < tol * np.max(np.abs(dR_lr))
+
+
+def test_tensor_core_active_site_charge_derivatives():
+    # the 60-atom active site in 59,463 charges (kmax 16: one N tile of 102 rows, 465 charge
+    # tiles) in FP64 with both reciprocal sums on the tensor cores: sampled MM-charge derivatives
+    # and the potential against the oracle
+    s = workloads.config2_active_site()
+    g = gpu_all(s, precision=0, setup=_tc)
+    assert rel_max(g["phi"], oracle.ewald_phi(s)) < TOL_FP64
+    idx = oracle.region1(s)[0]
+    rng = np.random.default_rng(11)
+    sub = np.sort(rng.choice(len(idx), 3, replace=False))
+    mm = idx[sub]
+    ref = oracle.forces(s, charge_subset=sub, mm_subset=mm)
+    assert rel_max(g["dE_dq"][mm], ref["dE_dq"][mm]) < TOL_FP64
+    assert rel_max(g["dE_dRmm"][mm], ref["dE_dRmm"][mm]) < TOL_FP64
