@@ -59,13 +59,14 @@ struct MmrArgs {
     double *dq, *dR;
     int *err;
     int nmm, npad, NX, NY, NZ, npair, nchunk;
-    int nr, kfirst, nk, nstg;  // N rows of this tile, its channels [kfirst, kfirst + nk), stages
+    int nr, cpt, nstg;         // N rows of a tile, channels per tile, stages
     int nacc;                  // accumulators (4 or 5)
     double box0;
 };
 }  // namespace
 
-// grid (mtiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set ch % nstg
+// grid (mtiles, N tiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set
+// ch % nstg
 __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -79,6 +80,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * MM;
+    // N tile blockIdx.y: channels [kfirst, kfirst + nk), its own B planes
+    const int kfirst = blockIdx.y * a.cpt, nk = min(a.cpt, 3 - kfirst);
+    const uint32_t *bpl = a.bpl + (size_t)blockIdx.y * a.nchunk * (ND * BPL / 4);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < NSTGMAX; ++k) {
@@ -117,7 +121,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             e_j[j] = cg * 4 + (lane & 3);
             e_off[j] = rg * CMN + cg * CMK + (lane >> 2) * 16 + (lane & 3) * 4;
         }
-        for (int ch = 0; ch < a.nchunk; ++ch) {
+        int z0 = 0;  // p0 mod NZ, p0 = ch * PCH (the chunk's first pair)
+        for (int ch = 0; ch < a.nchunk; ++ch, z0 = z0 + PCH >= a.NZ ? z0 + PCH - a.NZ : z0 + PCH) {
             const int st = ch % NSTG, u = ch / NSTG;
             if (ch >= NSTG && !tc::mbar_wait_thread(&empty[st], (u - 1) & 1, abort)) {
                 give_up();
@@ -129,13 +134,13 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             }
             unsigned char *sA = sm + st * STG;
             const int4 *Ys = reinterpret_cast<const int4 *>(pbuf0 + st * PBUF), *Zs = Ys + 2 * MM;
-            const int p0 = ch * PCH, iy0 = p0 / a.NZ;
+            const int p0 = ch * PCH;
 #pragma unroll
             for (int j = 0; j < AJ; ++j) {
                 const int m = e_m[j], jp = e_j[j], p = p0 + jp;
                 if (m0 + m < a.nmm && p < a.npair) {
-                    long long re, im;  // 2^60 scale
-                    cmul61(Ys[(p / a.NZ - iy0) * MM + m], Zs[jp * MM + m], re, im);
+                    long long re, im;  // 2^60 scale; the pair lies in row n_y0 + (z0 + jp >= NZ)
+                    cmul61(Ys[(z0 + jp >= a.NZ ? MM : 0) + m], Zs[jp * MM + m], re, im);
                     const Planes pr = planes(fixw(re, 12)), pi = planes(fixw(im, 12));
 #pragma unroll
                     for (int s = 0; s < ND; ++s)
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
                 break;
             }
             mbar_arrive_expect_tx(&bfull[st], ND * BPL);
-            bulk_g2s(sm + st * STG + ND * APL, a.bpl + (size_t)ch * (ND * BPL / 4), ND * BPL, &bfull[st]);
+            bulk_g2s(sm + st * STG + ND * APL, bpl + (size_t)ch * (ND * BPL / 4), ND * BPL, &bfull[st]);
             issued = ch + 1;
         }
         for (int ch = issued > NSTG ? issued - NSTG : 0; ch < issued; ++ch)
@@ -225,8 +230,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             double f[3] = {0.0, 0.0, 0.0};  // sum_nx Im(X T_k) (channel 0 weighted by G_x)
             for (int nx = 0; nx < a.NX; ++nx) {
                 const double gx = 6.283185307179586476925 * nx / a.box0;
-                for (int kl = 0; kl < a.nk; ++kl) {
-                    const int k = a.kfirst + kl, col = 2 * (kl * a.NX + nx);
+                for (int kl = 0; kl < nk; ++kl) {
+                    const int k = kfirst + kl, col = 2 * (kl * a.NX + nx);
                     uint32_t v[NACCMAX][2];
 #pragma unroll
                     for (int acc = 0; acc < NACCMAX; ++acc) {
@@ -261,8 +266,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             if (act) {
                 // each channel belongs to exactly one N tile: no two CTAs write the same output
                 const double q = a.mm_q[i];
-                if (a.kfirst == 0) a.dq[i] += pot;
-                for (int kl = 0; kl < a.nk; ++kl) a.dR[3 * i + a.kfirst + kl] += q * f[a.kfirst + kl];
+                if (kfirst == 0) a.dq[i] += pot;
+                for (int kl = 0; kl < nk; ++kl) a.dR[3 * i + kfirst + kl] += q * f[kfirst + kl];
             }
         }
     }
@@ -412,37 +417,35 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     const size_t tile_words = (size_t)sh.nchunk * ND * mmr_bpl(sh.nr) / 4;
     for (int tl = 0; tl < sh.ntiles; ++tl) {
         const int kfirst = tl * sh.cpt, nk = std::min(sh.cpt, 3 - kfirst);
-        uint32_t *bpl = b.bpl + tl * tile_words;
         const long long n = (long long)sh.nr * PCH * sh.nchunk;
         k_mmr_bplanes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr, sh.nchunk,
-                                                                    bpl);
-        if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
-        MmrArgs a;
-        a.Yt = Yt;
-        a.Zt = Zt;
-        a.bpl = bpl;
-        a.cscale = b.cscale;
-        a.mm_xyz = e.mm_xyz;
-        a.mm_q = e.mm_q;
-        a.dq = dq;
-        a.dR = dR;
-        a.err = err;
-        a.nmm = e.nmm;
-        a.npad = sh.npad;
-        a.NX = NX;
-        a.NY = NY;
-        a.NZ = NZ;
-        a.npair = sh.npair;
-        a.nchunk = sh.nchunk;
-        a.nr = sh.nr;
-        a.kfirst = kfirst;
-        a.nk = nk;
-        a.nstg = sh.nstg;
-        a.nacc = sh.nacc;
-        a.box0 = e.box[0];
-        k_mm_recip_tc<<<sh.mtiles, NTHR, smem, st>>>(a);
+                                                                    b.bpl + tl * tile_words);
         if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     }
+    MmrArgs a;
+    a.Yt = Yt;
+    a.Zt = Zt;
+    a.bpl = b.bpl;
+    a.cscale = b.cscale;
+    a.mm_xyz = e.mm_xyz;
+    a.mm_q = e.mm_q;
+    a.dq = dq;
+    a.dR = dR;
+    a.err = err;
+    a.nmm = e.nmm;
+    a.npad = sh.npad;
+    a.NX = NX;
+    a.NY = NY;
+    a.NZ = NZ;
+    a.npair = sh.npair;
+    a.nchunk = sh.nchunk;
+    a.nr = sh.nr;
+    a.cpt = sh.cpt;
+    a.nstg = sh.nstg;
+    a.nacc = sh.nacc;
+    a.box0 = e.box[0];
+    k_mm_recip_tc<<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
+    if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     return cudaSuccess;
 }
 
