@@ -175,7 +175,7 @@ struct qmmm_handle {
     DBuf<uint32_t> pp;
     DBuf<double4_32a> rI;
     DBuf<float4> rI_hi, rI_lo;
-    DBuf<double> dcls_kappa, gfac, preal, pr1, sums, phi, boys64, V, dm, F, mult, mult_init, gqm, gchg, dq_int,
+    DBuf<double> dcls_kappa, gfac, preal, precip, pr1, sums, phi, boys64, V, dm, F, mult, mult_init, gqm, gchg, dq_int,
         dR_int, dq_out, dR_out, Epart, partials, out4;
     DBuf<float> boys32;
     DBuf<double> centre_d;  // [3] QM centre for the kernels
@@ -259,7 +259,7 @@ struct qmmm_handle {
         mm_beta.release(); user_xyz.release(); user_q.release(); dshell_atom.release(); dshell_off.release();
         dshell_ao.release(); dperm.release(); mm_cls.release(); blk.release(); cls_count.release();
         rI_idx.release(); dcls_off.release(); sp.release(); pp.release(); rI.release(); rI_hi.release();
-        rI_lo.release(); dcls_kappa.release(); gfac.release(); preal.release(); pr1.release(); sums.release();
+        rI_lo.release(); dcls_kappa.release(); gfac.release(); preal.release(); precip.release(); pr1.release(); sums.release();
         phi.release(); boys64.release(); V.release(); dm.release(); F.release(); mult.release();
         mult_init.release(); gqm.release(); gchg.release(); dq_int.release(); dR_int.release();
         dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
@@ -1014,15 +1014,18 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sf_nslice = ewald_sf_nslice(e, h->nsm, false);
         h->ew.sf_nslice_df = ewald_sf_nslice(e, h->nsm, true);
         h->ew.real_nslice = ewald_real_nslice(e, h->nsm);
+        h->ew.recip_nslice = ewald_recip_nslice(e, h->nsm);
         if ((rc = h->gfac.ensure(nd)) || (rc = h->S.ensure(nd)) || (rc = h->A.ensure(nd)) || (rc = h->Az.ensure(nd)) ||
             (rc = h->Adf.ensure(nd)) || (rc = h->Azdf.ensure(nd)) ||
             (rc = h->Spart.ensure((size_t)nd * std::max(h->ew.sf_nslice, h->ew.sf_nslice_df))) ||
-            (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
+            (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) ||
+            (rc = h->precip.ensure((size_t)natm * h->ew.recip_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
             return rc;
         h->ew.gfac = h->gfac.p;
         h->ew.S = h->S.p;
         h->ew.Spart = h->Spart.p;
         h->ew.preal = h->preal.p;
+        h->ew.precip = h->precip.p;
         h->ew.pr1 = h->pr1.p;
         h->ew.A = h->A.p;
         h->ew.Az = h->Az.p;

@@ -195,6 +195,24 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double *out,
     __syncthreads();
 }
 
+// True when, with the minimum image only (no further images searched), the pair is certainly
+// farther apart than sqrt(lim2): an FP32 check in front of the FP64 evaluation.  lim2 carries a
+// margin (relative 1e-3 and 0.05 bohr) far above the FP32 rounding of the displacement, so no
+// pair the FP64 test accepts is dropped; with images beyond the minimum one it never filters.
+__device__ __forceinline__ bool far_min_image(const EwaldDev &e, double dx, double dy, double dz, float lim2)
+{
+    if (e.img[0] | e.img[1] | e.img[2]) return false;
+    const float bx = (float)e.box[0], by = (float)e.box[1], bz = (float)e.box[2];
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    const float x = fx - rintf(fx / bx) * bx, y = fy - rintf(fy / by) * by, z = fz - rintf(fz / bz) * bz;
+    return x * x + y * y + z * z > lim2;
+}
+__device__ __forceinline__ float filter_lim2(double rc, double rhat)
+{
+    const double r = fmax(rc, rhat) * 1.001 + 0.05;
+    return (float)(r * r);
+}
+
 // ---------------------------------------------------------------------------------------------
 // QM-site potential: real space (psi_SR and the T-hat correction of Eq. 10)
 // grid (nslice, natm); partial[(j*nslice + slice)*20 + c]
@@ -210,9 +228,11 @@ __global__ void __launch_bounds__(256) k_phi_real(EwaldDev e, double *partial)
     for (int k = 0; k < 20; ++k) acc[k] = 0.0;
     double T[20];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nmm; i += nslice * blockDim.x) {
-        const double q = e.mm_q[i], beta = e.mm_beta[i];
+        const double beta = e.mm_beta[i];
         const double xi = e.mm_xyz[3 * i], yi = e.mm_xyz[3 * i + 1], zi = e.mm_xyz[3 * i + 2];
         const double dx0 = Rx - xi, dy0 = Ry - yi, dz0 = Rz - zi;
+        if (far_min_image(e, dx0, dy0, dz0, filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0))) continue;
+        const double q = e.mm_q[i];
         const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
         const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
         for (int a = -e.img[0]; a <= e.img[0]; ++a)
@@ -471,27 +491,40 @@ __global__ void k_gfac(EwaldDev e, double *gfac)
     gfac[k] = 2.0 * 4.0 * PI / V * exp(-G2 / (4.0 * e.alpha * e.alpha)) / G2;
 }
 
-// QM-site reciprocal part + combination: grid natm
-__global__ void __launch_bounds__(256) k_phi_recip_combine(EwaldDev e, const double2 *S, const double *gfac,
-                                                            const double *, int, const double *, double,
-                                                            double *phi)
+// QM-site reciprocal part: grid (natm, nslice); block (j, sl) sums the dense entries of slice sl
+// for QM atom j into part[(j nslice + sl) 20 + c].  The phase exp(iG.R_j) = X(n_x) Y(n_y) Z(n_z)
+// comes from the atom's three phase rows in shared memory (one sincospi per entry), so a
+// (G, atom) term costs two complex multiplies instead of a sincos.
+constexpr int PHR_MAXN = 2 * 56 + 1;
+__global__ void __launch_bounds__(256) k_phi_recip(EwaldDev e, const double2 *S, const double *gfac, double *part)
 {
     __shared__ double scratch[8 * 20];
-    __shared__ double res[20];
-    const int j = blockIdx.x;
+    __shared__ double2 ph[3][PHR_MAXN];
+    const int j = blockIdx.x, sl = blockIdx.y, ns = gridDim.y;
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
     const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
-    const double Rx = e.qm_xyz[3 * j], Ry = e.qm_xyz[3 * j + 1], Rz = e.qm_xyz[3 * j + 2];
+    // rows: X(n_x) n_x = 0..kx; Y(n_y), Z(n_z) indexed n + k
+    for (int t = threadIdx.x; t < (kx + 1) + NY + NZ; t += blockDim.x) {
+        const int d = t <= kx ? 0 : t <= kx + NY ? 1 : 2;
+        const int idx = d == 0 ? t : d == 1 ? t - (kx + 1) : t - (kx + 1) - NY;
+        const int nn = d == 0 ? idx : idx - e.kmax[d];
+        double sn, cs;
+        sincospi(2.0 * nn * (e.qm_xyz[3 * j + d] / e.box[d]), &sn, &cs);
+        ph[d][idx] = make_double2(cs, sn);
+    }
+    __syncthreads();
+    const int per = (n + ns - 1) / ns, k0 = sl * per, k1 = min(n, k0 + per);
     double acc[20];
 #pragma unroll
     for (int k = 0; k < 20; ++k) acc[k] = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const double g = gfac[k];
         if (g == 0.0) continue;
-        const int nx = k / (NY * NZ), ny = (k / NZ) % NY - ky, nz = k % NZ - kz;
-        const double Gx = TWO_PI * nx / e.box[0], Gy = TWO_PI * ny / e.box[1], Gz = TWO_PI * nz / e.box[2];
-        double s, c;
-        sincos(Gx * Rx + Gy * Ry + Gz * Rz, &s, &c);
+        const int nx = k / (NY * NZ), iy = (k / NZ) % NY, iz = k % NZ;
+        const double Gx = TWO_PI * nx / e.box[0], Gy = TWO_PI * (iy - ky) / e.box[1],
+                     Gz = TWO_PI * (iz - kz) / e.box[2];
+        const double2 p = cmul(cmul(ph[0][nx], ph[1][iy]), ph[2][iz]);
+        const double c = p.x, s = p.y;
         const double2 Sk = S[k];
         // exp(i G.R_j) conj(S)
         const double re = g * (c * Sk.x + s * Sk.y);
@@ -507,8 +540,17 @@ __global__ void __launch_bounds__(256) k_phi_recip_combine(EwaldDev e, const dou
         acc[16] += s6 * G[1] * G[1] * G[1]; acc[17] += s6 * G[1] * G[1] * G[2]; acc[18] += s6 * G[1] * G[2] * G[2];
         acc[19] += s6 * G[2] * G[2] * G[2];
     }
-    block_reduce_store<20>(acc, res, scratch);
-    if (threadIdx.x < 20) phi[(size_t)j * 20 + threadIdx.x] = res[threadIdx.x];
+    block_reduce_store<20>(acc, part + ((size_t)j * ns + sl) * 20, scratch);
+}
+
+// G slices per QM atom of the reciprocal part: two blocks per SM in all
+int ewald_recip_nslice(const EwaldDev &e, int nsm)
+{
+    int ns = (2 * nsm + e.natm - 1) / (e.natm > 0 ? e.natm : 1);
+    const int n = ewald_dense_size(e);
+    if (ns > (n + 1023) / 1024) ns = (n + 1023) / 1024;
+    if (ns < 1) ns = 1;
+    return ns;
 }
 
 int ewald_dense_size(const EwaldDev &e)
@@ -590,12 +632,13 @@ cudaError_t launch_sum_strided(const double *x, int n, int stride, double *out, 
     return cudaGetLastError();
 }
 
-__global__ void k_phi_final(EwaldDev e, const double *res_recip, const double *preal, int nslice, const double *pr1,
-                            const double *sums, double *phi)
+__global__ void k_phi_final(EwaldDev e, const double *precip, int rslice, const double *preal, int nslice,
+                            const double *pr1, const double *sums, double *phi)
 {
     const int j = blockIdx.x, k = threadIdx.x;
     if (k >= 20) return;
-    double v = res_recip[(size_t)j * 20 + k];
+    double v = 0.0;
+    for (int sl = 0; sl < rslice; ++sl) v += precip[((size_t)j * rslice + sl) * 20 + k];
     for (int sl = 0; sl < nslice; ++sl) v += preal[((size_t)j * nslice + sl) * 20 + k];
     v += pr1[(size_t)j * 20 + k];
     if (k == 0) v += -PI / (e.box[0] * e.box[1] * e.box[2] * e.alpha * e.alpha) * sums[0];
@@ -641,10 +684,10 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
         k_sum_slices<<<(n + 255) / 256, 256, 0, st>>>(w.Spart, nslice, n, w.S);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    // reciprocal part at the QM sites into phi (temporarily), then the final combination
-    k_phi_recip_combine<<<e.natm, 256, 0, st>>>(e, w.S, w.gfac, nullptr, 0, nullptr, 0.0, phi);
+    // reciprocal part at the QM sites (G slices), then the final combination in a fixed order
+    k_phi_recip<<<dim3(e.natm, w.recip_nslice), 256, 0, st>>>(e, w.S, w.gfac, w.precip);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    k_phi_final<<<e.natm, 32, 0, st>>>(e, phi, w.preal, w.real_nslice, w.pr1, w.sums, phi);
+    k_phi_final<<<e.natm, 32, 0, st>>>(e, w.precip, w.recip_nslice, w.preal, w.real_nslice, w.pr1, w.sums, phi);
     return cudaGetLastError();
 }
 
@@ -706,10 +749,12 @@ __global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_real(EwaldDev e, const
     const double xi = e.mm_xyz[3 * ii], yi = e.mm_xyz[3 * ii + 1], zi = e.mm_xyz[3 * ii + 2];
     const double rc2 = e.ewald_rc * e.ewald_rc;
     const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
+    const float lim2 = filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0);
     double pot = 0.0, fld[3] = {0.0, 0.0, 0.0}, T[20];
     for (int j = warp; act && j < e.natm; j += MMQ_WARPS) {
         const double dx0 = __ldg(e.qm_xyz + 3 * j) - xi, dy0 = __ldg(e.qm_xyz + 3 * j + 1) - yi,
                      dz0 = __ldg(e.qm_xyz + 3 * j + 2) - zi;
+        if (far_min_image(e, dx0, dy0, dz0, lim2)) continue;
         const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
         for (int a = -e.img[0]; a <= e.img[0]; ++a)
             for (int b = -e.img[1]; b <= e.img[1]; ++b)

@@ -153,6 +153,8 @@ struct EwaldBuf {
     int sf_nslice_df = 1;  // the same for the double-float kernel
     double *preal = nullptr;     // natm * real_nslice * 20
     int real_nslice = 1;
+    double *precip = nullptr;    // natm * recip_nslice * 20 (reciprocal part per G slice)
+    int recip_nslice = 1;
     double *pr1 = nullptr;       // natm * 20
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
     double2 *Az = nullptr;       // G_z times A
@@ -169,6 +171,7 @@ struct EwaldBuf {
 int ewald_dense_size(const EwaldDev &e);
 int ewald_sf_nslice(const EwaldDev &e, int nsm, bool df);
 int ewald_real_nslice(const EwaldDev &e, int nsm);
+int ewald_recip_nslice(const EwaldDev &e, int nsm);
 cudaError_t launch_gfac(const EwaldDev &e, double *gfac, cudaStream_t st);
 // v_j,c (natm*20) at the current geometry
 // df: double-float reciprocal sums (mixed-precision path) instead of FP64
