@@ -179,7 +179,7 @@ struct qmmm_handle {
         dR_int, dq_out, dR_out, Epart, partials, out4;
     DBuf<float> boys32;
     DBuf<double> centre_d;  // [3] QM centre for the kernels
-    DBuf<double2> S, Spart, A, Az;
+    DBuf<double2> S, Spart, A, Az, atom_ph;
     DBuf<float4> Adf, Azdf;
     DBuf<int> err;
     DBuf<int4> tc_phase;  // tensor-core structure factor scratch (allocated on first use)
@@ -263,7 +263,7 @@ struct qmmm_handle {
         phi.release(); boys64.release(); V.release(); dm.release(); F.release(); mult.release();
         mult_init.release(); gqm.release(); gchg.release(); dq_int.release(); dR_int.release();
         dq_out.release(); dR_out.release(); Epart.release(); partials.release(); out4.release();
-        boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); err.release();
+        boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); atom_ph.release(); err.release();
         tc_phase.release(); tc_bpl.release(); tc_part.release(); tc_bmax.release();
         mmr_phase.release(); mmr_bpl.release(); mmr_cscale.release();
         Adf.release(); Azdf.release();
@@ -1019,13 +1019,15 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
             (rc = h->Adf.ensure(nd)) || (rc = h->Azdf.ensure(nd)) ||
             (rc = h->Spart.ensure((size_t)nd * std::max(h->ew.sf_nslice, h->ew.sf_nslice_df))) ||
             (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) ||
-            (rc = h->precip.ensure((size_t)natm * h->ew.recip_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)))
+            (rc = h->precip.ensure((size_t)natm * h->ew.recip_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)) ||
+            (rc = h->atom_ph.ensure((size_t)natm * 3 * (2 * 56 + 1))))
             return rc;
         h->ew.gfac = h->gfac.p;
         h->ew.S = h->S.p;
         h->ew.Spart = h->Spart.p;
         h->ew.preal = h->preal.p;
         h->ew.precip = h->precip.p;
+        h->ew.atom_ph = h->atom_ph.p;
         h->ew.pr1 = h->pr1.p;
         h->ew.A = h->A.p;
         h->ew.Az = h->Az.p;

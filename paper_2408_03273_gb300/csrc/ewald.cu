@@ -827,10 +827,28 @@ __global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_region1(EwaldDev e, co
     }
 }
 
+// Phase rows of the QM atoms: ph[(j 3 + d) PHR_MAXN + idx] = exp(2 pi i n u_jd), idx = n for
+// d = 0 (n = 0..kx) and n + k_d for d = 1, 2 (n = -k_d..k_d); one sincospi per entry
+__global__ void k_atom_phases(EwaldDev e, double2 *ph)
+{
+    const int j = blockIdx.x;
+    const int kx = e.kmax[0], NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    for (int t = threadIdx.x; t < (kx + 1) + NY + NZ; t += blockDim.x) {
+        const int d = t <= kx ? 0 : t <= kx + NY ? 1 : 2;
+        const int idx = d == 0 ? t : d == 1 ? t - (kx + 1) : t - (kx + 1) - NY;
+        const int nn = d == 0 ? idx : idx - e.kmax[d];
+        double sn, cs;
+        sincospi(2.0 * nn * (e.qm_xyz[3 * j + d] / e.box[d]), &sn, &cs);
+        ph[((size_t)j * 3 + d) * PHR_MAXN + idx] = make_double2(cs, sn);
+    }
+}
+
 // A(G) = 2 g(G) sum_j exp(i G.R_j) (Q_j + i G.mu_j - 1/2 G.theta_j.G) on the dense box, and
-// Az(G) = G_z A(G) (the z-field channel of the MM-side sum)
-__global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *gfac, const double *mult, double2 *A,
-                                                      double2 *Az, float4 *Adf, float4 *Azdf)
+// Az(G) = G_z A(G) (the z-field channel of the MM-side sum); exp(i G.R_j) from the atom's phase
+// rows (two complex multiplies)
+__global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *gfac, const double *mult,
+                                                      const double2 *ph, double2 *A, double2 *Az, float4 *Adf,
+                                                      float4 *Azdf)
 {
     const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
     const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
@@ -854,8 +872,9 @@ __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *
         const double mr = M[0] - 0.5 * (M[4] * Gx * Gx + 2.0 * M[5] * Gx * Gy + 2.0 * M[6] * Gx * Gz + M[7] * Gy * Gy +
                                         2.0 * M[8] * Gy * Gz + M[9] * Gz * Gz);
         const double mi = Gx * M[1] + Gy * M[2] + Gz * M[3];
-        double s, c;
-        sincos(Gx * e.qm_xyz[3 * j] + Gy * e.qm_xyz[3 * j + 1] + Gz * e.qm_xyz[3 * j + 2], &s, &c);
+        const double2 *pj = ph + (size_t)j * 3 * PHR_MAXN;
+        const double2 p = cmul(cmul(__ldg(pj + nx), __ldg(pj + PHR_MAXN + ny + ky)), __ldg(pj + 2 * PHR_MAXN + nz + kz));
+        const double s = p.y, c = p.x;
         re += c * mr - s * mi;
         im += s * mr + c * mi;
     }
@@ -1134,8 +1153,10 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
     }
     if (e.nmm > 0) {
         const int n = ewald_dense_size(e);
-        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.A, w.Az, df ? w.Adf : nullptr,
-                                                         df ? w.Azdf : nullptr);
+        k_atom_phases<<<e.natm, 128, 0, st>>>(e, w.atom_ph);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.atom_ph, w.A, w.Az,
+                                                         df ? w.Adf : nullptr, df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         const MmrShape &ms = w.mms[df ? 1 : 0];
         if (w.recip == 1 && ms.supported) {

@@ -154,6 +154,7 @@ struct EwaldBuf {
     double *preal = nullptr;     // natm * real_nslice * 20
     int real_nslice = 1;
     double *precip = nullptr;    // natm * recip_nslice * 20 (reciprocal part per G slice)
+    double2 *atom_ph = nullptr;  // natm * 3 * (2 * 56 + 1) phase rows of the QM atoms
     int recip_nslice = 1;
     double *pr1 = nullptr;       // natm * 20
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
