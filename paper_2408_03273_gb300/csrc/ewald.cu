@@ -217,45 +217,78 @@ __device__ __forceinline__ float filter_lim2(double rc, double rhat)
 // QM-site potential: real space (psi_SR and the T-hat correction of Eq. 10)
 // grid (nslice, natm); partial[(j*nslice + slice)*20 + c]
 // ---------------------------------------------------------------------------------------------
+// The charges of a slice are scanned 256 at a time with the FP32 filter; the survivors are
+// compacted into a shared queue in charge order (warp ballots and a block scan, so the order and
+// hence the sums are the same on every run) and evaluated in FP64 by all threads once 256 have
+// gathered, so the FP64 pipe runs full warps instead of one or two lanes of each.
+constexpr int PR_Q = 512;
 __global__ void __launch_bounds__(256) k_phi_real(EwaldDev e, double *partial)
 {
     __shared__ double scratch[8 * 20];
+    __shared__ int queue[PR_Q];
+    __shared__ int wcnt[8];
     const int j = blockIdx.y, nslice = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double Rx = e.qm_xyz[3 * j], Ry = e.qm_xyz[3 * j + 1], Rz = e.qm_xyz[3 * j + 2];
     const double rc2 = e.ewald_rc * e.ewald_rc;
+    const int per = (e.nmm + nslice - 1) / nslice, i0 = blockIdx.x * per, i1 = min(e.nmm, i0 + per);
     double acc[20];
 #pragma unroll
     for (int k = 0; k < 20; ++k) acc[k] = 0.0;
     double T[20];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nmm; i += nslice * blockDim.x) {
-        const double beta = e.mm_beta[i];
-        const double xi = e.mm_xyz[3 * i], yi = e.mm_xyz[3 * i + 1], zi = e.mm_xyz[3 * i + 2];
-        const double dx0 = Rx - xi, dy0 = Ry - yi, dz0 = Rz - zi;
-        if (far_min_image(e, dx0, dy0, dz0, filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0))) continue;
-        const double q = e.mm_q[i];
-        const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
-        const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
-        for (int a = -e.img[0]; a <= e.img[0]; ++a)
-            for (int b = -e.img[1]; b <= e.img[1]; ++b)
-                for (int c = -e.img[2]; c <= e.img[2]; ++c) {
-                    const double sx = (nx0 + a) * e.box[0], sy = (ny0 + b) * e.box[1], sz = (nz0 + c) * e.box[2];
-                    const double x = dx0 - sx, y = dy0 - sy, z = dz0 - sz;
-                    const double r2 = x * x + y * y + z * z;
-                    if (r2 < rc2) {
-                        double f, g1, g2, g3;
-                        screened_radial(r2, e.alpha, f, g1, g2, g3);
-                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+    int count = 0;  // block-uniform
+    for (int base = i0; base < i1; base += 256) {
+        const int i = base + threadIdx.x;
+        bool cand = false;
+        if (i < i1) {
+            const double beta = e.mm_beta[i];
+            cand = !far_min_image(e, Rx - e.mm_xyz[3 * i], Ry - e.mm_xyz[3 * i + 1], Rz - e.mm_xyz[3 * i + 2],
+                                  filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0));
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = count, tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) off += wcnt[w];
+            tot += wcnt[w];
+        }
+        if (cand) queue[off + __popc(bal & ((1u << lane) - 1u))] = i;
+        count += tot;
+        __syncthreads();
+        if (count < 256 && base + 256 < i1) continue;
+        // FP64 evaluation of the queued charges, entry q by thread q mod 256
+        for (int qi = threadIdx.x; qi < count; qi += 256) {
+            const int ic = queue[qi];
+            const double q = e.mm_q[ic], beta = e.mm_beta[ic];
+            const double xi = e.mm_xyz[3 * ic], yi = e.mm_xyz[3 * ic + 1], zi = e.mm_xyz[3 * ic + 2];
+            const double dx0 = Rx - xi, dy0 = Ry - yi, dz0 = Rz - zi;
+            const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
+            const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
+            for (int a = -e.img[0]; a <= e.img[0]; ++a)
+                for (int b = -e.img[1]; b <= e.img[1]; ++b)
+                    for (int c = -e.img[2]; c <= e.img[2]; ++c) {
+                        const double sx = (nx0 + a) * e.box[0], sy = (ny0 + b) * e.box[1], sz = (nz0 + c) * e.box[2];
+                        const double x = dx0 - sx, y = dy0 - sy, z = dz0 - sz;
+                        const double r2 = x * x + y * y + z * z;
+                        if (r2 < rc2) {
+                            double f, g1, g2, g3;
+                            screened_radial(r2, e.alpha, f, g1, g2, g3);
+                            radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
 #pragma unroll
-                        for (int k = 0; k < 20; ++k) acc[k] += q * T[k];
-                    }
-                    if (r2 < rhat2 && !in_region1(e, xi + sx, yi + sy, zi + sz)) {
-                        double f, g1, g2, g3;
-                        screened_radial(r2, beta, f, g1, g2, g3);
-                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+                            for (int k = 0; k < 20; ++k) acc[k] += q * T[k];
+                        }
+                        if (r2 < rhat2 && !in_region1(e, xi + sx, yi + sy, zi + sz)) {
+                            double f, g1, g2, g3;
+                            screened_radial(r2, beta, f, g1, g2, g3);
+                            radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
 #pragma unroll
-                        for (int k = 0; k < 20; ++k) acc[k] -= q * T[k];
+                            for (int k = 0; k < 20; ++k) acc[k] -= q * T[k];
+                        }
                     }
-                }
+        }
+        count = 0;
+        __syncthreads();
     }
     block_reduce_store<20>(acc, partial + ((size_t)j * nslice + blockIdx.x) * 20, scratch);
 }
@@ -738,59 +771,102 @@ __device__ __forceinline__ void mmq_reduce(double (&red)[4][MMQ_WARPS][MMQ_CH], 
             for (int v = 0; v < 4; ++v) out[v] += red[v][w][lane];
 }
 
-__global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_real(EwaldDev e, const double *mult, double *dq, double *dR)
+// Blocks of 32 MM charges.  The (charge, QM atom) pairs of a block are scanned 256 at a time with
+// the FP32 filter and the survivors compacted in pair order (charge-major) into a shared queue;
+// all threads then evaluate the queued pairs in FP64, and each charge's owner thread adds its
+// pairs' contributions in queue order (the same order on every run).
+constexpr int MR_Q = 1024;
+__global__ void __launch_bounds__(256) k_mm_real(EwaldDev e, const double *mult, double *dq, double *dR)
 {
-    __shared__ double red[4][MMQ_WARPS][MMQ_CH];
+    __shared__ int queue[MR_Q];
+    __shared__ double contrib[MR_Q][4];
+    __shared__ int wcnt[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * MMQ_CH + lane;
-    const bool act = i < e.nmm;
-    const int ii = act ? i : 0;
-    const double beta = e.mm_beta[ii];
-    const double xi = e.mm_xyz[3 * ii], yi = e.mm_xyz[3 * ii + 1], zi = e.mm_xyz[3 * ii + 2];
+    const int c0 = blockIdx.x * MMQ_CH, nch = min(MMQ_CH, e.nmm - c0), natm = e.natm;
+    const int npairs = nch * natm;
     const double rc2 = e.ewald_rc * e.ewald_rc;
-    const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
-    const float lim2 = filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0);
-    double pot = 0.0, fld[3] = {0.0, 0.0, 0.0}, T[20];
-    for (int j = warp; act && j < e.natm; j += MMQ_WARPS) {
-        const double dx0 = __ldg(e.qm_xyz + 3 * j) - xi, dy0 = __ldg(e.qm_xyz + 3 * j + 1) - yi,
-                     dz0 = __ldg(e.qm_xyz + 3 * j + 2) - zi;
-        if (far_min_image(e, dx0, dy0, dz0, lim2)) continue;
-        const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
-        for (int a = -e.img[0]; a <= e.img[0]; ++a)
-            for (int b = -e.img[1]; b <= e.img[1]; ++b)
-                for (int c = -e.img[2]; c <= e.img[2]; ++c) {
-                    const double sx = (nx0 + a) * e.box[0], sy = (ny0 + b) * e.box[1], sz = (nz0 + c) * e.box[2];
-                    const double x = dx0 - sx, y = dy0 - sy, z = dz0 - sz;
-                    const double r2 = x * x + y * y + z * z;
-                    const bool sr = r2 < rc2;
-                    const bool hat = r2 < rhat2 && !in_region1(e, xi + sx, yi + sy, zi + sz);
-                    if (!sr && !hat) continue;
-                    double Mj[10];
+    double sum[4] = {0.0, 0.0, 0.0, 0.0};  // charge threadIdx.x (< nch)
+    double T[20];
+    int count = 0;  // block-uniform
+    for (int base = 0; base < npairs; base += 256) {
+        const int t = base + threadIdx.x;
+        bool cand = false;
+        if (t < npairs) {
+            const int il = t / natm, j = t - il * natm, i = c0 + il;
+            const double beta = e.mm_beta[i];
+            cand = !far_min_image(e, __ldg(e.qm_xyz + 3 * j) - e.mm_xyz[3 * i],
+                                  __ldg(e.qm_xyz + 3 * j + 1) - e.mm_xyz[3 * i + 1],
+                                  __ldg(e.qm_xyz + 3 * j + 2) - e.mm_xyz[3 * i + 2],
+                                  filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0));
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = count, tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) off += wcnt[w];
+            tot += wcnt[w];
+        }
+        if (cand) queue[off + __popc(bal & ((1u << lane) - 1u))] = t;
+        count += tot;
+        __syncthreads();
+        if (count <= MR_Q - 256 && base + 256 < npairs) continue;
+        for (int qi = threadIdx.x; qi < count; qi += 256) {
+            const int tq = queue[qi], il = tq / natm, j = tq - il * natm, i = c0 + il;
+            const double beta = e.mm_beta[i];
+            const double xi = e.mm_xyz[3 * i], yi = e.mm_xyz[3 * i + 1], zi = e.mm_xyz[3 * i + 2];
+            const double rhat2 = beta > 0.0 ? (9.0 / beta) * (9.0 / beta) : -1.0;
+            const double dx0 = __ldg(e.qm_xyz + 3 * j) - xi, dy0 = __ldg(e.qm_xyz + 3 * j + 1) - yi,
+                         dz0 = __ldg(e.qm_xyz + 3 * j + 2) - zi;
+            const double nx0 = rint(dx0 / e.box[0]), ny0 = rint(dy0 / e.box[1]), nz0 = rint(dz0 / e.box[2]);
+            double pot = 0.0, fld[3] = {0.0, 0.0, 0.0};
+            for (int a = -e.img[0]; a <= e.img[0]; ++a)
+                for (int b = -e.img[1]; b <= e.img[1]; ++b)
+                    for (int c = -e.img[2]; c <= e.img[2]; ++c) {
+                        const double sx = (nx0 + a) * e.box[0], sy = (ny0 + b) * e.box[1], sz = (nz0 + c) * e.box[2];
+                        const double x = dx0 - sx, y = dy0 - sy, z = dz0 - sz;
+                        const double r2 = x * x + y * y + z * z;
+                        const bool sr = r2 < rc2;
+                        const bool hat = r2 < rhat2 && !in_region1(e, xi + sx, yi + sy, zi + sz);
+                        if (!sr && !hat) continue;
+                        double Mj[10];
 #pragma unroll
-                    for (int k = 0; k < 10; ++k) Mj[k] = __ldg(mult + 10 * j + k);
-                    double f, g1, g2, g3, p, fl[3];
-                    if (sr) {
-                        screened_radial(r2, e.alpha, f, g1, g2, g3);
-                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
-                        contract_pot_field(Mj, T, p, fl);
-                        pot += p; fld[0] += fl[0]; fld[1] += fl[1]; fld[2] += fl[2];
+                        for (int k = 0; k < 10; ++k) Mj[k] = __ldg(mult + 10 * j + k);
+                        double f, g1, g2, g3, p, fl[3];
+                        if (sr) {
+                            screened_radial(r2, e.alpha, f, g1, g2, g3);
+                            radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+                            contract_pot_field(Mj, T, p, fl);
+                            pot += p; fld[0] += fl[0]; fld[1] += fl[1]; fld[2] += fl[2];
+                        }
+                        if (hat) {
+                            screened_radial(r2, beta, f, g1, g2, g3);
+                            radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
+                            contract_pot_field(Mj, T, p, fl);
+                            pot -= p; fld[0] -= fl[0]; fld[1] -= fl[1]; fld[2] -= fl[2];
+                        }
                     }
-                    if (hat) {
-                        screened_radial(r2, beta, f, g1, g2, g3);
-                        radial_tensor(f, g1, g2, g3, x, y, z, T, 3);
-                        contract_pot_field(Mj, T, p, fl);
-                        pot -= p; fld[0] -= fl[0]; fld[1] -= fl[1]; fld[2] -= fl[2];
-                    }
-                }
+            contrib[qi][0] = pot;
+            contrib[qi][1] = fld[0];
+            contrib[qi][2] = fld[1];
+            contrib[qi][3] = fld[2];
+        }
+        __syncthreads();
+        if (threadIdx.x < nch)
+            for (int qi = 0; qi < count; ++qi)
+                if (queue[qi] / natm == (int)threadIdx.x)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) sum[v] += contrib[qi][v];
+        count = 0;
+        __syncthreads();
     }
-    double t[4];
-    mmq_reduce(red, pot, fld, t);
-    if (warp == 0 && act) {
+    if (threadIdx.x < nch) {
+        const int i = c0 + threadIdx.x;
         const double q = e.mm_q[i];
-        dq[i] += t[0];
-        dR[3 * i] += -q * t[1];
-        dR[3 * i + 1] += -q * t[2];
-        dR[3 * i + 2] += -q * t[3];
+        dq[i] += sum[0];
+        dR[3 * i] += -q * sum[1];
+        dR[3 * i + 1] += -q * sum[2];
+        dR[3 * i + 2] += -q * sum[3];
     }
 }
 
@@ -1144,7 +1220,7 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
     cudaError_t err;
     if ((err = launch_sum_strided(mult, e.natm, 10, w.sums + 1, st)) != cudaSuccess) return err;
     if (e.nmm > 0) {
-        k_mm_real<<<(e.nmm + MMQ_CH - 1) / MMQ_CH, MMQ_CH * MMQ_WARPS, 0, st>>>(e, mult, dq_int, dR_int);
+        k_mm_real<<<(e.nmm + MMQ_CH - 1) / MMQ_CH, 256, 0, st>>>(e, mult, dq_int, dR_int);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (nI > 0) {
