@@ -129,6 +129,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over all ranks: the job's time is that of its slowest replica."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_step, ms):
+    """Whole-job throughput: every replica processes units_per_step per step of ms milliseconds."""
+    return world * units_per_step / (ms * 1e-3)
+
+
 def cpu_baseline(s, seconds=10.0, seed=0):
     """The FP64 oracle on the host cores: V + adjoint for a random sample of shell pairs against
     all region-I charges (same per-(shell pair, charge) unit as the GPU metric)."""
@@ -402,11 +417,8 @@ def main():
     units_per_step = info["n_shell_pairs"] * info["n_region1"]
     with Clocks(local) as clk:
         ms, rec = timed(h, args.steps, args.warmup)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * units_per_step / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_rate(world, units_per_step, ms)
 
     # dominant kernel (region-I sweep) against the plain-ALU roofline
     t_v, t_g = float(np.mean(rec["vpot"])), float(np.mean(rec["grad"]))
@@ -454,7 +466,8 @@ def main():
         t_vm, t_gm = float(np.mean(rec_m["vpot"])), float(np.mean(rec_m["grad"]))
         flm = sweep_flops(info, t_gm >= t_vm)
         ach_m = flm / (max(t_gm, t_vm) * 1e-3) / 1e12
-        mixed = {"value": world * units_per_step / (ms_m * 1e-3), "ms_per_step": ms_m,
+        ms_m = max_over_ranks(ms_m, dist, dev)
+        mixed = {"value": job_rate(world, units_per_step, ms_m), "ms_per_step": ms_m,
                  "speedup_vs_fp64": ms / ms_m, "vpot_sweep_ms": t_vm, "adjoint_sweep_ms": t_gm,
                  "rel_fro_err_V": fro, "max_rel_err_forces": gerr,
                  "rel_err_E": float(abs(Em[0] - E64[0]) / escale),
@@ -489,7 +502,7 @@ def main():
     for _ in range(ne):
         step(h, qm_h, mm_h, q_h, dm_h, V_h, En_h, EII_h, M_h, gq_h, gm_h, gc_h)
     torch.cuda.synchronize()
-    ms_e2e = (time.perf_counter() - t0) * 1e3 / ne
+    ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3 / ne, dist, dev)
     h2d = 8 * (3 * natm + 3 * nmm + nmm + 2 * nao * nao)  # positions, charges, density (ewald + forces)
     d2h = 8 * (nao * nao + 1 + 1 + 10 * natm + 3 * natm + 3 * nmm + nmm)
 
@@ -507,7 +520,7 @@ def main():
                       "sweep_schedule": ("flop-model SM split, 256-thread blocks" if args.no_autotune else
                                          {"autotuned": tuning})},
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
-           "e2e": {"value": world * units_per_step / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+           "e2e": {"value": job_rate(world, units_per_step, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
     if mixed:
         out["mixed"] = mixed
