@@ -65,3 +65,16 @@ def test_config4_invariants(c4, c4_gpu):
         assert np.max(np.abs(tot)) < (1e-9 if p == 0 else 1e-6) * np.max(np.abs(g["dE_dRqm"]))
         sc = abs(g["E_I_elec"]) + abs(g["E_nuc_mm"]) + abs(g["E_II"])
         assert abs(np.dot(c4.mm_q, g["dE_dq"]) - g["E"]) < (1e-11 if p == 0 else 1e-6) * sc
+
+
+def test_config4_tensor_core_sums_match_cuda_cores(c4, c4_gpu):
+    # kmax 24 takes the tiled shapes of both tensor-core sums (two N tiles of the structure factor,
+    # three of the FP64-class MM-side sum): against the FP64 CUDA-core kernels, which the smaller
+    # workloads pin to the oracle, relative to the largest value of each quantity
+    import paper_2408_03273_gb300 as q
+    cc = gpu_all(c4, precision=0, setup=lambda h: h.set_recip_method(q.QMMM_RECIP_CUDA_CORES))
+    tc = c4_gpu[0]
+    assert rel_max(tc["phi"], cc["phi"]) < 1e-11
+    assert rel_max(tc["dE_dq"], cc["dE_dq"]) < 1e-11
+    assert rel_max(tc["dE_dRmm"], cc["dE_dRmm"]) < 1e-10
+    assert abs(tc["E"] - cc["E"]) < 1e-11 * (abs(cc["E_I_elec"]) + abs(cc["E_nuc_mm"]) + abs(cc["E_II"]))
