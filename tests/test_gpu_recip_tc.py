@@ -138,3 +138,21 @@ def test_tensor_core_active_site_charge_derivatives():
     ref = oracle.forces(s, charge_subset=sub, mm_subset=mm)
     assert rel_max(g["dE_dq"][mm], ref["dE_dq"][mm]) < TOL_FP64
     assert rel_max(g["dE_dRmm"][mm], ref["dE_dRmm"][mm]) < TOL_FP64
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tensor_cores_at_large_kmax(precision):
+    # kmax 40: the structure factor reads its phase rows from global memory (the staging buffers
+    # would not fit in shared memory) over three N tiles and 26 line tiles; the MM-side sum runs
+    # one channel per N tile.  Against the CUDA-core kernels of the same precision.
+    import paper_2408_03273_gb300 as q
+    s = workloads.small_system(45, n_atoms=3, lmax=2, n_waters=12, kmax=(40, 40, 40))
+    a = gpu_all(s, precision=precision, setup=_cuda_cores)
+    b = gpu_all(s, precision=precision, setup=_tc)
+    lr = oracle.ewald_phi(s, oracle.EW_LR)
+    dq_lr, dR_lr = oracle.ewald_mm(s, oracle.multipoles(s), oracle.EW_LR)
+    tol = 1e-11 if precision == 0 else 1e-8
+    assert np.max(np.abs(a["phi"] - b["phi"])) < 1e-11 * np.max(np.abs(lr))
+    assert np.max(np.abs(a["dE_dq"] - b["dE_dq"])) < tol * np.max(np.abs(dq_lr))
+    assert np.max(np.abs(a["dE_dRmm"] - b["dE_dRmm"])) < tol * np.max(np.abs(dR_lr))
+    assert q.QMMM_RECIP_TENSOR == 1
