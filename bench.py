@@ -346,7 +346,10 @@ def main():
                   q.QMMM_RECIP_TENSOR: "tensor cores (BF16 products of exact 7-bit digit planes, FP64 class)"}
 
     def recip_in_effect(precision):
-        return RECIP_NAME[q.QMMM_RECIP_TENSOR if RECIP == q.QMMM_RECIP_AUTO else RECIP]
+        if RECIP != q.QMMM_RECIP_AUTO:
+            return RECIP_NAME[RECIP]
+        work = (s.kmax[0] + 1) * (2 * s.kmax[1] + 1) * (2 * s.kmax[2] + 1) * s.nmm
+        return RECIP_NAME[q.QMMM_RECIP_TENSOR if work >= 4e7 else q.QMMM_RECIP_CUDA_CORES]
 
     def positions_ms(hh, n=10):
         # set_positions alone (region I and the region-II potential, i.e. the structure factor)
@@ -441,7 +444,7 @@ def main():
     ch_f = math.ceil(nI / (4096)) if nI else 0
     ch_g = math.ceil(nI / 2560) if nI else 0
     per_step = (11 + 1) + (ncls * ch_f + 2) + (ncls + 1) + (ncls + ncls * ch_g + 1 + 7 + 1 + 1)
-    if RECIP != q.QMMM_RECIP_CUDA_CORES:
+    if recip_in_effect(prec) == RECIP_NAME[q.QMMM_RECIP_TENSOR]:
         # structure factor: 5 kernels instead of 2; MM-side sum: phases, scales and, per N tile
         # (2 for FP64, 1 on the mixed path), B planes + MMA kernel, instead of 1
         per_step += 3 + (5 if prec == q.QMMM_FP64 else 3)

@@ -127,7 +127,8 @@ int qmmm_set_precision(qmmm_handle *h, int precision);
  *     1e-12 relative on the region-II potential and the MM gradients).  The mixed path keeps
  *     three exact levels in the MM-side sum instead of four (about 1e-9 relative; one N tile);
  *     the MM-side sum stays on the CUDA cores when 2 kz + 1 < 8;
- *   QMMM_RECIP_AUTO [default]: QMMM_RECIP_TENSOR.
+ *   QMMM_RECIP_AUTO [default]: QMMM_RECIP_TENSOR when (kx + 1)(2 ky + 1)(2 kz + 1) N_MM >= 4e7,
+ *     else QMMM_RECIP_CUDA_CORES (small systems, where the extra launches outweigh the work).
  * The tensor-core scratch is allocated the first time the method is in effect: fixed-point
  * phase rows (16 (kx + 4 ky + 4 kz + 5) bytes per charge), the B-operand digit planes and the
  * structure factor's partial sums (about 3 KB per charge at kmax 16 in all).

@@ -332,12 +332,18 @@ int copy_out(qmmm_handle *h, double *dst, const double *src, size_t n)
     return QMMM_OK;
 }
 
-// The reciprocal-sum method in effect (QMMM_RECIP_AUTO: the tensor cores); allocates the
-// tensor-core scratch the first time it is needed.
+// The reciprocal-sum method in effect; allocates the tensor-core scratch the first time it is
+// needed.  QMMM_RECIP_AUTO: the tensor cores once the reciprocal work is large enough to outweigh
+// the five extra launches of each tensor-core sum (the CUDA-core kernels win below ~4e7 dense G
+// entries x charges: on the 648-charge water workload, 1.2e6, by 0.14 ms per mixed step).
+constexpr double RECIP_TC_MIN_WORK = 4e7;
 int select_recip(qmmm_handle *h)
 {
     int m = h->recip_mode;
-    if (m == QMMM_RECIP_AUTO) m = QMMM_RECIP_TENSOR;
+    if (m == QMMM_RECIP_AUTO) {
+        const double work = (double)ewald_dense_size(h->ewald()) * (double)h->nmm;
+        m = work >= RECIP_TC_MIN_WORK ? QMMM_RECIP_TENSOR : QMMM_RECIP_CUDA_CORES;
+    }
     if (m == QMMM_RECIP_TENSOR && !h->tc_part.p) {
         const TcShape &sh = h->ew.tcs;
         int rc;

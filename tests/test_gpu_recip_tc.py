@@ -79,17 +79,18 @@ def test_tensor_core_water_workload():
 def test_switching_methods_recomputes_potential():
     import paper_2408_03273_gb300 as q
     s = _system("three_blocks")
-    h = q.Handle(s)  # QMMM_RECIP_AUTO: the tensor cores
+    h = q.Handle(s)
     try:
-        p0 = h.potential()
         h.set_recip_method(q.QMMM_RECIP_TENSOR)
-        assert np.array_equal(h.potential(), p0)
+        p0 = h.potential()
         h.set_recip_method(q.QMMM_RECIP_CUDA_CORES)
         p2 = h.potential()
         assert not np.array_equal(p2, p0)
         assert rel_max(p2, p0) < 1e-12
-        h.set_recip_method(q.QMMM_RECIP_AUTO)
+        h.set_recip_method(q.QMMM_RECIP_TENSOR)
         assert np.array_equal(h.potential(), p0)
+        h.set_recip_method(q.QMMM_RECIP_AUTO)  # small: the CUDA cores
+        assert np.array_equal(h.potential(), p2)
         with pytest.raises(q.QMMMError):
             h.set_recip_method(7)
     finally:
@@ -97,16 +98,21 @@ def test_switching_methods_recomputes_potential():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_auto_is_the_tensor_core_method(precision):
+def test_auto_picks_by_size(precision):
+    # QMMM_RECIP_AUTO: the CUDA cores for a small reciprocal workload, the tensor cores from
+    # 4e7 dense G entries x charges on
     import paper_2408_03273_gb300 as q
-    s = _system("three_blocks")
-    h = q.Handle(s, precision=precision)  # QMMM_RECIP_AUTO
-    try:
-        p_auto = h.potential()
-        h.set_recip_method(q.QMMM_RECIP_TENSOR)
-        assert np.array_equal(h.potential(), p_auto)
-    finally:
-        h.close()
+    small = _system("three_blocks")                                        # 1.5e6
+    large = workloads.small_system(46, n_atoms=3, lmax=2, n_waters=400, box_A=24.0,
+                                   kmax=(20, 20, 20))                      # 21 x 41 x 41 x 1194 = 4.2e7
+    for s, method in ((small, q.QMMM_RECIP_CUDA_CORES), (large, q.QMMM_RECIP_TENSOR)):
+        h = q.Handle(s, precision=precision)
+        try:
+            p_auto = h.potential()
+            h.set_recip_method(method)
+            assert np.array_equal(h.potential(), p_auto)
+        finally:
+            h.close()
 
 
 @pytest.mark.parametrize("name", list(CASES))
