@@ -335,7 +335,7 @@ int copy_out(qmmm_handle *h, double *dst, const double *src, size_t n)
 // The reciprocal-sum method in effect; allocates the tensor-core scratch the first time it is
 // needed.  QMMM_RECIP_AUTO: the tensor cores once the reciprocal work is large enough to outweigh
 // the five extra launches of each tensor-core sum (the CUDA-core kernels win below ~4e7 dense G
-// entries x charges: on the 648-charge water workload, 1.2e6, by 0.14 ms per mixed step).
+// entries x charges: on the 645-charge water workload, 1.2e6, by 0.14 ms per mixed step).
 constexpr double RECIP_TC_MIN_WORK = 4e7;
 int select_recip(qmmm_handle *h)
 {
