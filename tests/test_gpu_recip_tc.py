@@ -162,3 +162,30 @@ def test_tensor_cores_at_large_kmax(precision):
     assert np.max(np.abs(a["dE_dq"] - b["dE_dq"])) < tol * np.max(np.abs(dq_lr))
     assert np.max(np.abs(a["dE_dRmm"] - b["dE_dRmm"])) < tol * np.max(np.abs(dR_lr))
     assert q.QMMM_RECIP_TENSOR == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tensor_cores_with_three_charges(precision):
+    # one water: a charge block of 512 that is almost all padding, one charge tile of 128 with 125
+    # empty rows in the MM-side sum; everything against the oracle
+    s = workloads.small_system(47, n_atoms=3, lmax=2, n_waters=1, kmax=(5, 5, 5))
+    assert s.nmm == 3
+    ref = oracle.energy(s)
+    ref.update(oracle.forces(s))
+    g = gpu_all(s, precision=precision, setup=_tc)
+    assert rel_max(g["phi"], ref["phi"]) < TOL_FP64
+    tol = TOL_FP64 if precision == 0 else TOL_MIXED
+    for k in ("dE_dRqm", "dE_dRmm", "dE_dq"):
+        assert grad_err(g[k], ref, k, precision == 1) < tol, k
+
+
+def test_tensor_cores_with_empty_region1():
+    # region I empty: every charge in region II, both tensor-core sums carry all of it
+    s = workloads.small_system(seed=107, n_atoms=2, lmax=1, n_waters=6, cutoff_A=0.3)
+    ref = oracle.energy(s)
+    ref.update(oracle.forces(s))
+    g = gpu_all(s, precision=0, setup=_tc)
+    assert g["info"]["n_region1"] == 0
+    assert abs(g["E"] - ref["E"]) < TOL_FP64 * energy_scale(ref)
+    assert rel_max(g["dE_dRmm"], ref["dE_dRmm"]) < TOL_FP64
+    assert rel_max(g["dE_dq"], ref["dE_dq"]) < TOL_FP64
