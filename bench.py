@@ -438,16 +438,31 @@ def main():
                           if prec == q.QMMM_FP64 else "FP32 plain-ALU peak at 2070 MHz (152 SMs x 128 FFMA/clk)"),
             "flops_per_launch": fl}
 
-    # launches of our kernels per step (claim; the ncu launch list in profiles/ confirms it)
+    # launches of our kernels per step (claim; the ncu launch list in profiles/ confirms it: 62
+    # per FP64 step of the active site).  Per call:
+    #   set_positions: gather, region-I count/scan/fill, real-space, region-I tensors, background
+    #     sum, QM-site reciprocal, final = 9, plus the structure factor (tensor cores: max|q|,
+    #     phases, B planes, MMA, reduction = 5; CUDA cores: kernel + slice sum = 2)
+    #   vpot: one kernel per class and charge chunk + nuclear-MM term
+    #   ewald: one moments kernel per class + 2 (sum, energy terms)
+    #   forces: two moments kernels per class (Pulay) + the adjoint sweep per class and chunk + 8
+    #     fixed (nuclear-MM, sum, real space, region I, background, tensor gradient, scatter,
+    #     unpermute) + the MM-side reciprocal sum (tensor cores: atom phases, multipole structure
+    #     factor, phases, scales, B planes per N tile, MMA = 5 + tiles; CUDA cores: 3)
+    # Small systems whose classes ask for less than half the SMs add one V slice-sum kernel.
     ncls = sum(1 for n in info["n_prim_pairs_class"] if n > 0)
     nI = info["n_region1"]
     ch_f = math.ceil(nI / (4096)) if nI else 0
     ch_g = math.ceil(nI / 2560) if nI else 0
-    per_step = (11 + 1) + (ncls * ch_f + 2) + (ncls + 1) + (ncls + ncls * ch_g + 1 + 7 + 1 + 1)
-    if recip_in_effect(prec) == RECIP_NAME[q.QMMM_RECIP_TENSOR]:
-        # structure factor: 5 kernels instead of 2; MM-side sum: phases, scales and, per N tile
-        # (2 for FP64, 1 on the mixed path), B planes + MMA kernel, instead of 1
-        per_step += 3 + (5 if prec == q.QMMM_FP64 else 3)
+    tensor = recip_in_effect(prec) == RECIP_NAME[q.QMMM_RECIP_TENSOR]
+    # MM-side tiling as the library plans it: N rows per tile <= 96 (five accumulators, FP64) or
+    # 128 (four, mixed); channels per tile cpt; the sum stays on the CUDA cores if 2 kz + 1 < 8
+    kx, lim = s.kmax[0] + 1, (96 if prec == q.QMMM_FP64 else 128)
+    cpt = next((c for c in (3, 2, 1) if 2 * c * kx <= lim), 1)
+    mm_tc = tensor and (2 * cpt * kx + 15) // 16 * 16 <= lim and 2 * s.kmax[2] + 1 >= 8
+    mm_tiles = -(-3 // cpt)
+    per_step = (9 + (5 if tensor else 2)) + (ncls * ch_f + 1) + (ncls + 2) + \
+        (2 * ncls + ncls * ch_g + 8 + ((5 + mm_tiles) if mm_tc else 3))
     launches = per_step * args.steps
 
     # mixed precision beside FP64 (same GPU, same inputs), with its error against FP64
