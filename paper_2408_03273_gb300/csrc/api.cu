@@ -1042,8 +1042,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sums = h->sums.p;
         h->ew.err = h->err.p;
         tc_sf_shape(e, h->ew.tcs);
-        tc_mmr_shape(e, 5, h->ew.mms[0]);
-        tc_mmr_shape(e, 4, h->ew.mms[1]);
+        tc_mmr_shape(e, 5, 7, h->ew.mms[0]);
+        tc_mmr_shape(e, 4, 5, h->ew.mms[1]);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));

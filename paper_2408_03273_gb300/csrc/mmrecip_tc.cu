@@ -13,10 +13,11 @@
 // A operand (M = 128 charges x K): the outer products Y_i(n_y) Z_i(n_z), digitised on chip from
 // fixed-point phase rows staged by TMA; B operand (N = 112 rows (k, n_x, re/im) x K): C_k divided
 // by a power of two per (k, n_x) so that |C| <= 1, digitised once per call into the shared-memory
-// layout.  Digits as for the structure factor (tc_digits.cuh): 28 plane pairs per K-step into
-// FP32 accumulators in tensor memory, five (levels 0..3 kept apart, 4..6 merged: FP64 class; the
-// three channels then take two N tiles) or four (levels 0..2 apart, 3..6 merged: about 2^-35 of
-// the largest row coefficient, for the mixed-precision path, one N tile).  Level 0
+// layout.  Digits as for the structure factor (tc_digits.cuh).  FP64 class: seven planes per
+// operand, 28 plane pairs per K-step into five FP32 accumulators in tensor memory (levels 0..3
+// kept apart, 4..6 merged; the three channels then take two N tiles).  Mixed-precision path: five
+// planes (34-bit operands), 15 plane pairs, four accumulators (levels 0..2 apart, 3..4 merged:
+// about 2^-34 of the largest row coefficient), one N tile.  Level 0
 // is exact for any input while 4096 x 2 N_y N_z < 2^24 (kmax <= 20) and beyond that unless the
 // row-normalised coefficients, which decay as exp(-G^2/4 alpha^2), sum to more than 2^11 in
 // magnitude; levels 1 and 2 are sums of random-sign digit products, typically 2^17 or less.  The epilogue
@@ -48,12 +49,19 @@ constexpr uint32_t ROWB = MM * 16;               // one staged phase row (128 ch
 constexpr uint32_t PBUF = (2 + PCH) * ROWB;      // Y rows n_y0, n_y0 + 1 and one Z row per pair
 constexpr size_t SMEM_MAX = 232448;
 __host__ __device__ inline uint32_t mmr_bpl(int nr) { return (uint32_t)nr * KC * 2; }  // B plane bytes
-__host__ __device__ inline uint32_t mmr_stage(int nr) { return ND * (APL + mmr_bpl(nr)); }
-__host__ inline size_t mmr_smem(int nr, int nstg) { return nstg * (size_t)(mmr_stage(nr) + PBUF) + 256; }
+__host__ __device__ inline uint32_t mmr_stage(int nr, int np) { return np * (APL + mmr_bpl(nr)); }
+__host__ inline size_t mmr_smem(int nr, int nstg, int np) { return nstg * (size_t)(mmr_stage(nr, np) + PBUF) + 256; }
+// fixed-point width of an operand with NP planes, and the balanced input w of a value at 2^(bits + shift)
+__host__ __device__ constexpr int mmr_bits(int np) { return 6 + 7 * (np - 1); }
+template <int NP>
+__device__ __forceinline__ long long fixw_n(long long v, int shift)
+{
+    return (v + (1ll << (shift - 1)) + (bal<NP>() << shift)) >> shift;
+}
 
 struct MmrArgs {
     const int4 *Yt, *Zt;   // [NY][npad], [NZ][npad] split 2^61 fixed point, e^{-2 pi i n u}
-    const uint32_t *bpl;   // B planes per chunk (ND * BPL bytes)
+    const uint32_t *bpl;   // B planes per chunk (NP * BPL bytes)
     const double *cscale;  // [3][NX] power-of-two row scales
     const double *mm_xyz, *mm_q;
     double *dq, *dR;
@@ -66,12 +74,13 @@ struct MmrArgs {
 }  // namespace
 
 // grid (mtiles, N tiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set
-// ch % nstg
+// ch % nstg.  NP digit planes per operand (7: FP64 class; 5: the mixed path, 34-bit operands).
+template <int NP>
 __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int NSTG = a.nstg, NR = a.nr;
-    const uint32_t BPL = mmr_bpl(NR), STG = mmr_stage(NR);
+    const uint32_t BPL = mmr_bpl(NR), STG = mmr_stage(NR, NP);
     unsigned char *pbuf0 = sm + NSTG * STG;
     uint64_t *bars = reinterpret_cast<uint64_t *>(pbuf0 + NSTG * PBUF);
     uint64_t *full = bars, *bfull = bars + NSTGMAX, *pfull = bars + 2 * NSTGMAX, *empty = bars + 3 * NSTGMAX;
@@ -82,7 +91,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
     const int m0 = blockIdx.x * MM;
     // N tile blockIdx.y: channels [kfirst, kfirst + nk), its own B planes
     const int kfirst = blockIdx.y * a.cpt, nk = min(a.cpt, 3 - kfirst);
-    const uint32_t *bpl = a.bpl + (size_t)blockIdx.y * a.nchunk * (ND * BPL / 4);
+    const uint32_t *bpl = a.bpl + (size_t)blockIdx.y * a.nchunk * (NP * BPL / 4);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < NSTGMAX; ++k) {
@@ -141,13 +150,14 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
                 if (m0 + m < a.nmm && p < a.npair) {
                     long long re, im;  // 2^60 scale; the pair lies in row n_y0 + (z0 + jp >= NZ)
                     cmul61(Ys[(z0 + jp >= a.NZ ? MM : 0) + m], Zs[jp * MM + m], re, im);
-                    const Planes pr = planes(fixw(re, 12)), pi = planes(fixw(im, 12));
+                    constexpr int SH = 60 - mmr_bits(NP);
+                    const PlanesN<NP> pr = planes_n<NP>(fixw_n<NP>(re, SH)), pi = planes_n<NP>(fixw_n<NP>(im, SH));
 #pragma unroll
-                    for (int s = 0; s < ND; ++s)
+                    for (int s = 0; s < NP; ++s)
                         *reinterpret_cast<uint32_t *>(sA + s * APL + e_off[j]) = pack_bf16(pr.p[s], pi.p[s]);
                 } else {
 #pragma unroll
-                    for (int s = 0; s < ND; ++s) *reinterpret_cast<uint32_t *>(sA + s * APL + e_off[j]) = 0u;
+                    for (int s = 0; s < NP; ++s) *reinterpret_cast<uint32_t *>(sA + s * APL + e_off[j]) = 0u;
                 }
             }
             tc::fence_proxy_async_smem();
@@ -156,7 +166,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
         }
     } else if (warp == NPROD) {
         if (lane == 0) {
-            // ---------------- MMA issue: 28 plane pairs per chunk ----------------
+            // ---------------- MMA issue: NP (NP + 1) / 2 plane pairs per chunk ----------------
             const uint32_t idesc = tc::idesc_bf16_f32(MM, NR);
             for (int ch = 0; ch < a.nchunk; ++ch) {
                 const int st = ch % NSTG, u = ch / NSTG;
@@ -165,11 +175,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t sA = smem_addr(sm + st * STG), sB = sA + ND * APL;
+                const uint32_t sA = smem_addr(sm + st * STG), sB = sA + NP * APL;
 #pragma unroll
-                for (int s = 0; s < ND; ++s)
+                for (int s = 0; s < NP; ++s)
 #pragma unroll
-                    for (int t = 0; t < ND - s; ++t) {
+                    for (int t = 0; t < NP - s; ++t) {
                         const int acc = s + t < a.nacc - 1 ? s + t : a.nacc - 1;
                         const uint32_t first = (ch == 0 && s == 0 && t == acc);
                         const uint64_t ad = tc::smem_desc(sA + s * APL, CMK, CMN);
@@ -204,8 +214,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
                 give_up();
                 break;
             }
-            mbar_arrive_expect_tx(&bfull[st], ND * BPL);
-            bulk_g2s(sm + st * STG + ND * APL, bpl + (size_t)ch * (ND * BPL / 4), ND * BPL, &bfull[st]);
+            mbar_arrive_expect_tx(&bfull[st], NP * BPL);
+            bulk_g2s(sm + st * STG + NP * APL, bpl + (size_t)ch * (NP * BPL / 4), NP * BPL, &bfull[st]);
             issued = ch + 1;
         }
         for (int ch = issued > NSTG ? issued - NSTG : 0; ch < issued; ++ch)
@@ -341,6 +351,7 @@ __global__ void __launch_bounds__(256) k_mmr_scale(EwaldDev e, const double2 *A,
 // B planes of one N tile (channels [kfirst, kfirst + nk)), per chunk of 8 (n_y, n_z) pairs, in the
 // shared-memory layout: row (k, n_x, 0) holds (Re C, -Im C), row (k, n_x, 1) holds (Im C, Re C)
 // of C_k / cscale.  A warp writes 8 rows x 4 pairs: 128 contiguous bytes of each plane.
+template <int NP>
 __global__ void k_mmr_bplanes(EwaldDev e, const double2 *A, const double2 *Az, const double *cscale, int kfirst,
                               int nk, int nr, int nchunk, uint32_t *bpl)
 {
@@ -352,7 +363,7 @@ __global__ void k_mmr_bplanes(EwaldDev e, const double2 *A, const double2 *Az, c
     const int lane = it & 31, grp = it >> 5;
     const int j = (grp & 1) * 4 + (lane & 3), n = (grp >> 1) * 8 + (lane >> 2);
     const int p = ch * PCH + j;
-    long long w0 = BAL, w1 = BAL;
+    long long w0 = bal<NP>(), w1 = bal<NP>();
     if (n < 2 * nk * NX && p < NY * NZ) {
         const int kl = n / (2 * NX), nx = (n % (2 * NX)) >> 1, r = n & 1, k = kfirst + kl;
         const int iy = p / NZ, iz = p - iy * NZ;
@@ -360,14 +371,15 @@ __global__ void k_mmr_bplanes(EwaldDev e, const double2 *A, const double2 *Az, c
         const double2 c = mmr_channel(A, Az, k, ((size_t)nx * NY + iy) * NZ + iz, gy);
         const double sc = 1.0 / cscale[k * NX + nx];  // a power of two: exact
         const double re = c.x * sc, im = c.y * sc;
-        w0 += __double2ll_rn((r ? im : re) * 0x1p48);
-        w1 += __double2ll_rn((r ? re : -im) * 0x1p48);
+        constexpr double SC = (double)(1ll << mmr_bits(NP));
+        w0 += __double2ll_rn((r ? im : re) * SC);
+        w1 += __double2ll_rn((r ? re : -im) * SC);
     }
-    const Planes p0 = planes(w0), p1 = planes(w1);
+    const PlanesN<NP> p0 = planes_n<NP>(w0), p1 = planes_n<NP>(w1);
     const uint32_t words = mmr_bpl(nr) / 4;
-    uint32_t *dst = bpl + (size_t)ch * ND * words + ((n >> 3) * CMN + (j >> 2) * CMK + (n & 7) * 16 + (j & 3) * 4) / 4;
+    uint32_t *dst = bpl + (size_t)ch * NP * words + ((n >> 3) * CMN + (j >> 2) * CMK + (n & 7) * 16 + (j & 3) * 4) / 4;
 #pragma unroll
-    for (int s = 0; s < ND; ++s) dst[(size_t)s * words] = pack_bf16(p0.p[s], p1.p[s]);
+    for (int s = 0; s < NP; ++s) dst[(size_t)s * words] = pack_bf16(p0.p[s], p1.p[s]);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -375,8 +387,9 @@ __global__ void k_mmr_bplanes(EwaldDev e, const double2 *A, const double2 *Az, c
 // ---------------------------------------------------------------------------------------------
 // nacc = 5: levels 0..3 exact (channels split over N tiles so that 5 accumulators fit in 512
 // columns); nacc = 4: levels 0..2 exact and one tile where possible
-void tc_mmr_shape(const EwaldDev &e, int nacc, MmrShape &sh)
+void tc_mmr_shape(const EwaldDev &e, int nacc, int np, MmrShape &sh)
 {
+    sh.np = np;
     const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
     sh.nacc = nacc;
     sh.mtiles = (e.nmm + MM - 1) / MM;
@@ -390,9 +403,9 @@ void tc_mmr_shape(const EwaldDev &e, int nacc, MmrShape &sh)
     sh.ntiles = (3 + cpt - 1) / cpt;
     sh.nr = (2 * cpt * NX + 15) / 16 * 16;
     sh.supported = sh.nr <= maxr && NZ >= PCH;  // a chunk of 8 pairs spans at most two n_y rows
-    sh.nstg = mmr_smem(sh.nr, 3) <= SMEM_MAX ? 3 : 2;
+    sh.nstg = mmr_smem(sh.nr, 3, np) <= SMEM_MAX ? 3 : 2;
     sh.phase_rows = (size_t)(NY + NZ) * sh.npad;
-    sh.bplane_words = (size_t)sh.ntiles * sh.nchunk * ND * mmr_bpl(sh.nr) / 4;
+    sh.bplane_words = (size_t)sh.ntiles * sh.nchunk * np * mmr_bpl(sh.nr) / 4;
 }
 
 cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,
@@ -406,20 +419,25 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     k_mmr_scale<<<3 * NX, 256, 0, st>>>(e, A, Az, b.cscale);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
-    const size_t smem = mmr_smem(sh.nr, sh.nstg);
-    static size_t attr = 0;
-    if (smem > attr) {
-        if ((rc = cudaFuncSetAttribute(k_mm_recip_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
+    const size_t smem = mmr_smem(sh.nr, sh.nstg, sh.np);
+    const void *fn = sh.np == 7 ? (const void *)k_mm_recip_tc<7> : (const void *)k_mm_recip_tc<5>;
+    static size_t attr[2] = {0, 0};
+    size_t &at = attr[sh.np == 7 ? 0 : 1];
+    if (smem > at) {
+        if ((rc = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return rc;
-        attr = smem;
+        at = smem;
     }
-    const size_t tile_words = (size_t)sh.nchunk * ND * mmr_bpl(sh.nr) / 4;
+    const size_t tile_words = (size_t)sh.nchunk * sh.np * mmr_bpl(sh.nr) / 4;
     for (int tl = 0; tl < sh.ntiles; ++tl) {
         const int kfirst = tl * sh.cpt, nk = std::min(sh.cpt, 3 - kfirst);
         const long long n = (long long)sh.nr * PCH * sh.nchunk;
-        k_mmr_bplanes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr, sh.nchunk,
-                                                                    b.bpl + tl * tile_words);
+        if (sh.np == 7)
+            k_mmr_bplanes<7><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
+                                                                           sh.nchunk, b.bpl + tl * tile_words);
+        else
+            k_mmr_bplanes<5><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
+                                                                           sh.nchunk, b.bpl + tl * tile_words);
         if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     }
     MmrArgs a;
@@ -444,7 +462,10 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     a.nstg = sh.nstg;
     a.nacc = sh.nacc;
     a.box0 = e.box[0];
-    k_mm_recip_tc<<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
+    if (sh.np == 7)
+        k_mm_recip_tc<7><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
+    else
+        k_mm_recip_tc<5><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     return cudaSuccess;
 }

@@ -129,6 +129,7 @@ struct MmrShape {
     int mtiles = 0, npad = 0, npair = 0, nchunk = 0;  // charge tiles (128), padded charges, (n_y, n_z) pairs, chunks of 8
     int cpt = 3, ntiles = 1, nr = 0, nstg = 3;        // channels per N tile, N tiles, N rows, stages
     int nacc = 4;                                     // accumulators (exact levels + 1)
+    int np = 7;                                       // digit planes per operand (7 or 5)
     bool supported = false;                           // kx small enough for one channel per tile
     size_t phase_rows = 0;                            // Y and Z phase rows (int4)
     size_t bplane_words = 0;                          // B digit planes of all N tiles (32-bit words)
@@ -138,7 +139,7 @@ struct MmrBuf {
     uint32_t *bpl = nullptr;   // B planes per N tile and chunk
     double *cscale = nullptr;  // [3][NX] power-of-two row scales
 };
-void tc_mmr_shape(const EwaldDev &e, int nacc, MmrShape &sh);
+void tc_mmr_shape(const EwaldDev &e, int nacc, int np, MmrShape &sh);
 // dq[i] += sum_G Re[A e^{-iG.R_i}], dR[i] += q_i sum_G G Im[A e^{-iG.R_i}] (internal order), from the
 // dense A and A_z = G_z A of k_multipole_sf, on the BF16 tensor cores (exact digit planes)
 cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,

@@ -74,5 +74,29 @@ __device__ __forceinline__ long long fixw(long long v, int shift)
 
 __device__ __forceinline__ long long fix61(double v) { return __double2ll_rn(v * FIX61); }
 
+// The same balanced split with NP planes of a (6 + 7 (NP - 1))-bit value v: the leading plane
+// w >> 7 (NP - 1) in [-64, 64] and NP - 1 base-128 digits; bal<NP>() is the offset that makes the
+// digits balanced; NP = 7 is planes() above.
+template <int NP>
+__host__ __device__ constexpr long long bal()
+{
+    return 64ll * (((1ll << (7 * (NP - 1))) - 1) / 127);
+}
+template <int NP>
+struct PlanesN { float p[NP]; };
+template <int NP>
+__device__ __forceinline__ PlanesN<NP> planes_n(long long w)
+{
+    PlanesN<NP> r;
+    r.p[0] = (float)(int)(w >> (7 * (NP - 1)));
+#pragma unroll
+    for (int s = 1; s < NP; ++s) {
+        const uint32_t u = (uint32_t)((unsigned long long)w >> (7 * (NP - 1 - s))) & 127u;
+        const uint32_t mag = (uint32_t)(127 + 23 - 7 * s) << 23;  // 2^(23-7s): mantissa LSB 2^-7s
+        r.p[s] = __uint_as_float(mag | u) - __uint_as_float(mag | 64u);
+    }
+    return r;
+}
+
 }  // namespace tcd
 }  // namespace qmmm
