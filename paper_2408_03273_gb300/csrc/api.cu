@@ -486,11 +486,19 @@ int variant_threads(int kind, int cls, int variant)
     return (variant == 1 && w > 0) ? w : 256;
 }
 
+// Blocks a class sweep can fill with one charge slice: one 32-pair tile per warp.
+int tile_cap(const qmmm_handle *h, int kind, int cls, int variant)
+{
+    const int npp = h->class_off[cls + 1] - h->class_off[cls];
+    const int nwarp = variant_threads(kind, cls, variant) / 32;
+    return std::max(1, ((npp + 31) / 32 + nwarp - 1) / nwarp);
+}
+
 // Grid caps of the concurrent class sweeps: shares of the SMs in proportion to each class's
 // SM-time (primitive pairs x cost), but never more blocks than the class has warps' worth of
-// 32-pair tiles for; what a capped class cannot use goes to the others.  Returns false when no
-// class has work.
-bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share)
+// 32-pair tiles for (times maxsl, when a class may split its charges over maxsl block rows);
+// what a capped class cannot use goes to the others.  Returns false when no class has work.
+bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share, int maxsl = 1)
 {
     double w[NCLASS], s[NCLASS];
     int cap[NCLASS];
@@ -501,8 +509,7 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share)
         share[c] = 0;
         open[c] = npp > 0;
         if (!open[c]) continue;
-        const int nwarp = variant_threads(kind, c, variant[c]) / 32;
-        cap[c] = std::max(1, ((npp + 31) / 32 + nwarp - 1) / nwarp);
+        cap[c] = tile_cap(h, kind, c, variant[c]) * maxsl;
         w[c] = npp * std::max(h->cls_cost[kind][c], 1e-30);
         ++nopen;
     }
@@ -533,17 +540,26 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share)
 // Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
 // forked from and joined back into the handle's stream, its grid capped at its share of the SMs
 // (so small classes do not leave most SMs idle while they run alone).
+// maxsl > 1 (adjoint sweeps, whose charge slices need no buffers of their own): a class with
+// fewer 32-pair tiles than its share of the SMs asks for splits its charges over up to maxsl
+// block rows, so that a few high-l pairs do not hold the whole sweep on a few SMs.
 template <typename F>
-int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1)
+int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1)
 {
     int share[NCLASS];
-    if (!split_sms(h, kind, h->cls_variant[kind], share)) return QMMM_OK;
+    if (!split_sms(h, kind, h->cls_variant[kind], share, nslice == 1 ? maxsl : 1)) return QMMM_OK;
     CUDA_TRY(cudaEventRecord(h->fork, h->stream));
     for (int c = 0; c < NCLASS; ++c) {
         const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
         if (p1 <= p0) continue;
+        int sh = share[c], ns = nslice;
+        if (nslice == 1 && maxsl > 1) {
+            const int cap = tile_cap(h, kind, c, h->cls_variant[kind][c]);
+            ns = std::min(maxsl, (sh + cap - 1) / cap);
+            sh = (sh + ns - 1) / ns;
+        }
         CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
-        CUDA_TRY(launch(c, p0, p1, share[c], h->cls_variant[kind][c], nslice, h->side[c]));
+        CUDA_TRY(launch(c, p0, p1, sh, h->cls_variant[kind][c], ns, h->side[c]));
         CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
     }
     for (int c = 0; c < NCLASS; ++c)
@@ -1220,7 +1236,7 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
                 return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, 0, ddm, nullptr, h->gqm.p,
                                     h->gchg.p, cs);
             },
-            ns);
+            ns, std::max(1, std::min(8, (c1 - c0) / 256)));
         if (rc) return rc;
     }
     CUDA_TRY(mark(h, 1));

@@ -190,38 +190,48 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             }
             tc::commit(done);
         }
-    } else if (lane == 0) {
-        // ---------------- loader: phase rows and B planes of chunk ch ----------------
+    } else {
+        // ---------------- loader warp: phase rows and B planes of chunk ch ----------------
+        // lane 0 waits and posts the expected bytes; the copies of a chunk (two Y rows, one Z row
+        // per pair, the B planes) go out from separate lanes at once
         int issued = 0, pissued = 0;
         for (int ch = 0; ch < a.nchunk; ++ch) {
             const int st = ch % NSTG, u = ch / NSTG;
-            if (ch >= NSTG && !tc::mbar_wait_thread(&full[st], (u - 1) & 1, abort)) {
-                give_up();
+            int ok = 1;
+            if (lane == 0 && ch >= NSTG) ok = tc::mbar_wait_thread(&full[st], (u - 1) & 1, abort);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                if (lane == 0) give_up();
                 break;
             }
             const int p0 = ch * PCH, iy0 = p0 / a.NZ, iy1 = min(iy0 + 1, a.NY - 1);
             const int nvalid = min(PCH, a.npair - p0);
             unsigned char *dst = pbuf0 + st * PBUF;
-            mbar_arrive_expect_tx(&pfull[st], (2 + nvalid) * ROWB);
-            bulk_g2s(dst, a.Yt + (size_t)iy0 * a.npad + m0, ROWB, &pfull[st]);
-            bulk_g2s(dst + ROWB, a.Yt + (size_t)iy1 * a.npad + m0, ROWB, &pfull[st]);
-            for (int j = 0; j < nvalid; ++j) {
-                const int iz = (p0 + j) % a.NZ;
-                bulk_g2s(dst + (2 + j) * ROWB, a.Zt + (size_t)iz * a.npad + m0, ROWB, &pfull[st]);
+            if (lane == 0) mbar_arrive_expect_tx(&pfull[st], (2 + nvalid) * ROWB);
+            __syncwarp();
+            if (lane < 2) {
+                bulk_g2s(dst + lane * ROWB, a.Yt + (size_t)(lane ? iy1 : iy0) * a.npad + m0, ROWB, &pfull[st]);
+            } else if (lane < 2 + nvalid) {
+                const int iz = (p0 + lane - 2) % a.NZ;
+                bulk_g2s(dst + lane * ROWB, a.Zt + (size_t)iz * a.npad + m0, ROWB, &pfull[st]);
             }
             pissued = ch + 1;
-            if (ch >= NSTG && !tc::mbar_wait_thread(&empty[st], (u - 1) & 1, abort)) {
-                give_up();
+            if (lane == 0 && ch >= NSTG) ok = tc::mbar_wait_thread(&empty[st], (u - 1) & 1, abort);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                if (lane == 0) give_up();
                 break;
             }
-            mbar_arrive_expect_tx(&bfull[st], NP * BPL);
-            bulk_g2s(sm + st * STG + NP * APL, bpl + (size_t)ch * (NP * BPL / 4), NP * BPL, &bfull[st]);
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&bfull[st], NP * BPL);
+                bulk_g2s(sm + st * STG + NP * APL, bpl + (size_t)ch * (NP * BPL / 4), NP * BPL, &bfull[st]);
+            }
             issued = ch + 1;
         }
-        for (int ch = issued > NSTG ? issued - NSTG : 0; ch < issued; ++ch)
-            tc::mbar_wait_thread(&bfull[ch % NSTG], (ch / NSTG) & 1, abort);
-        for (int ch = pissued > NSTG ? pissued - NSTG : 0; ch < pissued; ++ch)
-            tc::mbar_wait_thread(&pfull[ch % NSTG], (ch / NSTG) & 1, abort);
+        if (lane == 0) {
+            for (int ch = issued > NSTG ? issued - NSTG : 0; ch < issued; ++ch)
+                tc::mbar_wait_thread(&bfull[ch % NSTG], (ch / NSTG) & 1, abort);
+            for (int ch = pissued > NSTG ? pissued - NSTG : 0; ch < pissued; ++ch)
+                tc::mbar_wait_thread(&pfull[ch % NSTG], (ch / NSTG) & 1, abort);
+        }
     }
 
     // ---------------- epilogue: one thread per charge (warps 0..3) ----------------

@@ -49,6 +49,176 @@ __device__ __forceinline__ PPLane load_pp(const BasisDev &bd, int i, int pp_end)
     return L;
 }
 
+// Density element of Cartesian components (ia, ib) of a primitive pair, times the pair
+// prefactor 2 pi / p c_a c_b K_AB: gamma_{ab} (+ gamma_{ba} for a shell pair off the diagonal,
+// whose mirror is not stored).  Zero for an inactive lane.
+__device__ __forceinline__ double pair_density(const PPLane &pl, const BasisDev &bd, const double *__restrict__ dm,
+                                               int ia, int ib)
+{
+    if (!pl.active) return 0.0;
+    const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
+    double g = dm[r * bd.nao + c];
+    if (pl.sp.shA != pl.sp.shB) g += dm[c * bd.nao + r];
+    return g * (TWO_PI * pl.ip * pl.cab);
+}
+
+// D0_tuv = sum_ab g_ab E^x_t E^y_u E^z_v: the density folded into the Hermite coefficients of the
+// pair (Eq. 9 contracted with the density matrix), once per primitive pair.
+template <int LA, int LB>
+__device__ __forceinline__ void fold_density(const PPLane &pl, const BasisDev &bd, const double *__restrict__ dm,
+                                             double (&D0)[nherm(LA + LB)])
+{
+    constexpr int L = LA + LB, NA = ncart(LA), NB = ncart(LB);
+#pragma unroll
+    for (int k = 0; k < nherm(L); ++k) D0[k] = 0.0;
+    double Ex[LA + 1][LB + 1][L + 1], Ey[LA + 1][LB + 1][L + 1], Ez[LA + 1][LB + 1][L + 1];
+    hermite_E<LA, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
+    hermite_E<LA, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
+    hermite_E<LA, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < NB; ++ib) {
+            const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+            const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+            const double g = pair_density(pl, bd, dm, ia, ib);
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                for (int u = 0; u <= ay + by; ++u) {
+                    const double gxy = g * Ex[ax][bx][t] * Ey[ay][by][u];
+#pragma unroll
+                    for (int w = 0; w <= az + bz; ++w) D0[hidx(t, u, w)] += gxy * Ez[az][bz][w];
+                }
+        }
+}
+
+// The centre-A derivative coefficients themselves, Da_tuv = sum_ab g_ab E'^a_{tuv} (E'^a as in
+// contract_dA below), for a sweep that contracts them with partial charge sums.
+template <int LA, int LB>
+__device__ __forceinline__ void fold_density_dA(const PPLane &pl, const BasisDev &bd, const double *__restrict__ dm,
+                                                double (&Dx)[nherm(LA + LB)], double (&Dy)[nherm(LA + LB)],
+                                                double (&Dz)[nherm(LA + LB)])
+{
+    constexpr int L = LA + LB, NA = ncart(LA), NB = ncart(LB);
+    const double aop = pl.a * pl.ip;
+#pragma unroll
+    for (int k = 0; k < nherm(L); ++k) Dx[k] = Dy[k] = Dz[k] = 0.0;
+    double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
+    hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
+    hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
+    hermite_E<LA + 1, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < NB; ++ib) {
+            const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+            const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+            const double g = pair_density(pl, bd, dm, ia, ib);
+            double dEx[L + 1], dEy[L + 1], dEz[L + 1];
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t) {
+                double e = 2.0 * pl.a * Ex[ax + 1][bx][t];
+                if (ax > 0) e -= ax * Ex[ax - 1][bx][t];
+                if (t > 0) e -= aop * Ex[ax][bx][t - 1];
+                dEx[t] = g * e;
+            }
+#pragma unroll
+            for (int u = 0; u <= ay + by; ++u) {
+                double e = 2.0 * pl.a * Ey[ay + 1][by][u];
+                if (ay > 0) e -= ay * Ey[ay - 1][by][u];
+                if (u > 0) e -= aop * Ey[ay][by][u - 1];
+                dEy[u] = e;
+            }
+#pragma unroll
+            for (int w = 0; w <= az + bz; ++w) {
+                double e = 2.0 * pl.a * Ez[az + 1][bz][w];
+                if (az > 0) e -= az * Ez[az - 1][bz][w];
+                if (w > 0) e -= aop * Ez[az][bz][w - 1];
+                dEz[w] = e;
+            }
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                    for (int w = 0; w <= az + bz; ++w) {
+                        const int k = hidx(t, u, w);
+                        const double gx = g * Ex[ax][bx][t], ey = Ey[ay][by][u], ez = Ez[az][bz][w];
+                        Dx[k] += dEx[t] * ey * ez;
+                        Dy[k] += gx * dEy[u] * ez;
+                        Dz[k] += gx * ey * dEz[w];
+                    }
+        }
+}
+
+// The centre-A derivative part of the adjoint for one primitive pair, contracted with the
+// charge sums S_tuv = sum_C q_C R_tuv(P - C):
+//   d_a = sum_ab g_ab sum_tuv E'^a_{tuv} S_tuv,   a = x, y, z,
+// where E'^a is the product of Hermite coefficients with the a-factor replaced by
+//   E'^{ij}_t = dE^{ij}_t / dX_AB = 2a E^{i+1,j}_t - i E^{i-1,j}_t - (a/p) E^{ij}_{t-1}
+// (t <= i + j; E'_{i+j+1} vanishes).  Per-charge terms d_a(C) = sum E' R(C) enter the pair
+// gradient only through their q-weighted sum, so summing R over the charges first and
+// contracting once per pair gives the same sum.
+template <int LA, int LB>
+__device__ __forceinline__ void contract_dA(const PPLane &pl, const BasisDev &bd, const double *__restrict__ dm,
+                                            const double (&S)[nherm(LA + LB)], double (&d)[3])
+{
+    constexpr int L = LA + LB, NA = ncart(LA), NB = ncart(LB);
+    const double aop = pl.a * pl.ip;
+    d[0] = d[1] = d[2] = 0.0;
+    double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
+    hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
+    hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
+    hermite_E<LA + 1, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < NB; ++ib) {
+            const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+            const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+            const double g = pair_density(pl, bd, dm, ia, ib);
+            double dEx[L + 1], dEy[L + 1], dEz[L + 1];
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t) {
+                double e = 2.0 * pl.a * Ex[ax + 1][bx][t];
+                if (ax > 0) e -= ax * Ex[ax - 1][bx][t];
+                if (t > 0) e -= aop * Ex[ax][bx][t - 1];
+                dEx[t] = e;
+            }
+#pragma unroll
+            for (int u = 0; u <= ay + by; ++u) {
+                double e = 2.0 * pl.a * Ey[ay + 1][by][u];
+                if (ay > 0) e -= ay * Ey[ay - 1][by][u];
+                if (u > 0) e -= aop * Ey[ay][by][u - 1];
+                dEy[u] = e;
+            }
+#pragma unroll
+            for (int w = 0; w <= az + bz; ++w) {
+                double e = 2.0 * pl.a * Ez[az + 1][bz][w];
+                if (az > 0) e -= az * Ez[az - 1][bz][w];
+                if (w > 0) e -= aop * Ez[az][bz][w - 1];
+                dEz[w] = e;
+            }
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                    for (int w = 0; w <= az + bz; ++w) {
+                        const double s = S[hidx(t, u, w)];
+                        const double ex = Ex[ax][bx][t], ey = Ey[ay][by][u], ez = Ez[az][bz][w];
+                        sx += dEx[t] * ey * ez * s;
+                        sy += ex * dEy[u] * ez * s;
+                        sz += ex * ey * dEz[w] * s;
+                    }
+            d[0] += g * sx;
+            d[1] += g * sy;
+            d[2] += g * sz;
+        }
+}
+
 // Inverse of class_of: the angular momenta of a class index.
 __host__ __device__ constexpr int la_of_class(int c)
 {
@@ -75,10 +245,18 @@ __host__ __device__ constexpr int sweep_wide_threads(int kind, int cls)
         {1024, 640, 512, 640, 384, 384, 512, 0, 0, 0},  // vpot_f64 : 64 87 105 96 150 158 120 regs
         {896, 768, 512, 512, 384, 0, 384, 0, 0, 0},     // vpot_f32 : 68 80 106 102 154 - 136
         {640, 512, 0, 0, 0, 0, 0, 0, 0, 0},             // vgrad_f64: 93 117
-        {768, 640, 384, 384, 0, 0, 0, 0, 0, 0},         // vgrad_f32: 80 96 168 148
+        {768, 640, 384, 384, 384, 384, 0, 0, 0, 0},     // vgrad_f32: 80 96 168 148 (255 255: setup)
     };
     return (kind >= 0 && kind < SW_NKIND && cls >= 0 && cls < 10) ? T[kind][cls] : 0;
 }
+
+// Dynamic shared memory of every FP64 sweep block is at least this much: more than half of an
+// SM's 228 KB, so no two FP64 sweep blocks share an SM.  The concurrent class sweeps split the
+// SMs in shares, one block per SM; with a region I small enough for two charge chunks to fit in
+// one SM, the block scheduler would otherwise stack blocks of different classes on some SMs
+// (which then share one saturated FP64 pipe) while others stay idle.  The FP32 sweeps are
+// latency-bound instead and gain from a second block on an SM, so they are not padded.
+constexpr size_t SWEEP_SMEM_MIN = 116 * 1024;
 
 // Class-split compilation.  A sweep source (vpot_*.cu, vgrad_*.cu) is compiled once per angular
 // class with -DQMMM_SPLIT_CLASS=<class index>, which defines that class's kernel and explicitly

@@ -1,7 +1,9 @@
 // vgrad_f32.cu -- adjoint of the region-I term, mixed precision (see vgrad_f64.cu for the
 // derivative algebra).  The density-folded Hermite coefficients D0, Dx, Dy, Dz are built in
-// FP64 once per primitive pair and rounded to FP32; the per-charge Boys/R recursion to order L+1
-// and the seven contractions run in FP32, with no FP64 instruction inside the charge loop.
+// FP64 once per primitive pair and rounded to FP32; the per-charge Boys/R recursion to order L+1,
+// the four D0 contractions (e_0, e_x, e_y, e_z) and the charge sum S_tuv += q R_tuv run in FP32,
+// with no FP64 instruction inside the charge loop.  Every 16 charges the group's S is contracted
+// with Dx, Dy, Dz, which wait in the thread's local memory (kept out of the loop's registers).
 // Per-pair sums go through FP32 partials over 16 charges folded into double-float pairs;
 // per-charge sums over the warp's 32 primitive pairs use a reduce-scatter (6 shuffles for four
 // values) and compensated FP32 shared-memory atomics: the atomic returns the old value, so the
@@ -22,13 +24,25 @@ struct VgradF32 {
 
 constexpr int GFOLD = 16;
 
+// 16-byte loads and stores of this thread's local memory (an array kept out of registers)
+__device__ __forceinline__ void st_local4(uint32_t a, const float (&v)[4])
+{
+    asm volatile("st.local.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                 : "memory");
+}
+__device__ __forceinline__ void ld_local4(uint32_t a, float (&v)[4])
+{
+    asm volatile("ld.local.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a)
+                 : "memory");
+}
+
 template <int LA, int LB, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
             const float *__restrict__ boys_g, unsigned boys_bytes, const double *__restrict__ dm,
             double *__restrict__ gqm, double *__restrict__ gchg, int *err)
 {
-    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1), NA = ncart(LA), NB = ncart(LB);
+    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     {
@@ -55,10 +69,11 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int ntile = (pp_end - pp_begin + 31) >> 5;
+    constexpr int ND4 = (3 * NH + 3) / 4;
+    float4 dl[ND4];  // this lane's Dx, Dy, Dz (FP32), accessed only through ld/st.local
+    const uint32_t dl_addr = (uint32_t)__cvta_generic_to_local(dl);
     for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
         const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
-        const bool mirror = pl.sp.shA != pl.sp.shB;
-        const double coef = TWO_PI * pl.ip * pl.cab;
         const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
         float Ph[3], Plo[3];
 #pragma unroll
@@ -68,71 +83,26 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
             Plo[x] = (float)(d - (double)Ph[x]);
         }
 
-        float D0[NH], Dx[NH], Dy[NH], Dz[NH];
+        float D0[NH];
         {
-            double d0[NH], dx[NH], dy[NH], dz[NH];
+            double d0[NH];
+            fold_density<LA, LB>(pl, bd, dm, d0);
 #pragma unroll
-            for (int k = 0; k < NH; ++k) d0[k] = dx[k] = dy[k] = dz[k] = 0.0;
-            double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
-            hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
-            hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
-            hermite_E<LA + 1, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
+            for (int k = 0; k < NH; ++k) D0[k] = (float)d0[k];
+        }
+        {
+            // Dx, Dy, Dz as FP32 in this thread's local memory: read once per GFOLD charges
+            double dx[NH], dy[NH], dz[NH];
+            fold_density_dA<LA, LB>(pl, bd, dm, dx, dy, dz);
 #pragma unroll
-            for (int ia = 0; ia < NA; ++ia) {
+            for (int i = 0; i < ND4; ++i) {
+                float v[4];
 #pragma unroll
-                for (int ib = 0; ib < NB; ++ib) {
-                    const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
-                    const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
-                    double g = 0.0;
-                    if (pl.active) {
-                        const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
-                        g = dm[r * bd.nao + c];
-                        if (mirror) g += dm[c * bd.nao + r];
-                        g *= coef;
-                    }
-                    double dEx[L + 1], dEy[L + 1], dEz[L + 1];
-#pragma unroll
-                    for (int t = 0; t <= ax + bx; ++t) {
-                        double e = 2.0 * pl.a * Ex[ax + 1][bx][t];
-                        if (ax > 0) e -= ax * Ex[ax - 1][bx][t];
-                        if (t > 0) e -= aop * Ex[ax][bx][t - 1];
-                        dEx[t] = e;
-                    }
-#pragma unroll
-                    for (int u = 0; u <= ay + by; ++u) {
-                        double e = 2.0 * pl.a * Ey[ay + 1][by][u];
-                        if (ay > 0) e -= ay * Ey[ay - 1][by][u];
-                        if (u > 0) e -= aop * Ey[ay][by][u - 1];
-                        dEy[u] = e;
-                    }
-#pragma unroll
-                    for (int w = 0; w <= az + bz; ++w) {
-                        double e = 2.0 * pl.a * Ez[az + 1][bz][w];
-                        if (az > 0) e -= az * Ez[az - 1][bz][w];
-                        if (w > 0) e -= aop * Ez[az][bz][w - 1];
-                        dEz[w] = e;
-                    }
-#pragma unroll
-                    for (int t = 0; t <= ax + bx; ++t)
-#pragma unroll
-                        for (int u = 0; u <= ay + by; ++u)
-#pragma unroll
-                            for (int w = 0; w <= az + bz; ++w) {
-                                const int k = hidx(t, u, w);
-                                const double ex = Ex[ax][bx][t], ey = Ey[ay][by][u], ez = Ez[az][bz][w];
-                                d0[k] += g * ex * ey * ez;
-                                dx[k] += g * dEx[t] * ey * ez;
-                                dy[k] += g * ex * dEy[u] * ez;
-                                dz[k] += g * ex * ey * dEz[w];
-                            }
+                for (int c = 0; c < 4; ++c) {
+                    const int e = 4 * i + c;
+                    v[c] = e < NH ? (float)dx[e] : e < 2 * NH ? (float)dy[e - NH] : e < 3 * NH ? (float)dz[e - 2 * NH] : 0.0f;
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < NH; ++k) {
-                D0[k] = (float)d0[k];
-                Dx[k] = (float)dx[k];
-                Dy[k] = (float)dy[k];
-                Dz[k] = (float)dz[k];
+                st_local4(dl_addr + 16u * i, v);
             }
         }
 
@@ -147,7 +117,10 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
             const float rho = (float)(pl.p * td), m2rho = -2.0f * rho, sq = (float)sqrt(td);
             for (int j0 = lo; j0 < hi; j0 += GFOLD) {
                 const int j1 = min(hi, j0 + GFOLD);
-                float tdx = 0, tdy = 0, tdz = 0, tex = 0, tey = 0, tez = 0;
+                float tex = 0, tey = 0, tez = 0;
+                float S[NH];  // sum over this group's charges of q R_tuv (k < NH)
+#pragma unroll
+                for (int k = 0; k < NH; ++k) S[k] = 0.0f;
                 for (int j = j0; j < j1; ++j) {
                     const float4 ch = chi[j], cl = clo[j];
                     const float X = (Ph[0] - ch.x) + (Plo[0] - cl.x);
@@ -166,7 +139,8 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                     }
                     float R[NH1];
                     hermite_R<L + 1, float>(R, Fn, X, Y, Z);
-                    float e0 = 0, ex = 0, ey = 0, ez = 0, dx = 0, dy = 0, dz = 0;
+                    float e0 = 0, ex = 0, ey = 0, ez = 0;
+                    const float q = ch.w;
 #pragma unroll
                     for (int t = 0; t <= L; ++t)
 #pragma unroll
@@ -178,12 +152,8 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                                 ex += D0[k] * R[hidx(t + 1, u, w)];
                                 ey += D0[k] * R[hidx(t, u + 1, w)];
                                 ez += D0[k] * R[hidx(t, u, w + 1)];
-                                dx += Dx[k] * R[k];
-                                dy += Dy[k] * R[k];
-                                dz += Dz[k] * R[k];
+                                S[k] += q * R[k];
                             }
-                    const float q = ch.w;
-                    tdx += q * dx; tdy += q * dy; tdz += q * dz;
                     tex += q * ex; tey += q * ey; tez += q * ez;
                     // per-charge sums over the 32 primitive pairs: 4 values -> halve twice (each lane
                     // keeps one component summed over 4 lanes), then a 3-step butterfly; lane 8c ends
@@ -210,6 +180,20 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                             const float sum = old + k, bv = sum - old;
                             atomicAdd(acc_lo + 4 * j + comp, (old - (sum - bv)) + (k - bv));
                         }
+                    }
+                }
+                // this group's sum_C q_C d_a(C) = sum_k Da_k S_k, Da from local memory
+                float tdx = 0, tdy = 0, tdz = 0;
+#pragma unroll
+                for (int i = 0; i < ND4; ++i) {
+                    float v[4];
+                    ld_local4(dl_addr + 16u * i, v);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int e = 4 * i + c;
+                        if (e < NH) tdx += v[c] * S[e];
+                        else if (e < 2 * NH) tdy += v[c] * S[e - NH];
+                        else if (e < 3 * NH) tdz += v[c] * S[e - 2 * NH];
                     }
                 }
                 df_add(sh[0], sl[0], tdx); df_add(sh[1], sl[1], tdy); df_add(sh[2], sl[2], tdz);

@@ -8,9 +8,14 @@
 // Moving A shifts P by a/p, so with e_a = sum D0_tuv R_{tuv + 1_a} and d_a = sum Da_tuv R_tuv
 // (R recomputed up to L+1 for every charge, never stored):
 //   dI/dA_a = d_a + (a/p) e_a,   dI/dB_a = -d_a + (b/p) e_a,   dI/dC_a = -e_a,
-// and E contains -q_C I.  Per-pair sums over charges stay in registers; per-charge sums over the
+// and E contains -q_C I.  The d_a enter only through sum_C q_C d_a(C) = sum Da_tuv S_tuv with
+// S_tuv = sum_C q_C R_tuv, so the sweep accumulates S (NH terms per charge instead of the 3 NH
+// of the three contractions) and Da is formed and contracted once per pair after it (contract_dA).
+// Per-pair sums over charges stay in registers; per-charge sums over the
 // 32 primitive pairs of a tile use a warp butterfly and go to shared-memory accumulators that
 // are flushed to global memory once per block.
+#include <algorithm>
+
 #include "pp_tile.cuh"
 
 namespace qmmm {
@@ -31,7 +36,7 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
             const double *__restrict__ boys, const double *__restrict__ dm, double *__restrict__ gqm,
             double *__restrict__ gchg, int *err)
 {
-    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1), NA = ncart(LA), NB = ncart(LB);
+    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     {
@@ -51,72 +56,16 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
     const int ntile = (pp_end - pp_begin + 31) >> 5;
     for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
         const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
-        const bool mirror = pl.sp.shA != pl.sp.shB;
-        const double coef = TWO_PI * pl.ip * pl.cab;
         const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
+        double D0[NH];
+        fold_density<LA, LB>(pl, bd, dm, D0);
+        // S_tuv = sum_C q_C R_tuv(P - C): the centre-A derivative coefficients are contracted with
+        // it once per pair after the charge sweep
+        double S[NH];
+#pragma unroll
+        for (int k = 0; k < NH; ++k) S[k] = 0.0;
 
-        double D0[NH], Dx[NH], Dy[NH], Dz[NH];
-#pragma unroll
-        for (int k = 0; k < NH; ++k) D0[k] = Dx[k] = Dy[k] = Dz[k] = 0.0;
-        {
-            double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
-            hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
-            hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
-            hermite_E<LA + 1, LB, double>(Ez, pl.P[2] - pl.A[2], pl.P[2] - pl.B[2], 0.5 * pl.ip);
-#pragma unroll
-            for (int ia = 0; ia < NA; ++ia) {
-#pragma unroll
-                for (int ib = 0; ib < NB; ++ib) {
-                    const int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
-                    const int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
-                    double g = 0.0;
-                    if (pl.active) {
-                        const size_t r = pl.sp.aoA + ia, c = pl.sp.aoB + ib;
-                        g = dm[r * bd.nao + c];
-                        if (mirror) g += dm[c * bd.nao + r];
-                        g *= coef;
-                    }
-                    // derivative coefficients along each direction (t runs to i+j; E'_{i+j+1} = 0)
-                    double dEx[L + 1], dEy[L + 1], dEz[L + 1];
-#pragma unroll
-                    for (int t = 0; t <= ax + bx; ++t) {
-                        double e = 2.0 * pl.a * Ex[ax + 1][bx][t];
-                        if (ax > 0) e -= ax * Ex[ax - 1][bx][t];
-                        if (t > 0) e -= aop * Ex[ax][bx][t - 1];
-                        dEx[t] = e;
-                    }
-#pragma unroll
-                    for (int u = 0; u <= ay + by; ++u) {
-                        double e = 2.0 * pl.a * Ey[ay + 1][by][u];
-                        if (ay > 0) e -= ay * Ey[ay - 1][by][u];
-                        if (u > 0) e -= aop * Ey[ay][by][u - 1];
-                        dEy[u] = e;
-                    }
-#pragma unroll
-                    for (int w = 0; w <= az + bz; ++w) {
-                        double e = 2.0 * pl.a * Ez[az + 1][bz][w];
-                        if (az > 0) e -= az * Ez[az - 1][bz][w];
-                        if (w > 0) e -= aop * Ez[az][bz][w - 1];
-                        dEz[w] = e;
-                    }
-#pragma unroll
-                    for (int t = 0; t <= ax + bx; ++t)
-#pragma unroll
-                        for (int u = 0; u <= ay + by; ++u)
-#pragma unroll
-                            for (int w = 0; w <= az + bz; ++w) {
-                                const int k = hidx(t, u, w);
-                                const double ex = Ex[ax][bx][t], ey = Ey[ay][by][u], ez = Ez[az][bz][w];
-                                D0[k] += g * ex * ey * ez;
-                                Dx[k] += g * dEx[t] * ey * ez;
-                                Dy[k] += g * ex * dEy[u] * ez;
-                                Dz[k] += g * ex * ey * dEz[w];
-                            }
-                }
-            }
-        }
-
-        double sdx = 0, sdy = 0, sdz = 0, sex = 0, sey = 0, sez = 0;
+        double sex = 0, sey = 0, sez = 0;
         for (int c = 0; c < rg.ncls; ++c) {
             const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
             const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
@@ -139,7 +88,8 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                 }
                 double R[NH1];
                 hermite_R<L + 1, double>(R, Fn, X, Y, Z);
-                double e0 = 0, ex = 0, ey = 0, ez = 0, dx = 0, dy = 0, dz = 0;
+                double e0 = 0, ex = 0, ey = 0, ez = 0;
+                const double q = ch.w;
 #pragma unroll
                 for (int t = 0; t <= L; ++t)
 #pragma unroll
@@ -151,12 +101,8 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                             ex += D0[k] * R[hidx(t + 1, u, w)];
                             ey += D0[k] * R[hidx(t, u + 1, w)];
                             ez += D0[k] * R[hidx(t, u, w + 1)];
-                            dx += Dx[k] * R[k];
-                            dy += Dy[k] * R[k];
-                            dz += Dz[k] * R[k];
+                            S[k] += q * R[k];
                         }
-                const double q = ch.w;
-                sdx += q * dx; sdy += q * dy; sdz += q * dz;
                 sex += q * ex; sey += q * ey; sez += q * ez;
                 // per-charge sums over the 32 primitive pairs of (dE/dC_x, dE/dC_y, dE/dC_z, dE/dq) =
                 // (q e_x, q e_y, q e_z, -e0): halve the four values twice (each lane keeps one
@@ -179,6 +125,9 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                 }
             }
         }
+        double sd[3];
+        contract_dA<LA, LB>(pl, bd, dm, S, sd);
+        const double sdx = sd[0], sdy = sd[1], sdz = sd[2];
         // dE/dA = -(sd + a/p se), dE/dB = sd - b/p se
         double g[6] = {-(sdx + aop * sex), -(sdy + aop * sey), -(sdz + aop * sez),
                        sdx - bop * sex, sdy - bop * sey, sdz - bop * sez};
@@ -207,7 +156,7 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
                              int nsm, int nslice, cudaStream_t st)
 {
     const int nper = (ch_end - ch_begin + nslice - 1) / nslice;  // charges per slice
-    const size_t smem = (size_t)nper * (sizeof(double4_32a) + 4 * sizeof(double));
+    const size_t smem = std::max((size_t)nper * (sizeof(double4_32a) + 4 * sizeof(double)), SWEEP_SMEM_MIN);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_vgrad_f64<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

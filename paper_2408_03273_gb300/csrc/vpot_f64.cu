@@ -12,6 +12,8 @@
 // head lane adds the block into V (and its mirror).  A shell pair spans at most two tiles when
 // it has at most 32 primitive pairs, so at most two additions reach any element: the result does
 // not depend on scheduling.
+#include <algorithm>
+
 #include "pp_tile.cuh"
 
 namespace qmmm {
@@ -122,7 +124,7 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
                              size_t vstride, cudaStream_t st)
 {
     const int per = (ch_end - ch_begin + nslice - 1) / nslice;
-    const size_t smem = (size_t)per * sizeof(double4_32a);
+    const size_t smem = std::max((size_t)per * sizeof(double4_32a), SWEEP_SMEM_MIN);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_vpot_f64<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
