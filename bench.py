@@ -54,15 +54,19 @@ def flops_forward(L):
 
 def flops_adjoint(L):
     """Per (primitive pair, charge) of the adjoint sweep: Boys to L+1 (28+3L), R recursion to L+1
-    2 C(L+5,4), seven contractions 14 C(L+3,3), setup/accumulation/reduction 47."""
-    return 28 + 3 * L + 2 * comb(L + 5, 4) + 14 * comb(L + 3, 3) + 47
+    2 C(L+5,4), the four density contractions (e_0, e_x, e_y, e_z) and the charge sum
+    S += q R over the C(L+3,3) Hermite terms 10 C(L+3,3), setup/accumulation/reduction 47.  The
+    centre-A derivative coefficients meet S once per pair, not per charge, so they are not
+    counted per term."""
+    return 28 + 3 * L + 2 * comb(L + 5, 4) + 10 * comb(L + 3, 3) + 47
 
 
 CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la(la+1)/2 + lb
 
 # DRAM bytes (read + write) of one adjoint sweep (all class kernels of one launch round), from
-# the ncu capture summarised in profiles/vgrad_traffic_c2.md; None where not captured.
-SWEEP_TRAFFIC = {("c2", "fp64"): 25_316_608, ("c2", "mixed"): 21_309_184}
+# the ncu capture summarised in profiles/vgrad_traffic_c2.md; None where not captured (or where
+# the kernels changed after the capture).
+SWEEP_TRAFFIC = {("c2", "fp64"): 24_514_560, ("c2", "mixed"): 20_645_120}
 
 
 def sweep_flops(info, adjoint):

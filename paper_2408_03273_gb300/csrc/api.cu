@@ -672,13 +672,13 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
     int rc;
     float t_model = 0.f, t_tuned = 0.f;
     if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, -1, 0, 0); }, &t_model))) return rc;
-    double ms[NCLASS] = {};
+    double ms[NCLASS] = {}, ms0[NCLASS] = {}, cost0[NCLASS] = {};
     for (int round = 0; round < 2; ++round) {
         split_sms(h, kind, h->cls_variant[kind], share);
         double cost[NCLASS];
         int var[NCLASS];
         for (int c = 0; c < NCLASS; ++c) {
-            cost[c] = h->cls_cost[kind][c];
+            cost[c] = cost0[c] = h->cls_cost[kind][c];
             var[c] = h->cls_variant[kind][c];
             const int npp = h->class_off[c + 1] - h->class_off[c];
             if (npp <= 0) continue;
@@ -690,6 +690,10 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
                 const int nwarp = variant_threads(kind, c, v) / 32;
                 const int blocks = std::min(share[c], ((npp + 31) / 32 + nwarp - 1) / nwarp);
                 const double smt = (double)t * blocks;
+                if (v == 0) {
+                    cost0[c] = smt / npp;
+                    ms0[c] = t;
+                }
                 if (smt < best) {
                     best = smt;
                     var[c] = v;
@@ -704,8 +708,28 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
         }
     }
     if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, -1, 0, 0); }, &t_tuned))) return rc;
-    if (t_tuned < t_model) {
-        for (int c = 0; c < NCLASS; ++c) h->cls_ms[kind][c] = ms[c];
+    // A wide block that wins alone can lose in the concurrent sweep (its lower register cap
+    // spills, and the spill traffic of all classes meets in L2): also try the measured split with
+    // 256-thread blocks only, and keep the fastest of the three schedules.
+    double tc[NCLASS];
+    int tv[NCLASS];
+    for (int c = 0; c < NCLASS; ++c) {
+        tc[c] = h->cls_cost[kind][c];
+        tv[c] = h->cls_variant[kind][c];
+        h->cls_cost[kind][c] = cost0[c];
+        h->cls_variant[kind][c] = 0;
+    }
+    float t_narrow = 0.f;
+    if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, -1, 0, 0); }, &t_narrow))) return rc;
+    if (t_narrow < t_model && t_narrow <= t_tuned) {
+        for (int c = 0; c < NCLASS; ++c) h->cls_ms[kind][c] = ms0[c];
+        h->tuned_mask |= 1 << kind;
+    } else if (t_tuned < t_model) {
+        for (int c = 0; c < NCLASS; ++c) {
+            h->cls_cost[kind][c] = tc[c];
+            h->cls_variant[kind][c] = tv[c];
+            h->cls_ms[kind][c] = ms[c];
+        }
         h->tuned_mask |= 1 << kind;
     } else {
         reset_tuning(h, kind);
