@@ -57,7 +57,8 @@ def flops_adjoint(L):
     2 C(L+5,4), the four density contractions (e_0, e_x, e_y, e_z) and the charge sum
     S += q R over the C(L+3,3) Hermite terms 10 C(L+3,3), setup/accumulation/reduction 47.  The
     centre-A derivative coefficients meet S once per pair, not per charge, so they are not
-    counted per term."""
+    counted per term (the FP64 kernels of the f-shell classes with L >= 5 contract them per
+    charge instead: 4 C(L+3,3) more than counted here)."""
     return 28 + 3 * L + 2 * comb(L + 5, 4) + 10 * comb(L + 3, 3) + 47
 
 

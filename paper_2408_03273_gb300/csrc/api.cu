@@ -540,11 +540,34 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share, i
 // Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
 // forked from and joined back into the handle's stream, its grid capped at its share of the SMs
 // (so small classes do not leave most SMs idle while they run alone).
-// maxsl > 1 (adjoint sweeps, whose charge slices need no buffers of their own): a class with
-// fewer 32-pair tiles than its share of the SMs asks for splits its charges over up to maxsl
-// block rows, so that a few high-l pairs do not hold the whole sweep on a few SMs.
+// Charge slices of one adjoint class.  The warps of a class sweep take whole 32-pair tiles, so
+// the class finishes when its busiest warp does, after ceil(tiles / warps) tiles: a high-l class
+// with 1.2 tiles per warp on average runs as long as with 2.  Splitting the charges over ns block
+// rows makes the work units ns times finer.  Picks the rows ns <= maxsl and blocks per row gx
+// (gx ns <= share) that minimise the busiest warp's work, in charges, with the per-pair setup
+// that every row repeats counted as `setup` charges; fewer rows win near-ties.
+void class_slices(int tiles, int nwarp, int share, int nch, int maxsl, double setup, int *gx, int *ns)
+{
+    double best = 1e300;
+    *gx = std::max(1, share);
+    *ns = 1;
+    for (int s = 1; s <= maxsl && share / s >= 1; ++s) {
+        const int g = std::min(share / s, (tiles + nwarp - 1) / nwarp);
+        const int per_warp = (tiles + g * nwarp - 1) / (g * nwarp);
+        const double t = per_warp * (setup + (double)((nch + s - 1) / s));
+        if (t < 0.98 * best) {
+            best = t;
+            *gx = g;
+            *ns = s;
+        }
+    }
+}
+
+// maxsl > 1 (adjoint sweeps over nch charges, whose charge slices need no buffers of their own):
+// every class picks its own charge slices (class_slices), and a class with fewer tiles than its
+// share of the SMs may take up to maxsl times its tile count in blocks.
 template <typename F>
-int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1)
+int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1, int nch = 0)
 {
     int share[NCLASS];
     if (!split_sms(h, kind, h->cls_variant[kind], share, nslice == 1 ? maxsl : 1)) return QMMM_OK;
@@ -554,9 +577,11 @@ int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 
         if (p1 <= p0) continue;
         int sh = share[c], ns = nslice;
         if (nslice == 1 && maxsl > 1) {
-            const int cap = tile_cap(h, kind, c, h->cls_variant[kind][c]);
-            ns = std::min(maxsl, (sh + cap - 1) / cap);
-            sh = (sh + ns - 1) / ns;
+            const int nwarp = variant_threads(kind, c, h->cls_variant[kind][c]) / 32;
+            // per-pair setup in charges of sweep work: FP64 Hermite/density setup against an FP64
+            // charge loop (~1%), or against an FP32 one (several percent)
+            const double setup = kind_is_mixed(kind) ? 64.0 : 16.0;
+            class_slices((p1 - p0 + 31) / 32, nwarp, sh, nch, maxsl, setup, &sh, &ns);
         }
         CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
         CUDA_TRY(launch(c, p0, p1, sh, h->cls_variant[kind][c], ns, h->side[c]));
@@ -656,7 +681,10 @@ int tune_launch(qmmm_handle *h, int kind, int cls, int share, int variant)
         return launch_sweep(h, kind, c, p0, p1, 0, c1, s, v, ns, 0, h->tune_dm.p, h->tune_V.p, h->tune_gqm.p,
                             h->tune_gchg.p, cs);
     };
-    if (cls < 0) return run_classes(h, kind, one);
+    if (cls < 0) {
+        if (kind_is_grad(kind)) return run_classes(h, kind, one, 1, std::max(1, std::min(8, c1 / 128)), c1);
+        return run_classes(h, kind, one);
+    }
     CUDA_TRY(one(cls, h->class_off[cls], h->class_off[cls + 1], share, variant, 1, h->stream));
     return QMMM_OK;
 }
@@ -687,9 +715,14 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
             for (int v = 0; v < nvar; ++v) {
                 float t = 0.f;
                 if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, c, share[c], v); }, &t))) return rc;
-                const int nwarp = variant_threads(kind, c, v) / 32;
-                const int blocks = std::min(share[c], ((npp + 31) / 32 + nwarp - 1) / nwarp);
-                const double smt = (double)t * blocks;
+                // SM-time.  Adjoint: with every warp equally loaded (the kernel ran
+                // ceil(tiles / warps) tile passes, so its time per pass times tiles / warps per
+                // block is the class's work free of the tile quantisation, which the adjoint's
+                // charge slices remove); V: as launched.
+                const int nwarp = variant_threads(kind, c, v) / 32, tiles = (npp + 31) / 32;
+                const int blocks = std::min(share[c], (tiles + nwarp - 1) / nwarp);
+                const int passes = (tiles + blocks * nwarp - 1) / (blocks * nwarp);
+                const double smt = kind_is_grad(kind) ? (double)t / passes * tiles / nwarp : (double)t * blocks;
                 if (v == 0) {
                     cost0[c] = smt / npp;
                     ms0[c] = t;
@@ -1260,7 +1293,7 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
                 return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, 0, ddm, nullptr, h->gqm.p,
                                     h->gchg.p, cs);
             },
-            ns, std::max(1, std::min(8, (c1 - c0) / 256)));
+            ns, std::max(1, std::min(8, (c1 - c0) / 128)), c1 - c0);
         if (rc) return rc;
     }
     CUDA_TRY(mark(h, 1));

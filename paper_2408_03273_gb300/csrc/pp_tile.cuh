@@ -95,15 +95,19 @@ __device__ __forceinline__ void fold_density(const PPLane &pl, const BasisDev &b
 
 // The centre-A derivative coefficients themselves, Da_tuv = sum_ab g_ab E'^a_{tuv} (E'^a as in
 // contract_dA below), for a sweep that contracts them with partial charge sums.
-template <int LA, int LB>
+// With WITH_D0, D0 (as in fold_density) is formed in the same pass.
+template <int LA, int LB, bool WITH_D0 = false>
 __device__ __forceinline__ void fold_density_dA(const PPLane &pl, const BasisDev &bd, const double *__restrict__ dm,
                                                 double (&Dx)[nherm(LA + LB)], double (&Dy)[nherm(LA + LB)],
-                                                double (&Dz)[nherm(LA + LB)])
+                                                double (&Dz)[nherm(LA + LB)], double *D0 = nullptr)
 {
     constexpr int L = LA + LB, NA = ncart(LA), NB = ncart(LB);
     const double aop = pl.a * pl.ip;
 #pragma unroll
-    for (int k = 0; k < nherm(L); ++k) Dx[k] = Dy[k] = Dz[k] = 0.0;
+    for (int k = 0; k < nherm(L); ++k) {
+        Dx[k] = Dy[k] = Dz[k] = 0.0;
+        if constexpr (WITH_D0) D0[k] = 0.0;
+    }
     double Ex[LA + 2][LB + 1][L + 2], Ey[LA + 2][LB + 1][L + 2], Ez[LA + 2][LB + 1][L + 2];
     hermite_E<LA + 1, LB, double>(Ex, pl.P[0] - pl.A[0], pl.P[0] - pl.B[0], 0.5 * pl.ip);
     hermite_E<LA + 1, LB, double>(Ey, pl.P[1] - pl.A[1], pl.P[1] - pl.B[1], 0.5 * pl.ip);
@@ -148,6 +152,7 @@ __device__ __forceinline__ void fold_density_dA(const PPLane &pl, const BasisDev
                         Dx[k] += dEx[t] * ey * ez;
                         Dy[k] += gx * dEy[u] * ez;
                         Dz[k] += gx * ey * dEz[w];
+                        if constexpr (WITH_D0) D0[k] += gx * ey * ez;
                     }
         }
 }

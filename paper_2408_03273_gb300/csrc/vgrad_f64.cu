@@ -9,8 +9,9 @@
 // (R recomputed up to L+1 for every charge, never stored):
 //   dI/dA_a = d_a + (a/p) e_a,   dI/dB_a = -d_a + (b/p) e_a,   dI/dC_a = -e_a,
 // and E contains -q_C I.  The d_a enter only through sum_C q_C d_a(C) = sum Da_tuv S_tuv with
-// S_tuv = sum_C q_C R_tuv, so the sweep accumulates S (NH terms per charge instead of the 3 NH
-// of the three contractions) and Da is formed and contracted once per pair after it (contract_dA).
+// S_tuv = sum_C q_C R_tuv, so up to L = 4 the sweep accumulates S (NH terms per charge instead
+// of the 3 NH of the three contractions) and Da is formed and contracted once per pair after it
+// (contract_dA); for L >= 5 the three contractions stay in the loop (see CSUM).
 // Per-pair sums over charges stay in registers; per-charge sums over the
 // 32 primitive pairs of a tile use a warp butterfly and go to shared-memory accumulators that
 // are flushed to global memory once per block.
@@ -58,14 +59,21 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
         const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
         const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
         double D0[NH];
-        fold_density<LA, LB>(pl, bd, dm, D0);
-        // S_tuv = sum_C q_C R_tuv(P - C): the centre-A derivative coefficients are contracted with
-        // it once per pair after the charge sweep
-        double S[NH];
+        // L <= 4: S_tuv = sum_C q_C R_tuv(P - C), contracted with the centre-A derivative
+        // coefficients once per pair after the charge sweep.  L >= 5 (f shells with d or f): S
+        // would be read and written every charge from a register file already full, so there
+        // the derivative coefficients are contracted per charge (only read in the loop).
+        constexpr bool CSUM = L <= 4;
+        double S[CSUM ? NH : 1], Dx[CSUM ? 1 : NH], Dy[CSUM ? 1 : NH], Dz[CSUM ? 1 : NH];
+        if constexpr (CSUM) {
+            fold_density<LA, LB>(pl, bd, dm, D0);
 #pragma unroll
-        for (int k = 0; k < NH; ++k) S[k] = 0.0;
+            for (int k = 0; k < NH; ++k) S[k] = 0.0;
+        } else {
+            fold_density_dA<LA, LB, true>(pl, bd, dm, Dx, Dy, Dz, D0);
+        }
 
-        double sex = 0, sey = 0, sez = 0;
+        double sex = 0, sey = 0, sez = 0, sdx = 0, sdy = 0, sdz = 0;
         for (int c = 0; c < rg.ncls; ++c) {
             const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
             const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
@@ -88,7 +96,7 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                 }
                 double R[NH1];
                 hermite_R<L + 1, double>(R, Fn, X, Y, Z);
-                double e0 = 0, ex = 0, ey = 0, ez = 0;
+                double e0 = 0, ex = 0, ey = 0, ez = 0, dx = 0, dy = 0, dz = 0;
                 const double q = ch.w;
 #pragma unroll
                 for (int t = 0; t <= L; ++t)
@@ -101,9 +109,18 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                             ex += D0[k] * R[hidx(t + 1, u, w)];
                             ey += D0[k] * R[hidx(t, u + 1, w)];
                             ez += D0[k] * R[hidx(t, u, w + 1)];
-                            S[k] += q * R[k];
+                            if constexpr (CSUM) {
+                                S[k] += q * R[k];
+                            } else {
+                                dx += Dx[k] * R[k];
+                                dy += Dy[k] * R[k];
+                                dz += Dz[k] * R[k];
+                            }
                         }
                 sex += q * ex; sey += q * ey; sez += q * ez;
+                if constexpr (!CSUM) {
+                    sdx += q * dx; sdy += q * dy; sdz += q * dz;
+                }
                 // per-charge sums over the 32 primitive pairs of (dE/dC_x, dE/dC_y, dE/dC_z, dE/dq) =
                 // (q e_x, q e_y, q e_z, -e0): halve the four values twice (each lane keeps one
                 // component summed over 4 lanes), then a 3-step butterfly; lane 8c ends with
@@ -125,9 +142,13 @@ k_vgrad_f64(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                 }
             }
         }
-        double sd[3];
-        contract_dA<LA, LB>(pl, bd, dm, S, sd);
-        const double sdx = sd[0], sdy = sd[1], sdz = sd[2];
+        if constexpr (CSUM) {
+            double sd[3];
+            contract_dA<LA, LB>(pl, bd, dm, S, sd);
+            sdx = sd[0];
+            sdy = sd[1];
+            sdz = sd[2];
+        }
         // dE/dA = -(sd + a/p se), dE/dB = sd - b/p se
         double g[6] = {-(sdx + aop * sex), -(sdy + aop * sey), -(sdz + aop * sez),
                        sdx - bop * sex, sdy - bop * sey, sdz - bop * sez};
