@@ -443,8 +443,8 @@ def main():
                           if prec == q.QMMM_FP64 else "FP32 plain-ALU peak at 2070 MHz (152 SMs x 128 FFMA/clk)"),
             "flops_per_launch": fl}
 
-    # launches of our kernels per step (claim; the ncu launch list in profiles/ confirms it: 62
-    # per FP64 step of the active site).  Per call:
+    # launches of our kernels per step (claim; the ncu launch list in profiles/ confirms the
+    # composition: 63 per FP64 step of the active site).  Per call:
     #   set_positions: gather, region-I count/scan/fill, real-space, region-I tensors, background
     #     sum, QM-site reciprocal, final = 9, plus the structure factor (tensor cores: max|q|,
     #     phases, B planes, MMA, reduction = 5; CUDA cores: kernel + slice sum = 2)
@@ -454,9 +454,12 @@ def main():
     #     fixed (nuclear-MM, sum, real space, region I, background, tensor gradient, scatter,
     #     unpermute) + the MM-side reciprocal sum (tensor cores: atom phases, multipole structure
     #     factor, phases, scales, B planes per N tile, MMA = 5 + tiles; CUDA cores: 3)
-    # Small systems whose classes ask for less than half the SMs add one V slice-sum kernel.
+    # vpot adds one V slice-sum kernel when its classes split their charges (per-class slices:
+    # 256 or more region-I charges and room for two partial matrices in 512 MB; or small systems
+    # whose classes ask for less than half the SMs, which have fewer charges than that here).
     ncls = sum(1 for n in info["n_prim_pairs_class"] if n > 0)
     nI = info["n_region1"]
+    v_maxsl = min(8, min(nI, 4096) // 128, (512 << 20) // max(1, 8 * s.nao * s.nao))
     ch_f = math.ceil(nI / (4096)) if nI else 0
     ch_g = math.ceil(nI / 2560) if nI else 0
     tensor = recip_in_effect(prec) == RECIP_NAME[q.QMMM_RECIP_TENSOR]
@@ -466,7 +469,7 @@ def main():
     cpt = next((c for c in (3, 2, 1) if 2 * c * kx <= lim), 1)
     mm_tc = tensor and (2 * cpt * kx + 15) // 16 * 16 <= lim and 2 * s.kmax[2] + 1 >= 8
     mm_tiles = -(-3 // cpt)
-    per_step = (9 + (5 if tensor else 2)) + (ncls * ch_f + 1) + (ncls + 2) + \
+    per_step = (9 + (5 if tensor else 2)) + (ncls * ch_f + 1 + (1 if v_maxsl > 1 else 0)) + (ncls + 2) + \
         (2 * ncls + ncls * ch_g + 8 + ((5 + mm_tiles) if mm_tc else 3))
     launches = per_step * args.steps
 

@@ -540,7 +540,16 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share, i
 // Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
 // forked from and joined back into the handle's stream, its grid capped at its share of the SMs
 // (so small classes do not leave most SMs idle while they run alone).
-// Charge slices of one adjoint class.  The warps of a class sweep take whole 32-pair tiles, so
+// Most charge slices per V class: at least 128 charges each, at most 8, and the partial
+// matrices (one per slice, each V element written by one class and slice, summed in a fixed
+// order) within 512 MB.
+int vpot_max_slices(int nch, size_t n2)
+{
+    const size_t cap = ((size_t)512 << 20) / std::max<size_t>(1, n2 * sizeof(double));
+    return std::max(1, std::min({8, nch / 128, (int)std::min<size_t>(cap, 8)}));
+}
+
+// Charge slices of one class.  The warps of a class sweep take whole 32-pair tiles, so
 // the class finishes when its busiest warp does, after ceil(tiles / warps) tiles: a high-l class
 // with 1.2 tiles per warp on average runs as long as with 2.  Splitting the charges over ns block
 // rows makes the work units ns times finer.  Picks the rows ns <= maxsl and blocks per row gx
@@ -563,9 +572,9 @@ void class_slices(int tiles, int nwarp, int share, int nch, int maxsl, double se
     }
 }
 
-// maxsl > 1 (adjoint sweeps over nch charges, whose charge slices need no buffers of their own):
-// every class picks its own charge slices (class_slices), and a class with fewer tiles than its
-// share of the SMs may take up to maxsl times its tile count in blocks.
+// maxsl > 1 (sweeps over nch charges; V sweeps then write slice s of a class into partial
+// matrix s): every class picks its own charge slices (class_slices), and a class with fewer
+// tiles than its share of the SMs may take up to maxsl times its tile count in blocks.
 template <typename F>
 int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1, int nch = 0)
 {
@@ -682,8 +691,10 @@ int tune_launch(qmmm_handle *h, int kind, int cls, int share, int variant)
                             h->tune_gchg.p, cs);
     };
     if (cls < 0) {
-        if (kind_is_grad(kind)) return run_classes(h, kind, one, 1, std::max(1, std::min(8, c1 / 128)), c1);
-        return run_classes(h, kind, one);
+        // the slices of the real sweep (V slices all add into the one scratch matrix here)
+        const int maxsl = kind_is_grad(kind) ? std::max(1, std::min(8, c1 / 128))
+                                             : vpot_max_slices(c1, (size_t)h->nao * h->nao);
+        return run_classes(h, kind, one, 1, maxsl, c1);
     }
     CUDA_TRY(one(cls, h->class_off[cls], h->class_off[cls + 1], share, variant, 1, h->stream));
     return QMMM_OK;
@@ -715,14 +726,13 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
             for (int v = 0; v < nvar; ++v) {
                 float t = 0.f;
                 if ((rc = time_best(h, e0, e1, [&] { return tune_launch(h, kind, c, share[c], v); }, &t))) return rc;
-                // SM-time.  Adjoint: with every warp equally loaded (the kernel ran
-                // ceil(tiles / warps) tile passes, so its time per pass times tiles / warps per
-                // block is the class's work free of the tile quantisation, which the adjoint's
-                // charge slices remove); V: as launched.
+                // SM-time with every warp equally loaded: the kernel ran ceil(tiles / warps)
+                // tile passes, so its time per pass times tiles / warps per block is the class's
+                // work free of the tile quantisation, which the per-class charge slices remove
                 const int nwarp = variant_threads(kind, c, v) / 32, tiles = (npp + 31) / 32;
                 const int blocks = std::min(share[c], (tiles + nwarp - 1) / nwarp);
                 const int passes = (tiles + blocks * nwarp - 1) / (blocks * nwarp);
-                const double smt = kind_is_grad(kind) ? (double)t / passes * tiles / nwarp : (double)t * blocks;
+                const double smt = (double)t / passes * tiles / nwarp;
                 if (v == 0) {
                     cost0[c] = smt / npp;
                     ms0[c] = t;
@@ -1182,10 +1192,14 @@ int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
     const int kind = sweep_kind(h, false), ch = chunk_for_kind(kind);
     const size_t n2 = (size_t)h->nao * h->nao;
     const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
+    // otherwise per-class charge slices (class_slices), as many as the per-slice partial
+    // matrices' memory allows
+    const int maxsl = ns > 1 ? 1 : vpot_max_slices(std::min(h->nI, ch), n2);
+    const int nbuf = std::max(ns, maxsl);
     double *Vdst = h->V.p;
-    if (ns > 1) {  // per-slice partial V, summed in a fixed order afterwards
-        if ((rc = h->Vslices.ensure((size_t)ns * n2))) return rc;
-        CUDA_TRY(cudaMemsetAsync(h->Vslices.p, 0, (size_t)ns * n2 * sizeof(double), st));
+    if (nbuf > 1) {  // per-slice partial V, summed in a fixed order afterwards
+        if ((rc = h->Vslices.ensure((size_t)nbuf * n2))) return rc;
+        CUDA_TRY(cudaMemsetAsync(h->Vslices.p, 0, (size_t)nbuf * n2 * sizeof(double), st));
         Vdst = h->Vslices.p;
     }
     CUDA_TRY(mark(h, 0));
@@ -1194,13 +1208,13 @@ int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
         rc = run_classes(
             h, kind,
             [&](int cls, int p0, int p1, int share, int variant, int nsl, cudaStream_t cs) {
-                return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, nsl > 1 ? n2 : 0, nullptr, Vdst,
-                                    nullptr, nullptr, cs);
+                return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, nbuf > 1 ? n2 : 0, nullptr,
+                                    Vdst, nullptr, nullptr, cs);
             },
-            ns);
+            ns, maxsl, c1 - c0);
         if (rc) return rc;
     }
-    if (ns > 1) CUDA_TRY(launch_sum_slices_d(h->Vslices.p, ns, n2, h->V.p, st));
+    if (nbuf > 1) CUDA_TRY(launch_sum_slices_d(h->Vslices.p, nbuf, n2, h->V.p, st));
     CUDA_TRY(mark(h, 1));
     CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
                            nullptr, 0, st));
