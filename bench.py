@@ -67,7 +67,7 @@ CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la
 # DRAM bytes (read + write) of one adjoint sweep (all class kernels of one launch round), from
 # the ncu capture summarised in profiles/vgrad_traffic_c2.md; None where not captured (or where
 # the kernels changed after the capture).
-SWEEP_TRAFFIC = {("c2", "fp64"): 24_514_560, ("c2", "mixed"): 20_645_120}
+SWEEP_TRAFFIC = {("c2", "fp64"): 24_183_040, ("c2", "mixed"): 21_820_672}
 
 
 def sweep_flops(info, adjoint):
