@@ -537,9 +537,6 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share, i
     return true;
 }
 
-// Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
-// forked from and joined back into the handle's stream, its grid capped at its share of the SMs
-// (so small classes do not leave most SMs idle while they run alone).
 // Most charge slices per V class: at least 128 charges each, at most 8, and the partial
 // matrices (one per slice, each V element written by one class and slice, summed in a fixed
 // order) within 512 MB.
@@ -572,9 +569,12 @@ void class_slices(int tiles, int nwarp, int share, int nch, int maxsl, double se
     }
 }
 
-// maxsl > 1 (sweeps over nch charges; V sweeps then write slice s of a class into partial
-// matrix s): every class picks its own charge slices (class_slices), and a class with fewer
-// tiles than its share of the SMs may take up to maxsl times its tile count in blocks.
+// Launch the sweep of every non-empty angular class concurrently: each class on its own stream,
+// forked from and joined back into the handle's stream, its grid capped at its share of the SMs
+// (so small classes do not leave most SMs idle while they run alone).  With maxsl > 1 (sweeps
+// over nch charges; V sweeps then write slice s of a class into partial matrix s) every class
+// picks its own charge slices (class_slices), and a class with fewer tiles than its share of the
+// SMs may take up to maxsl times its tile count in blocks.
 template <typename F>
 int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1, int nch = 0)
 {
