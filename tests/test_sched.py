@@ -1,0 +1,110 @@
+"""Host-side scheduling rules of the concurrent class sweeps (csrc/sched.h), compiled with the
+host C++ compiler and checked against brute force and the invariants the launcher relies on:
+the blocks never exceed the class's share of the SMs or its tile count, the slice count stays
+within its bound, the chosen slices are never worse than none, and their busiest-warp work is
+within the 2% near-tie margin of the best slicing."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2408_03273_gb300", "csrc")
+
+DRIVER = r"""
+#include <cstdio>
+#include "sched.h"
+int main()
+{
+    char op;
+    while (std::scanf(" %c", &op) == 1) {
+        if (op == 'c') {
+            int tiles, nwarp, share, nch, maxsl;
+            double setup;
+            if (std::scanf("%d %d %d %d %d %lf", &tiles, &nwarp, &share, &nch, &maxsl, &setup) != 6) return 1;
+            int gx = 0, ns = 0;
+            qmmm::class_slices(tiles, nwarp, share, nch, maxsl, setup, &gx, &ns);
+            std::printf("%d %d\n", gx, ns);
+        } else if (op == 'v') {
+            int nch;
+            unsigned long long n2;
+            if (std::scanf("%d %llu", &nch, &n2) != 2) return 1;
+            std::printf("%d\n", qmmm::vpot_max_slices(nch, (size_t)n2));
+        }
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def sched(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("sched")
+    src, exe = d / "drv.cpp", d / "drv"
+    src.write_text(DRIVER)
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+
+    def run(lines):
+        out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True,
+                             check=True).stdout.split("\n")
+        return [tuple(int(x) for x in ln.split()) for ln in out if ln.strip()]
+
+    return run
+
+
+def busiest(tiles, nwarp, gx, ns, nch, setup):
+    per_warp = -(-tiles // (gx * nwarp))
+    return per_warp * (setup + -(-nch // ns))
+
+
+def test_active_site_dd_class(sched):
+    # FP64 (d,d) class of the active site: 269 tiles, 8 warps per block, 28 SMs, 1730 charges.
+    # One slice leaves 2 tiles on the busiest warp against 1.2 on average; four slices of 7
+    # blocks give it 5 tiles of 433 charges (2164 + setup) instead of 2 x 1730.
+    (gx, ns), = sched(["c 269 8 28 1730 8 16"])
+    assert (gx, ns) == (7, 4)
+    assert busiest(269, 8, gx, ns, 1730, 16) < 0.7 * busiest(269, 8, 28, 1, 1730, 16)
+
+
+def test_many_tiles_need_no_slices(sched):
+    # (s,s) class: 1344 tiles on 12 blocks of 8 warps = 14 passes exactly; slices cannot help
+    (gx, ns), = sched(["c 1344 8 12 1730 8 16"])
+    assert (gx, ns) == (12, 1)
+
+
+def test_rules_against_brute_force(sched):
+    rng = np.random.default_rng(2408)
+    cases = []
+    for _ in range(400):
+        tiles = int(rng.integers(1, 3000))
+        nwarp = int(rng.choice([8, 12, 16, 20, 24, 28, 32]))
+        share = int(rng.integers(1, 153))
+        nch = int(rng.integers(1, 4097))
+        maxsl = int(rng.integers(1, 9))
+        setup = float(rng.choice([16.0, 64.0]))
+        cases.append((tiles, nwarp, share, nch, maxsl, setup))
+    res = sched([f"c {t} {w} {s} {n} {m} {u}" for t, w, s, n, m, u in cases])
+    for (tiles, nwarp, share, nch, maxsl, setup), (gx, ns) in zip(cases, res):
+        assert 1 <= ns <= maxsl
+        assert gx >= 1 and gx * ns <= share
+        assert gx <= -(-tiles // nwarp)
+        chosen = busiest(tiles, nwarp, gx, ns, nch, setup)
+        none = busiest(tiles, nwarp, min(share, -(-tiles // nwarp)), 1, nch, setup)
+        assert chosen <= none
+        best = min(busiest(tiles, nwarp, min(share // s, -(-tiles // nwarp)), s, nch, setup)
+                   for s in range(1, maxsl + 1) if share // s >= 1)
+        assert chosen <= best / 0.98 + 1e-9
+
+
+def test_vpot_slice_bound(sched):
+    n2_small = 1560 * 1560          # active site: 19.5 MB per partial matrix
+    n2_large = 5100 * 5100          # large site: 208 MB per partial matrix
+    n2_huge = 9000 * 9000           # 648 MB: no room for two
+    res = sched([f"v 1730 {n2_small}", f"v 200 {n2_small}", f"v 100 {n2_small}",
+                 f"v 1321 {n2_large}", f"v 4096 {n2_huge}", f"v 4096 1"])
+    assert [r[0] for r in res] == [8, 1, 1, 2, 1, 8]
