@@ -501,40 +501,25 @@ int tile_cap(const qmmm_handle *h, int kind, int cls, int variant)
 // what a capped class cannot use goes to the others.  Returns false when no class has work.
 bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share, int maxsl = 1)
 {
-    double w[NCLASS], s[NCLASS];
+    double w[NCLASS];
     int cap[NCLASS];
     bool open[NCLASS];
     int nopen = 0;
     for (int c = 0; c < NCLASS; ++c) {
         const int npp = h->class_off[c + 1] - h->class_off[c];
-        share[c] = 0;
         open[c] = npp > 0;
+        cap[c] = 0;
+        w[c] = 0.0;
         if (!open[c]) continue;
         cap[c] = tile_cap(h, kind, c, variant[c]) * maxsl;
         w[c] = npp * std::max(h->cls_cost[kind][c], 1e-30);
         ++nopen;
     }
-    if (!nopen) return false;
-    double left = h->nsm;
-    for (bool again = true; again;) {
-        again = false;
-        double W = 0.0;
-        for (int c = 0; c < NCLASS; ++c)
-            if (open[c]) W += w[c];
-        for (int c = 0; c < NCLASS; ++c) {
-            if (!open[c]) continue;
-            s[c] = W > 0.0 ? left * w[c] / W : 0.0;
-            if (s[c] >= cap[c]) {  // capped: fix it and share the rest again
-                share[c] = cap[c];
-                left -= cap[c];
-                open[c] = false;
-                again = true;
-                break;
-            }
-        }
+    if (!nopen) {
+        for (int c = 0; c < NCLASS; ++c) share[c] = 0;
+        return false;
     }
-    for (int c = 0; c < NCLASS; ++c)
-        if (open[c]) share[c] = std::min(cap[c], std::max(1, (int)std::lround(s[c])));
+    split_shares(NCLASS, w, cap, open, h->nsm, share);
     return true;
 }
 

@@ -39,4 +39,56 @@ inline void class_slices(int tiles, int nwarp, int share, int nch, int maxsl, do
     }
 }
 
+// Shares of nsm SMs for n classes in proportion to their weights w (SM-time: primitive pairs x
+// cost), each at most cap[c] blocks; a class whose proportional share reaches its cap is fixed at
+// the cap and the rest is shared again.  Rounding keeps the total within nsm (largest remainders
+// first, never above a cap) so that one-block-per-SM sweeps are not oversubscribed; every open
+// class gets at least one block.  Classes with open[c] false get 0.
+inline void split_shares(int n, const double *w, const int *cap, const bool *open_in, int nsm, int *share)
+{
+    bool open[64];
+    double s[64];
+    for (int c = 0; c < n; ++c) {
+        open[c] = open_in[c];
+        share[c] = 0;
+        s[c] = 0.0;
+    }
+    double left = nsm;
+    for (bool again = true; again;) {
+        again = false;
+        double W = 0.0;
+        for (int c = 0; c < n; ++c)
+            if (open[c]) W += w[c];
+        for (int c = 0; c < n; ++c) {
+            if (!open[c]) continue;
+            s[c] = W > 0.0 ? left * w[c] / W : 0.0;
+            if (s[c] >= cap[c]) {  // capped: fix it and share the rest again
+                share[c] = cap[c];
+                left -= cap[c];
+                open[c] = false;
+                again = true;
+                break;
+            }
+        }
+    }
+    int given = 0;
+    for (int c = 0; c < n; ++c)
+        if (open[c]) {
+            share[c] = std::min(cap[c], std::max(1, (int)s[c]));
+            given += share[c];
+        }
+    // the SMs the floors left over, to the largest remainders
+    for (int extra = (int)left - given; extra > 0; --extra) {
+        int best = -1;
+        double frac = -1.0;
+        for (int c = 0; c < n; ++c)
+            if (open[c] && share[c] < cap[c] && s[c] - share[c] > frac) {
+                frac = s[c] - share[c];
+                best = c;
+            }
+        if (best < 0 || frac <= 0.0) break;
+        ++share[best];
+    }
+}
+
 }  // namespace qmmm

@@ -27,6 +27,17 @@ int main()
             int gx = 0, ns = 0;
             qmmm::class_slices(tiles, nwarp, share, nch, maxsl, setup, &gx, &ns);
             std::printf("%d %d\n", gx, ns);
+        } else if (op == 's') {
+            int n, nsm;
+            if (std::scanf("%d %d", &n, &nsm) != 2 || n > 64) return 1;
+            double w[64];
+            int cap[64], share[64], o;
+            bool open[64];
+            for (int c = 0; c < n; ++c)
+                if (std::scanf("%lf %d %d", &w[c], &cap[c], &o) != 3) return 1; else open[c] = o != 0;
+            qmmm::split_shares(n, w, cap, open, nsm, share);
+            for (int c = 0; c < n; ++c) std::printf("%d ", share[c]);
+            std::printf("\n");
         } else if (op == 'v') {
             int nch;
             unsigned long long n2;
@@ -108,3 +119,66 @@ def test_vpot_slice_bound(sched):
     res = sched([f"v 1730 {n2_small}", f"v 200 {n2_small}", f"v 100 {n2_small}",
                  f"v 1321 {n2_large}", f"v 4096 {n2_huge}", f"v 4096 1"])
     assert [r[0] for r in res] == [8, 1, 1, 2, 1, 8]
+
+
+def exact_shares(w, cap, open_, nsm):
+    """The proportional split with caps, unrounded (the rule the host code follows)."""
+    open_ = list(open_)
+    fixed = [0.0] * len(w)
+    left = float(nsm)
+    while True:
+        W = sum(wc for wc, o in zip(w, open_) if o)
+        for c, o in enumerate(open_):
+            if o and W > 0 and left * w[c] / W >= cap[c]:
+                fixed[c] = cap[c]
+                left -= cap[c]
+                open_[c] = False
+                break
+        else:
+            break
+    return [fixed[c] if not open_[c] else (left * w[c] / W if W > 0 else 0.0) for c in range(len(w))], open_
+
+
+def test_shares_never_oversubscribe(sched):
+    # six classes whose proportional shares all end in .5: rounding each to nearest asked for
+    # 155 blocks on 152 SMs; the largest-remainder rounding keeps the total at 152
+    w = [15.5, 30.5, 16.5, 30.5, 36.5, 22.5]
+    line = "s 6 152 " + " ".join(f"{x} 1000 1" for x in w)
+    (share,) = sched([line])
+    assert sum(share) == 152
+    assert all(abs(a - b) < 1.0 for a, b in zip(share, w))
+
+
+def test_shares_against_exact_split(sched):
+    rng = np.random.default_rng(3273)
+    cases = []
+    for _ in range(300):
+        n = 10
+        open_ = [bool(x) for x in rng.integers(0, 2, n)]
+        if not any(open_):
+            open_[0] = True
+        w = [float(x) for x in rng.uniform(0.05, 5.0, n)]
+        cap = [int(x) for x in rng.integers(1, 80, n)]
+        nsm = int(rng.choice([16, 76, 152]))
+        cases.append((w, cap, open_, nsm))
+    lines = ["s 10 %d " % nsm + " ".join(f"{wc} {cc} {int(o)}" for wc, cc, o in zip(w, cap, open_))
+             for w, cap, open_, nsm in cases]
+    for (w, cap, open_, nsm), share in zip(cases, sched(lines)):
+        exact, still_open = exact_shares(w, cap, open_, nsm)
+        for c in range(10):
+            if not open_[c]:
+                assert share[c] == 0
+                continue
+            assert 1 <= share[c] <= cap[c]
+            if still_open[c]:
+                assert abs(share[c] - exact[c]) < 1.0 or (exact[c] < 1.0 and share[c] == 1)
+            else:
+                assert share[c] == cap[c]
+        n_open = sum(open_)
+        if all(exact[c] >= 1.0 for c in range(10) if open_[c]):
+            # no floor raised to one: the total stays within the SMs, and uses them all when
+            # the caps allow
+            assert sum(share) <= nsm
+            assert sum(share) == min(nsm, sum(cap[c] for c in range(10) if open_[c]))
+        else:
+            assert sum(share) <= max(nsm, n_open) + n_open
