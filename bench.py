@@ -9,9 +9,10 @@ Metric: shell-pair x charge integrals/s = (screened shell pairs x region-I charg
 time, plus ms per V+forces call; FP64 is the headline (the active-site workload is quoted in FP64)
 and the mixed-precision path is measured beside it with its error against FP64.
 
-Default workload: 60 QM atoms (600 shells, 1560 AOs), 59463 MM charges (TIP3P waters) in a 58 A
-box, cutoff 12 A, alpha 0.3 A^-1, kmax 16 (synthetic, seeded).  Inputs are smaller than L2 so the
-L2 is flushed (256 MiB write) before every timed step, outside the timed interval.
+Default workload: the largest single-GPU configuration, a large active site of 150 QM atoms with f
+shells (1500 shells, 5100 AOs) and 198723 MM charges (TIP3P waters) in an 86 A box, cutoff 12 A,
+alpha 0.3 A^-1, kmax 24 (synthetic, seeded); --config c2 is the 60-atom active site.  The L2 is
+flushed (256 MiB write) before every timed step, outside the timed interval.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c1|c2|c4|c5]
 (c5: 64 uneven frames through the batch API, one CUDA graph, against a loop of FP64 calls)
@@ -64,10 +65,10 @@ def flops_adjoint(L):
 
 CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la(la+1)/2 + lb
 
-# DRAM bytes (read + write) of one adjoint sweep (all class kernels of one launch round), from
-# the ncu capture summarised in profiles/vgrad_traffic_c2.md; None where not captured (or where
-# the kernels changed after the capture).
-SWEEP_TRAFFIC = {("c2", "fp64"): 24_183_040, ("c2", "mixed"): 21_820_672}
+# DRAM bytes (read + write) of one adjoint sweep (all angular-class kernels of one call), per
+# (workload, precision), from one ncu capture of the current kernels; a workload or precision
+# without a capture of the current kernels reports None.
+SWEEP_TRAFFIC = {}
 
 
 def sweep_flops(info, adjoint):
@@ -149,34 +150,116 @@ def job_rate(world, units_per_step, ms):
     return world * units_per_step / (ms * 1e-3)
 
 
-def cpu_baseline(s, seconds=10.0, seed=0):
-    """The FP64 oracle on the host cores: V + adjoint for a random sample of shell pairs against
-    all region-I charges (same per-(shell pair, charge) unit as the GPU metric)."""
+def _shell_subset(s, shells):
+    """The workload restricted to a subset of its shells (same atoms, MM charges and Ewald
+    parameters; the density is the matching AO block): a bounded sample of the moment work."""
+    ao = np.concatenate([[0], np.cumsum([(l + 1) * (l + 2) // 2 for l in s.shell_l])])
+    t = s.copy()
+    t.shell_atom = np.ascontiguousarray(s.shell_atom[shells])
+    t.shell_l = np.ascontiguousarray(s.shell_l[shells])
+    t.shell_nprim = np.ascontiguousarray(s.shell_nprim[shells])
+    offs, exps, coefs = [], [], []
+    for sh in shells:
+        o, n = int(s.shell_prim_offset[sh]), int(s.shell_nprim[sh])
+        offs.append(len(exps))
+        exps += list(s.prim_exp[o:o + n])
+        coefs += list(s.prim_coeff[o:o + n])
+    t.shell_prim_offset = np.asarray(offs, dtype=s.shell_prim_offset.dtype)
+    t.prim_exp, t.prim_coeff = np.asarray(exps), np.asarray(coefs)
+    idx = np.concatenate([np.arange(ao[sh], ao[sh + 1]) for sh in shells])
+    t.dm = np.ascontiguousarray(s.dm[np.ix_(idx, idx)])
+    return t
+
+
+def _charge_subset(s, sub):
+    t = s.copy()
+    t.mm_xyz = np.ascontiguousarray(s.mm_xyz[sub])
+    t.mm_q = np.ascontiguousarray(s.mm_q[sub])
+    t.mm_sigma = np.ascontiguousarray(s.mm_sigma[sub])
+    return t
+
+
+# Screened shell pairs of each seeded workload as the library's planner counts them (reported by
+# qmmm_get_info; the GPU arm checks its own count against this): the reference arm, which runs no
+# GPU code, needs the same units per step as the GPU arm.
+SCREENED_SHELL_PAIRS = {"c1": 78, "c2": 46072, "c4": 167031}
+
+
+def cpu_baseline(s, seconds=12.0, seed=0, n_shell_pairs=None):
+    """The FP64 oracle on the host cores, for the whole V+forces step of the workload, from bounded
+    samples scaled to the full step (each piece's cost is linear in what is sampled):
+      * region-I V + adjoint (Obara-Saika): a random sample of shell pairs x all region-I charges;
+      * Mulliken moments and multipoles: a random subset of the shells (cost per shell pair);
+      * region-II potential at the QM sites (real-space + reciprocal Ewald, region-I and Gaussian
+        corrections): a random subset of the MM charges;
+      * the MM-side Ewald derivatives (dE/dq, dE/dR_MM): a random subset of the MM charges.
+    The Pulay and QM tensor-gradient terms (O(shell pairs) moment derivatives, O(natm)) are not
+    timed.  Same per-(shell pair, charge) unit as the GPU metric."""
     import oracle
     rng = np.random.default_rng(seed)
     cores = os.cpu_count()
     idx = oracle.region1(s)[0]
     nI = len(idx)
+    npairs = s.nshell * (s.nshell + 1) // 2
+    units = (n_shell_pairs if n_shell_pairs is not None else npairs) * nI  # the GPU arm's unit count
+
+    # region-I V + adjoint on sampled shell pairs (about half the budget)
     pairs_all = [(i, j) for i in range(s.nshell) for j in range(i, s.nshell)]
-    k = 2
-    elapsed, units = 0.0, 0
+    k, t_pairs, n_pairs = 2, 0.0, 0
     while True:
         pick = rng.choice(len(pairs_all), k, replace=False)
         pairs = [pairs_all[p] for p in pick]
-        # orient like the GPU planner (higher l first)
         pairs = [(a, b) if s.shell_l[a] >= s.shell_l[b] else (b, a) for a, b in pairs]
         t0 = time.perf_counter()
         oracle.vpot(s, pairs=pairs)
         oracle.vgrad_pairs(s, pairs)
         dt = time.perf_counter() - t0
-        elapsed += dt
-        units += k * nI
-        if elapsed >= seconds or k >= len(pairs_all):
+        t_pairs += dt
+        n_pairs += k
+        if t_pairs >= 0.5 * seconds or n_pairs >= len(pairs_all):
             break
-        k = min(len(pairs_all), max(2 * k, int(k * (seconds - elapsed) / max(dt, 1e-3))))
-    return {"value": units / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{units // nI} random shell pairs x {nI} region-I charges, V + adjoint "
-                      f"(Obara-Saika, FP64, OpenMP), {elapsed:.1f} s; Ewald/multipole work not included"}
+        k = min(len(pairs_all) - n_pairs, max(2 * k, int(k * (0.5 * seconds - t_pairs) / max(dt, 1e-3))))
+    t_region1 = t_pairs * npairs / n_pairs
+
+    # moments and multipoles on a shell subset
+    nsh = max(2, min(s.nshell, int(round(s.nshell / 6))))
+    shells = np.sort(rng.choice(s.nshell, nsh, replace=False))
+    sub_s = _shell_subset(s, shells)
+    t0 = time.perf_counter()
+    M_sub = oracle.multipoles(sub_s)
+    t_mult_s = time.perf_counter() - t0
+    t_mult = t_mult_s * npairs / (nsh * (nsh + 1) // 2)
+    del M_sub
+
+    # region-II potential at the QM sites, on a charge subset
+    nsub = max(1, min(s.nmm, 1500))
+    sub = np.sort(rng.choice(s.nmm, nsub, replace=False))
+    t0 = time.perf_counter()
+    oracle.ewald_phi(_charge_subset(s, sub))
+    t_phi_s = time.perf_counter() - t0
+    t_phi = t_phi_s * s.nmm / nsub
+
+    # MM-side Ewald derivatives for a charge subset (multipoles of the full density)
+    M = np.zeros((s.natm, 10))
+    M[:, 0] = s.atom_Z * 0.1
+    nmm_sub = max(1, min(s.nmm, 300))
+    t0 = time.perf_counter()
+    oracle.ewald_mm(s, M, mm_subset=sub[:nmm_sub])
+    t_mm_s = time.perf_counter() - t0
+    t_mm = t_mm_s * s.nmm / nmm_sub
+
+    t_step = t_region1 + t_mult + t_phi + t_mm
+    sampled = t_pairs + t_mult_s + t_phi_s + t_mm_s
+    return {"value": units / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"whole V+forces step estimated from bounded samples ({sampled:.1f} s of oracle time): "
+                       f"V + adjoint on {n_pairs} random shell pairs x {nI} region-I charges ({t_region1:.0f} s "
+                       f"scaled), moments/multipoles on {nsh} random shells ({t_mult:.1f} s scaled), region-II "
+                       f"potential on {nsub} random MM charges ({t_phi:.1f} s scaled), MM-side Ewald derivatives "
+                       f"on {nmm_sub} MM charges ({t_mm:.1f} s scaled); Pulay and QM tensor-gradient terms not "
+                       f"timed; FP64, OpenMP"),
+            "step_s": t_step,
+            "pieces_s": {"region1_v_adjoint": t_region1, "multipoles": t_mult, "region2_potential": t_phi,
+                         "mm_ewald_derivatives": t_mm}}
 
 
 def run_reference(args):
@@ -188,7 +271,7 @@ def run_reference(args):
     per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(s, seconds=per_step, seed=i)
+        cb = cpu_baseline(s, seconds=per_step, seed=i, n_shell_pairs=SCREENED_SHELL_PAIRS.get(args.config))
         if i >= args.warmup:
             vals.append(cb)
     value = float(np.mean([v["value"] for v in vals]))
@@ -309,7 +392,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4", "c5"])
+    ap.add_argument("--config", default="c4", choices=["c1", "c2", "c4", "c5"])
     ap.add_argument("--frames", type=int, default=64, help="frames of the c5 (batched) workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -443,34 +526,41 @@ def main():
                           if prec == q.QMMM_FP64 else "FP32 plain-ALU peak at 2070 MHz (152 SMs x 128 FFMA/clk)"),
             "flops_per_launch": fl}
 
-    # launches of our kernels per step (claim; the ncu launch list in profiles/ confirms the
-    # composition: 63 per FP64 step of the active site).  Per call:
+    # launches of our kernels per step (a claim; the ncu launch list of this command confirms the
+    # composition).  Per call:
     #   set_positions: gather, region-I count/scan/fill, real-space, region-I tensors, background
     #     sum, QM-site reciprocal, final = 9, plus the structure factor (tensor cores: max|q|,
     #     phases, B planes, MMA, reduction = 5; CUDA cores: kernel + slice sum = 2)
     #   vpot: one kernel per class and charge chunk + nuclear-MM term
     #   ewald: one moments kernel per class + 2 (sum, energy terms)
-    #   forces: two moments kernels per class (Pulay) + the adjoint sweep per class and chunk + 8
-    #     fixed (nuclear-MM, sum, real space, region I, background, tensor gradient, scatter,
-    #     unpermute) + the MM-side reciprocal sum (tensor cores: atom phases, multipole structure
-    #     factor, phases, scales, B planes per N tile, MMA = 5 + tiles; CUDA cores: 3)
+    #   forces: two moments kernels per class (Pulay) + the adjoint sweep per class and chunk
+    #     (mixed path, classes with l_A + l_B >= 3: pair records, charge-lane sweep, pair
+    #     gradients = 3) + 8 fixed (nuclear-MM, sum, real space, region I, background, tensor
+    #     gradient, scatter, unpermute) + the MM-side reciprocal sum (tensor cores: atom phases,
+    #     multipole structure factor, phases, scales, B planes per N tile, MMA = 5 + tiles; CUDA
+    #     cores: 3)
     # vpot adds one V slice-sum kernel when its classes split their charges (per-class slices:
     # 256 or more region-I charges and room for two partial matrices in 512 MB; or small systems
     # whose classes ask for less than half the SMs, which have fewer charges than that here).
-    ncls = sum(1 for n in info["n_prim_pairs_class"] if n > 0)
-    nI = info["n_region1"]
-    v_maxsl = min(8, min(nI, 4096) // 128, (512 << 20) // max(1, 8 * s.nao * s.nao))
-    ch_f = math.ceil(nI / (4096)) if nI else 0
-    ch_g = math.ceil(nI / 2560) if nI else 0
-    tensor = recip_in_effect(prec) == RECIP_NAME[q.QMMM_RECIP_TENSOR]
-    # MM-side tiling as the library plans it: N rows per tile <= 96 (five accumulators, FP64) or
-    # 128 (four, mixed); channels per tile cpt; the sum stays on the CUDA cores if 2 kz + 1 < 8
-    kx, lim = s.kmax[0] + 1, (96 if prec == q.QMMM_FP64 else 128)
-    cpt = next((c for c in (3, 2, 1) if 2 * c * kx <= lim), 1)
-    mm_tc = tensor and (2 * cpt * kx + 15) // 16 * 16 <= lim and 2 * s.kmax[2] + 1 >= 8
-    mm_tiles = -(-3 // cpt)
-    per_step = (9 + (5 if tensor else 2)) + (ncls * ch_f + 1 + (1 if v_maxsl > 1 else 0)) + (ncls + 2) + \
-        (2 * ncls + ncls * ch_g + 8 + ((5 + mm_tiles) if mm_tc else 3))
+    def launches_per_step(precision):
+        ncls = sum(1 for n in info["n_prim_pairs_class"] if n > 0)
+        ncl = sum(1 for c, n in enumerate(info["n_prim_pairs_class"]) if n > 0 and CLASS_L[c] >= 3)
+        nI = info["n_region1"]
+        v_maxsl = min(8, min(nI, 4096) // 128, (512 << 20) // max(1, 8 * s.nao * s.nao))
+        ch_f = math.ceil(nI / 4096) if nI else 0
+        ch_g = math.ceil(nI / 2560) if nI else 0
+        tensor = recip_in_effect(precision) == RECIP_NAME[q.QMMM_RECIP_TENSOR]
+        # MM-side tiling as the library plans it (both precisions: seven planes, five accumulators,
+        # N rows per tile <= 96); the sum stays on the CUDA cores if 2 kz + 1 < 8
+        kx, lim = s.kmax[0] + 1, 96
+        cpt = next((c for c in (3, 2, 1) if 2 * c * kx <= lim), 1)
+        mm_tc = tensor and (2 * cpt * kx + 15) // 16 * 16 <= lim and 2 * s.kmax[2] + 1 >= 8
+        mm_tiles = -(-3 // cpt)
+        sweep_g = ncls * ch_g + (2 * ncl * ch_g if precision == q.QMMM_MIXED else 0)
+        return (9 + (5 if tensor else 2)) + (ncls * ch_f + 1 + (1 if v_maxsl > 1 else 0)) + (ncls + 2) + \
+            (2 * ncls + sweep_g + 8 + ((5 + mm_tiles) if mm_tc else 3))
+
+    per_step = launches_per_step(prec)
     launches = per_step * args.steps
 
     # mixed precision beside FP64 (same GPU, same inputs), with its error against FP64
@@ -485,9 +575,11 @@ def main():
         ms_m, rec_m = timed(hm, args.steps, args.warmup)
         Em = hm.energy(dm_d)
         fro = float(torch.linalg.norm(V_d - V64) / torch.linalg.norm(V64))
-        gerr = max(float((gq_d - gq64).abs().max() / gq64.abs().max()),
-                   float((gm_d - gm64).abs().max() / gm64.abs().max()),
-                   float((gc_d - gc64).abs().max() / gc64.abs().max()))
+        # raw max-relative error of each gradient: max |mixed - FP64| / max |FP64|
+        raw = {"dE_dRqm": float((gq_d - gq64).abs().max() / gq64.abs().max()),
+               "dE_dRmm": float((gm_d - gm64).abs().max() / gm64.abs().max()),
+               "dE_dq": float((gc_d - gc64).abs().max() / gc64.abs().max())}
+        gerr = max(raw.values())
         escale = float(E64[1].abs() + E64[2].abs() + E64[3].abs())
         t_vm, t_gm = float(np.mean(rec_m["vpot"])), float(np.mean(rec_m["grad"]))
         flm = sweep_flops(info, t_gm >= t_vm)
@@ -495,8 +587,10 @@ def main():
         ms_m = max_over_ranks(ms_m, dist, dev)
         mixed = {"value": job_rate(world, units_per_step, ms_m), "ms_per_step": ms_m,
                  "speedup_vs_fp64": ms / ms_m, "vpot_sweep_ms": t_vm, "adjoint_sweep_ms": t_gm,
-                 "rel_fro_err_V": fro, "max_rel_err_forces": gerr,
+                 "rel_fro_err_V": fro, "max_rel_err_forces": gerr, "max_rel_err_forces_raw": raw,
                  "rel_err_E": float(abs(Em[0] - E64[0]) / escale),
+                 "rel_err_E_raw": float(abs(Em[0] - E64[0]) / abs(E64[0])),
+                 "gpu_launches_per_step": launches_per_step(q.QMMM_MIXED),
                  "roofline": {"bound": "alu", "achieved": ach_m, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": ach_m / FP32_PEAK_TFLOPS,
                               "traffic": SWEEP_TRAFFIC.get((args.config, "mixed")) if t_gm >= t_vm else None}}
@@ -550,8 +644,10 @@ def main():
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
     if mixed:
         out["mixed"] = mixed
+    if info["n_shell_pairs"] != SCREENED_SHELL_PAIRS.get(args.config, info["n_shell_pairs"]):
+        out["config"]["note"] = "screened shell-pair count differs from the reference arm's table"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(s, seconds=12.0)
+        out["cpu_baseline"] = cpu_baseline(s, seconds=16.0, n_shell_pairs=info["n_shell_pairs"])
     h.close()
     if rank == 0:
         print(json.dumps(out))

@@ -156,6 +156,13 @@ int qmmm_ewald(qmmm_handle *h, const double *dm, double *E_II, double *multipole
  * prior qmmm_vpot at the current geometry (QMMM_ERR_STATE otherwise). */
 int qmmm_energy(qmmm_handle *h, const double *dm, double *E);
 
+/* Derivative of E_QM-MM with respect to the density matrix, the embedding's contribution to the
+ * Fock/KS matrix (Eqs. 11-14): G[nao*nao] = dE/dgamma = V + F_II, V the region-I matrix of the
+ * last qmmm_vpot (Eq. 9) and F_II the region-II multipole term as in qmmm_ewald at density dm.
+ * Needs a prior qmmm_vpot at the current geometry (QMMM_ERR_STATE otherwise).  dm and G: host or
+ * device memory. */
+int qmmm_density_gradient(qmmm_handle *h, const double *dm, double *G);
+
 /* Gradient of E_QM-MM at fixed dm (region-I integral derivatives, nuclear-MM term, tensor
  * derivatives, and the multipole Pulay term of Eq. 15): dE_dRqm[natm*3], dE_dRmm[nmm*3],
  * dE_dq[nmm].  Any output may be NULL. */
@@ -309,6 +316,8 @@ const char *qmmm_last_error(void);
  * belongs to the host program's pool allocator).  The paper has no counterpart: it is a variant
  * of the kernel behind qmmm_vpot's E_nuc_mm, taking the charges directly instead of a handle.
  *   E[0] = sum_j sum_i Z[j] q_i erf(r_ij / sigma[i]) / r_ij  (1/r_ij where sigma[i] <= 0),
+ *   with the limit 2 / (sigma[i] sqrt(pi)) for a Gaussian charge centred on a nucleus; a point
+ *   charge on a nucleus makes E non-finite (+-inf or NaN), as the energy is;
  *   qm_xyz[natm*3], Z[natm], charges[ncharge*4] = (x, y, z, q) per charge (bohr, e),
  *   sigma[ncharge] (bohr), E[1]: all DEVICE memory owned by the caller.  Work is queued on
  *   `stream` (a cudaStream_t; NULL = legacy stream) and the call returns without waiting.

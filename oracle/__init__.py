@@ -364,6 +364,28 @@ def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None, mm_subset=None):
             "elec": {"dE_dRqm": elec_qm, "dE_dRmm": elec_mm, "dE_dq": elec_q}}
 
 
+def forces_mm_subset(s, charge_subset, dm=None, mode: int = EW_ALL):
+    """dE/dq and dE/dR_MM of the MM charges behind the listed region-I entries (each charge with a
+    single image in region I), composed as in ``forces`` without the QM-side terms: the region-I
+    electronic and nuclear parts over those entries plus the MM-side Ewald derivatives from the
+    multipoles of the full density.  Returns (mm indices, dE_dq[k], dE_dRmm[k, 3])."""
+    dm = _d(s.dm if dm is None else dm)
+    b = _Basis(s)
+    idx, cx, cq, cs = region1_charges(s)
+    sub = np.asarray(charge_subset)
+    idx, cx, cq, cs = idx[sub], np.ascontiguousarray(cx[sub]), cq[sub], cs[sub]
+    n = len(cq)
+    dRqm, dC, dqc = np.zeros((s.natm, 3)), np.zeros((n, 3)), np.zeros(n)
+    qm = _d(s.atom_xyz)
+    lib().oracle_vgrad(*b.args(), s.natm, _dp(qm), n, _dp(cx), _dp(cq), _dp(cs), s.nao, _dp(dm), 0, None, _dp(dRqm),
+                       _dp(dC), _dp(dqc))
+    lib().oracle_enucmm(s.natm, _dp(qm), _dp(_d(s.atom_Z)), n, _dp(cx), _dp(cq), _dp(cs), _dp(dRqm), _dp(dC),
+                        _dp(dqc))
+    M = multipoles(s, dm)
+    dq2, dR2 = ewald_mm(s, M, mode, mm_subset=idx)
+    return idx, dqc + dq2[idx], dC + dR2[idx]
+
+
 def vgrad_pairs(s, pairs, dm=None):
     """Region-I gradient pieces restricted to the listed ordered shell pairs (timing samples)."""
     dm = _d(s.dm if dm is None else dm)

@@ -36,6 +36,7 @@ from ._lib import (  # noqa: F401
     qmmm_create,
     qmmm_destroy,
     qmmm_energy,
+    qmmm_density_gradient,
     qmmm_ewald,
     qmmm_forces,
     qmmm_get_info,

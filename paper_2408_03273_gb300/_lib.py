@@ -58,7 +58,7 @@ class QMMMError(RuntimeError):
 _L = None
 
 EXPORTS = ("qmmm_create", "qmmm_set_stream", "qmmm_set_precision", "qmmm_set_recip_method", "qmmm_set_positions", "qmmm_vpot", "qmmm_ewald",
-           "qmmm_energy", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
+           "qmmm_energy", "qmmm_density_gradient", "qmmm_forces", "qmmm_get_info", "qmmm_nao", "qmmm_get_potential", "qmmm_last_timing",
            "qmmm_qm_images", "qmmm_aspc_predict", "qmmm_selftest_bounded_wait", "qmmm_octupole_error", "qmmm_rcut_search", "qmmm_autotune", "qmmm_get_tuning", "qmmm_set_tuning", "qmmm_batch_create", "qmmm_batch_run",
            "qmmm_batch_timing", "qmmm_batch_captures", "qmmm_batch_counts", "qmmm_batch_destroy", "qmmm_destroy", "qmmm_strerror", "qmmm_last_error", "qmmm_nuclear_mm_energy_static")
 
@@ -88,6 +88,7 @@ def load(build_if_needed: bool = True):
         "qmmm_vpot": (c_int, [c_void_p, c_void_p, c_void_p]),
         "qmmm_ewald": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "qmmm_energy": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "qmmm_density_gradient": (c_int, [c_void_p, c_void_p, c_void_p]),
         "qmmm_forces": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "qmmm_get_info": (c_int, [c_void_p, P(QmmmInfo)]),
         "qmmm_nao": (c_int, [c_void_p]),
@@ -249,6 +250,14 @@ def qmmm_ewald(h, dm, E_II=None, multipoles=None, F_II=None, want_F=False):
     F = F_II if F_II is not None else (_out(None, (info["nao"], info["nao"]), dm) if want_F else None)
     _check(load().qmmm_ewald(h, _ptr(dm), _ptr(E), _ptr(M), _ptr(F)), "qmmm_ewald")
     return E, M, F
+
+
+def qmmm_density_gradient(h, dm, G=None):
+    """G = dE/dgamma = V + F_II (the embedding's Fock contribution, Eqs. 11-14)."""
+    info = qmmm_get_info(h)
+    G = _out(G, (info["nao"], info["nao"]), dm)
+    _check(load().qmmm_density_gradient(h, _ptr(dm), _ptr(G)), "qmmm_density_gradient")
+    return G
 
 
 def qmmm_energy(h, dm, E=None):

@@ -190,6 +190,11 @@ struct qmmm_handle {
     DBuf<int4> mmr_phase;  // tensor-core MM-side reciprocal sum scratch
     DBuf<uint32_t> mmr_bpl;
     DBuf<double> mmr_cscale;
+    // charge-lane adjoint sweep (mixed path, classes with l_A + l_B >= CL_MIN_L): pair records and
+    // per-pair charge sums, one region per class (classes run concurrently)
+    DBuf<float4> cl_rec;
+    DBuf<double> cl_psum;
+    size_t cl_rec_off[NCLASS] = {}, cl_psum_off[NCLASS] = {};
 
     BasisDev basis() const
     {
@@ -268,6 +273,10 @@ struct qmmm_handle {
         tc_phase.release(); tc_bpl.release(); tc_part.release(); tc_bmax.release();
         mmr_phase.release(); mmr_bpl.release(); mmr_cscale.release();
         Adf.release(); Azdf.release();
+        tune_V.release(); tune_dm.release(); tune_gqm.release(); tune_gchg.release();
+        oct.release(); oct_bins.release(); oct_err.release();
+        qmq_P.release(); qmq_u.release(); qmq_g.release(); qmq_E.release(); qmq_F.release();
+        Vslices.release(); centre_d.release(); cl_rec.release(); cl_psum.release();
     }
 };
 
@@ -357,10 +366,10 @@ int select_recip(qmmm_handle *h)
         h->ew.tcb.bpl = h->tc_bpl.p;
         h->ew.tcb.part = h->tc_part.p;
         h->ew.tcb.bmax = h->tc_bmax.p;
-        const MmrShape &m0 = h->ew.mms[0], &m1 = h->ew.mms[1];
-        if (m0.supported || m1.supported) {
+        const MmrShape &m0 = h->ew.mms;
+        if (m0.supported) {
             if ((rc = h->mmr_phase.ensure(m0.phase_rows)) ||
-                (rc = h->mmr_bpl.ensure(std::max(m0.bplane_words, m1.bplane_words))) ||
+                (rc = h->mmr_bpl.ensure(m0.bplane_words)) ||
                 (rc = h->mmr_cscale.ensure(3 * (h->kmax[0] + 1))))
                 return rc;
             // the rows of padding charges are copied but never used; keep them defined
@@ -535,7 +544,11 @@ int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 
     int share[NCLASS];
     if (!split_sms(h, kind, h->cls_variant[kind], share, nslice == 1 ? maxsl : 1)) return QMMM_OK;
     CUDA_TRY(cudaEventRecord(h->fork, h->stream));
-    for (int c = 0; c < NCLASS; ++c) {
+    // the charge-lane sweeps (mixed adjoint) size their own fine-grained grids and are launched
+    // highest class first (their blocks are the longest), so that the short low-l blocks fill the tail
+    const bool cl = kind == SW_VGRAD_F32;
+    for (int i = 0; i < NCLASS; ++i) {
+        const int c = cl ? NCLASS - 1 - i : i;
         const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
         if (p1 <= p0) continue;
         int sh = share[c], ns = nslice;
@@ -589,6 +602,25 @@ int sweep_slices(const qmmm_handle *h, int kind, int nch)
 
 // One class sweep of the given kind over region-I charges [c0, c1), split into nslice block rows;
 // V kernels write slice s into V + s * vstride.
+// Scratch of the charge-lane adjoint sweep for every class that takes it (allocated on first use).
+int ensure_cl(qmmm_handle *h)
+{
+    size_t nrec = 0, nps = 0;
+    for (int c = 0; c < NCLASS; ++c) {
+        const int L = la_of_class(c) + lb_of_class(c);
+        const size_t npp = (size_t)(h->class_off[c + 1] - h->class_off[c]);
+        h->cl_rec_off[c] = nrec;
+        h->cl_psum_off[c] = nps;
+        if (L < CL_MIN_L) continue;
+        nrec += npp * (cl_rec_floats(L) / 4);
+        nps += npp * 6;
+    }
+    int rc;
+    if ((rc = h->cl_rec.ensure(std::max<size_t>(nrec, 1))) || (rc = h->cl_psum.ensure(std::max<size_t>(nps, 1))))
+        return rc;
+    return QMMM_OK;
+}
+
 cudaError_t launch_sweep(const qmmm_handle *h, int kind, int cls, int p0, int p1, int c0, int c1, int share,
                          int variant, int nslice, size_t vstride, const double *ddm, double *V, double *gqm,
                          double *gchg, cudaStream_t cs)
@@ -605,9 +637,15 @@ cudaError_t launch_sweep(const qmmm_handle *h, int kind, int cls, int p0, int p1
     case SW_VGRAD_F64:
         return launch_vgrad_f64(b, r, cls, p0, p1, c0, c1, h->boys64.p, ddm, gqm, gchg, h->err.p, share, variant,
                                 nslice, cs);
-    case SW_VGRAD_F32:
+    case SW_VGRAD_F32: {
+        ClScratch cl;
+        if (h->cl_rec.p && h->cl_psum.p) {
+            cl.rec = h->cl_rec.p + h->cl_rec_off[cls];
+            cl.psum = h->cl_psum.p + h->cl_psum_off[cls];
+        }
         return launch_vgrad_f32(b, r, cls, p0, p1, c0, c1, h->boys32.p, ddm, gqm, gchg, h->err.p, share, variant,
-                                nslice, cs);
+                                nslice, cl, cs);
+    }
     default: return cudaErrorInvalidValue;
     }
 }
@@ -686,7 +724,10 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
                 const int nwarp = variant_threads(kind, c, v) / 32, tiles = (npp + 31) / 32;
                 const int blocks = std::min(share[c], (tiles + nwarp - 1) / nwarp);
                 const int passes = (tiles + blocks * nwarp - 1) / (blocks * nwarp);
-                const double smt = (double)t / passes * tiles / nwarp;
+                double smt = (double)t / passes * tiles / nwarp;
+                // the charge-lane sweep runs its fine-grained grid on the whole GPU: SM-time
+                if (kind == SW_VGRAD_F32 && la_of_class(c) + lb_of_class(c) >= CL_MIN_L)
+                    smt = (double)t * h->nsm;
                 if (v == 0) {
                     cost0[c] = smt / npp;
                     ms0[c] = t;
@@ -1036,7 +1077,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         if ((rc = h->boys64.ensure(t64.size()))) return rc;
         CUDA_TRY(cudaMemcpy(h->boys64.p, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
         std::vector<double> t32d;
-        boys_table(BOYS_NROW_F, BOYS_NCOL_F, BOYS_STEP, t32d);
+        boys_table(BOYS_NROW_F, BOYS_NCOL_F, BOYS_STEP_F, t32d);
         // one table per order M: F_{M+j}(T_k) / j!, j = 0..4, then e^{-T_k}
         std::vector<float> t32((size_t)BOYS_MAXM * BOYS_TAB_F, 0.0f);
         for (int M = 0; M < BOYS_MAXM; ++M)
@@ -1079,8 +1120,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sums = h->sums.p;
         h->ew.err = h->err.p;
         tc_sf_shape(e, h->ew.tcs);
-        tc_mmr_shape(e, 5, 7, h->ew.mms[0]);
-        tc_mmr_shape(e, 4, 5, h->ew.mms[1]);
+        tc_mmr_shape(e, 5, MMR_NP, h->ew.mms);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
@@ -1219,6 +1259,23 @@ int qmmm_ewald(qmmm_handle *h, const double *dmat, double *E_II, double *multipo
     return QMMM_OK;
 }
 
+int qmmm_density_gradient(qmmm_handle *h, const double *dmat, double *G)
+{
+    if (!h || !dmat || !G) return fail(QMMM_ERR_ARG, "null argument");
+    if (!h->V_valid) return fail(QMMM_ERR_STATE, "qmmm_vpot must run at the current geometry first");
+    cudaStream_t st = h->stream;
+    int rc;
+    const double *ddm;
+    const size_t n2 = (size_t)h->nao * h->nao;
+    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    if ((rc = h->F.ensure(n2))) return rc;
+    // start from V; the moment kernels add the region-II Fock term into it
+    CUDA_TRY(cudaMemcpyAsync(h->F.p, h->V.p, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if ((rc = compute_multipoles(h, ddm, h->F.p, 0))) return rc;
+    if ((rc = copy_out(h, G, h->F.p, n2))) return rc;
+    return finish(h, 0);
+}
+
 int qmmm_energy(qmmm_handle *h, const double *dmat, double *E)
 {
     if (!h || !dmat || !E) return fail(QMMM_ERR_ARG, "null argument");
@@ -1251,6 +1308,7 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
     if ((rc = compute_multipoles(h, ddm, nullptr, MOM_PULAY))) return rc;
     // region-I adjoint sweep
     const int kind = sweep_kind(h, true), ch = chunk_for_kind(kind);
+    if (kind == SW_VGRAD_F32 && (rc = ensure_cl(h))) return rc;
     const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
     CUDA_TRY(mark(h, 0));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
@@ -1416,7 +1474,7 @@ int qmmm_autotune(qmmm_handle *h, int flags)
     const int nch = std::min(h->nI, TUNE_CHARGES);
     int rc;
     if ((rc = h->tune_V.ensure(n2)) || (rc = h->tune_dm.ensure(n2)) || (rc = h->tune_gqm.ensure(3 * (size_t)h->natm)) ||
-        (rc = h->tune_gchg.ensure(4 * (size_t)nch)))
+        (rc = h->tune_gchg.ensure(4 * (size_t)nch)) || (rc = ensure_cl(h)))
         return rc;
     // a zero density: the sweeps' work does not depend on its values
     CUDA_TRY(cudaMemsetAsync(h->tune_dm.p, 0, n2 * sizeof(double), h->stream));

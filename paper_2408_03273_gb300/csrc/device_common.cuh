@@ -6,7 +6,8 @@
 //      int Lambda_tuv(r) erf(sqrt(kappa)|r-C|)/|r-C| dr = (2 pi/p) sqrt(kappa/(p+kappa)) R_tuv,
 //      R^{(n)}_000 = (-2 rho)^n F_n(rho |P-C|^2), rho = p kappa / (p + kappa),
 //      R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X_PC R^{(n+1)}_{t,u,v}  (and for u, v).
-//  * Boys function F_m(T): tabulated F_{m+j}(T_k) on a 0.1 grid with a Taylor expansion about
+//  * Boys function F_m(T): tabulated F_{m+j}(T_k) on a grid (0.1 for FP64, 1/16 for FP32) with a
+//    Taylor expansion about
 //    the nearest point and downward recursion F_{m-1} = (2T F_m + e^{-T})/(2m-1) for small T;
 //    F_0 = sqrt(pi)/2 T^{-1/2} with the upward recursion F_{m+1} = ((2m+1) F_m - e^{-T})/(2T)
 //    for large T (the grid-plus-recursion scheme of Helgaker, Jorgensen and Olsen, Molecular
@@ -36,7 +37,9 @@ constexpr int BOYS_TAYLOR_D = 7;              // terms of the FP64 Taylor expans
 constexpr int BOYS_ROW_D = 8;                 // device row for order M: F_{M+j}(T_k) / j!, j = 0..6,
                                               // then e^{-T_k} (64 B: four aligned double2 loads)
 constexpr float BOYS_TMAX_F = 20.0f;          // FP32 table range
-constexpr int BOYS_NROW_F = 201;
+constexpr double BOYS_STEP_F = 0.0625;        // FP32 grid T_k = k / 16: exact in FP32, so T - T_k is exact
+constexpr float BOYS_INV_STEP_F = 16.0f;
+constexpr int BOYS_NROW_F = 321;
 constexpr int BOYS_NCOL_F = 17;               // host table: orders 0..15 + exp column
 constexpr int BOYS_TAYLOR_F = 5;
 constexpr int BOYS_ROW_F = 7;                 // device row for order M: F_{M+j}(T_k) / j!, j = 0..4,
@@ -141,14 +144,25 @@ __device__ __forceinline__ void boys_arg_f32(float rho, float X, float Y, float 
     Tl = fmaf(rho, s2, -Th) + rho * lo;
 }
 
-// tab: the order-M FP32 table (BOYS_NROW_F rows of BOYS_ROW_F), staged in shared memory.
+// tab: the order-M FP32 table (BOYS_NROW_F rows of BOYS_ROW_F), staged in shared memory.  The
+// argument is the unevaluated sum T + Tlo (boys_arg_f32), and every step keeps the FP32 result
+// within about one rounding of F_m:
+//  * T < 20: Taylor expansion of F_M about T_k = k/16 (T - T_k exact), e^{-T} = e^{-T_k} e^{x} with
+//    e^{-T_k} from the table and a 5-term series of e^{x}, |x| <= 1/32 (no argument-proportional
+//    error of a hardware exponential), downward recursion with 2 (T + Tlo);
+//  * T >= 20: F_0 = sqrt(pi)/2 (T + Tlo)^{-1/2} (rsqrtf and one Newton step against the full
+//    argument), 1/(2 (T + Tlo)) from rs^2 = s2 + s2e (exact product) corrected by the residual
+//    g = 1 - (T + Tlo) rs^2, then the upward recursion F_{m+1} = ((2m+1) F_m - e^{-T}) / (2T).
 template <int M>
 __device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float *__restrict__ tab /* smem */,
                                          float Tlo = 0.0f)
 {
     if (T < BOYS_TMAX_F) {
-        const int k = __float2int_rn(T * 10.0f);
-        const float x = ((float)k * 0.1f - T) - Tlo;
+        // nearest grid index without the conversion pipe: adding 1.5 * 2^23 rounds 16 T to an
+        // integer held in the low mantissa bits (exact for 16 T < 2^22)
+        const float kf = fmaf(T, BOYS_INV_STEP_F, 12582912.0f);
+        const int k = __float_as_int(kf) - 0x4B400000;
+        const float x = ((kf - 12582912.0f) * (float)BOYS_STEP_F - T) - Tlo;  // -(T + Tlo - T_k)
         const float *row = tab + k * BOYS_ROW_F;  // the order-M table: 1/j! folded in
         float f = fmaf(row[4], x, row[3]);
         f = fmaf(f, x, row[2]);
@@ -156,10 +170,14 @@ __device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float
         f = fmaf(f, x, row[0]);
         F[M] = f;
         if (M > 0) {
-            const float e = __expf(-T);
-            const float T2 = 2.0f * T;
+            float ex = fmaf(x, 1.0f / 24.0f, 1.0f / 6.0f);
+            ex = fmaf(ex, x, 0.5f);
+            ex = fmaf(ex, x, 1.0f);
+            ex = fmaf(ex, x, 1.0f);
+            const float e = row[BOYS_TAYLOR_F] * ex;
+            const float T2 = 2.0f * T, T2l = 2.0f * Tlo;
 #pragma unroll
-            for (int m = M; m > 0; --m) F[m - 1] = (T2 * F[m] + e) * (1.0f / (2 * m - 1));
+            for (int m = M; m > 0; --m) F[m - 1] = fmaf(T2, F[m], fmaf(T2l, F[m], e)) * (1.0f / (2 * m - 1));
         }
     } else {
         // one Newton step on rsqrtf against the full argument T + Tlo: ~1 ulp of T^{-1/2}
@@ -169,10 +187,12 @@ __device__ __forceinline__ void boys_f32(float T, float (&F)[M + 1], const float
         rs = fmaf(0.5f * rs, h, rs);
         F[0] = (float)HALF_SQRT_PI * rs;
         if (M > 0) {
-            const float e = __expf(-T);
-            const float inv2T = 0.5f * rs * rs;
+            const float e = __expf(-T);  // enters only through (2m+1) F_m - e, where it is < 1e-3 of F_m
+            const float s2 = rs * rs, s2e = fmaf(rs, rs, -s2);
+            const float g = (fmaf(-T, s2, 1.0f) - T * s2e) - Tlo * s2;  // 1 - (T + Tlo)(s2 + s2e)
+            const float inv2T = 0.5f * (s2 + fmaf(s2, g, s2e));
 #pragma unroll
-            for (int m = 0; m < M; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * inv2T;
+            for (int m = 0; m < M; ++m) F[m + 1] = fmaf((float)(2 * m + 1), F[m], -e) * inv2T;
         }
     }
 }
@@ -390,6 +410,19 @@ __device__ __forceinline__ bool stage_to_smem(void *dst, const void *src, unsign
 {
     Seg s{dst, src, bytes};
     return stage_segments(&s, 1, bar, err);
+}
+
+// A coordinate relative to the QM centre as hi + lo floats with hi on a grid of 2^-16 bohr.  For
+// |d| < 128 bohr hi is exact in FP32, and the difference of two hi parts (a multiple of 2^-16
+// below 256 in magnitude, at most 24 significant bits) is exact too, so a displacement formed as
+// (hi_P - hi_C) + (lo_P - lo_C) is rounded once: correctly rounded FP32 (to about 2^-41 bohr).
+// A plain split (hi = (float)d) rounds the hi difference as well; in the region-I sums that
+// rounding, raised to the tensor order by the Boys argument and the Hermite polynomials, was the
+// largest error of the mixed-precision gradient.
+__device__ __forceinline__ void split_grid(double d, float &hi, float &lo)
+{
+    hi = (float)(rint(d * 65536.0) * (1.0 / 65536.0));
+    lo = (float)(d - (double)hi);
 }
 
 // double-float accumulation: (hi, lo) += x with an error-free two-sum

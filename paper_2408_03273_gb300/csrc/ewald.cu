@@ -148,10 +148,12 @@ __global__ void k_region1_fill(EwaldDev e, const int *blk_off, double4_32a *chg,
             double4_32a c;
             c.x = px; c.y = py; c.z = pz; c.w = q;
             chg[o] = c;
-            const double rx = px - e.centre[0], ry = py - e.centre[1], rz = pz - e.centre[2];
-            const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+            float hx, hy, hz, lx, ly, lz;  // grid-split hi/lo about the QM centre (split_grid)
+            split_grid(px - e.centre[0], hx, lx);
+            split_grid(py - e.centre[1], hy, ly);
+            split_grid(pz - e.centre[2], hz, lz);
             hi[o] = make_float4(hx, hy, hz, (float)q);
-            lo[o] = make_float4((float)(rx - hx), (float)(ry - hy), (float)(rz - hz), 0.0f);
+            lo[o] = make_float4(lx, ly, lz, 0.0f);
             idx[o] = i;
         });
     }
@@ -1234,7 +1236,7 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
         k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.atom_ph, w.A, w.Az,
                                                          df ? w.Adf : nullptr, df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        const MmrShape &ms = w.mms[df ? 1 : 0];
+        const MmrShape &ms = w.mms;
         if (w.recip == 1 && ms.supported) {
             if ((err = launch_mm_recip_tc(e, ms, w.mmb, w.A, w.Az, dq_int, dR_int, w.err, st)) != cudaSuccess)
                 return err;
@@ -1294,18 +1296,25 @@ k_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI,
         if (act) {
             const double x = qm_xyz[3 * j] - c.x, y = qm_xyz[3 * j + 1] - c.y, z = qm_xyz[3 * j + 2] - c.z;
             const double r2 = x * x + y * y + z * z, r = sqrt(r2);
-            double f, fp;
+            double f, fpr;  // f(r) and f'(r)/r
             if (beta > 0.0) {
-                f = erf(beta * r) / r;
-                fp = (beta * (2.0 / 1.7724538509055160273) * exp(-beta * beta * r2) - f) / r;
+                const double c2 = beta * (2.0 / 1.7724538509055160273), br2 = beta * beta * r2;
+                if (br2 < 1e-8) {
+                    // charge centre on (or next to) the nucleus: series of erf(beta r)/r about r = 0
+                    f = c2 * (1.0 - br2 * (1.0 / 3.0));
+                    fpr = -(2.0 / 3.0) * c2 * beta * beta * (1.0 - 0.6 * br2);
+                } else {
+                    f = erf(beta * r) / r;
+                    fpr = (c2 * exp(-br2) - f) / r2;
+                }
             } else {
                 f = 1.0 / r;
-                fp = -f / r;
+                fpr = -f / r2;
             }
             const double Zj = Z[j];
             E += Zj * c.w * f;
             dq += Zj * f;
-            const double s = Zj * c.w * fp / r;
+            const double s = Zj * c.w * fpr;
             g[0] = s * x; g[1] = s * y; g[2] = s * z;
             dC[0] -= g[0]; dC[1] -= g[1]; dC[2] -= g[2];
         }

@@ -13,14 +13,12 @@
 // A operand (M = 128 charges x K): the outer products Y_i(n_y) Z_i(n_z), digitised on chip from
 // fixed-point phase rows staged by TMA; B operand (N = 112 rows (k, n_x, re/im) x K): C_k divided
 // by a power of two per (k, n_x) so that |C| <= 1, digitised once per call into the shared-memory
-// layout.  Digits as for the structure factor (tc_digits.cuh).  FP64 class: seven planes per
-// operand, 28 plane pairs per K-step into five FP32 accumulators in tensor memory (levels 0..3
-// kept apart, 4..6 merged; the three channels then take two N tiles).  Mixed-precision path: five
-// planes (34-bit operands), 15 plane pairs, four accumulators (levels 0..2 apart, 3..4 merged:
-// about 2^-34 of the largest row coefficient), one N tile.  Level 0
+// layout.  Digits as for the structure factor (tc_digits.cuh).  FP64 class on both precision
+// paths: seven planes per operand, 28 plane pairs per K-step into five FP32 accumulators in tensor
+// memory (levels 0..3 kept apart, 4..6 merged; the three channels then take two N tiles).  Level 0
 // is exact for any input while 4096 x 2 N_y N_z < 2^24 (kmax <= 20) and beyond that unless the
 // row-normalised coefficients, which decay as exp(-G^2/4 alpha^2), sum to more than 2^11 in
-// magnitude; levels 1 and 2 are sums of random-sign digit products, typically 2^17 or less.  The epilogue
+// magnitude; levels 1 to 3 are sums of random-sign digit products, typically 2^17 or less.  The epilogue
 // (one thread per charge) combines the levels exactly in 64-bit integers, applies the row scales
 // and contracts with X_i(n_x) in FP64.
 #include <algorithm>
@@ -74,7 +72,8 @@ struct MmrArgs {
 }  // namespace
 
 // grid (mtiles, N tiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set
-// ch % nstg.  NP digit planes per operand (7: FP64 class; 5: the mixed path, 34-bit operands).
+// ch % nstg.  NP digit planes per operand (MMR_NP = 7: 48-bit operands, FP64 class, for both
+// precisions: the mixed path's reciprocal sum stays FP64-class as well).
 template <int NP>
 __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
 {
@@ -227,10 +226,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             issued = ch + 1;
         }
         if (lane == 0) {
+            // copies possibly still in flight (after a give-up): wait for them to land, bounded in
+            // time only (not cut short by the abort flag), before the block may leave
             for (int ch = issued > NSTG ? issued - NSTG : 0; ch < issued; ++ch)
-                tc::mbar_wait_thread(&bfull[ch % NSTG], (ch / NSTG) & 1, abort);
+                tc::mbar_drain(&bfull[ch % NSTG], (ch / NSTG) & 1);
             for (int ch = pissued > NSTG ? pissued - NSTG : 0; ch < pissued; ++ch)
-                tc::mbar_wait_thread(&pfull[ch % NSTG], (ch / NSTG) & 1, abort);
+                tc::mbar_drain(&pfull[ch % NSTG], (ch / NSTG) & 1);
         }
     }
 
@@ -238,6 +239,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
     if (warp < 4) {
         if (!tc::mbar_wait_thread(done, 0, abort)) {
             give_up();
+            // the MMA thread commits `done` on every path: wait for it (bounded in time only), so
+            // that no MMA still writes tensor memory when it is freed below
+            tc::mbar_drain(done, 0);
         } else {
             tc::fence_after_sync();
             const int row = 32 * warp + lane, i = m0 + row;
@@ -430,9 +434,9 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     k_mmr_scale<<<3 * NX, 256, 0, st>>>(e, A, Az, b.cscale);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     const size_t smem = mmr_smem(sh.nr, sh.nstg, sh.np);
-    const void *fn = sh.np == 7 ? (const void *)k_mm_recip_tc<7> : (const void *)k_mm_recip_tc<5>;
-    static size_t attr[2] = {0, 0};
-    size_t &at = attr[sh.np == 7 ? 0 : 1];
+    if (sh.np != MMR_NP) return cudaErrorInvalidValue;
+    const void *fn = (const void *)k_mm_recip_tc<MMR_NP>;
+    static size_t at = 0;
     if (smem > at) {
         if ((rc = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return rc;
@@ -442,12 +446,8 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     for (int tl = 0; tl < sh.ntiles; ++tl) {
         const int kfirst = tl * sh.cpt, nk = std::min(sh.cpt, 3 - kfirst);
         const long long n = (long long)sh.nr * PCH * sh.nchunk;
-        if (sh.np == 7)
-            k_mmr_bplanes<7><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
-                                                                           sh.nchunk, b.bpl + tl * tile_words);
-        else
-            k_mmr_bplanes<5><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
-                                                                           sh.nchunk, b.bpl + tl * tile_words);
+        k_mmr_bplanes<MMR_NP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
+                                                                            sh.nchunk, b.bpl + tl * tile_words);
         if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     }
     MmrArgs a;
@@ -472,10 +472,7 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     a.nstg = sh.nstg;
     a.nacc = sh.nacc;
     a.box0 = e.box[0];
-    if (sh.np == 7)
-        k_mm_recip_tc<7><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
-    else
-        k_mm_recip_tc<5><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
+    k_mm_recip_tc<MMR_NP><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     return cudaSuccess;
 }

@@ -40,7 +40,15 @@ k_enucmm_static(const double *__restrict__ qm_xyz, const double *__restrict__ Z,
         for (int j = 0; j < natm; ++j) {
             const double x = qm_xyz[3 * j] - cx, y = qm_xyz[3 * j + 1] - cy, z = qm_xyz[3 * j + 2] - cz;
             const double r = sqrt(x * x + y * y + z * z);
-            const double f = beta > 0.0 ? erf(beta * r) / r : 1.0 / r;
+            double f;
+            if (beta > 0.0) {
+                // a Gaussian charge on (or next to) the nucleus: erf(beta r)/r tends to 2 beta/sqrt(pi);
+                // the two-term series is exact to rounding for beta r < 1e-4
+                const double br = beta * r;
+                f = br < 1e-4 ? beta * (2.0 / 1.7724538509055160273) * (1.0 - br * br * (1.0 / 3.0)) : erf(br) / r;
+            } else {
+                f = 1.0 / r;  // a point charge on a nucleus gives an infinite energy (+-inf or NaN in E)
+            }
             E += Z[j] * q * f;
         }
     }

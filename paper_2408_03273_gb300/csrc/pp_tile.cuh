@@ -224,6 +224,67 @@ __device__ __forceinline__ void contract_dA(const PPLane &pl, const BasisDev &bd
         }
 }
 
+// ------------------------------------------------------------------------------------------
+// Charge-lane adjoint sweep (mixed precision, classes with l_A + l_B >= CL_MIN_L): one lane per
+// region-I charge, the primitive pairs' density-folded Hermite coefficients read from shared
+// memory.  A pair record (built once per call in FP64, rounded to FP32) holds, in floats:
+//   [0..2] P - centre (hi part, split_grid), [3..5] lo part, [6..7] p (double),
+//   then per Hermite index k: (D0_k, Dx_k, Dy_k, Dz_k).
+// ------------------------------------------------------------------------------------------
+constexpr int CL_MIN_L = 0;   // classes with l_A + l_B >= CL_MIN_L take the charge-lane sweep
+constexpr int CL_NT = 256;    // threads per block
+__host__ __device__ constexpr int cl_rec_floats(int L) { return 8 + 4 * nherm(L); }
+// primitive pairs per staged batch (two batches of records in shared memory: <= 22 KB)
+__host__ __device__ constexpr int cl_batch(int L) { return L <= 4 ? 16 : 8; }
+constexpr int CL_BPB = 8;  // batches per block
+// Charge-lane variants: (charges per lane, blocks per SM) for variant v of class order L; 0 where
+// the class has no such variant.  Charges per lane amortise the per-pair warp reduction and give
+// each lane independent chains; the register budget (65536 / (256 x blocks per SM)) bounds them.
+__host__ __device__ constexpr int cl_variant(int L, int v, int field)
+{
+    constexpr int T[7][2][2] = {{{4, 2}, {8, 1}}, {{4, 2}, {2, 2}}, {{2, 2}, {1, 2}}, {{1, 2}, {2, 1}},
+                                {{1, 2}, {2, 1}}, {{1, 1}, {0, 0}}, {{1, 1}, {0, 0}}};
+    return (L >= 0 && L <= 6) ? T[L][v][field] : 0;
+}
+
+// Hermite R tensors as hermite_R, with every loop of constant trip count (bounds as guards) so
+// that the nest unrolls completely and R stays in registers.
+template <int L, typename T>
+__device__ __forceinline__ void hermite_R_u(T (&R)[nherm(L)], const T (&Fn)[L + 1], T X, T Y, T Z)
+{
+    R[0] = Fn[L];
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll
+        for (int k = L; k >= 1; --k) {
+            if (k > L - n) continue;
+#pragma unroll
+            for (int t = L; t >= 0; --t) {
+                if (t > k) continue;
+#pragma unroll
+                for (int u = L; u >= 0; --u) {
+                    if (u > k - t) continue;
+                    const int v = k - t - u;
+                    if (t > 0) {
+                        T r = X * R[hidx(t - 1, u, v)];
+                        if (t > 1) r = fma((T)(t - 1), R[hidx(t - 2, u, v)], r);
+                        R[hidx(t, u, v)] = r;
+                    } else if (u > 0) {
+                        T r = Y * R[hidx(t, u - 1, v)];
+                        if (u > 1) r = fma((T)(u - 1), R[hidx(t, u - 2, v)], r);
+                        R[hidx(t, u, v)] = r;
+                    } else {
+                        T r = Z * R[hidx(t, u, v - 1)];
+                        if (v > 1) r = fma((T)(v - 1), R[hidx(t, u, v - 2)], r);
+                        R[hidx(t, u, v)] = r;
+                    }
+                }
+            }
+        }
+        R[0] = Fn[n];
+    }
+}
+
 // Inverse of class_of: the angular momenta of a class index.
 __host__ __device__ constexpr int la_of_class(int c)
 {
@@ -250,7 +311,8 @@ __host__ __device__ constexpr int sweep_wide_threads(int kind, int cls)
         {1024, 640, 512, 640, 384, 384, 512, 0, 0, 0},  // vpot_f64 : 64 87 105 96 150 158 120 regs
         {896, 768, 512, 512, 384, 0, 384, 0, 0, 0},     // vpot_f32 : 68 80 106 102 154 - 136
         {640, 512, 0, 0, 0, 0, 0, 0, 0, 0},             // vgrad_f64: 93 117
-        {768, 640, 384, 384, 384, 384, 0, 0, 0, 0},     // vgrad_f32: 80 96 168 148 (255 255: setup)
+        {256, 256, 256, 256, 256, 256, 256, 256, 0, 0}, // vgrad_f32: charge lanes, variant 1 as
+                                                        // cl_variant (256 threads either way)
     };
     return (kind >= 0 && kind < SW_NKIND && cls >= 0 && cls < 10) ? T[kind][cls] : 0;
 }

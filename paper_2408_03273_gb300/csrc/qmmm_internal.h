@@ -61,9 +61,16 @@ cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
                              double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, int variant, int nslice,
                              cudaStream_t st);
+// Scratch of one class's charge-lane adjoint sweep (classes with l_A + l_B >= CL_MIN_L): pair
+// records (cl_rec_floats(L) floats per primitive pair) and per-pair charge sums (6 doubles).
+struct ClScratch {
+    float4 *rec = nullptr;
+    double *psum = nullptr;
+};
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, int variant, int nslice, cudaStream_t st);
+                             double *gchg, int *err, int nsm, int variant, int nslice, ClScratch cl,
+                             cudaStream_t st);
 
 // moments / multipoles / Fock / Pulay (mode bits below)
 enum { MOM_MULT = 1, MOM_FOCK = 2, MOM_PULAY = 4 };
@@ -125,11 +132,12 @@ cudaError_t launch_structure_factor_tc(const EwaldDev &e, const TcShape &sh, con
                                        cudaStream_t st);
 
 // Tensor-core MM-side reciprocal sum (mmrecip_tc.cu): tiling and scratch.
+constexpr int MMR_NP = 7;  // digit planes per operand of the MM-side tensor-core sum (48-bit fixed point)
 struct MmrShape {
     int mtiles = 0, npad = 0, npair = 0, nchunk = 0;  // charge tiles (128), padded charges, (n_y, n_z) pairs, chunks of 8
     int cpt = 3, ntiles = 1, nr = 0, nstg = 3;        // channels per N tile, N tiles, N rows, stages
     int nacc = 4;                                     // accumulators (exact levels + 1)
-    int np = 7;                                       // digit planes per operand (7 or 5)
+    int np = 7;                                       // digit planes per operand (MMR_NP)
     bool supported = false;                           // kx small enough for one channel per tile
     size_t phase_rows = 0;                            // Y and Z phase rows (int4)
     size_t bplane_words = 0;                          // B digit planes of all N tiles (32-bit words)
@@ -166,7 +174,7 @@ struct EwaldBuf {
     int recip = 0;               // reciprocal sums: 0 CUDA cores (FP64 / double-float), 1 tensor cores
     TcShape tcs;
     TcBuf tcb;
-    MmrShape mms[2];             // MM-side sum: [0] FP64 class (5 accumulators), [1] mixed path (4)
+    MmrShape mms;                // MM-side sum (FP64 class: 7 planes, 5 accumulators), both precisions
     MmrBuf mmb;
     int *err = nullptr;          // device error word of the handle
 };

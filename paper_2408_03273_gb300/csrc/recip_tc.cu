@@ -233,17 +233,21 @@ __global__ void __launch_bounds__(TCTHREADS, 1) k_sf_tc(TcSfArgs a)
             bulk_g2s(sm + st * stage + TCND * A_PLANE, src, bbytes, &bfull[st]);
             issued = ch + 1;
         }
-        // copies still in flight (only after a give-up): wait for them, bounded, before leaving
+        // copies possibly still in flight (after a give-up): wait for them to land, bounded in time
+        // only (not cut short by the abort flag), before the block may leave
         for (int ch = issued > NSTAGE ? issued - NSTAGE : 0; ch < issued; ++ch)
-            tc::mbar_wait_thread(&bfull[ch % NSTAGE], (ch / NSTAGE) & 1, abort);
+            tc::mbar_drain(&bfull[ch % NSTAGE], (ch / NSTAGE) & 1);
         for (int ch = pissued > NSTAGE ? pissued - NSTAGE : 0; ch < pissued; ++ch)
-            tc::mbar_wait_thread(&pfull[ch % NSTAGE], (ch / NSTAGE) & 1, abort);
+            tc::mbar_drain(&pfull[ch % NSTAGE], (ch / NSTAGE) & 1);
     }
 
     // ---------------- epilogue: tensor memory -> per-CTA partials (warps 0..7) ----------------
     if (warp < 8) {
         if (!tc::mbar_wait_thread(done, 0, abort)) {
             give_up();
+            // the MMA thread commits `done` on every path: wait for it (bounded in time only), so
+            // that no MMA still writes tensor memory when it is freed below
+            tc::mbar_drain(done, 0);
         } else {
             tc::fence_after_sync();
             const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;

@@ -99,16 +99,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 
 // Per-thread bounded wait for the completion of phase `parity` (no block-wide agreement: for
 // warp-specialised kernels).  Gives up after `limit_ns` of global-timer time, 2^24 polls, or when
-// another thread raised *abort; returns false then.
+// another thread raised *abort; returns false then.  With abort == nullptr only the time and poll
+// limits apply: the form for draining work already issued (bulk copies in flight, MMAs not yet
+// complete) after a give-up, before the block frees what that work writes into.
 __device__ __forceinline__ bool mbar_wait_thread(uint64_t *bar, unsigned parity, const volatile int *abort,
                                                  uint64_t limit_ns = MBAR_LIMIT_NS)
 {
     const uint64_t t0 = global_ns();
     for (int it = 0; it < (1 << 24); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31) == 31 && (*abort || global_ns() - t0 > limit_ns)) return false;
+        if ((it & 31) == 31 && ((abort && *abort) || global_ns() - t0 > limit_ns)) return false;
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, unsigned parity)
+{
+    return mbar_wait_thread(bar, parity, nullptr);
 }
 
 }  // namespace tc

@@ -1,13 +1,17 @@
 // vgrad_f32.cu -- adjoint of the region-I term, mixed precision (see vgrad_f64.cu for the
-// derivative algebra).  The density-folded Hermite coefficients D0, Dx, Dy, Dz are built in
-// FP64 once per primitive pair and rounded to FP32; the per-charge Boys/R recursion to order L+1,
-// the four D0 contractions (e_0, e_x, e_y, e_z) and the charge sum S_tuv += q R_tuv run in FP32,
-// with no FP64 instruction inside the charge loop.  Every 16 charges the group's S is contracted
-// with Dx, Dy, Dz, which wait in the thread's local memory (kept out of the loop's registers).
-// Per-pair sums go through FP32 partials over 16 charges folded into double-float pairs;
-// per-charge sums over the warp's 32 primitive pairs use a reduce-scatter (6 shuffles for four
-// values) and compensated FP32 shared-memory atomics: the atomic returns the old value, so the
-// rounding error of every addition is recovered exactly and kept in a second FP32 word.
+// derivative algebra).  Two kernels, by angular class:
+//
+//  * l_A + l_B <= 2 (k_vgrad_f32): one lane per primitive pair.  The density-folded Hermite
+//    coefficients D0, Dx, Dy, Dz are built in FP64 once per primitive pair and rounded to FP32;
+//    the per-charge Boys/R recursion to order L+1, the four D0 contractions (e_0, e_x, e_y, e_z)
+//    and the charge sum S_tuv += q R_tuv run in FP32, every index static (loops of constant trip
+//    count), so all of it stays in registers.  Every 16 charges the group's S is contracted with
+//    Dx, Dy, Dz.  Per-pair sums go through FP32 partials over 16 charges folded into double-float
+//    pairs; per-charge sums over the warp's 32 primitive pairs use a reduce-scatter (6 shuffles for
+//    four values) and compensated FP32 shared-memory atomics: the atomic returns the old value, so
+//    the rounding error of every addition is recovered exactly and kept in a second FP32 word.
+//  * l_A + l_B >= 3 (k_vgrad_cl): one lane per region-I charge, the pairs' coefficients read from
+//    shared memory (see the comment above k_vgrad_cl).
 #include "pp_tile.cuh"
 
 namespace qmmm {
@@ -16,25 +20,13 @@ template <int LA, int LB>
 struct VgradF32 {
     static cudaError_t run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                            int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                           int nsm, int variant, int nslice,
+                           int nsm, int variant, int nslice, ClScratch cl,
                            cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
 constexpr int GFOLD = 16;
-
-// 16-byte loads and stores of this thread's local memory (an array kept out of registers)
-__device__ __forceinline__ void st_local4(uint32_t a, const float (&v)[4])
-{
-    asm volatile("st.local.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-                 : "memory");
-}
-__device__ __forceinline__ void ld_local4(uint32_t a, float (&v)[4])
-{
-    asm volatile("ld.local.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a)
-                 : "memory");
-}
 
 template <int LA, int LB, int NT>
 __global__ void __launch_bounds__(NT, 1)
@@ -69,9 +61,6 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int ntile = (pp_end - pp_begin + 31) >> 5;
-    constexpr int ND4 = (3 * NH + 3) / 4;
-    float4 dl[ND4];  // this lane's Dx, Dy, Dz (FP32), accessed only through ld/st.local
-    const uint32_t dl_addr = (uint32_t)__cvta_generic_to_local(dl);
     for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
         const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
         const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
@@ -79,30 +68,19 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
             const double d = pl.P[x] - rg.centre[x];
-            Ph[x] = (float)d;
-            Plo[x] = (float)(d - (double)Ph[x]);
+            split_grid(d, Ph[x], Plo[x]);
         }
 
-        float D0[NH];
+        float D0[NH], Da[3][NH];  // registers: every index below is static (loops of constant trip count)
         {
-            double d0[NH];
-            fold_density<LA, LB>(pl, bd, dm, d0);
+            double d0[NH], dx[NH], dy[NH], dz[NH];
+            fold_density_dA<LA, LB, true>(pl, bd, dm, dx, dy, dz, d0);
 #pragma unroll
-            for (int k = 0; k < NH; ++k) D0[k] = (float)d0[k];
-        }
-        {
-            // Dx, Dy, Dz as FP32 in this thread's local memory: read once per GFOLD charges
-            double dx[NH], dy[NH], dz[NH];
-            fold_density_dA<LA, LB>(pl, bd, dm, dx, dy, dz);
-#pragma unroll
-            for (int i = 0; i < ND4; ++i) {
-                float v[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int e = 4 * i + c;
-                    v[c] = e < NH ? (float)dx[e] : e < 2 * NH ? (float)dy[e - NH] : e < 3 * NH ? (float)dz[e - 2 * NH] : 0.0f;
-                }
-                st_local4(dl_addr + 16u * i, v);
+            for (int k = 0; k < NH; ++k) {
+                D0[k] = (float)d0[k];
+                Da[0][k] = (float)dx[k];
+                Da[1][k] = (float)dy[k];
+                Da[2][k] = (float)dz[k];
             }
         }
 
@@ -138,15 +116,16 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                         sc *= m2rho;
                     }
                     float R[NH1];
-                    hermite_R<L + 1, float>(R, Fn, X, Y, Z);
+                    hermite_R_u<L + 1, float>(R, Fn, X, Y, Z);
                     float e0 = 0, ex = 0, ey = 0, ez = 0;
                     const float q = ch.w;
 #pragma unroll
                     for (int t = 0; t <= L; ++t)
 #pragma unroll
-                        for (int u = 0; u <= L - t; ++u)
+                        for (int u = 0; u <= L; ++u)
 #pragma unroll
-                            for (int w = 0; w <= L - t - u; ++w) {
+                            for (int w = 0; w <= L; ++w) {
+                                if (t + u + w > L) continue;
                                 const int k = hidx(t, u, w);
                                 e0 += D0[k] * R[k];
                                 ex += D0[k] * R[hidx(t + 1, u, w)];
@@ -182,19 +161,13 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
                         }
                     }
                 }
-                // this group's sum_C q_C d_a(C) = sum_k Da_k S_k, Da from local memory
+                // this group's sum_C q_C d_a(C) = sum_k Da_k S_k
                 float tdx = 0, tdy = 0, tdz = 0;
 #pragma unroll
-                for (int i = 0; i < ND4; ++i) {
-                    float v[4];
-                    ld_local4(dl_addr + 16u * i, v);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int e = 4 * i + c;
-                        if (e < NH) tdx += v[c] * S[e];
-                        else if (e < 2 * NH) tdy += v[c] * S[e - NH];
-                        else if (e < 3 * NH) tdz += v[c] * S[e - 2 * NH];
-                    }
+                for (int k = 0; k < NH; ++k) {
+                    tdx = fmaf(Da[0][k], S[k], tdx);
+                    tdy = fmaf(Da[1][k], S[k], tdy);
+                    tdz = fmaf(Da[2][k], S[k], tdz);
                 }
                 df_add(sh[0], sl[0], tdx); df_add(sh[1], sl[1], tdy); df_add(sh[2], sl[2], tdz);
                 df_add(sh[3], sl[3], tex); df_add(sh[4], sl[4], tey); df_add(sh[5], sl[5], tez);
@@ -221,6 +194,316 @@ k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, i
         const double v = (double)acc_hi[k] + (double)acc_lo[k];
         if (v != 0.0) atomicAdd(gchg + 4 * (size_t)ch_begin + k, v);
     }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Charge-lane sweep (classes with l_A + l_B >= CL_MIN_L).  With one lane per primitive pair the
+// high-l classes hold D0, S and R (126 floats for (d, d), 288 for (f, f)) in registers and spill
+// to local memory; here a lane owns one region-I charge and holds only R, while the pairs'
+// density-folded coefficients (D0, Dx, Dy, Dz per Hermite index, one 16-byte broadcast load) come
+// from shared memory, batch by batch.  Per (pair, charge), all FP32:
+//   e0 = D0.R, e_a = D0.R(+a), h_a = D_a.R                         (7 contractions of nherm(L))
+//   charge: dq -= e0, dC_a += q e_a                                 (lane registers, double-float)
+//   pair:   sum over the block's charges of q h_a and q e_a        (warp reduce-scatter, then
+//           compensated shared-memory atomics, then one FP64 global atomic per block)
+// The pair gradient g_A = -(sum q h + a/p sum q e), g_B = sum q h - b/p sum q e is formed in FP64
+// by k_cl_pairs once every charge tile has added its sums.
+// ---------------------------------------------------------------------------------------------
+
+// Pair records of one class (FP64 Hermite/density algebra, rounded to FP32), once per call.
+template <int LA, int LB>
+__global__ void __launch_bounds__(128)
+k_cl_records(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, const double *__restrict__ dm,
+             float4 *__restrict__ rec)
+{
+    constexpr int L = LA + LB, NH = nherm(L), R4 = cl_rec_floats(L) / 4;
+    const int i = pp_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= pp_end) return;
+    const PPLane pl = load_pp(bd, i, pp_end);
+    float4 *r = rec + (size_t)(i - pp_begin) * R4;
+    float ph[3], pl_[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) split_grid(pl.P[x] - rg.centre[x], ph[x], pl_[x]);
+    const long long pb = __double_as_longlong(pl.p);
+    r[0] = make_float4(ph[0], ph[1], ph[2], pl_[0]);
+    r[1] = make_float4(pl_[1], pl_[2], __int_as_float((int)(pb & 0xffffffffll)), __int_as_float((int)(pb >> 32)));
+    double D0[NH], Dx[NH], Dy[NH], Dz[NH];
+    fold_density_dA<LA, LB, true>(pl, bd, dm, Dx, Dy, Dz, D0);
+#pragma unroll
+    for (int k = 0; k < NH; ++k) r[2 + k] = make_float4((float)D0[k], (float)Dx[k], (float)Dy[k], (float)Dz[k]);
+}
+
+// CPL charges per lane (a block's tile holds CL_NT * CPL charges of one width class, each lane
+// CPL consecutive ones): the per-pair reduction is paid once per CPL charges and the lane has CPL
+// independent chains of Boys/R work; NB pairs per staged batch.
+template <int LA, int LB, int CPL, int MINB>
+__global__ void __launch_bounds__(CL_NT, MINB)
+k_vgrad_cl(RegionDev rg, int npair, const float4 *__restrict__ rec, int ch_begin, int ch_end,
+           const float *__restrict__ boys_g, double *__restrict__ psum, double *__restrict__ gchg)
+{
+    constexpr int L = LA + LB, NH1 = nherm(L + 1), R4 = cl_rec_floats(L) / 4, NB = cl_batch(L);
+    constexpr int TILE = CL_NT * CPL;
+    constexpr int PF = (NB * R4 + CL_NT - 1) / CL_NT;  // float4 per thread of a prefetched batch
+    __shared__ __align__(16) float tab[BOYS_TAB_F];
+    __shared__ __align__(16) float4 buf[2][NB * R4];
+    __shared__ float2 rsq[2][NB];  // (rho, sqrt(kappa / (p + kappa))) per pair of a batch
+    __shared__ float ps_h[2][NB * 8], ps_l[2][NB * 8];
+
+    // this block's charge tile: TILE charges of one width class within [ch_begin, ch_end)
+    int t = (int)blockIdx.y, cbeg = -1, cend = 0;
+    double kap = 0.0;
+    for (int c = 0; c < rg.ncls; ++c) {
+        const int lo = max(__ldg(rg.cls_off + c), ch_begin), hi = min(__ldg(rg.cls_off + c + 1), ch_end);
+        if (lo >= hi) continue;
+        const int nt = (hi - lo + TILE - 1) / TILE;
+        if (t < nt) {
+            cbeg = lo + t * TILE;
+            cend = min(hi, cbeg + TILE);
+            kap = __ldg(rg.cls_kappa + c);
+            break;
+        }
+        t -= nt;
+    }
+    // this block's pair batches
+    const int nbatch = (npair + NB - 1) / NB;
+    const int bper = (nbatch + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int b0 = (int)blockIdx.x * bper, b1 = min(nbatch, b0 + bper);
+    if (cbeg < 0 || b0 >= b1) return;  // block-uniform
+
+    for (int k = threadIdx.x; k < BOYS_TAB_F; k += CL_NT) tab[k] = __ldg(boys_g + k);
+    for (int k = threadIdx.x; k < 2 * NB * 8; k += CL_NT) {
+        (&ps_h[0][0])[k] = 0.0f;
+        (&ps_l[0][0])[k] = 0.0f;
+    }
+    // this lane's charges: CPL consecutive region-I entries (inactive ones carry q = 0)
+    float4 ch[CPL], cl[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+        const int j = cbeg + CPL * (int)threadIdx.x + i;
+        ch[i] = cl[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < cend) {
+            ch[i] = __ldg(rg.chg_hi + j);
+            cl[i] = __ldg(rg.chg_lo + j);
+        }
+    }
+
+    // a batch's records: element idx of the batch into smem; the thread holding a record's second
+    // float4 (with p) also forms (rho, sq) for the block's width class, in FP64
+    auto put = [&](int s, int idx, float4 v) {
+        buf[s][idx] = v;
+        if (idx % R4 == 1) {
+            const double p = __longlong_as_double(((long long)__float_as_int(v.w) << 32) |
+                                                  (unsigned int)__float_as_int(v.z));
+            const double td = kap > 0.0 ? kap / (p + kap) : 1.0;
+            rsq[s][idx / R4] = make_float2((float)(p * td), (float)sqrt(td));
+        }
+    };
+    {
+        const int nb = min(NB, npair - b0 * NB);
+        for (int idx = threadIdx.x; idx < nb * R4; idx += CL_NT) put(0, idx, __ldg(rec + (size_t)b0 * NB * R4 + idx));
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    float ah[CPL][4], al[CPL][4];  // per-charge sums (double-float): dC_x, dC_y, dC_z, dq
+#pragma unroll
+    for (int i = 0; i < CPL; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ah[i][c] = al[i][c] = 0.0f;
+    for (int b = b0; b < b1; ++b) {
+        const int s = (b - b0) & 1;
+        const int nb = min(NB, npair - b * NB);
+        // prefetch the next batch into registers while this one is computed
+        float4 pf[PF];
+        const int nbn = b + 1 < b1 ? min(NB, npair - (b + 1) * NB) : 0;
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int idx = (int)threadIdx.x + i * CL_NT;
+            if (idx < nbn * R4) pf[i] = __ldg(rec + (size_t)(b + 1) * NB * R4 + idx);
+        }
+        float bp[CPL][4];
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) bp[i][0] = bp[i][1] = bp[i][2] = bp[i][3] = 0.0f;
+        for (int p = 0; p < nb; ++p) {
+            const float4 *r = buf[s] + p * R4;
+            const float4 h0 = r[0], h1 = r[1];
+            const float2 rq = rsq[s][p];
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // this lane's pair sums
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                // correctly rounded displacement (grid-split hi parts subtract exactly)
+                const float X = (h0.x - ch[i].x) + (h0.w - cl[i].x);
+                const float Y = (h0.y - ch[i].y) + (h1.x - cl[i].y);
+                const float Z = (h0.z - ch[i].z) + (h1.y - cl[i].z);
+                float T, Tl;
+                boys_arg_f32(rq.x, X, Y, Z, T, Tl);
+                float F[L + 2];
+                boys_f32<L + 1>(T, F, tab, Tl);
+                float Fn[L + 2];
+                {
+                    float sc = rq.y;
+                    const float m2rho = -2.0f * rq.x;
+#pragma unroll
+                    for (int n = 0; n <= L + 1; ++n) {
+                        Fn[n] = sc * F[n];
+                        sc *= m2rho;
+                    }
+                }
+                float R[NH1];
+                hermite_R_u<L + 1, float>(R, Fn, X, Y, Z);
+                float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+#pragma unroll
+                for (int tt = 0; tt <= L; ++tt)
+#pragma unroll
+                    for (int uu = 0; uu <= L; ++uu)
+#pragma unroll
+                        for (int ww = 0; ww <= L; ++ww) {
+                            if (tt + uu + ww > L) continue;
+                            const int k = hidx(tt, uu, ww);
+                            const float4 d = r[2 + k];
+                            e0 = fmaf(d.x, R[k], e0);
+                            ex = fmaf(d.x, R[hidx(tt + 1, uu, ww)], ex);
+                            ey = fmaf(d.x, R[hidx(tt, uu + 1, ww)], ey);
+                            ez = fmaf(d.x, R[hidx(tt, uu, ww + 1)], ez);
+                            hx = fmaf(d.y, R[k], hx);
+                            hy = fmaf(d.z, R[k], hy);
+                            hz = fmaf(d.w, R[k], hz);
+                        }
+                const float q = ch[i].w;
+                bp[i][0] = fmaf(q, ex, bp[i][0]);
+                bp[i][1] = fmaf(q, ey, bp[i][1]);
+                bp[i][2] = fmaf(q, ez, bp[i][2]);
+                bp[i][3] -= e0;
+                v[0] = fmaf(q, hx, v[0]);
+                v[1] = fmaf(q, hy, v[1]);
+                v[2] = fmaf(q, hz, v[2]);
+                v[3] = fmaf(q, ex, v[3]);
+                v[4] = fmaf(q, ey, v[4]);
+                v[5] = fmaf(q, ez, v[5]);
+            }
+            // pair sums over the warp's 32 lanes: reduce-scatter of 8 values (6 used), combining
+            // neighbouring lanes first: consecutive region-I charges are the atoms of one water, so
+            // the partial sums cancel early and stay small (a 16-apart pairing first sums unrelated
+            // monopoles and leaves the FP32 rounding of large partials in the small total).  Lanes
+            // 0..7 end with value vi = bits (0, 1, 2) of the lane number.
+            float w4[4], w2[2], w1;
+            {
+                const bool up = lane & 1;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float keep = up ? v[i + 4] : v[i], send = up ? v[i] : v[i + 4];
+                    w4[i] = keep + __shfl_xor_sync(FULL, send, 1);
+                }
+                const bool up2 = lane & 2;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float keep = up2 ? w4[i + 2] : w4[i], send = up2 ? w4[i] : w4[i + 2];
+                    w2[i] = keep + __shfl_xor_sync(FULL, send, 2);
+                }
+                const bool up4 = lane & 4;
+                {
+                    const float keep = up4 ? w2[1] : w2[0], send = up4 ? w2[0] : w2[1];
+                    w1 = keep + __shfl_xor_sync(FULL, send, 4);
+                }
+                w1 += __shfl_xor_sync(FULL, w1, 8);
+                w1 += __shfl_xor_sync(FULL, w1, 16);
+            }
+            const int vi = (lane & 1) * 4 + ((lane >> 1) & 1) * 2 + ((lane >> 2) & 1);
+            if (lane < 8 && vi < 6) {
+                // compensated shared-memory atomic: the old value gives the rounding error exactly
+                float *hp = &ps_h[s][p * 8 + vi];
+                const float old = atomicAdd(hp, w1);
+                const float sum = old + w1, bv = sum - old;
+                atomicAdd(&ps_l[s][p * 8 + vi], (old - (sum - bv)) + (w1 - bv));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) df_add(ah[i][c], al[i][c], bp[i][c]);
+        __syncthreads();  // batch b read by all warps; its pair sums complete
+        if ((int)threadIdx.x < nb * 6) {
+            // each of these threads reads one sum and clears it for batch b + 2 (slots 6, 7 of a
+            // pair are never written)
+            const int pp = (int)threadIdx.x / 6, vv = (int)threadIdx.x % 6, o = pp * 8 + vv;
+            atomicAdd(psum + (size_t)(b * NB + pp) * 6 + vv, (double)ps_h[s][o] + (double)ps_l[s][o]);
+            ps_h[s][o] = ps_l[s][o] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int idx = (int)threadIdx.x + i * CL_NT;
+            if (idx < nbn * R4) put(s ^ 1, idx, pf[i]);
+        }
+        __syncthreads();  // batch b + 1 staged
+    }
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+        const int j = cbeg + CPL * (int)threadIdx.x + i;
+        if (j < cend) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(gchg + 4 * (size_t)j + c, (double)ah[i][c] + (double)al[i][c]);
+        }
+    }
+}
+
+// Pair gradients from the per-pair charge sums (FP64), summed per shell pair and atom.
+template <int LA, int LB>
+__global__ void __launch_bounds__(128)
+k_cl_pairs(BasisDev bd, int pp_begin, int pp_end, const double *__restrict__ psum, double *__restrict__ gqm)
+{
+    const int i = pp_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int lane = threadIdx.x & 31;
+    const PPLane pl = load_pp(bd, i, pp_end);
+    double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (pl.active) {
+        const double *sm = psum + (size_t)(i - pp_begin) * 6;
+        const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            g[x] = -(sm[x] + aop * sm[3 + x]);
+            g[3 + x] = sm[x] - bop * sm[3 + x];
+        }
+    }
+    bool take[5], head;
+    seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] = seg_reduce(g[k], take);
+    if (head && pl.active) {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            atomicAdd(gqm + 3 * pl.atomA + x, g[x]);
+            atomicAdd(gqm + 3 * pl.atomB + x, g[3 + x]);
+        }
+    }
+}
+
+template <int LA, int LB, int CPL, int MINB>
+static cudaError_t launch_cl(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
+                             int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int nsm,
+                             ClScratch cl, cudaStream_t st)
+{
+    const int npair = pp_end - pp_begin;
+    if (!cl.rec || !cl.psum) return cudaErrorInvalidValue;
+    k_cl_records<LA, LB><<<(npair + 127) / 128, 128, 0, st>>>(bd, rg, pp_begin, pp_end, dm, cl.rec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cl.psum, 0, (size_t)npair * 6 * sizeof(double), st)) != cudaSuccess) return e;
+    // charge tiles: at most one more per width class than the charges fill
+    constexpr int TILE = CL_NT * CPL, NB = cl_batch(LA + LB);
+    const int ntile = (ch_end - ch_begin + TILE - 1) / TILE + max(rg.ncls, 1) - 1;
+    const int nbatch = (npair + NB - 1) / NB;
+    // fine-grained blocks (CL_BPB batches each): the class kernels are launched together, highest
+    // class first, and the block scheduler packs their blocks onto the SMs as others finish, so
+    // short blocks keep the tail of the concurrent sweep short (no fixed share of the SMs)
+    (void)nsm;
+    const int gx = max(1, (nbatch + CL_BPB - 1) / CL_BPB);
+    k_vgrad_cl<LA, LB, CPL, MINB><<<dim3(gx, ntile), CL_NT, 0, st>>>(rg, npair, cl.rec, ch_begin, ch_end,
+                                                                    boys + (size_t)(LA + LB + 1) * BOYS_TAB_F,
+                                                                    cl.psum, gchg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_cl_pairs<LA, LB><<<(npair + 127) / 128, 128, 0, st>>>(bd, pp_begin, pp_end, cl.psum, gqm);
+    return cudaGetLastError();
 }
 
 // bytes of one order's FP32 Boys table (what a block stages)
@@ -256,16 +539,28 @@ template <int LA, int LB>
 cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                                   int ch_end, const float *boys, const double *dm, double *gqm, double *gchg,
                                   int *err,
-                                  int nsm, int variant, int nslice,
+                                  int nsm, int variant, int nslice, ClScratch cl,
                                   cudaStream_t st)
 {
-    constexpr int W = sweep_wide_threads(SW_VGRAD_F32, class_of(LA, LB));
-    if constexpr (W > 0)
-        if (variant == 1)
-            return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                        nslice, st);
-    return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                  nslice, st);
+    // charge-lane sweep: (charges per lane, blocks per SM) of variant 0 and 1 (cl_variant)
+    constexpr int L = LA + LB;
+    if constexpr (L >= CL_MIN_L) {
+        if (variant == 1) {
+            if constexpr (cl_variant(L, 1, 0) > 0)
+                return launch_cl<LA, LB, cl_variant(L, 1, 0), cl_variant(L, 1, 1)>(
+                    bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, nsm, cl, st);
+        }
+        return launch_cl<LA, LB, cl_variant(L, 0, 0), cl_variant(L, 0, 1)>(bd, rg, pp_begin, pp_end, ch_begin,
+                                                                           ch_end, boys, dm, gqm, gchg, nsm, cl, st);
+    } else {
+        constexpr int W = sweep_wide_threads(SW_VGRAD_F32, class_of(LA, LB));
+        if constexpr (W > 0)
+            if (variant == 1)
+                return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err,
+                                            nsm, nslice, st);
+        return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
+                                      nslice, st);
+    }
 }
 
 template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
@@ -274,11 +569,12 @@ template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_C
 
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
-                             double *gchg, int *err, int nsm, int variant, int nslice, cudaStream_t st)
+                             double *gchg, int *err, int nsm, int variant, int nslice, ClScratch cl,
+                             cudaStream_t st)
 {
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VgradF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                    variant, nslice, st);
+                                    variant, nslice, cl, st);
 }
 
 #endif

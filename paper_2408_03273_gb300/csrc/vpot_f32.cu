@@ -60,8 +60,7 @@ k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
             const double d = pl.P[x] - rg.centre[x];
-            Ph[x] = (float)d;
-            Plo[x] = (float)(d - (double)Ph[x]);
+            split_grid(d, Ph[x], Plo[x]);
         }
         float Wh[NH], Wl[NH];
 #pragma unroll

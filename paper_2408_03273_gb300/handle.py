@@ -48,6 +48,10 @@ class Handle:
     def energy(self, dm, E=None):
         return L.qmmm_energy(self.h, dm, E)
 
+    def density_gradient(self, dm, G=None):
+        """dE/dgamma = V + F_II (needs vpot at the current geometry)."""
+        return L.qmmm_density_gradient(self.h, dm, G)
+
     def forces(self, dm, dE_dRqm=None, dE_dRmm=None, dE_dq=None):
         return L.qmmm_forces(self.h, dm, dE_dRqm, dE_dRmm, dE_dq)
 
@@ -138,22 +142,21 @@ def _autograd_function():
             h = handle.h
             L.qmmm_set_stream(h, torch.cuda.current_stream())
             L.qmmm_set_positions(h, qm_xyz.detach(), mm_xyz.detach(), mm_q.detach())
-            V, _ = L.qmmm_vpot(h, like=dm)
+            L.qmmm_vpot(h, like=dm)  # V stays in the handle for the energy and dE/dgamma
             E = L.qmmm_energy(h, dm.detach())
             ctx.handle = handle
-            ctx.save_for_backward(dm, V)
+            ctx.save_for_backward(dm)
             return E[0].clone()
 
         @staticmethod
         def backward(ctx, gE):
-            dm, V = ctx.saved_tensors
+            (dm,) = ctx.saved_tensors
             h = ctx.handle.h
             L.qmmm_set_stream(h, torch.cuda.current_stream())
             gq, gm, gc = L.qmmm_forces(h, dm.detach())
             gdm = None
             if ctx.needs_input_grad[1]:
-                _, _, F = L.qmmm_ewald(h, dm.detach(), want_F=True)
-                gdm = gE * (V + F)
+                gdm = gE * L.qmmm_density_gradient(h, dm.detach())  # V + F_II, formed in the library
             return None, gdm, gE * gq, gE * gm, gE * gc
 
     return QMMMEnergy

@@ -1,10 +1,14 @@
 """Batches of frames through one recorded CUDA graph (qmmm_batch_*): every frame's V, energy and
-gradient against the same handle's plain calls, graph replay without re-recording, a position
-update between runs, and the argument checks."""
+gradient against the same handle's plain calls, frames of the uneven-frames workload (water
+clusters of 21 and 45 QM atoms in ~30000 MM charges) inside a recorded graph against the FP64
+oracle, graph replay without re-recording, a position update between runs, and the argument
+checks."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads
+from _gpuutil import TOL_FP64, TOL_MIXED, TOL_MIXED_ELEM, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +35,62 @@ def _dev_outputs(torch, frames):
 def _close(a, b, tol):
     a, b = np.asarray(a), np.asarray(b)
     return float(np.max(np.abs(a - b))) <= tol * max(float(np.max(np.abs(b))), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def c5_pair():
+    # two frames of the uneven-frames workload (QM water clusters of 21 and 45 atoms, 30666 and
+    # 26658 MM charges), with the oracle's V, energy, QM gradient and three sampled MM charges
+    frames = workloads.config5_frames(64)
+    out = []
+    for f in (53, 63):
+        s = frames[f]
+        idx = oracle.region1(s)[0]
+        rng = np.random.default_rng(500 + f)
+        mm = idx[np.sort(rng.choice(len(idx), 3, replace=False))]
+        ref = oracle.energy(s)
+        ref.update(oracle.forces(s, mm_subset=mm))
+        out.append((s, mm, ref))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_frames_against_oracle(c5_pair, precision):
+    torch = pytest.importorskip("torch")
+    import paper_2408_03273_gb300 as q
+    frames = [s for s, _, _ in c5_pair]
+    hs = [q.Handle(s, precision=precision) for s in frames]
+    try:
+        dev = torch.device("cuda")
+        dm = [torch.as_tensor(s.dm, device=dev) for s in frames]
+        V, E, gq, gm, gc = _dev_outputs(torch, frames)
+        b = q.Batch(hs)
+        try:
+            for _ in range(2):  # the recording run, then a graph replay
+                b.run(dm, V, E, gq, gm, gc)
+            assert b.captures() == 1
+        finally:
+            b.close()
+        for i, (s, mm, ref) in enumerate(c5_pair):
+            Vi, Ei = V[i].cpu().numpy(), E[i].cpu().numpy()
+            sc = abs(ref["E_I_elec"]) + abs(ref["E_nuc_mm"]) + abs(ref["E_II"])
+            if precision == 0:
+                assert np.max(np.abs(Vi - ref["V"])) < TOL_FP64 * np.max(np.abs(ref["V"])), i
+                assert abs(Ei[0] - ref["E"]) < TOL_FP64 * sc, i
+            else:
+                assert rel_fro(Vi, ref["V"]) < TOL_MIXED, i
+                assert np.max(np.abs(Vi - ref["V"])) < TOL_MIXED_ELEM * np.max(np.abs(ref["V"])), i
+                assert abs(Ei[0] - ref["E"]) < TOL_MIXED * sc, i
+            tol = TOL_FP64 if precision == 0 else TOL_MIXED
+            # raw errors: relative to the largest value of each whole gradient
+            g = gq[i].cpu().numpy()
+            assert np.max(np.abs(g - ref["dE_dRqm"])) < tol * np.max(np.abs(ref["dE_dRqm"])), i
+            gmi, gci = gm[i].cpu().numpy(), gc[i].cpu().numpy()
+            assert np.max(np.abs(gci[mm] - ref["dE_dq"][mm])) < tol * np.max(np.abs(gci)), i
+            assert np.max(np.abs(gmi[mm] - ref["dE_dRmm"][mm])) < tol * np.max(np.abs(gmi)), i
+    finally:
+        for h in hs:
+            h.close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -1,7 +1,7 @@
 """Large active site with f shells (150 QM atoms, 1500 shells, 5100 AOs, ~200000 MM charges in an
 86 A box, kmax 24): sampled V blocks of every angular class up to (f, f) against the oracle, the
-mixed path against FP64, and invariants of the full gradient.  (The oracle's charge derivatives
-take minutes at this size; the active-site workload and the small systems cover them.)"""
+charge derivatives of sampled region-I charges against the oracle (the full adjoint launch shape
+of every class up to (f, f)), the mixed path against FP64, and invariants of the full gradient."""
 import numpy as np
 import pytest
 
@@ -48,6 +48,20 @@ def test_config4_sampled_V_blocks(c4, c4_gpu, precision):
     ref = np.concatenate([Vref[off[a]:off[a + 1], off[b]:off[b + 1]].ravel() for a, b in pairs])
     tol = TOL_FP64 if precision == 0 else TOL_MIXED_ELEM
     assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(V))
+
+
+def test_config4_sampled_charge_derivatives(c4, c4_gpu):
+    # dE/dq and dE/dR_MM of two region-I charges: their region-I sums run over every primitive pair
+    # of every class (the per-charge sums of the adjoint sweeps at full size) plus the nuclear and
+    # MM-side Ewald terms; raw error relative to the largest value of each quantity
+    rng = np.random.default_rng(44)
+    nI = len(oracle.region1(c4)[0])
+    sub = np.sort(rng.choice(nI, 2, replace=False))
+    mm, dq, dR = oracle.forces_mm_subset(c4, sub)
+    for p, tol in ((0, TOL_FP64), (1, TOL_MIXED)):
+        g = c4_gpu[p]
+        assert np.max(np.abs(g["dE_dq"][mm] - dq)) < tol * np.max(np.abs(g["dE_dq"])), p
+        assert np.max(np.abs(g["dE_dRmm"][mm] - dR)) < tol * np.max(np.abs(g["dE_dRmm"])), p
 
 
 def test_config4_mixed_vs_fp64(c4_gpu):

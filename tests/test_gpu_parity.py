@@ -57,6 +57,21 @@ def test_fock_term(case):
     assert rel_max(g["F"], F) < TOL_FP64
 
 
+def test_density_gradient(case):
+    # dE/dgamma = V + F_II (Eqs. 11-14) formed by the library, against the oracle's V and F_II
+    import paper_2408_03273_gb300 as q
+    name, s, ref = case
+    h = q.Handle(s, screen_tol=0.0)
+    try:
+        with pytest.raises(q.QMMMError):
+            h.density_gradient(s.dm)  # V not computed yet at this geometry
+        h.vpot()
+        G = h.density_gradient(s.dm)
+    finally:
+        h.close()
+    assert rel_max(G, ref["V"] + oracle.fock_ii(s, ref["phi"])) < TOL_FP64
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_forces(case, precision):
     name, s, ref = case

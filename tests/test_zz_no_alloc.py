@@ -6,10 +6,11 @@ would implicitly synchronise the device), or a plugin whose memory belongs to th
 pool allocator.  qmmm_nuclear_mm_energy_static serves them: it takes only caller-owned device
 arrays and keeps its scratch in a fixed array inside the library.  Here its result is compared,
 through the C ABI and on two calls in a row, with the E_nuc_mm that qmmm_vpot returns for the
-same charges.  This file is collected last on purpose."""
+same charges and with the FP64 CPU oracle's sum.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2408_03273_gb300 as q
 import workloads
 from _gpuutil import TOL_FP64
@@ -53,9 +54,38 @@ def test_static_scratch_energy_matches_handle_twice():
         q.qmmm_nuclear_mm_energy_static(qm, Z, chg, sig, E, stream)
         torch.cuda.synchronize()
         got.append(float(E.item()))
+    # the same sum by the FP64 CPU oracle, over the same charges
+    ora = oracle.enucmm(s, charges=(s.mm_xyz, s.mm_q, s.mm_sigma))
+    assert abs(ref - ora) < TOL_FP64 * abs(ora), (ref, ora)
     for g in got:
         assert abs(g - ref) < TOL_FP64 * abs(ref), (g, ref)
+        assert abs(g - ora) < TOL_FP64 * abs(ora), (g, ora)
     assert got[0] == got[1]
+
+
+def test_static_scratch_gaussian_charge_on_a_nucleus():
+    # a Gaussian charge centred exactly on a QM nucleus contributes its limit 2 Z q / (sigma sqrt(pi));
+    # every other (nucleus, charge) pair is summed by the oracle as usual
+    import torch
+    s = workloads.small_system(seed=77, n_atoms=3, lmax=1, n_waters=4)
+    xyz = np.array(s.mm_xyz)
+    xyz[0] = s.atom_xyz[1]
+    sig = np.full(len(s.mm_q), 0.3)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    q.qmmm_nuclear_mm_energy_static(t(s.atom_xyz), t(s.atom_Z), t(np.concatenate([xyz, s.mm_q[:, None]], 1)),
+                                    t(sig), E, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    rest = oracle.enucmm(s, charges=(xyz[1:], s.mm_q[1:], sig[1:]))
+    others = s.copy()
+    others.atom_xyz = np.ascontiguousarray(s.atom_xyz[[0, 2]])
+    others.atom_Z = np.ascontiguousarray(s.atom_Z[[0, 2]])
+    c0 = oracle.enucmm(others, charges=(xyz[:1], s.mm_q[:1], sig[:1]))
+    limit = s.atom_Z[1] * s.mm_q[0] * 2.0 / (sig[0] * np.sqrt(np.pi))
+    ref = rest + c0 + limit
+    assert np.isfinite(E.item())
+    assert abs(E.item() - ref) < 1e-12 * abs(ref), (E.item(), ref)
 
 
 def test_static_scratch_rejects_oversize_and_host_memory():
