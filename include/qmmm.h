@@ -112,9 +112,19 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
 /* Stream for all later work of the handle (a cudaStream_t passed as void*; NULL = legacy). */
 int qmmm_set_stream(qmmm_handle *h, void *stream);
 
-/* Switch the V / adjoint arithmetic: QMMM_FP64, or QMMM_MIXED (FP32 Hermite recursions and
- * charge sweeps with FP32 tile sums folded into FP64; Ewald sums and final reductions stay
- * FP64). */
+/* Switch the region-I V / adjoint arithmetic: QMMM_FP64, or QMMM_MIXED.  On the mixed path the
+ * per-(primitive pair, charge) work of Eq. 9 and its derivatives runs in FP32: correctly rounded
+ * FP32 displacements (coordinates split into hi parts on a 2^-16 bohr grid and lo parts), the
+ * Boys function from an FP32 table with its argument carried as an unevaluated FP32 pair, the
+ * Hermite recursion and the contractions with the density-folded coefficients (built per pair
+ * in FP64, rounded to FP32).  Per-pair and per-charge sums are carried in double-float (FP32
+ * pairs) and finished in FP64.  Everything else stays FP64-class on both paths: the per-pair
+ * Hermite/density algebra, the nuclear-MM term, the real-space Ewald sums, the multipoles and
+ * moment integrals, and the two reciprocal Ewald sums, which on the tensor cores are exact
+ * products of BF16 digit planes of 48-bit fixed-point operands (QMMM_RECIP_TENSOR) and on the
+ * CUDA cores FP64 (double-float on the mixed path, about 47 bits).  Measured error of the
+ * mixed path against FP64: 1e-7 to 3e-7 in V (relative Frobenius norm) and up to 8e-7 in the
+ * gradients (max |error| / max |gradient|) on the benchmark workloads. */
 int qmmm_set_precision(qmmm_handle *h, int precision);
 
 /* Method of the two reciprocal Ewald sums (SI, "Multipolar Ewald", long-range part): the MM

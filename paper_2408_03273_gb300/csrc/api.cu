@@ -190,8 +190,8 @@ struct qmmm_handle {
     DBuf<int4> mmr_phase;  // tensor-core MM-side reciprocal sum scratch
     DBuf<uint32_t> mmr_bpl;
     DBuf<double> mmr_cscale;
-    // charge-lane adjoint sweep (mixed path, classes with l_A + l_B >= CL_MIN_L): pair records and
-    // per-pair charge sums, one region per class (classes run concurrently)
+    // charge-lane adjoint sweep (mixed path): pair records and per-pair charge sums, one region
+    // per class (classes run concurrently)
     DBuf<float4> cl_rec;
     DBuf<double> cl_psum;
     size_t cl_rec_off[NCLASS] = {}, cl_psum_off[NCLASS] = {};
@@ -611,7 +611,6 @@ int ensure_cl(qmmm_handle *h)
         const size_t npp = (size_t)(h->class_off[c + 1] - h->class_off[c]);
         h->cl_rec_off[c] = nrec;
         h->cl_psum_off[c] = nps;
-        if (L < CL_MIN_L) continue;
         nrec += npp * (cl_rec_floats(L) / 4);
         nps += npp * 6;
     }
@@ -726,8 +725,7 @@ int tune_kind(qmmm_handle *h, int kind, cudaEvent_t e0, cudaEvent_t e1)
                 const int passes = (tiles + blocks * nwarp - 1) / (blocks * nwarp);
                 double smt = (double)t / passes * tiles / nwarp;
                 // the charge-lane sweep runs its fine-grained grid on the whole GPU: SM-time
-                if (kind == SW_VGRAD_F32 && la_of_class(c) + lb_of_class(c) >= CL_MIN_L)
-                    smt = (double)t * h->nsm;
+                if (kind == SW_VGRAD_F32) smt = (double)t * h->nsm;
                 if (v == 0) {
                     cost0[c] = smt / npp;
                     ms0[c] = t;

@@ -225,13 +225,12 @@ __device__ __forceinline__ void contract_dA(const PPLane &pl, const BasisDev &bd
 }
 
 // ------------------------------------------------------------------------------------------
-// Charge-lane adjoint sweep (mixed precision, classes with l_A + l_B >= CL_MIN_L): one lane per
-// region-I charge, the primitive pairs' density-folded Hermite coefficients read from shared
-// memory.  A pair record (built once per call in FP64, rounded to FP32) holds, in floats:
+// Charge-lane adjoint sweep (mixed precision, every angular class): lanes own region-I charges,
+// the primitive pairs' density-folded Hermite coefficients are read from shared memory.  A pair
+// record (built once per call in FP64, rounded to FP32) holds, in floats:
 //   [0..2] P - centre (hi part, split_grid), [3..5] lo part, [6..7] p (double),
 //   then per Hermite index k: (D0_k, Dx_k, Dy_k, Dz_k).
 // ------------------------------------------------------------------------------------------
-constexpr int CL_MIN_L = 0;   // classes with l_A + l_B >= CL_MIN_L take the charge-lane sweep
 constexpr int CL_NT = 256;    // threads per block
 __host__ __device__ constexpr int cl_rec_floats(int L) { return 8 + 4 * nherm(L); }
 // primitive pairs per staged batch (two batches of records in shared memory: <= 22 KB)

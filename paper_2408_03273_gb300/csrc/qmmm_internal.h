@@ -61,7 +61,7 @@ cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
                              double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, int variant, int nslice,
                              cudaStream_t st);
-// Scratch of one class's charge-lane adjoint sweep (classes with l_A + l_B >= CL_MIN_L): pair
+// Scratch of one class's charge-lane adjoint sweep (mixed path): pair
 // records (cl_rec_floats(L) floats per primitive pair) and per-pair charge sums (6 doubles).
 struct ClScratch {
     float4 *rec = nullptr;

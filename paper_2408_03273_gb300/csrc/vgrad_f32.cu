@@ -1,17 +1,10 @@
 // vgrad_f32.cu -- adjoint of the region-I term, mixed precision (see vgrad_f64.cu for the
-// derivative algebra).  Two kernels, by angular class:
-//
-//  * l_A + l_B <= 2 (k_vgrad_f32): one lane per primitive pair.  The density-folded Hermite
-//    coefficients D0, Dx, Dy, Dz are built in FP64 once per primitive pair and rounded to FP32;
-//    the per-charge Boys/R recursion to order L+1, the four D0 contractions (e_0, e_x, e_y, e_z)
-//    and the charge sum S_tuv += q R_tuv run in FP32, every index static (loops of constant trip
-//    count), so all of it stays in registers.  Every 16 charges the group's S is contracted with
-//    Dx, Dy, Dz.  Per-pair sums go through FP32 partials over 16 charges folded into double-float
-//    pairs; per-charge sums over the warp's 32 primitive pairs use a reduce-scatter (6 shuffles for
-//    four values) and compensated FP32 shared-memory atomics: the atomic returns the old value, so
-//    the rounding error of every addition is recovered exactly and kept in a second FP32 word.
-//  * l_A + l_B >= 3 (k_vgrad_cl): one lane per region-I charge, the pairs' coefficients read from
-//    shared memory (see the comment above k_vgrad_cl).
+// derivative algebra), as a charge-lane sweep: one lane per region-I charge (CPL charges per lane),
+// the primitive pairs' density-folded Hermite coefficients (D0, Dx, Dy, Dz, built in FP64 once
+// per call and rounded to FP32) read from shared memory batch by batch.  The per-charge Boys/R
+// recursion to order L+1 and the seven contractions run in FP32; per-charge sums are kept in
+// double-float registers, per-pair sums go through a warp reduce-scatter, compensated FP32
+// shared-memory atomics and one FP64 global atomic per block (see the comment above k_vgrad_cl).
 #include "pp_tile.cuh"
 
 namespace qmmm {
@@ -26,183 +19,13 @@ struct VgradF32 {
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
-constexpr int GFOLD = 16;
-
-template <int LA, int LB, int NT>
-__global__ void __launch_bounds__(NT, 1)
-k_vgrad_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
-            const float *__restrict__ boys_g, unsigned boys_bytes, const double *__restrict__ dm,
-            double *__restrict__ gqm, double *__restrict__ gchg, int *err)
-{
-    constexpr int L = LA + LB, NH = nherm(L), NH1 = nherm(L + 1);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint64_t bar;
-    {
-        // this block row's slice of the charge chunk (gridDim.y > 1 spreads small systems over more SMs)
-        const int per = (ch_end - ch_begin + (int)gridDim.y - 1) / (int)gridDim.y;
-        ch_begin += (int)blockIdx.y * per;
-        ch_end = min(ch_end, ch_begin + per);
-    }
-    if (ch_begin >= ch_end) return;
-    const int nch = ch_end - ch_begin;
-    float4 *chi = reinterpret_cast<float4 *>(smem_raw);
-    float4 *clo = chi + nch;
-    float *tab = reinterpret_cast<float *>(clo + nch);
-    // per-charge accumulators as FP32 (hi, lo) pairs: acc_hi[4 nch], acc_lo[4 nch]
-    float *acc_hi = reinterpret_cast<float *>(smem_raw + (size_t)nch * 2 * sizeof(float4) + boys_bytes);
-    float *acc_lo = acc_hi + 4 * nch;
-    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) acc_hi[k] = acc_lo[k] = 0.0f;
-    {
-        Seg s[3] = {{chi, rg.chg_hi + ch_begin, (unsigned)(nch * sizeof(float4))},
-                    {clo, rg.chg_lo + ch_begin, (unsigned)(nch * sizeof(float4))},
-                    {tab, boys_g, boys_bytes}};
-        if (!stage_segments(s, 3, &bar, err)) return;
-    }
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int ntile = (pp_end - pp_begin + 31) >> 5;
-    for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
-        const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
-        const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
-        float Ph[3], Plo[3];
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-            const double d = pl.P[x] - rg.centre[x];
-            split_grid(d, Ph[x], Plo[x]);
-        }
-
-        float D0[NH], Da[3][NH];  // registers: every index below is static (loops of constant trip count)
-        {
-            double d0[NH], dx[NH], dy[NH], dz[NH];
-            fold_density_dA<LA, LB, true>(pl, bd, dm, dx, dy, dz, d0);
-#pragma unroll
-            for (int k = 0; k < NH; ++k) {
-                D0[k] = (float)d0[k];
-                Da[0][k] = (float)dx[k];
-                Da[1][k] = (float)dy[k];
-                Da[2][k] = (float)dz[k];
-            }
-        }
-
-        // per-pair sums over charges as double-float pairs (no FP64 instruction in the charge loop)
-        float sh[6] = {0, 0, 0, 0, 0, 0}, sl[6] = {0, 0, 0, 0, 0, 0};
-        for (int c = 0; c < rg.ncls; ++c) {
-            const int lo = max(__ldg(rg.cls_off + c), ch_begin) - ch_begin;
-            const int hi = min(__ldg(rg.cls_off + c + 1), ch_end) - ch_begin;
-            if (lo >= hi) continue;
-            const double kap = __ldg(rg.cls_kappa + c);
-            const double td = kap > 0.0 ? kap / (pl.p + kap) : 1.0;
-            const float rho = (float)(pl.p * td), m2rho = -2.0f * rho, sq = (float)sqrt(td);
-            for (int j0 = lo; j0 < hi; j0 += GFOLD) {
-                const int j1 = min(hi, j0 + GFOLD);
-                float tex = 0, tey = 0, tez = 0;
-                float S[NH];  // sum over this group's charges of q R_tuv (k < NH)
-#pragma unroll
-                for (int k = 0; k < NH; ++k) S[k] = 0.0f;
-                for (int j = j0; j < j1; ++j) {
-                    const float4 ch = chi[j], cl = clo[j];
-                    const float X = (Ph[0] - ch.x) + (Plo[0] - cl.x);
-                    const float Y = (Ph[1] - ch.y) + (Plo[1] - cl.y);
-                    const float Z = (Ph[2] - ch.z) + (Plo[2] - cl.z);
-                    float T, Tl;
-                    boys_arg_f32(rho, X, Y, Z, T, Tl);
-                    float F[L + 2];
-                    boys_f32<L + 1>(T, F, tab, Tl);
-                    float Fn[L + 2];
-                    float sc = sq;
-#pragma unroll
-                    for (int n = 0; n <= L + 1; ++n) {
-                        Fn[n] = sc * F[n];
-                        sc *= m2rho;
-                    }
-                    float R[NH1];
-                    hermite_R_u<L + 1, float>(R, Fn, X, Y, Z);
-                    float e0 = 0, ex = 0, ey = 0, ez = 0;
-                    const float q = ch.w;
-#pragma unroll
-                    for (int t = 0; t <= L; ++t)
-#pragma unroll
-                        for (int u = 0; u <= L; ++u)
-#pragma unroll
-                            for (int w = 0; w <= L; ++w) {
-                                if (t + u + w > L) continue;
-                                const int k = hidx(t, u, w);
-                                e0 += D0[k] * R[k];
-                                ex += D0[k] * R[hidx(t + 1, u, w)];
-                                ey += D0[k] * R[hidx(t, u + 1, w)];
-                                ez += D0[k] * R[hidx(t, u, w + 1)];
-                                S[k] += q * R[k];
-                            }
-                    tex += q * ex; tey += q * ey; tez += q * ez;
-                    // per-charge sums over the 32 primitive pairs: 4 values -> halve twice (each lane
-                    // keeps one component summed over 4 lanes), then a 3-step butterfly; lane 8c ends
-                    // with component c = (dC_x, dC_y, dC_z, dq)
-                    float v0 = q * ex, v1 = q * ey, v2 = q * ez, v3 = -e0;
-                    {
-                        const bool up = lane & 16;
-                        float k0 = up ? v2 : v0, k1 = up ? v3 : v1;
-                        const float s0 = up ? v0 : v2, s1 = up ? v1 : v3;
-                        k0 += __shfl_xor_sync(FULL, s0, 16);
-                        k1 += __shfl_xor_sync(FULL, s1, 16);
-                        const bool up8 = lane & 8;
-                        float k = up8 ? k1 : k0;
-                        k += __shfl_xor_sync(FULL, up8 ? k0 : k1, 8);
-                        k += __shfl_xor_sync(FULL, k, 4);
-                        k += __shfl_xor_sync(FULL, k, 2);
-                        k += __shfl_xor_sync(FULL, k, 1);
-                        if ((lane & 7) == 0) {
-                            // component index: bit 4 -> (2,3) vs (0,1); bit 3 -> second of the pair
-                            const int comp = ((lane >> 4) << 1) | ((lane >> 3) & 1);
-                            // compensated atomic: recover the rounding error of the addition exactly
-                            float *h = acc_hi + 4 * j + comp;
-                            const float old = atomicAdd(h, k);
-                            const float sum = old + k, bv = sum - old;
-                            atomicAdd(acc_lo + 4 * j + comp, (old - (sum - bv)) + (k - bv));
-                        }
-                    }
-                }
-                // this group's sum_C q_C d_a(C) = sum_k Da_k S_k
-                float tdx = 0, tdy = 0, tdz = 0;
-#pragma unroll
-                for (int k = 0; k < NH; ++k) {
-                    tdx = fmaf(Da[0][k], S[k], tdx);
-                    tdy = fmaf(Da[1][k], S[k], tdy);
-                    tdz = fmaf(Da[2][k], S[k], tdz);
-                }
-                df_add(sh[0], sl[0], tdx); df_add(sh[1], sl[1], tdy); df_add(sh[2], sl[2], tdz);
-                df_add(sh[3], sl[3], tex); df_add(sh[4], sl[4], tey); df_add(sh[5], sl[5], tez);
-            }
-        }
-        const double sdx = (double)sh[0] + sl[0], sdy = (double)sh[1] + sl[1], sdz = (double)sh[2] + sl[2];
-        const double sex = (double)sh[3] + sl[3], sey = (double)sh[4] + sl[4], sez = (double)sh[5] + sl[5];
-        double g[6] = {-(sdx + aop * sex), -(sdy + aop * sey), -(sdz + aop * sez),
-                       sdx - bop * sex, sdy - bop * sey, sdz - bop * sez};
-        bool take[5], head;
-        seg_setup(pl.active ? pl.s : -1 - lane, lane, take, head);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) g[k] = seg_reduce(g[k], take);
-        if (head && pl.active) {
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-                atomicAdd(gqm + 3 * pl.atomA + x, g[x]);
-                atomicAdd(gqm + 3 * pl.atomB + x, g[3 + x]);
-            }
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 4 * nch; k += blockDim.x) {
-        const double v = (double)acc_hi[k] + (double)acc_lo[k];
-        if (v != 0.0) atomicAdd(gchg + 4 * (size_t)ch_begin + k, v);
-    }
-}
-
-
 // ---------------------------------------------------------------------------------------------
-// Charge-lane sweep (classes with l_A + l_B >= CL_MIN_L).  With one lane per primitive pair the
-// high-l classes hold D0, S and R (126 floats for (d, d), 288 for (f, f)) in registers and spill
-// to local memory; here a lane owns one region-I charge and holds only R, while the pairs'
-// density-folded coefficients (D0, Dx, Dy, Dz per Hermite index, one 16-byte broadcast load) come
-// from shared memory, batch by batch.  Per (pair, charge), all FP32:
+// Charge-lane sweep.  With one lane per primitive pair a lane holds D0, S and R (126 floats for
+// (d, d), 288 for (f, f)) and the high-l classes spill to local memory, while every charge needs a
+// reduction over the warp's pairs; here a lane owns region-I charges and holds only their R, the
+// pairs' density-folded coefficients (D0, Dx, Dy, Dz per Hermite index, one 16-byte broadcast
+// load) come from shared memory batch by batch, and the per-pair sums are reduced once per pair
+// and warp.  Per (pair, charge), all FP32:
 //   e0 = D0.R, e_a = D0.R(+a), h_a = D_a.R                         (7 contractions of nherm(L))
 //   charge: dq -= e0, dC_a += q e_a                                 (lane registers, double-float)
 //   pair:   sum over the block's charges of q h_a and q e_a        (warp reduce-scatter, then
@@ -506,35 +329,6 @@ static cudaError_t launch_cl(const BasisDev &bd, const RegionDev &rg, int pp_beg
     return cudaGetLastError();
 }
 
-// bytes of one order's FP32 Boys table (what a block stages)
-inline unsigned boys32_bytes_g() { return (unsigned)(BOYS_TAB_F * sizeof(float)); }
-
-template <int LA, int LB, int NT>
-static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                             int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
-                             int nsm, int nslice, cudaStream_t st)
-{
-    const unsigned tb = boys32_bytes_g();
-    const size_t per = 2 * sizeof(float4) + 4 * sizeof(double);
-    const int nper = (ch_end - ch_begin + nslice - 1) / nslice;  // charges per slice
-    const size_t smem = (size_t)nper * per + tb;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_vgrad_f32<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(CHUNK_GRAD * per + tb));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int ntile = (pp_end - pp_begin + 31) / 32;
-    int grid = (ntile + NT / 32 - 1) / (NT / 32);
-    if (grid > nsm) grid = nsm;
-    if (grid < 1) return cudaSuccess;
-    k_vgrad_f32<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
-                                                                  boys + (size_t)(LA + LB + 1) * BOYS_TAB_F, tb,
-                                                                  dm, gqm, gchg, err);
-    return cudaGetLastError();
-}
-
 template <int LA, int LB>
 cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
                                   int ch_end, const float *boys, const double *dm, double *gqm, double *gchg,
@@ -543,24 +337,17 @@ cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int p
                                   cudaStream_t st)
 {
     // charge-lane sweep: (charges per lane, blocks per SM) of variant 0 and 1 (cl_variant)
+    (void)err;
+    (void)nslice;
     constexpr int L = LA + LB;
-    if constexpr (L >= CL_MIN_L) {
-        if (variant == 1) {
-            if constexpr (cl_variant(L, 1, 0) > 0)
-                return launch_cl<LA, LB, cl_variant(L, 1, 0), cl_variant(L, 1, 1)>(
-                    bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, nsm, cl, st);
-        }
-        return launch_cl<LA, LB, cl_variant(L, 0, 0), cl_variant(L, 0, 1)>(bd, rg, pp_begin, pp_end, ch_begin,
-                                                                           ch_end, boys, dm, gqm, gchg, nsm, cl, st);
-    } else {
-        constexpr int W = sweep_wide_threads(SW_VGRAD_F32, class_of(LA, LB));
-        if constexpr (W > 0)
-            if (variant == 1)
-                return launch_nt<LA, LB, W>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err,
-                                            nsm, nslice, st);
-        return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
-                                      nslice, st);
+    if (variant == 1) {
+        if constexpr (cl_variant(L, 1, 0) > 0)
+            return launch_cl<LA, LB, cl_variant(L, 1, 0), cl_variant(L, 1, 1)>(bd, rg, pp_begin, pp_end, ch_begin,
+                                                                               ch_end, boys, dm, gqm, gchg, nsm, cl,
+                                                                               st);
     }
+    return launch_cl<LA, LB, cl_variant(L, 0, 0), cl_variant(L, 0, 1)>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
+                                                                       boys, dm, gqm, gchg, nsm, cl, st);
 }
 
 template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;

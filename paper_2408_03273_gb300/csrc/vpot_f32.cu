@@ -95,7 +95,7 @@ k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
                         sc *= m2rho;
                     }
                     float R[NH];
-                    hermite_R<L, float>(R, Fn, X, Y, Z);
+                    hermite_R_u<L, float>(R, Fn, X, Y, Z);
 #pragma unroll
                     for (int k = 0; k < NH; ++k) Wt[k] += R[k];
                 }
