@@ -127,6 +127,21 @@ double pair_bound(double a, double b, double ca, double cb, double ab2, int la, 
     return std::fabs(ca * cb) * std::exp(-a * b / p * ab2) * std::pow(PI / p, 1.5) * std::pow(pa, la) * std::pow(pb, lb);
 }
 
+// The largest pair_bound over every distance in [|AB| - 2 margin, |AB| + 2 margin]: the Gaussian
+// factor at the shortest distance, the polynomial factors at the longest.  A pair kept by this
+// bound stays kept while no QM atom moves farther than `margin` from where the list was planned.
+double pair_bound_margin(double a, double b, double ca, double cb, double ab2, int la, int lb, double margin)
+{
+    const double p = a + b, r = 1.0 / std::sqrt(p), ab = std::sqrt(ab2);
+    const double lo = std::max(0.0, ab - 2.0 * margin), hi = ab + 2.0 * margin;
+    const double pa = b / p * hi + r, pb = a / p * hi + r;
+    return std::fabs(ca * cb) * std::exp(-a * b / p * lo * lo) * std::pow(PI / p, 1.5) * std::pow(pa, la) *
+           std::pow(pb, lb);
+}
+
+// QM displacement (bohr) the screened pair list tolerates before it is planned again
+constexpr double SCREEN_MARGIN = 0.25;
+
 }  // namespace
 
 struct qmmm_handle {
@@ -147,6 +162,8 @@ struct qmmm_handle {
     int ncls = 0;
     long long n_sp = 0, n_pp = 0;
     int class_off[NCLASS + 1] = {0};
+    std::vector<double> screen_xyz;  // QM positions the pair list was screened at
+    long long plan_gen = 0;          // incremented whenever the pair list is planned again
     long long sp_class[NCLASS] = {0};
     int nI = 0;
     std::vector<int> cls_off_I;
@@ -383,6 +400,99 @@ int select_recip(qmmm_handle *h)
     return QMMM_OK;
 }
 
+// Shell pairs (l_A >= l_B) sorted by angular class, primitive pairs screened (R16, with the
+// margin of pair_bound_margin), uploaded; the QM positions used are kept so that
+// qmmm_set_positions plans again once a QM atom has moved farther than SCREEN_MARGIN.
+int plan_pairs(qmmm_handle *h)
+{
+    const int nshell = h->nshell;
+    std::vector<std::vector<SPair>> sp_cls(NCLASS);
+    std::vector<std::vector<uint32_t>> pp_cls(NCLASS);
+    auto ab2_of = [&](int i, int j) {
+        const double *A = &h->qm_xyz[3 * h->shell_atom[i]], *B = &h->qm_xyz[3 * h->shell_atom[j]];
+        return (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+    };
+    // pass 1: largest screening value
+    double vmax = 0.0;
+    for (int i = 0; i < nshell; ++i)
+        for (int j = i; j < nshell; ++j) {
+            const double ab2 = ab2_of(i, j);
+            for (int ka = 0; ka < h->shell_nprim[i]; ++ka)
+                for (int kb = 0; kb < h->shell_nprim[j]; ++kb) {
+                    const double a = h->exps[h->shell_off[i] + ka], b = h->exps[h->shell_off[j] + kb];
+                    const double v = pair_bound(a, b, h->ncoef[h->shell_off[i] + ka], h->ncoef[h->shell_off[j] + kb],
+                                                ab2, h->shell_l[i], h->shell_l[j]);
+                    vmax = std::max(vmax, v);
+                }
+        }
+    // pass 2: the pairs kept, with the displacement margin
+    const double thr = h->screen_tol * vmax;
+    long long nsp = 0;
+    for (int i = 0; i < nshell; ++i)
+        for (int j = i; j < nshell; ++j) {
+            int sA = i, sB = j;
+            if (h->shell_l[j] > h->shell_l[i]) std::swap(sA, sB);
+            const int cls = class_of(h->shell_l[sA], h->shell_l[sB]);
+            const double ab2 = ab2_of(sA, sB);
+            std::vector<uint32_t> kept;
+            for (int ka = 0; ka < h->shell_nprim[sA]; ++ka)
+                for (int kb = 0; kb < h->shell_nprim[sB]; ++kb) {
+                    const double a = h->exps[h->shell_off[sA] + ka], b = h->exps[h->shell_off[sB] + kb];
+                    const double v = pair_bound_margin(a, b, h->ncoef[h->shell_off[sA] + ka],
+                                                       h->ncoef[h->shell_off[sB] + kb], ab2, h->shell_l[sA],
+                                                       h->shell_l[sB], SCREEN_MARGIN);
+                    if (h->screen_tol == 0.0 || v >= thr) kept.push_back((uint32_t)((ka << 4) | kb));
+                }
+            if (kept.empty()) continue;
+            const int sidx = (int)sp_cls[cls].size();
+            sp_cls[cls].push_back(SPair{sA, sB, h->shell_ao[sA], h->shell_ao[sB]});
+            for (uint32_t c : kept) pp_cls[cls].push_back(((uint32_t)sidx << 8) | c);  // re-based below
+            ++nsp;
+        }
+    if (nsp >= (1LL << 24)) return fail(QMMM_ERR_ARG, "too many shell pairs (>= 2^24)");
+    std::vector<SPair> sp_all;
+    std::vector<uint32_t> pp_all;
+    h->class_off[0] = 0;
+    for (int c = 0; c < NCLASS; ++c) {
+        const uint32_t base = (uint32_t)sp_all.size();
+        for (const SPair &sp : sp_cls[c]) sp_all.push_back(sp);
+        for (uint32_t code : pp_cls[c]) pp_all.push_back(((((code >> 8) + base)) << 8) | (code & 0xff));
+        h->class_off[c + 1] = (int)pp_all.size();
+        h->sp_class[c] = (long long)sp_cls[c].size();
+    }
+    h->n_sp = (long long)sp_all.size();
+    h->n_pp = (long long)pp_all.size();
+    int rc;
+    if ((rc = h->sp.ensure(std::max<size_t>(sp_all.size(), 1))) || (rc = h->pp.ensure(std::max<size_t>(pp_all.size(), 1))))
+        return rc;
+    if (!sp_all.empty())
+        CUDA_TRY(cudaMemcpy(h->sp.p, sp_all.data(), sp_all.size() * sizeof(SPair), cudaMemcpyHostToDevice));
+    if (!pp_all.empty())
+        CUDA_TRY(cudaMemcpy(h->pp.p, pp_all.data(), pp_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    h->screen_xyz = h->qm_xyz;
+    ++h->plan_gen;
+    h->V_valid = false;
+    return QMMM_OK;
+}
+
+// Plan the pair list again if a QM atom moved farther than SCREEN_MARGIN since it was planned.
+int replan_if_moved(qmmm_handle *h)
+{
+    if (h->screen_tol == 0.0 || h->screen_xyz.size() != h->qm_xyz.size()) return QMMM_OK;
+    double d2max = 0.0;
+    for (int j = 0; j < h->natm; ++j) {
+        double d2 = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            const double d = h->qm_xyz[3 * j + x] - h->screen_xyz[3 * j + x];
+            d2 += d * d;
+        }
+        d2max = std::max(d2max, d2);
+    }
+    if (d2max <= SCREEN_MARGIN * SCREEN_MARGIN) return QMMM_OK;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));  // kernels in flight may still read the old list
+    return plan_pairs(h);
+}
+
 int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, const double *mm_q)
 {
     cudaStream_t st = h->stream;
@@ -396,6 +506,10 @@ int run_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xyz, co
             std::memcpy(h->qm_xyz.data(), qm_xyz, 3 * h->natm * sizeof(double));
             CUDA_TRY(cudaMemcpyAsync(h->qm.p, h->qm_xyz.data(), 3 * h->natm * sizeof(double), cudaMemcpyHostToDevice, st));
         }
+    }
+    if (qm_xyz) {
+        int rc = replan_if_moved(h);
+        if (rc) return rc;
     }
     for (int x = 0; x < 3; ++x) {
         double c = 0.0;
@@ -914,66 +1028,9 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         for (int k = 0; k < n; ++k) h->ncoef[o + k] /= std::sqrt(ss);
     }
 
-    // shell pairs sorted by class; primitive pairs screened
     {
-        struct Cand { int s; int code; double v; };
-        std::vector<std::vector<SPair>> sp_cls(NCLASS);
-        std::vector<std::vector<uint32_t>> pp_cls(NCLASS);
-        std::vector<double> vals;
-        double vmax = 0.0;
-        // pass 1: maximum screening value
-        for (int i = 0; i < nshell; ++i)
-            for (int j = i; j < nshell; ++j) {
-                const double *A = &h->qm_xyz[3 * h->shell_atom[i]], *B = &h->qm_xyz[3 * h->shell_atom[j]];
-                const double ab2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
-                for (int ka = 0; ka < h->shell_nprim[i]; ++ka)
-                    for (int kb = 0; kb < h->shell_nprim[j]; ++kb) {
-                        const double a = h->exps[h->shell_off[i] + ka], b = h->exps[h->shell_off[j] + kb];
-                        const double v = pair_bound(a, b, h->ncoef[h->shell_off[i] + ka], h->ncoef[h->shell_off[j] + kb],
-                                                    ab2, h->shell_l[i], h->shell_l[j]);
-                        vmax = std::max(vmax, v);
-                    }
-            }
-        const double thr = h->screen_tol * vmax;
-        long long nsp = 0;
-        for (int i = 0; i < nshell; ++i)
-            for (int j = i; j < nshell; ++j) {
-                int sA = i, sB = j;
-                if (h->shell_l[j] > h->shell_l[i]) std::swap(sA, sB);
-                const int cls = class_of(h->shell_l[sA], h->shell_l[sB]);
-                const double *A = &h->qm_xyz[3 * h->shell_atom[sA]], *B = &h->qm_xyz[3 * h->shell_atom[sB]];
-                const double ab2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
-                std::vector<uint32_t> kept;
-                for (int ka = 0; ka < h->shell_nprim[sA]; ++ka)
-                    for (int kb = 0; kb < h->shell_nprim[sB]; ++kb) {
-                        const double a = h->exps[h->shell_off[sA] + ka], b = h->exps[h->shell_off[sB] + kb];
-                        const double v = pair_bound(a, b, h->ncoef[h->shell_off[sA] + ka], h->ncoef[h->shell_off[sB] + kb],
-                                                    ab2, h->shell_l[sA], h->shell_l[sB]);
-                        if (h->screen_tol == 0.0 || v >= thr) kept.push_back((uint32_t)((ka << 4) | kb));
-                    }
-                if (kept.empty()) continue;
-                const int sidx = (int)sp_cls[cls].size();
-                sp_cls[cls].push_back(SPair{sA, sB, h->shell_ao[sA], h->shell_ao[sB]});
-                for (uint32_t c : kept) pp_cls[cls].push_back(((uint32_t)sidx << 8) | c);  // re-based below
-                ++nsp;
-            }
-        if (nsp >= (1LL << 24)) return fail(QMMM_ERR_ARG, "too many shell pairs (>= 2^24)");
-        std::vector<SPair> sp_all;
-        std::vector<uint32_t> pp_all;
-        h->class_off[0] = 0;
-        for (int c = 0; c < NCLASS; ++c) {
-            const uint32_t base = (uint32_t)sp_all.size();
-            for (const SPair &s : sp_cls[c]) sp_all.push_back(s);
-            for (uint32_t code : pp_cls[c]) pp_all.push_back(((((code >> 8) + base)) << 8) | (code & 0xff));
-            h->class_off[c + 1] = (int)pp_all.size();
-            h->sp_class[c] = (long long)sp_cls[c].size();
-        }
-        h->n_sp = (long long)sp_all.size();
-        h->n_pp = (long long)pp_all.size();
-        int rc;
-        if ((rc = h->sp.ensure(sp_all.size())) || (rc = h->pp.ensure(pp_all.size()))) return rc;
-        CUDA_TRY(cudaMemcpy(h->sp.p, sp_all.data(), sp_all.size() * sizeof(SPair), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(h->pp.p, pp_all.data(), pp_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        int rc = plan_pairs(h);
+        if (rc) return rc;
     }
 
     // MM charges: width classes, internal order by (class, cell)
@@ -1583,6 +1640,7 @@ std::vector<long long> batch_key(const qmmm_batch *b, const double *const *dm, d
     for (size_t i = 0; i < b->f.size(); ++i) {
         const qmmm_handle *h = b->f[i];
         k.push_back(h->nI);
+        k.push_back(h->plan_gen);
         k.push_back(h->precision);
         for (int kind = 0; kind < SW_NKIND; ++kind)
             for (int c = 0; c < NCLASS; ++c) {

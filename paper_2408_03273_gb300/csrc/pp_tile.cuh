@@ -241,7 +241,7 @@ constexpr int CL_BPB = 8;  // batches per block
 // each lane independent chains; the register budget (65536 / (256 x blocks per SM)) bounds them.
 __host__ __device__ constexpr int cl_variant(int L, int v, int field)
 {
-    constexpr int T[7][2][2] = {{{4, 2}, {8, 1}}, {{4, 2}, {2, 2}}, {{2, 2}, {1, 2}}, {{1, 2}, {2, 1}},
+    constexpr int T[7][2][2] = {{{4, 2}, {2, 3}}, {{4, 2}, {2, 3}}, {{2, 2}, {1, 3}}, {{1, 2}, {2, 1}},
                                 {{1, 2}, {2, 1}}, {{1, 1}, {0, 0}}, {{1, 1}, {0, 0}}};
     return (L >= 0 && L <= 6) ? T[L][v][field] : 0;
 }
