@@ -140,7 +140,7 @@ double pair_bound_margin(double a, double b, double ca, double cb, double ab2, i
 }
 
 // QM displacement (bohr) the screened pair list tolerates before it is planned again
-constexpr double SCREEN_MARGIN = 0.25;
+constexpr double SCREEN_MARGIN = 0.1;
 
 }  // namespace
 
@@ -383,10 +383,10 @@ int select_recip(qmmm_handle *h)
         h->ew.tcb.bpl = h->tc_bpl.p;
         h->ew.tcb.part = h->tc_part.p;
         h->ew.tcb.bmax = h->tc_bmax.p;
-        const MmrShape &m0 = h->ew.mms;
-        if (m0.supported) {
+        const MmrShape &m0 = h->ew.mms[0], &m1 = h->ew.mms[1];
+        if (m0.supported || m1.supported) {
             if ((rc = h->mmr_phase.ensure(m0.phase_rows)) ||
-                (rc = h->mmr_bpl.ensure(m0.bplane_words)) ||
+                (rc = h->mmr_bpl.ensure(std::max(m0.bplane_words, m1.bplane_words))) ||
                 (rc = h->mmr_cscale.ensure(3 * (h->kmax[0] + 1))))
                 return rc;
             // the rows of padding charges are copied but never used; keep them defined
@@ -1175,7 +1175,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sums = h->sums.p;
         h->ew.err = h->err.p;
         tc_sf_shape(e, h->ew.tcs);
-        tc_mmr_shape(e, 5, MMR_NP, h->ew.mms);
+        tc_mmr_shape(e, 5, MMR_NP, h->ew.mms[0]);
+        tc_mmr_shape(e, 4, MMR_NP, h->ew.mms[1]);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));

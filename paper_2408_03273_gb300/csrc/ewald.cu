@@ -1236,7 +1236,7 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
         k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.atom_ph, w.A, w.Az,
                                                          df ? w.Adf : nullptr, df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        const MmrShape &ms = w.mms;
+        const MmrShape &ms = w.mms[df ? 1 : 0];
         if (w.recip == 1 && ms.supported) {
             if ((err = launch_mm_recip_tc(e, ms, w.mmb, w.A, w.Az, dq_int, dR_int, w.err, st)) != cudaSuccess)
                 return err;

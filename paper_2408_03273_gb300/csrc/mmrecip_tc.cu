@@ -13,9 +13,12 @@
 // A operand (M = 128 charges x K): the outer products Y_i(n_y) Z_i(n_z), digitised on chip from
 // fixed-point phase rows staged by TMA; B operand (N = 112 rows (k, n_x, re/im) x K): C_k divided
 // by a power of two per (k, n_x) so that |C| <= 1, digitised once per call into the shared-memory
-// layout.  Digits as for the structure factor (tc_digits.cuh).  FP64 class on both precision
-// paths: seven planes per operand, 28 plane pairs per K-step into five FP32 accumulators in tensor
-// memory (levels 0..3 kept apart, 4..6 merged; the three channels then take two N tiles).  Level 0
+// layout.  Digits as for the structure factor (tc_digits.cuh): seven planes per operand (48-bit
+// fixed point) on both precision paths, 28 plane pairs per K-step into FP32 accumulators in tensor
+// memory.  FP64 path: five accumulators (levels 0..3 kept apart, 4..6 merged), so at most 96 N rows
+// per tile; mixed path: four (levels 0..2 apart, 3..6 merged: about 7e-11 of the reciprocal part,
+// far below the FP32 region-I sweep's error), 128 rows per tile, so the three channels take one
+// N tile fewer and the A operand is digitised once less.  Level 0
 // is exact for any input while 4096 x 2 N_y N_z < 2^24 (kmax <= 20) and beyond that unless the
 // row-normalised coefficients, which decay as exp(-G^2/4 alpha^2), sum to more than 2^11 in
 // magnitude; levels 1 to 3 are sums of random-sign digit products, typically 2^17 or less.  The epilogue

@@ -174,7 +174,8 @@ struct EwaldBuf {
     int recip = 0;               // reciprocal sums: 0 CUDA cores (FP64 / double-float), 1 tensor cores
     TcShape tcs;
     TcBuf tcb;
-    MmrShape mms;                // MM-side sum (FP64 class: 7 planes, 5 accumulators), both precisions
+    MmrShape mms[2];             // MM-side sum, 7 planes: [0] FP64 path (5 accumulators: levels 0-3
+                                 // exact), [1] mixed path (4: levels 0-2 exact, 3-6 merged)
     MmrBuf mmb;
     int *err = nullptr;          // device error word of the handle
 };
