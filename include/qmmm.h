@@ -120,9 +120,10 @@ int qmmm_set_stream(qmmm_handle *h, void *stream);
  * in FP64, rounded to FP32).  Per-pair and per-charge sums are carried in double-float (FP32
  * pairs) and finished in FP64.  Everything else stays FP64-class on both paths: the per-pair
  * Hermite/density algebra, the nuclear-MM term, the real-space Ewald sums, the multipoles and
- * moment integrals, and the two reciprocal Ewald sums, which on the tensor cores are exact
- * products of BF16 digit planes of 48-bit fixed-point operands (QMMM_RECIP_TENSOR) and on the
- * CUDA cores FP64 (double-float on the mixed path, about 47 bits).  Measured error of the
+ * moment integrals.  The two reciprocal Ewald sums are, on the tensor cores, exact products of
+ * BF16 digit planes of fixed-point operands (QMMM_RECIP_TENSOR: 48-bit, except the mixed path's
+ * MM-side sum, 34-bit, about 1e-10 relative) and on the CUDA cores FP64 (double-float on the
+ * mixed path, about 47 bits).  Measured error of the
  * mixed path against FP64: 1e-7 to 3e-7 in V (relative Frobenius norm) and up to 8e-7 in the
  * gradients (max |error| / max |gradient|) on the benchmark workloads. */
 int qmmm_set_precision(qmmm_handle *h, int precision);
@@ -134,8 +135,9 @@ int qmmm_set_precision(qmmm_handle *h, int precision);
  *   QMMM_RECIP_TENSOR: each sum as a product of two matrices on the BF16 tensor cores, every
  *     operand split exactly into seven digit planes (a leading one and six of 7 bits, 48-bit
  *     fixed point) with exact FP32 accumulation of the leading digit levels: FP64 class (about
- *     1e-12 relative on the region-II potential and the MM gradients).  The mixed path keeps
- *     three exact levels in the MM-side sum instead of four (about 1e-9 relative; one N tile);
+ *     1e-12 relative on the region-II potential and the MM gradients).  The mixed path's MM-side
+ *     sum takes five planes (34-bit fixed point) and three exact levels instead of seven and four
+ *     (about 1e-10 relative; 15 plane products instead of 28, one N tile fewer);
  *     the MM-side sum stays on the CUDA cores when 2 kz + 1 < 8;
  *   QMMM_RECIP_AUTO [default]: QMMM_RECIP_TENSOR when (kx + 1)(2 ky + 1)(2 kz + 1) N_MM >= 4e7,
  *     else QMMM_RECIP_CUDA_CORES (small systems, where the extra launches outweigh the work).

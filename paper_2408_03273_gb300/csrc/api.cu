@@ -321,7 +321,8 @@ int check_device_errors(qmmm_handle *h)
 cudaError_t mark(qmmm_handle *h, int k) { return h->quiet ? cudaSuccess : cudaEventRecord(h->ev[k], h->stream); }
 
 // End of a call: wait for the device, check its error flag and read the `nmarks` timing marks
-// (3: sweep = mark 0..1, rest = 1..2; 2: everything = 0..1).  Inside a batch capture nothing
+// (3: sweep = mark 0..1, rest = 1..2; 4: the same with mark 3..0 added to the rest; 2:
+// everything = 0..1).  Inside a batch capture nothing
 // waits: the batch checks every frame after the graph has run.
 int finish(qmmm_handle *h, int nmarks)
 {
@@ -331,6 +332,12 @@ int finish(qmmm_handle *h, int nmarks)
     if (nmarks == 3) {
         cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+    } else if (nmarks == 4) {
+        float before = 0.f;
+        cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&before, h->ev[3], h->ev[0]);
+        cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
+        h->t_other += before;
     } else if (nmarks == 2) {
         h->t_sweep = 0.f;
         cudaEventElapsedTime(&h->t_other, h->ev[0], h->ev[1]);
@@ -1175,8 +1182,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.sums = h->sums.p;
         h->ew.err = h->err.p;
         tc_sf_shape(e, h->ew.tcs);
-        tc_mmr_shape(e, 5, MMR_NP, h->ew.mms[0]);
-        tc_mmr_shape(e, 4, MMR_NP, h->ew.mms[1]);
+        tc_mmr_shape(e, 5, MMR_NP_FP64, h->ew.mms[0]);
+        tc_mmr_shape(e, 4, MMR_NP_MIXED, h->ew.mms[1]);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
@@ -1348,25 +1355,37 @@ int qmmm_energy(qmmm_handle *h, const double *dmat, double *E)
     return finish(h, 0);
 }
 
-int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_dRmm, double *dE_dq)
+// The forces in three parts, so that a batch can run the region-I adjoint sweeps of all its
+// frames together between the first and the last.  forces_begin: the density, cleared outputs,
+// multipoles with the Pulay term, the nuclear-MM region-I term and the multipolar Ewald sums
+// (everything but the sweep; all of them add into the same gradients as the sweep).
+static int forces_begin(qmmm_handle *h, const double *dmat, const double **ddm)
 {
-    if (!h || !dmat) return fail(QMMM_ERR_ARG, "null handle or density");
     cudaStream_t st = h->stream;
     int rc;
-    const double *ddm;
     const size_t n2 = (size_t)h->nao * h->nao;
-    if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
+    CUDA_TRY(mark(h, 3));
+    if ((rc = stage_input(h, dmat, n2, h->dm, ddm))) return rc;
     CUDA_TRY(cudaMemsetAsync(h->gqm.p, 0, 3 * (size_t)h->natm * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(h->gchg.p, 0, 4 * (size_t)std::max(h->nI, 1) * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(h->dq_int.p, 0, (size_t)std::max(h->nmm, 1) * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(h->dR_int.p, 0, 3 * (size_t)std::max(h->nmm, 1) * sizeof(double), st));
-    // multipoles and the Pulay term
-    if ((rc = compute_multipoles(h, ddm, nullptr, MOM_PULAY))) return rc;
-    // region-I adjoint sweep
+    if ((rc = compute_multipoles(h, *ddm, nullptr, MOM_PULAY))) return rc;
+    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, h->gqm.p,
+                           h->gchg.p, 1, st));
+    const EwaldDev e = h->ewald();
+    CUDA_TRY(launch_ewald_mm(e, h->rI.p, h->nmm > 0 ? h->nI : 0, h->mult.p, h->phi.p, h->ew, h->dq_int.p,
+                             h->dR_int.p, h->gchg.p, h->gqm.p, h->precision == QMMM_MIXED, st));
+    return QMMM_OK;
+}
+
+// The region-I adjoint sweep of one frame (all classes concurrently).
+static int forces_sweep(qmmm_handle *h, const double *ddm)
+{
+    int rc;
     const int kind = sweep_kind(h, true), ch = chunk_for_kind(kind);
     if (kind == SW_VGRAD_F32 && (rc = ensure_cl(h))) return rc;
     const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
-    CUDA_TRY(mark(h, 0));
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
         rc = run_classes(
@@ -1378,28 +1397,38 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
             ns, std::max(1, std::min(8, (c1 - c0) / 128)), c1 - c0);
         if (rc) return rc;
     }
-    CUDA_TRY(mark(h, 1));
-    // nuclear-MM region I, multipolar Ewald (MM side + QM tensor part), scatter to MM atoms
-    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, h->gqm.p,
-                           h->gchg.p, 1, st));
-    const EwaldDev e = h->ewald();
+    return QMMM_OK;
+}
+
+// Region-I charge gradients to the MM atoms, the user's order, copies out.
+static int forces_end(qmmm_handle *h, double *dE_dRqm, double *dE_dRmm, double *dE_dq)
+{
+    cudaStream_t st = h->stream;
+    int rc;
     if (h->nmm > 0) {
-        CUDA_TRY(launch_ewald_mm(e, h->rI.p, h->nI, h->mult.p, h->phi.p, h->ew, h->dq_int.p, h->dR_int.p, h->gchg.p,
-                                 h->gqm.p, h->precision == QMMM_MIXED, st));
         CUDA_TRY(launch_scatter_region(h->rI_idx.p, h->nI, h->gchg.p, h->dq_int.p, h->dR_int.p, st));
         CUDA_TRY(launch_unpermute(h->dq_int.p, h->dR_int.p, h->dperm.p, h->nmm, h->dq_out.p, h->dR_out.p, st));
-    } else {
-        CUDA_TRY(launch_ewald_mm(e, h->rI.p, 0, h->mult.p, h->phi.p, h->ew, h->dq_int.p, h->dR_int.p, h->gchg.p,
-                                 h->gqm.p, h->precision == QMMM_MIXED, st));
     }
     if ((rc = copy_out(h, dE_dRqm, h->gqm.p, 3 * (size_t)h->natm))) return rc;
     if (h->nmm > 0) {
         if ((rc = copy_out(h, dE_dRmm, h->dR_out.p, 3 * (size_t)h->nmm))) return rc;
         if ((rc = copy_out(h, dE_dq, h->dq_out.p, (size_t)h->nmm))) return rc;
     }
-    CUDA_TRY(mark(h, 2));
-    if ((rc = finish(h, 3))) return rc;
     return QMMM_OK;
+}
+
+int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_dRmm, double *dE_dq)
+{
+    if (!h || !dmat) return fail(QMMM_ERR_ARG, "null handle or density");
+    int rc;
+    const double *ddm;
+    if ((rc = forces_begin(h, dmat, &ddm))) return rc;
+    CUDA_TRY(mark(h, 0));
+    if ((rc = forces_sweep(h, ddm))) return rc;
+    CUDA_TRY(mark(h, 1));
+    if ((rc = forces_end(h, dE_dRqm, dE_dRmm, dE_dq))) return rc;
+    CUDA_TRY(mark(h, 2));
+    return finish(h, 4);
 }
 
 int qmmm_get_info(const qmmm_handle *h, qmmm_info_t *info)
@@ -1609,6 +1638,15 @@ struct qmmm_batch {
     std::vector<cudaEvent_t> done;  // frame f complete (recorded by the graph, for timing)
     std::vector<cudaEvent_t> join;  // frame f joins the batch stream
     cudaEvent_t start = nullptr, fork = nullptr;
+    // batched region-I adjoint of the mixed frames: frame f reached its sweep (adone), all did
+    // (all_a), class c's sweep over every frame done (cjoin), all classes done (sweeps); per class
+    // a stream, a device job table region (jobs + job_off[c]) and a work counter
+    std::vector<cudaEvent_t> adone;
+    cudaEvent_t all_a = nullptr, sweeps = nullptr, cjoin[NCLASS] = {};
+    cudaStream_t cst[NCLASS] = {};
+    DBuf<ClJob> jobs;
+    DBuf<int> counter;
+    int job_off[NCLASS] = {}, njob[NCLASS] = {}, nthr[NCLASS] = {}, nitems[NCLASS] = {}, variant[NCLASS] = {};
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> key;  // what the graph was recorded for
     std::vector<int> planned_nI; // each frame's region-I size at the last plain pass (buffer sizes)
@@ -1625,6 +1663,16 @@ struct qmmm_batch {
             if (s) cudaStreamDestroy(s);
         if (start) cudaEventDestroy(start);
         if (fork) cudaEventDestroy(fork);
+        for (cudaEvent_t e : adone)
+            if (e) cudaEventDestroy(e);
+        if (all_a) cudaEventDestroy(all_a);
+        if (sweeps) cudaEventDestroy(sweeps);
+        for (int c = 0; c < NCLASS; ++c) {
+            if (cjoin[c]) cudaEventDestroy(cjoin[c]);
+            if (cst[c]) cudaStreamDestroy(cst[c]);
+        }
+        jobs.release();
+        counter.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -1669,6 +1717,93 @@ int batch_frame(qmmm_handle *h, const double *dm, double *V, double *E, double *
     return qmmm_forces(h, dm, gq, gm, gc);
 }
 
+// Frames whose region-I adjoint the batch runs for all of them at once: the charge-lane sweep
+// (mixed precision) over a non-empty region I.
+bool batch_defers(const qmmm_handle *h) { return sweep_kind(h, true) == SW_VGRAD_F32 && h->nI > 0; }
+
+// The job tables of the batched adjoint: per class, one job per deferring frame with pairs in
+// that class, in descending order of the pair batches per item (the longest items are taken
+// first), uploaded to b->jobs.  Every class takes one block variant: that of the frame with the
+// most pair x charge work in the class.
+int batch_build_jobs(qmmm_batch *b, const double *const *dm)
+{
+    std::vector<ClJob> all;
+    for (int c = 0; c < NCLASS; ++c) {
+        b->job_off[c] = (int)all.size();
+        b->njob[c] = b->nthr[c] = b->nitems[c] = 0;
+        const int L = la_of_class(c) + lb_of_class(c);
+        double best = -1.0;
+        b->variant[c] = 0;
+        for (qmmm_handle *h : b->f) {
+            if (!batch_defers(h)) continue;
+            const double w = (double)(h->class_off[c + 1] - h->class_off[c]) * h->nI;
+            if (w > best) {
+                best = w;
+                b->variant[c] = h->cls_variant[SW_VGRAD_F32][c];
+            }
+        }
+        std::vector<ClJob> cj;
+        for (size_t i = 0; i < b->f.size(); ++i) {
+            qmmm_handle *h = b->f[i];
+            const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
+            if (!batch_defers(h) || p1 <= p0) continue;
+            ClJob J{};
+            J.bd = h->basis();
+            J.rg = h->region();
+            J.dm = dm[i];
+            J.rec = h->cl_rec.p + h->cl_rec_off[c];
+            J.psum = h->cl_psum.p + h->cl_psum_off[c];
+            J.gqm = h->gqm.p;
+            J.gchg = h->gchg.p;
+            J.pp_begin = p0;
+            J.pp_end = p1;
+            J.ch_begin = 0;
+            J.ch_end = h->nI;
+            cl_decompose(L, b->variant[c], p1 - p0, h->nI, h->ncls, J.gx, J.ntile);
+            cj.push_back(J);
+        }
+        const int nb = cl_batch(L);
+        auto bper = [nb](const ClJob &J) { return ((J.pp_end - J.pp_begin + nb - 1) / nb + J.gx - 1) / J.gx; };
+        std::stable_sort(cj.begin(), cj.end(), [&](const ClJob &x, const ClJob &y) { return bper(x) > bper(y); });
+        int item = 0, thr = 0;
+        for (ClJob &J : cj) {
+            J.item0 = item;
+            J.thr0 = thr;
+            item += J.gx * J.ntile;
+            thr += (J.pp_end - J.pp_begin + 31) / 32 * 32;
+        }
+        b->njob[c] = (int)cj.size();
+        b->nitems[c] = item;
+        b->nthr[c] = thr;
+        all.insert(all.end(), cj.begin(), cj.end());
+    }
+    int rc;
+    if ((rc = b->jobs.ensure(std::max<size_t>(all.size(), 1))) || (rc = b->counter.ensure(NCLASS))) return rc;
+    if (!all.empty())
+        CUDA_TRY(cudaMemcpy(b->jobs.p, all.data(), all.size() * sizeof(ClJob), cudaMemcpyHostToDevice));
+    return QMMM_OK;
+}
+
+// The batched adjoint inside the capture: every class over the deferring frames once they have all
+// reached their sweep (one launch of each of the class's three kernels), highest class first.
+int batch_sweeps(qmmm_batch *b, const std::vector<int> &deferred)
+{
+    for (int i : deferred) CUDA_TRY(cudaStreamWaitEvent(b->stream, b->adone[i], 0));
+    CUDA_TRY(cudaEventRecord(b->all_a, b->stream));
+    const qmmm_handle *h0 = b->f[deferred[0]];
+    for (int i = 0; i < NCLASS; ++i) {
+        const int c = NCLASS - 1 - i;
+        if (!b->njob[c]) continue;
+        CUDA_TRY(cudaStreamWaitEvent(b->cst[c], b->all_a, 0));
+        CUDA_TRY(launch_vgrad_cl_jobs(c, b->jobs.p + b->job_off[c], b->njob[c], b->nthr[c], b->nitems[c],
+                                      b->counter.p + c, h0->boys32.p, b->variant[c], h0->nsm, b->cst[c]));
+        CUDA_TRY(cudaEventRecord(b->cjoin[c], b->cst[c]));
+        CUDA_TRY(cudaStreamWaitEvent(b->stream, b->cjoin[c], 0));
+    }
+    CUDA_TRY(cudaEventRecord(b->sweeps, b->stream));
+    return QMMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1694,10 +1829,18 @@ int qmmm_batch_create(qmmm_handle *const *frames, int nframes, void *stream, qmm
     b->join.assign(nframes, nullptr);
     CUDA_TRY(cudaEventCreate(&b->start));
     CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    b->adone.assign(nframes, nullptr);
     for (int i = 0; i < nframes; ++i) {
         CUDA_TRY(cudaStreamCreateWithFlags(&b->fst[i], cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreate(&b->done[i]));
         CUDA_TRY(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&b->adone[i], cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaEventCreateWithFlags(&b->all_a, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->sweeps, cudaEventDisableTiming));
+    for (int c = 0; c < NCLASS; ++c) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->cst[c], cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&b->cjoin[c], cudaEventDisableTiming));
     }
     b->ms.assign(nframes + 1, 0.0);
     *out = b.release();
@@ -1744,15 +1887,57 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
             b->planned_nI.assign(n, 0);
             for (int i = 0; i < n; ++i) b->planned_nI[i] = b->f[i]->nI;
         }
+        // the frames whose adjoint sweeps run batched: their scratch sized and their job tables
+        // written before the capture (nothing is allocated or copied synchronously inside it)
+        std::vector<int> deferred;
+        for (int i = 0; i < n; ++i)
+            if (batch_defers(b->f[i])) deferred.push_back(i);
+        for (int i : deferred)
+            if ((rc = ensure_cl(b->f[i]))) break;
+        if (!rc && !deferred.empty()) rc = batch_build_jobs(b, dm);
+        if (rc) {
+            restore();
+            return rc;
+        }
+        std::vector<char> defer(n, 0);
+        for (int i : deferred) defer[i] = 1;
+        // every frame issues its work on its batch stream, which joins the capture (a frame left on
+        // its own stream would run at once, outside the graph)
+        for (int i = 0; i < n; ++i) b->f[i]->stream = b->fst[i];
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->start, b->stream, cudaEventRecordExternal);
         if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+        // each frame up to its sweep (the whole frame where it is not deferred)
         for (int i = 0; i < n && e == cudaSuccess && !rc; ++i) {
             qmmm_handle *h = b->f[i];
             if ((e = cudaStreamWaitEvent(b->fst[i], b->fork, 0)) != cudaSuccess) break;
             h->quiet = true;
+            if (defer[i]) {
+                const double *ddm = nullptr;
+                rc = qmmm_vpot(h, at(V, i), nullptr);
+                if (!rc && at(E, i)) rc = qmmm_energy(h, dm[i], at(E, i));
+                if (!rc) rc = forces_begin(h, dm[i], &ddm);
+                h->quiet = false;
+                if (rc) break;
+                e = cudaEventRecord(b->adone[i], b->fst[i]);
+                continue;
+            }
             rc = batch_frame(h, dm[i], at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
+            h->quiet = false;
+            if (rc) break;
+            if ((e = cudaEventRecordWithFlags(b->done[i], b->fst[i], cudaEventRecordExternal)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(b->join[i], b->fst[i])) != cudaSuccess) break;
+            e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+        }
+        // the deferred frames' sweeps, all classes over all of them, then each frame's last part
+        if (e == cudaSuccess && !rc && !deferred.empty()) rc = batch_sweeps(b, deferred);
+        for (size_t k = 0; k < deferred.size() && e == cudaSuccess && !rc; ++k) {
+            const int i = deferred[k];
+            qmmm_handle *h = b->f[i];
+            if ((e = cudaStreamWaitEvent(b->fst[i], b->sweeps, 0)) != cudaSuccess) break;
+            h->quiet = true;
+            rc = forces_end(h, at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
             h->quiet = false;
             if (rc) break;
             if ((e = cudaEventRecordWithFlags(b->done[i], b->fst[i], cudaEventRecordExternal)) != cudaSuccess) break;

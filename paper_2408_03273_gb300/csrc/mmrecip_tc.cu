@@ -13,12 +13,13 @@
 // A operand (M = 128 charges x K): the outer products Y_i(n_y) Z_i(n_z), digitised on chip from
 // fixed-point phase rows staged by TMA; B operand (N = 112 rows (k, n_x, re/im) x K): C_k divided
 // by a power of two per (k, n_x) so that |C| <= 1, digitised once per call into the shared-memory
-// layout.  Digits as for the structure factor (tc_digits.cuh): seven planes per operand (48-bit
-// fixed point) on both precision paths, 28 plane pairs per K-step into FP32 accumulators in tensor
-// memory.  FP64 path: five accumulators (levels 0..3 kept apart, 4..6 merged), so at most 96 N rows
-// per tile; mixed path: four (levels 0..2 apart, 3..6 merged: about 7e-11 of the reciprocal part,
-// far below the FP32 region-I sweep's error), 128 rows per tile, so the three channels take one
-// N tile fewer and the A operand is digitised once less.  Level 0
+// layout.  Digits as for the structure factor (tc_digits.cuh).  FP64 path: seven planes per operand
+// (48-bit fixed point), 28 plane pairs per K-step into FP32 accumulators in tensor memory, five
+// accumulators (levels 0..3 kept apart, 4..6 merged), so at most 96 N rows per tile.  Mixed path:
+// five planes (34-bit operands, 15 plane pairs: about 1e-10 of the reciprocal part, three orders
+// below the FP32 region-I sweep's error), four accumulators (levels 0..2 apart, 3..4 merged), 128
+// rows per tile, so the three channels take one N tile fewer and the A operand is digitised once
+// less.  Level 0
 // is exact for any input while 4096 x 2 N_y N_z < 2^24 (kmax <= 20) and beyond that unless the
 // row-normalised coefficients, which decay as exp(-G^2/4 alpha^2), sum to more than 2^11 in
 // magnitude; levels 1 to 3 are sums of random-sign digit products, typically 2^17 or less.  The epilogue
@@ -75,8 +76,8 @@ struct MmrArgs {
 }  // namespace
 
 // grid (mtiles, N tiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set
-// ch % nstg.  NP digit planes per operand (MMR_NP = 7: 48-bit operands, FP64 class, for both
-// precisions: the mixed path's reciprocal sum stays FP64-class as well).
+// ch % nstg.  NP digit planes per operand: 7 (48-bit operands, FP64 class) on the FP64 path, 5
+// (34-bit) on the mixed path.
 template <int NP>
 __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
 {
@@ -425,6 +426,11 @@ void tc_mmr_shape(const EwaldDev &e, int nacc, int np, MmrShape &sh)
     sh.bplane_words = (size_t)sh.ntiles * sh.nchunk * np * mmr_bpl(sh.nr) / 4;
 }
 
+template <int NP>
+static cudaError_t mm_recip_np(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,
+                               const double2 *Az, const int4 *Yt, const int4 *Zt, double *dq, double *dR, int *err,
+                               cudaStream_t st);
+
 cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,
                                const double2 *Az, double *dq, double *dR, int *err, cudaStream_t st)
 {
@@ -436,21 +442,33 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     k_mmr_scale<<<3 * NX, 256, 0, st>>>(e, A, Az, b.cscale);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
-    const size_t smem = mmr_smem(sh.nr, sh.nstg, sh.np);
-    if (sh.np != MMR_NP) return cudaErrorInvalidValue;
-    const void *fn = (const void *)k_mm_recip_tc<MMR_NP>;
+    if (sh.np == MMR_NP_FP64) return mm_recip_np<MMR_NP_FP64>(e, sh, b, A, Az, Yt, Zt, dq, dR, err, st);
+    if (sh.np == MMR_NP_MIXED) return mm_recip_np<MMR_NP_MIXED>(e, sh, b, A, Az, Yt, Zt, dq, dR, err, st);
+    return cudaErrorInvalidValue;
+}
+
+// B planes and the MMA kernel with NP planes per operand
+template <int NP>
+static cudaError_t mm_recip_np(const EwaldDev &e, const MmrShape &sh, const MmrBuf &b, const double2 *A,
+                               const double2 *Az, const int4 *Yt, const int4 *Zt, double *dq, double *dR, int *err,
+                               cudaStream_t st)
+{
+    cudaError_t rc;
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    const size_t smem = mmr_smem(sh.nr, sh.nstg, NP);
     static size_t at = 0;
     if (smem > at) {
-        if ((rc = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        if ((rc = cudaFuncSetAttribute((const void *)k_mm_recip_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem)) != cudaSuccess)
             return rc;
         at = smem;
     }
-    const size_t tile_words = (size_t)sh.nchunk * sh.np * mmr_bpl(sh.nr) / 4;
+    const size_t tile_words = (size_t)sh.nchunk * NP * mmr_bpl(sh.nr) / 4;
     for (int tl = 0; tl < sh.ntiles; ++tl) {
         const int kfirst = tl * sh.cpt, nk = std::min(sh.cpt, 3 - kfirst);
         const long long n = (long long)sh.nr * PCH * sh.nchunk;
-        k_mmr_bplanes<MMR_NP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
-                                                                            sh.nchunk, b.bpl + tl * tile_words);
+        k_mmr_bplanes<NP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
+                                                                        sh.nchunk, b.bpl + tl * tile_words);
         if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     }
     MmrArgs a;
@@ -475,7 +493,7 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
     a.nstg = sh.nstg;
     a.nacc = sh.nacc;
     a.box0 = e.box[0];
-    k_mm_recip_tc<MMR_NP><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
+    k_mm_recip_tc<NP><<<dim3(sh.mtiles, sh.ntiles), NTHR, smem, st>>>(a);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     return cudaSuccess;
 }

@@ -71,6 +71,28 @@ cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
                              double *gchg, int *err, int nsm, int variant, int nslice, ClScratch cl,
                              cudaStream_t st);
+// One frame's share of a class's charge-lane adjoint: its basis, region I, density and outputs,
+// the primitive pairs [pp_begin, pp_end) and region-I charges [ch_begin, ch_end), its work items
+// (ntile charge tiles x gx ranges of pair batches, from cl_decompose) and where its items and
+// threads start in the flat ranges of a batched launch (item0, thr0; thr0 a multiple of 32).
+struct ClJob {
+    BasisDev bd;
+    RegionDev rg;
+    const double *dm;
+    float4 *rec;
+    double *psum;
+    double *gqm, *gchg;
+    int pp_begin, pp_end, ch_begin, ch_end;
+    int gx, ntile;
+    int item0, thr0;
+};
+// work items of one class's charge-lane sweep: gx ranges of pair batches x ntile charge tiles
+void cl_decompose(int L, int variant, int npair, int nch, int ncls, int &gx, int &ntile);
+// The charge-lane adjoint of class cls over njob frames with one launch of each of its kernels
+// (records, a persistent sweep over nitems items, pair gradients); jobs is a device array,
+// counter a device int (cleared here).
+cudaError_t launch_vgrad_cl_jobs(int cls, const ClJob *jobs, int njob, int nthr, int nitems, int *counter,
+                                 const float *boys, int variant, int nsm, cudaStream_t st);
 
 // moments / multipoles / Fock / Pulay (mode bits below)
 enum { MOM_MULT = 1, MOM_FOCK = 2, MOM_PULAY = 4 };
@@ -132,12 +154,15 @@ cudaError_t launch_structure_factor_tc(const EwaldDev &e, const TcShape &sh, con
                                        cudaStream_t st);
 
 // Tensor-core MM-side reciprocal sum (mmrecip_tc.cu): tiling and scratch.
-constexpr int MMR_NP = 7;  // digit planes per operand of the MM-side tensor-core sum (48-bit fixed point)
+// digit planes per operand of the MM-side tensor-core sum: 7 (48-bit fixed point) on the FP64
+// path, 5 (34-bit, 15 plane pairs instead of 28) on the mixed path, whose error is set by its FP32
+// region-I sweeps (about 1e-7) and not by the reciprocal sum (about 1e-10 of it with 5 planes)
+constexpr int MMR_NP_FP64 = 7, MMR_NP_MIXED = 5;
 struct MmrShape {
     int mtiles = 0, npad = 0, npair = 0, nchunk = 0;  // charge tiles (128), padded charges, (n_y, n_z) pairs, chunks of 8
     int cpt = 3, ntiles = 1, nr = 0, nstg = 3;        // channels per N tile, N tiles, N rows, stages
     int nacc = 4;                                     // accumulators (exact levels + 1)
-    int np = 7;                                       // digit planes per operand (MMR_NP)
+    int np = 7;                                       // digit planes per operand (5 or 7)
     bool supported = false;                           // kx small enough for one channel per tile
     size_t phase_rows = 0;                            // Y and Z phase rows (int4)
     size_t bplane_words = 0;                          // B digit planes of all N tiles (32-bit words)
@@ -174,8 +199,8 @@ struct EwaldBuf {
     int recip = 0;               // reciprocal sums: 0 CUDA cores (FP64 / double-float), 1 tensor cores
     TcShape tcs;
     TcBuf tcb;
-    MmrShape mms[2];             // MM-side sum, 7 planes: [0] FP64 path (5 accumulators: levels 0-3
-                                 // exact), [1] mixed path (4: levels 0-2 exact, 3-6 merged)
+    MmrShape mms[2];             // MM-side sum: [0] FP64 path (7 planes, 5 accumulators: levels 0-3
+                                 // exact), [1] mixed path (5 planes, 4: levels 0-2 exact, 3-4 merged)
     MmrBuf mmb;
     int *err = nullptr;          // device error word of the handle
 };

@@ -15,6 +15,8 @@ struct VgradF32 {
                            int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int *err,
                            int nsm, int variant, int nslice, ClScratch cl,
                            cudaStream_t st);
+    static cudaError_t run_jobs(const ClJob *jobs, int njob, int nthr, int nitems, int *counter, const float *boys,
+                                int variant, int nsm, cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
@@ -34,36 +36,69 @@ struct VgradF32 {
 // by k_cl_pairs once every charge tile has added its sums.
 // ---------------------------------------------------------------------------------------------
 
-// Pair records of one class (FP64 Hermite/density algebra, rounded to FP32), once per call.
+// Every kernel below serves one class over one or many frames ("jobs"): with jobs == nullptr the
+// single job `one` (a kernel parameter), otherwise the device array jobs[njob], each job's share of
+// the flat thread / item range starting at its thr0 / item0.
+__device__ __forceinline__ int cl_job_by_thread(const ClJob *jobs, int njob, int t)
+{
+    int lo = 0, hi = njob - 1;  // the last job with thr0 <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&jobs[mid].thr0) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int cl_job_by_item(const ClJob *jobs, int njob, int item)
+{
+    int lo = 0, hi = njob - 1;  // the last job with item0 <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&jobs[mid].item0) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Pair records of one class (FP64 Hermite/density algebra, rounded to FP32), once per call; the
+// pair's charge sums are cleared here too.
 template <int LA, int LB>
 __global__ void __launch_bounds__(128)
-k_cl_records(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, const double *__restrict__ dm,
-             float4 *__restrict__ rec)
+k_cl_records(ClJob one, const ClJob *__restrict__ jobs, int njob, int nthr)
 {
     constexpr int L = LA + LB, NH = nherm(L), R4 = cl_rec_floats(L) / 4;
-    const int i = pp_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (i >= pp_end) return;
-    const PPLane pl = load_pp(bd, i, pp_end);
-    float4 *r = rec + (size_t)(i - pp_begin) * R4;
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (t >= nthr) return;
+    const ClJob &J = jobs ? jobs[cl_job_by_thread(jobs, njob, t)] : one;
+    const int i = J.pp_begin + (t - J.thr0);
+    if (i >= J.pp_end) return;
+    const PPLane pl = load_pp(J.bd, i, J.pp_end);
+    float4 *r = J.rec + (size_t)(i - J.pp_begin) * R4;
     float ph[3], pl_[3];
 #pragma unroll
-    for (int x = 0; x < 3; ++x) split_grid(pl.P[x] - rg.centre[x], ph[x], pl_[x]);
+    for (int x = 0; x < 3; ++x) split_grid(pl.P[x] - J.rg.centre[x], ph[x], pl_[x]);
     const long long pb = __double_as_longlong(pl.p);
     r[0] = make_float4(ph[0], ph[1], ph[2], pl_[0]);
     r[1] = make_float4(pl_[1], pl_[2], __int_as_float((int)(pb & 0xffffffffll)), __int_as_float((int)(pb >> 32)));
     double D0[NH], Dx[NH], Dy[NH], Dz[NH];
-    fold_density_dA<LA, LB, true>(pl, bd, dm, Dx, Dy, Dz, D0);
+    fold_density_dA<LA, LB, true>(pl, J.bd, J.dm, Dx, Dy, Dz, D0);
 #pragma unroll
     for (int k = 0; k < NH; ++k) r[2 + k] = make_float4((float)D0[k], (float)Dx[k], (float)Dy[k], (float)Dz[k]);
+    double *ps = J.psum + (size_t)(i - J.pp_begin) * 6;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) ps[v] = 0.0;
 }
 
 // CPL charges per lane (a block's tile holds CL_NT * CPL charges of one width class, each lane
 // CPL consecutive ones): the per-pair reduction is paid once per CPL charges and the lane has CPL
-// independent chains of Boys/R work; NB pairs per staged batch.
+// independent chains of Boys/R work; NB pairs per staged batch.  A work item is one (charge tile,
+// range of pair batches) of a job.  With counter == nullptr each block does item blockIdx.x;
+// otherwise the grid is persistent and its blocks take items from *counter until nitems are done
+// (the batched form over many frames).
 template <int LA, int LB, int CPL, int MINB>
 __global__ void __launch_bounds__(CL_NT, MINB)
-k_vgrad_cl(RegionDev rg, int npair, const float4 *__restrict__ rec, int ch_begin, int ch_end,
-           const float *__restrict__ boys_g, double *__restrict__ psum, double *__restrict__ gchg)
+k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int *__restrict__ counter,
+           const float *__restrict__ boys_g)
 {
     constexpr int L = LA + LB, NH1 = nherm(L + 1), R4 = cl_rec_floats(L) / 4, NB = cl_batch(L);
     constexpr int TILE = CL_NT * CPL;
@@ -72,215 +107,238 @@ k_vgrad_cl(RegionDev rg, int npair, const float4 *__restrict__ rec, int ch_begin
     __shared__ __align__(16) float4 buf[2][NB * R4];
     __shared__ float2 rsq[2][NB];  // (rho, sqrt(kappa / (p + kappa))) per pair of a batch
     __shared__ float ps_h[2][NB * 8], ps_l[2][NB * 8];
-
-    // this block's charge tile: TILE charges of one width class within [ch_begin, ch_end)
-    int t = (int)blockIdx.y, cbeg = -1, cend = 0;
-    double kap = 0.0;
-    for (int c = 0; c < rg.ncls; ++c) {
-        const int lo = max(__ldg(rg.cls_off + c), ch_begin), hi = min(__ldg(rg.cls_off + c + 1), ch_end);
-        if (lo >= hi) continue;
-        const int nt = (hi - lo + TILE - 1) / TILE;
-        if (t < nt) {
-            cbeg = lo + t * TILE;
-            cend = min(hi, cbeg + TILE);
-            kap = __ldg(rg.cls_kappa + c);
-            break;
-        }
-        t -= nt;
-    }
-    // this block's pair batches
-    const int nbatch = (npair + NB - 1) / NB;
-    const int bper = (nbatch + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int b0 = (int)blockIdx.x * bper, b1 = min(nbatch, b0 + bper);
-    if (cbeg < 0 || b0 >= b1) return;  // block-uniform
+    __shared__ int s_item;
 
     for (int k = threadIdx.x; k < BOYS_TAB_F; k += CL_NT) tab[k] = __ldg(boys_g + k);
     for (int k = threadIdx.x; k < 2 * NB * 8; k += CL_NT) {
-        (&ps_h[0][0])[k] = 0.0f;
+        (&ps_h[0][0])[k] = 0.0f;  // every batch clears the sums it used, so they stay zero
         (&ps_l[0][0])[k] = 0.0f;
     }
-    // this lane's charges: CPL consecutive region-I entries (inactive ones carry q = 0)
-    float4 ch[CPL], cl[CPL];
-#pragma unroll
-    for (int i = 0; i < CPL; ++i) {
-        const int j = cbeg + CPL * (int)threadIdx.x + i;
-        ch[i] = cl[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < cend) {
-            ch[i] = __ldg(rg.chg_hi + j);
-            cl[i] = __ldg(rg.chg_lo + j);
-        }
-    }
-
-    // a batch's records: element idx of the batch into smem; the thread holding a record's second
-    // float4 (with p) also forms (rho, sq) for the block's width class, in FP64
-    auto put = [&](int s, int idx, float4 v) {
-        buf[s][idx] = v;
-        if (idx % R4 == 1) {
-            const double p = __longlong_as_double(((long long)__float_as_int(v.w) << 32) |
-                                                  (unsigned int)__float_as_int(v.z));
-            const double td = kap > 0.0 ? kap / (p + kap) : 1.0;
-            rsq[s][idx / R4] = make_float2((float)(p * td), (float)sqrt(td));
-        }
-    };
-    {
-        const int nb = min(NB, npair - b0 * NB);
-        for (int idx = threadIdx.x; idx < nb * R4; idx += CL_NT) put(0, idx, __ldg(rec + (size_t)b0 * NB * R4 + idx));
-    }
-    __syncthreads();
-
     const int lane = threadIdx.x & 31;
-    float ah[CPL][4], al[CPL][4];  // per-charge sums (double-float): dC_x, dC_y, dC_z, dq
-#pragma unroll
-    for (int i = 0; i < CPL; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) ah[i][c] = al[i][c] = 0.0f;
-    for (int b = b0; b < b1; ++b) {
-        const int s = (b - b0) & 1;
-        const int nb = min(NB, npair - b * NB);
-        // prefetch the next batch into registers while this one is computed
-        float4 pf[PF];
-        const int nbn = b + 1 < b1 ? min(NB, npair - (b + 1) * NB) : 0;
-#pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int idx = (int)threadIdx.x + i * CL_NT;
-            if (idx < nbn * R4) pf[i] = __ldg(rec + (size_t)(b + 1) * NB * R4 + idx);
+    int item = (int)blockIdx.x;
+    for (;;) {
+        if (counter) {
+            if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+            __syncthreads();
+            item = s_item;
         }
-        float bp[CPL][4];
-#pragma unroll
-        for (int i = 0; i < CPL; ++i) bp[i][0] = bp[i][1] = bp[i][2] = bp[i][3] = 0.0f;
-        for (int p = 0; p < nb; ++p) {
-            const float4 *r = buf[s] + p * R4;
-            const float4 h0 = r[0], h1 = r[1];
-            const float2 rq = rsq[s][p];
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // this lane's pair sums
+        if (item >= nitems) break;
+        const ClJob &J = jobs ? jobs[cl_job_by_item(jobs, njob, item)] : one;
+        const int local = item - J.item0, gx = J.gx, npair = J.pp_end - J.pp_begin;
+        const RegionDev &rg = J.rg;
+        const float4 *__restrict__ rec = J.rec;
+        double *__restrict__ psum = J.psum;
+        // this item's charge tile: TILE charges of one width class within [ch_begin, ch_end)
+        int t = local / gx, cbeg = -1, cend = 0;
+        double kap = 0.0;
+        for (int c = 0; c < rg.ncls; ++c) {
+            const int lo = max(__ldg(rg.cls_off + c), J.ch_begin), hi = min(__ldg(rg.cls_off + c + 1), J.ch_end);
+            if (lo >= hi) continue;
+            const int nt = (hi - lo + TILE - 1) / TILE;
+            if (t < nt) {
+                cbeg = lo + t * TILE;
+                cend = min(hi, cbeg + TILE);
+                kap = __ldg(rg.cls_kappa + c);
+                break;
+            }
+            t -= nt;
+        }
+        // this item's pair batches
+        const int nbatch = (npair + NB - 1) / NB;
+        const int bper = (nbatch + gx - 1) / gx;
+        const int b0 = (local % gx) * bper, b1 = min(nbatch, b0 + bper);
+        if (cbeg >= 0 && b0 < b1) {  // item-uniform
+            // this lane's charges: CPL consecutive region-I entries (inactive ones carry q = 0)
+            float4 ch[CPL], cl[CPL];
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                // correctly rounded displacement (grid-split hi parts subtract exactly)
-                const float X = (h0.x - ch[i].x) + (h0.w - cl[i].x);
-                const float Y = (h0.y - ch[i].y) + (h1.x - cl[i].y);
-                const float Z = (h0.z - ch[i].z) + (h1.y - cl[i].z);
-                float T, Tl;
-                boys_arg_f32(rq.x, X, Y, Z, T, Tl);
-                float F[L + 2];
-                boys_f32<L + 1>(T, F, tab, Tl);
-                float Fn[L + 2];
-                {
-                    float sc = rq.y;
-                    const float m2rho = -2.0f * rq.x;
+                const int j = cbeg + CPL * (int)threadIdx.x + i;
+                ch[i] = cl[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < cend) {
+                    ch[i] = __ldg(rg.chg_hi + j);
+                    cl[i] = __ldg(rg.chg_lo + j);
+                }
+            }
+
+            // a batch's records: element idx of the batch into smem; the thread holding a record's
+            // second float4 (with p) also forms (rho, sq) for the tile's width class, in FP64
+            auto put = [&](int s, int idx, float4 v) {
+                buf[s][idx] = v;
+                if (idx % R4 == 1) {
+                    const double p = __longlong_as_double(((long long)__float_as_int(v.w) << 32) |
+                                                          (unsigned int)__float_as_int(v.z));
+                    const double td = kap > 0.0 ? kap / (p + kap) : 1.0;
+                    rsq[s][idx / R4] = make_float2((float)(p * td), (float)sqrt(td));
+                }
+            };
+            {
+                const int nb = min(NB, npair - b0 * NB);
+                for (int idx = threadIdx.x; idx < nb * R4; idx += CL_NT)
+                    put(0, idx, __ldg(rec + (size_t)b0 * NB * R4 + idx));
+            }
+            __syncthreads();
+
+            float ah[CPL][4], al[CPL][4];  // per-charge sums (double-float): dC_x, dC_y, dC_z, dq
 #pragma unroll
-                    for (int n = 0; n <= L + 1; ++n) {
-                        Fn[n] = sc * F[n];
-                        sc *= m2rho;
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) ah[i][c] = al[i][c] = 0.0f;
+            for (int b = b0; b < b1; ++b) {
+                const int s = (b - b0) & 1;
+                const int nb = min(NB, npair - b * NB);
+                // prefetch the next batch into registers while this one is computed
+                float4 pf[PF];
+                const int nbn = b + 1 < b1 ? min(NB, npair - (b + 1) * NB) : 0;
+#pragma unroll
+                for (int i = 0; i < PF; ++i) {
+                    const int idx = (int)threadIdx.x + i * CL_NT;
+                    if (idx < nbn * R4) pf[i] = __ldg(rec + (size_t)(b + 1) * NB * R4 + idx);
+                }
+                float bp[CPL][4];
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) bp[i][0] = bp[i][1] = bp[i][2] = bp[i][3] = 0.0f;
+                for (int p = 0; p < nb; ++p) {
+                    const float4 *r = buf[s] + p * R4;
+                    const float4 h0 = r[0], h1 = r[1];
+                    const float2 rq = rsq[s][p];
+                    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // this lane's pair sums
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        // correctly rounded displacement (grid-split hi parts subtract exactly)
+                        const float X = (h0.x - ch[i].x) + (h0.w - cl[i].x);
+                        const float Y = (h0.y - ch[i].y) + (h1.x - cl[i].y);
+                        const float Z = (h0.z - ch[i].z) + (h1.y - cl[i].z);
+                        float T, Tl;
+                        boys_arg_f32(rq.x, X, Y, Z, T, Tl);
+                        float F[L + 2];
+                        boys_f32<L + 1>(T, F, tab, Tl);
+                        float Fn[L + 2];
+                        {
+                            float sc = rq.y;
+                            const float m2rho = -2.0f * rq.x;
+#pragma unroll
+                            for (int n = 0; n <= L + 1; ++n) {
+                                Fn[n] = sc * F[n];
+                                sc *= m2rho;
+                            }
+                        }
+                        float R[NH1];
+                        hermite_R_u<L + 1, float>(R, Fn, X, Y, Z);
+                        float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+#pragma unroll
+                        for (int tt = 0; tt <= L; ++tt)
+#pragma unroll
+                            for (int uu = 0; uu <= L; ++uu)
+#pragma unroll
+                                for (int ww = 0; ww <= L; ++ww) {
+                                    if (tt + uu + ww > L) continue;
+                                    const int k = hidx(tt, uu, ww);
+                                    const float4 d = r[2 + k];
+                                    e0 = fmaf(d.x, R[k], e0);
+                                    ex = fmaf(d.x, R[hidx(tt + 1, uu, ww)], ex);
+                                    ey = fmaf(d.x, R[hidx(tt, uu + 1, ww)], ey);
+                                    ez = fmaf(d.x, R[hidx(tt, uu, ww + 1)], ez);
+                                    hx = fmaf(d.y, R[k], hx);
+                                    hy = fmaf(d.z, R[k], hy);
+                                    hz = fmaf(d.w, R[k], hz);
+                                }
+                        const float q = ch[i].w;
+                        bp[i][0] = fmaf(q, ex, bp[i][0]);
+                        bp[i][1] = fmaf(q, ey, bp[i][1]);
+                        bp[i][2] = fmaf(q, ez, bp[i][2]);
+                        bp[i][3] -= e0;
+                        v[0] = fmaf(q, hx, v[0]);
+                        v[1] = fmaf(q, hy, v[1]);
+                        v[2] = fmaf(q, hz, v[2]);
+                        v[3] = fmaf(q, ex, v[3]);
+                        v[4] = fmaf(q, ey, v[4]);
+                        v[5] = fmaf(q, ez, v[5]);
+                    }
+                    // pair sums over the warp's 32 lanes: reduce-scatter of 8 values (6 used), combining
+                    // neighbouring lanes first: consecutive region-I charges are the atoms of one water, so
+                    // the partial sums cancel early and stay small (a 16-apart pairing first sums unrelated
+                    // monopoles and leaves the FP32 rounding of large partials in the small total).  Lanes
+                    // 0..7 end with value vi = bits (0, 1, 2) of the lane number.
+                    float w4[4], w2[2], w1;
+                    {
+                        const bool up = lane & 1;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float keep = up ? v[i + 4] : v[i], send = up ? v[i] : v[i + 4];
+                            w4[i] = keep + __shfl_xor_sync(FULL, send, 1);
+                        }
+                        const bool up2 = lane & 2;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const float keep = up2 ? w4[i + 2] : w4[i], send = up2 ? w4[i] : w4[i + 2];
+                            w2[i] = keep + __shfl_xor_sync(FULL, send, 2);
+                        }
+                        const bool up4 = lane & 4;
+                        {
+                            const float keep = up4 ? w2[1] : w2[0], send = up4 ? w2[0] : w2[1];
+                            w1 = keep + __shfl_xor_sync(FULL, send, 4);
+                        }
+                        w1 += __shfl_xor_sync(FULL, w1, 8);
+                        w1 += __shfl_xor_sync(FULL, w1, 16);
+                    }
+                    const int vi = (lane & 1) * 4 + ((lane >> 1) & 1) * 2 + ((lane >> 2) & 1);
+                    if (lane < 8 && vi < 6) {
+                        // compensated shared-memory atomic: the old value gives the rounding error exactly
+                        float *hp = &ps_h[s][p * 8 + vi];
+                        const float old = atomicAdd(hp, w1);
+                        const float sum = old + w1, bv = sum - old;
+                        atomicAdd(&ps_l[s][p * 8 + vi], (old - (sum - bv)) + (w1 - bv));
                     }
                 }
-                float R[NH1];
-                hermite_R_u<L + 1, float>(R, Fn, X, Y, Z);
-                float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
 #pragma unroll
-                for (int tt = 0; tt <= L; ++tt)
+                for (int i = 0; i < CPL; ++i)
 #pragma unroll
-                    for (int uu = 0; uu <= L; ++uu)
+                    for (int c = 0; c < 4; ++c) df_add(ah[i][c], al[i][c], bp[i][c]);
+                __syncthreads();  // batch b read by all warps; its pair sums complete
+                if ((int)threadIdx.x < nb * 6) {
+                    // each of these threads reads one sum and clears it for batch b + 2 (slots 6, 7 of a
+                    // pair are never written)
+                    const int pp = (int)threadIdx.x / 6, vv = (int)threadIdx.x % 6, o = pp * 8 + vv;
+                    atomicAdd(psum + (size_t)(b * NB + pp) * 6 + vv, (double)ps_h[s][o] + (double)ps_l[s][o]);
+                    ps_h[s][o] = ps_l[s][o] = 0.0f;
+                }
 #pragma unroll
-                        for (int ww = 0; ww <= L; ++ww) {
-                            if (tt + uu + ww > L) continue;
-                            const int k = hidx(tt, uu, ww);
-                            const float4 d = r[2 + k];
-                            e0 = fmaf(d.x, R[k], e0);
-                            ex = fmaf(d.x, R[hidx(tt + 1, uu, ww)], ex);
-                            ey = fmaf(d.x, R[hidx(tt, uu + 1, ww)], ey);
-                            ez = fmaf(d.x, R[hidx(tt, uu, ww + 1)], ez);
-                            hx = fmaf(d.y, R[k], hx);
-                            hy = fmaf(d.z, R[k], hy);
-                            hz = fmaf(d.w, R[k], hz);
-                        }
-                const float q = ch[i].w;
-                bp[i][0] = fmaf(q, ex, bp[i][0]);
-                bp[i][1] = fmaf(q, ey, bp[i][1]);
-                bp[i][2] = fmaf(q, ez, bp[i][2]);
-                bp[i][3] -= e0;
-                v[0] = fmaf(q, hx, v[0]);
-                v[1] = fmaf(q, hy, v[1]);
-                v[2] = fmaf(q, hz, v[2]);
-                v[3] = fmaf(q, ex, v[3]);
-                v[4] = fmaf(q, ey, v[4]);
-                v[5] = fmaf(q, ez, v[5]);
+                for (int i = 0; i < PF; ++i) {
+                    const int idx = (int)threadIdx.x + i * CL_NT;
+                    if (idx < nbn * R4) put(s ^ 1, idx, pf[i]);
+                }
+                __syncthreads();  // batch b + 1 staged
             }
-            // pair sums over the warp's 32 lanes: reduce-scatter of 8 values (6 used), combining
-            // neighbouring lanes first: consecutive region-I charges are the atoms of one water, so
-            // the partial sums cancel early and stay small (a 16-apart pairing first sums unrelated
-            // monopoles and leaves the FP32 rounding of large partials in the small total).  Lanes
-            // 0..7 end with value vi = bits (0, 1, 2) of the lane number.
-            float w4[4], w2[2], w1;
-            {
-                const bool up = lane & 1;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float keep = up ? v[i + 4] : v[i], send = up ? v[i] : v[i + 4];
-                    w4[i] = keep + __shfl_xor_sync(FULL, send, 1);
-                }
-                const bool up2 = lane & 2;
+            for (int i = 0; i < CPL; ++i) {
+                const int j = cbeg + CPL * (int)threadIdx.x + i;
+                if (j < cend) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float keep = up2 ? w4[i + 2] : w4[i], send = up2 ? w4[i] : w4[i + 2];
-                    w2[i] = keep + __shfl_xor_sync(FULL, send, 2);
+                    for (int c = 0; c < 4; ++c)
+                        atomicAdd(J.gchg + 4 * (size_t)j + c, (double)ah[i][c] + (double)al[i][c]);
                 }
-                const bool up4 = lane & 4;
-                {
-                    const float keep = up4 ? w2[1] : w2[0], send = up4 ? w2[0] : w2[1];
-                    w1 = keep + __shfl_xor_sync(FULL, send, 4);
-                }
-                w1 += __shfl_xor_sync(FULL, w1, 8);
-                w1 += __shfl_xor_sync(FULL, w1, 16);
-            }
-            const int vi = (lane & 1) * 4 + ((lane >> 1) & 1) * 2 + ((lane >> 2) & 1);
-            if (lane < 8 && vi < 6) {
-                // compensated shared-memory atomic: the old value gives the rounding error exactly
-                float *hp = &ps_h[s][p * 8 + vi];
-                const float old = atomicAdd(hp, w1);
-                const float sum = old + w1, bv = sum - old;
-                atomicAdd(&ps_l[s][p * 8 + vi], (old - (sum - bv)) + (w1 - bv));
             }
         }
-#pragma unroll
-        for (int i = 0; i < CPL; ++i)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) df_add(ah[i][c], al[i][c], bp[i][c]);
-        __syncthreads();  // batch b read by all warps; its pair sums complete
-        if ((int)threadIdx.x < nb * 6) {
-            // each of these threads reads one sum and clears it for batch b + 2 (slots 6, 7 of a
-            // pair are never written)
-            const int pp = (int)threadIdx.x / 6, vv = (int)threadIdx.x % 6, o = pp * 8 + vv;
-            atomicAdd(psum + (size_t)(b * NB + pp) * 6 + vv, (double)ps_h[s][o] + (double)ps_l[s][o]);
-            ps_h[s][o] = ps_l[s][o] = 0.0f;
-        }
-#pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int idx = (int)threadIdx.x + i * CL_NT;
-            if (idx < nbn * R4) put(s ^ 1, idx, pf[i]);
-        }
-        __syncthreads();  // batch b + 1 staged
-    }
-#pragma unroll
-    for (int i = 0; i < CPL; ++i) {
-        const int j = cbeg + CPL * (int)threadIdx.x + i;
-        if (j < cend) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) atomicAdd(gchg + 4 * (size_t)j + c, (double)ah[i][c] + (double)al[i][c]);
-        }
+        if (!counter) break;
+        __syncthreads();  // every thread has read s_item and left this item's shared buffers
     }
 }
 
-// Pair gradients from the per-pair charge sums (FP64), summed per shell pair and atom.
+// Pair gradients from the per-pair charge sums (FP64), summed per shell pair and atom.  Each job's
+// thread range starts at a multiple of 32, so a warp never mixes jobs.
 template <int LA, int LB>
 __global__ void __launch_bounds__(128)
-k_cl_pairs(BasisDev bd, int pp_begin, int pp_end, const double *__restrict__ psum, double *__restrict__ gqm)
+k_cl_pairs(ClJob one, const ClJob *__restrict__ jobs, int njob, int nthr)
 {
-    const int i = pp_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (t - (int)(threadIdx.x & 31) >= nthr) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
-    const PPLane pl = load_pp(bd, i, pp_end);
+    const ClJob &J = jobs ? jobs[cl_job_by_thread(jobs, njob, t)] : one;
+    const int i = J.pp_begin + (t - J.thr0);
+    const PPLane pl = load_pp(J.bd, i, J.pp_end);
     double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (pl.active) {
-        const double *sm = psum + (size_t)(i - pp_begin) * 6;
+        const double *sm = J.psum + (size_t)(i - J.pp_begin) * 6;
         const double aop = pl.a * pl.ip, bop = pl.b * pl.ip;
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
@@ -295,37 +353,35 @@ k_cl_pairs(BasisDev bd, int pp_begin, int pp_end, const double *__restrict__ psu
     if (head && pl.active) {
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
-            atomicAdd(gqm + 3 * pl.atomA + x, g[x]);
-            atomicAdd(gqm + 3 * pl.atomB + x, g[3 + x]);
+            atomicAdd(J.gqm + 3 * pl.atomA + x, g[x]);
+            atomicAdd(J.gqm + 3 * pl.atomB + x, g[3 + x]);
         }
     }
 }
 
+// The three kernels of one class over the jobs (records, sweep, pair gradients); jobs == nullptr:
+// the single job `one`, its sweep one block per item (fine-grained blocks of CL_BPB batches: the
+// class kernels are launched together, highest class first, and the block scheduler packs their
+// blocks onto the SMs as others finish); otherwise a persistent sweep of nsm * MINB blocks taking
+// items from *counter (cleared here).
 template <int LA, int LB, int CPL, int MINB>
-static cudaError_t launch_cl(const BasisDev &bd, const RegionDev &rg, int pp_begin, int pp_end, int ch_begin,
-                             int ch_end, const float *boys, const double *dm, double *gqm, double *gchg, int nsm,
-                             ClScratch cl, cudaStream_t st)
+static cudaError_t launch_cl(const ClJob &one, const ClJob *jobs, int njob, int nthr, int nitems, int *counter,
+                             const float *boys, int nsm, cudaStream_t st)
 {
-    const int npair = pp_end - pp_begin;
-    if (!cl.rec || !cl.psum) return cudaErrorInvalidValue;
-    k_cl_records<LA, LB><<<(npair + 127) / 128, 128, 0, st>>>(bd, rg, pp_begin, pp_end, dm, cl.rec);
+    if (nthr <= 0 || nitems <= 0) return cudaSuccess;
+    k_cl_records<LA, LB><<<(nthr + 127) / 128, 128, 0, st>>>(one, jobs, njob, nthr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(cl.psum, 0, (size_t)npair * 6 * sizeof(double), st)) != cudaSuccess) return e;
-    // charge tiles: at most one more per width class than the charges fill
-    constexpr int TILE = CL_NT * CPL, NB = cl_batch(LA + LB);
-    const int ntile = (ch_end - ch_begin + TILE - 1) / TILE + max(rg.ncls, 1) - 1;
-    const int nbatch = (npair + NB - 1) / NB;
-    // fine-grained blocks (CL_BPB batches each): the class kernels are launched together, highest
-    // class first, and the block scheduler packs their blocks onto the SMs as others finish, so
-    // short blocks keep the tail of the concurrent sweep short (no fixed share of the SMs)
-    (void)nsm;
-    const int gx = max(1, (nbatch + CL_BPB - 1) / CL_BPB);
-    k_vgrad_cl<LA, LB, CPL, MINB><<<dim3(gx, ntile), CL_NT, 0, st>>>(rg, npair, cl.rec, ch_begin, ch_end,
-                                                                    boys + (size_t)(LA + LB + 1) * BOYS_TAB_F,
-                                                                    cl.psum, gchg);
+    const float *tab = boys + (size_t)(LA + LB + 1) * BOYS_TAB_F;
+    if (counter) {
+        if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+        const int grid = std::min(nitems, MINB * std::max(nsm, 1));
+        k_vgrad_cl<LA, LB, CPL, MINB><<<grid, CL_NT, 0, st>>>(one, jobs, njob, nitems, counter, tab);
+    } else {
+        k_vgrad_cl<LA, LB, CPL, MINB><<<nitems, CL_NT, 0, st>>>(one, jobs, njob, nitems, nullptr, tab);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_cl_pairs<LA, LB><<<(npair + 127) / 128, 128, 0, st>>>(bd, pp_begin, pp_end, cl.psum, gqm);
+    k_cl_pairs<LA, LB><<<(nthr + 127) / 128, 128, 0, st>>>(one, jobs, njob, nthr);
     return cudaGetLastError();
 }
 
@@ -339,20 +395,59 @@ cudaError_t VgradF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int p
     // charge-lane sweep: (charges per lane, blocks per SM) of variant 0 and 1 (cl_variant)
     (void)err;
     (void)nslice;
+    if (!cl.rec || !cl.psum) return cudaErrorInvalidValue;
+    ClJob one{};
+    one.bd = bd;
+    one.rg = rg;
+    one.dm = dm;
+    one.rec = cl.rec;
+    one.psum = cl.psum;
+    one.gqm = gqm;
+    one.gchg = gchg;
+    one.pp_begin = pp_begin;
+    one.pp_end = pp_end;
+    one.ch_begin = ch_begin;
+    one.ch_end = ch_end;
     constexpr int L = LA + LB;
+    cl_decompose(L, variant, pp_end - pp_begin, ch_end - ch_begin, rg.ncls, one.gx, one.ntile);
+    const int nthr = (pp_end - pp_begin + 31) / 32 * 32, nitems = one.gx * one.ntile;
     if (variant == 1) {
         if constexpr (cl_variant(L, 1, 0) > 0)
-            return launch_cl<LA, LB, cl_variant(L, 1, 0), cl_variant(L, 1, 1)>(bd, rg, pp_begin, pp_end, ch_begin,
-                                                                               ch_end, boys, dm, gqm, gchg, nsm, cl,
-                                                                               st);
+            return launch_cl<LA, LB, cl_variant(L, 1, 0), cl_variant(L, 1, 1)>(one, nullptr, 1, nthr, nitems,
+                                                                               nullptr, boys, nsm, st);
     }
-    return launch_cl<LA, LB, cl_variant(L, 0, 0), cl_variant(L, 0, 1)>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
-                                                                       boys, dm, gqm, gchg, nsm, cl, st);
+    return launch_cl<LA, LB, cl_variant(L, 0, 0), cl_variant(L, 0, 1)>(one, nullptr, 1, nthr, nitems, nullptr, boys,
+                                                                       nsm, st);
+}
+
+template <int LA, int LB>
+cudaError_t VgradF32<LA, LB>::run_jobs(const ClJob *jobs, int njob, int nthr, int nitems, int *counter,
+                                       const float *boys, int variant, int nsm, cudaStream_t st)
+{
+    constexpr int L = LA + LB;
+    const ClJob none{};
+    if (variant == 1) {
+        if constexpr (cl_variant(L, 1, 0) > 0)
+            return launch_cl<LA, LB, cl_variant(L, 1, 0), cl_variant(L, 1, 1)>(none, jobs, njob, nthr, nitems,
+                                                                               counter, boys, nsm, st);
+    }
+    return launch_cl<LA, LB, cl_variant(L, 0, 0), cl_variant(L, 0, 1)>(none, jobs, njob, nthr, nitems, counter, boys,
+                                                                       nsm, st);
 }
 
 template struct VgradF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
 
 #else  // the dispatcher
+
+void cl_decompose(int L, int variant, int npair, int nch, int ncls, int &gx, int &ntile)
+{
+    const int cpl = (variant == 1 && cl_variant(L, 1, 0) > 0) ? cl_variant(L, 1, 0) : cl_variant(L, 0, 0);
+    const int tile = CL_NT * cpl, nb = cl_batch(L);
+    const int nbatch = (npair + nb - 1) / nb;
+    gx = std::max(1, (nbatch + CL_BPB - 1) / CL_BPB);
+    // a tile never spans two width classes: at most one partial tile per class boundary
+    ntile = nch > 0 ? (nch + tile - 1) / tile + std::max(ncls, 1) - 1 : 0;
+}
 
 cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const float *boys, const double *dm, double *gqm,
@@ -362,6 +457,24 @@ cudaError_t launch_vgrad_f32(const BasisDev &b, const RegionDev &r, int cls, int
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VgradF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, dm, gqm, gchg, err, nsm,
                                     variant, nslice, cl, st);
+}
+
+namespace {
+template <int LA, int LB>
+struct VgradJobs {
+    static cudaError_t run(const ClJob *jobs, int njob, int nthr, int nitems, int *counter, const float *boys,
+                           int variant, int nsm, cudaStream_t st)
+    {
+        return VgradF32<LA, LB>::run_jobs(jobs, njob, nthr, nitems, counter, boys, variant, nsm, st);
+    }
+};
+}  // namespace
+
+cudaError_t launch_vgrad_cl_jobs(int cls, const ClJob *jobs, int njob, int nthr, int nitems, int *counter,
+                                 const float *boys, int variant, int nsm, cudaStream_t st)
+{
+    if (njob <= 0 || nitems <= 0) return cudaSuccess;
+    return dispatch_class<VgradJobs>(cls, jobs, njob, nthr, nitems, counter, boys, variant, nsm, st);
 }
 
 #endif

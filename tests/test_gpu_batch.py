@@ -194,17 +194,25 @@ def test_batch_follows_md_steps(precision):
                         pos[i] = (qm, mm)
                         h.set_positions(qm, mm)
                 sizes.append([h.info["n_region1"] for h in hs])
-                b.run(dm, V, E, gq, gm, gc)
+                refs = []
                 for i, s in enumerate(frames):
                     r = q.Handle(s, precision=precision)
                     try:
                         r.set_positions(*pos[i])
-                        ref = _plain(r, s, s.dm)
+                        refs.append(_plain(r, s, s.dm))
                     finally:
                         r.close()
-                    assert _close(V[i].cpu(), ref["V"], tol), (step, i)
-                    assert _close(E[i].cpu(), ref["E"], tol), (step, i)
-                    assert _close(gm[i].cpu(), ref["gm"], tol), (step, i)
+                # the run that records the step's graph, then a replay into cleared outputs: every
+                # result must come from the graph (a frame left out of the recording would only
+                # have been computed once, outside it)
+                for replay in (False, True):
+                    if replay:
+                        for t in V + E + gq + gm + gc:
+                            t.zero_()
+                    b.run(dm, V, E, gq, gm, gc)
+                    for i, ref in enumerate(refs):
+                        for got, key in ((V, "V"), (E, "E"), (gq, "gq"), (gm, "gm"), (gc, "gc")):
+                            assert _close(got[i].cpu(), ref[key], tol), (step, i, key, replay)
             recorded, inst, upd = b.counts()
             assert 1 <= recorded <= 4 and inst + upd == recorded and inst >= 1
             assert len({tuple(x) for x in sizes}) > 1  # region I did change between steps
