@@ -556,9 +556,9 @@ def main():
         ch_g = math.ceil(nI / 2560) if nI else 0
         tensor = recip_in_effect(precision) == RECIP_NAME[q.QMMM_RECIP_TENSOR]
         # MM-side tiling as the library plans it (N rows per tile <= 96 with the FP64 path's five
-        # accumulators, <= 128 with the mixed path's four); the sum stays on the CUDA cores if
+        # accumulators, <= 160 with the mixed path's three); the sum stays on the CUDA cores if
         # 2 kz + 1 < 8
-        kx, lim = s.kmax[0] + 1, (96 if precision == q.QMMM_FP64 else 128)
+        kx, lim = s.kmax[0] + 1, (96 if precision == q.QMMM_FP64 else 160)
         cpt = next((c for c in (3, 2, 1) if 2 * c * kx <= lim), 1)
         mm_tc = tensor and (2 * cpt * kx + 15) // 16 * 16 <= lim and 2 * s.kmax[2] + 1 >= 8
         mm_tiles = -(-3 // cpt)

@@ -122,10 +122,10 @@ int qmmm_set_stream(qmmm_handle *h, void *stream);
  * Hermite/density algebra, the nuclear-MM term, the real-space Ewald sums, the multipoles and
  * moment integrals.  The two reciprocal Ewald sums are, on the tensor cores, exact products of
  * BF16 digit planes of fixed-point operands (QMMM_RECIP_TENSOR: 48-bit, except the mixed path's
- * MM-side sum, 34-bit, about 1e-10 relative) and on the CUDA cores FP64 (double-float on the
- * mixed path, about 47 bits).  Measured error of the
- * mixed path against FP64: 1e-7 to 3e-7 in V (relative Frobenius norm) and up to 8e-7 in the
- * gradients (max |error| / max |gradient|) on the benchmark workloads. */
+ * MM-side sum, 34-bit, within about 1e-8 of the largest MM gradient) and on the CUDA cores FP64
+ * (double-float on the mixed path, about 47 bits).  Measured error of the mixed path against
+ * FP64: 1e-7 to 8e-7 in V (relative Frobenius norm) and up to 8e-7 in the gradients
+ * (max |error| / max |gradient|) on the benchmark workloads. */
 int qmmm_set_precision(qmmm_handle *h, int precision);
 
 /* Method of the two reciprocal Ewald sums (SI, "Multipolar Ewald", long-range part): the MM
@@ -136,9 +136,9 @@ int qmmm_set_precision(qmmm_handle *h, int precision);
  *     operand split exactly into seven digit planes (a leading one and six of 7 bits, 48-bit
  *     fixed point) with exact FP32 accumulation of the leading digit levels: FP64 class (about
  *     1e-12 relative on the region-II potential and the MM gradients).  The mixed path's MM-side
- *     sum takes five planes (34-bit fixed point) and three exact levels instead of seven and four
- *     (about 1e-10 relative; 15 plane products instead of 28, one N tile fewer);
- *     the MM-side sum stays on the CUDA cores when 2 kz + 1 < 8;
+ *     sum takes five planes (34-bit fixed point) and two exact levels instead of seven and four
+ *     (within about 1e-8 of the largest MM gradient; 15 plane products instead of 28, and a
+ *     single N tile up to kx = 25); the MM-side sum stays on the CUDA cores when 2 kz + 1 < 8;
  *   QMMM_RECIP_AUTO [default]: QMMM_RECIP_TENSOR when (kx + 1)(2 ky + 1)(2 kz + 1) N_MM >= 4e7,
  *     else QMMM_RECIP_CUDA_CORES (small systems, where the extra launches outweigh the work).
  * The tensor-core scratch is allocated the first time the method is in effect: fixed-point

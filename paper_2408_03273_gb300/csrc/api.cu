@@ -1183,7 +1183,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.err = h->err.p;
         tc_sf_shape(e, h->ew.tcs);
         tc_mmr_shape(e, 5, MMR_NP_FP64, h->ew.mms[0]);
-        tc_mmr_shape(e, 4, MMR_NP_MIXED, h->ew.mms[1]);
+        tc_mmr_shape(e, 3, MMR_NP_MIXED, h->ew.mms[1]);
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));

@@ -16,10 +16,12 @@
 // layout.  Digits as for the structure factor (tc_digits.cuh).  FP64 path: seven planes per operand
 // (48-bit fixed point), 28 plane pairs per K-step into FP32 accumulators in tensor memory, five
 // accumulators (levels 0..3 kept apart, 4..6 merged), so at most 96 N rows per tile.  Mixed path:
-// five planes (34-bit operands, 15 plane pairs: about 1e-10 of the reciprocal part, three orders
-// below the FP32 region-I sweep's error), four accumulators (levels 0..2 apart, 3..4 merged), 128
-// rows per tile, so the three channels take one N tile fewer and the A operand is digitised once
-// less.  Level 0
+// five planes (34-bit operands, 15 plane pairs) and three accumulators (levels 0 and 1 apart, 2..4
+// merged: the merged sum's FP32 rounding is about 2^-31 of level 0's scale), so 160 rows per tile
+// and the three channels of kx <= 25 take a single N tile: the A operand is digitised once and no
+// N row beyond the 6 (kx + 1) in use is computed.  Against the double-float CUDA-core kernel the
+// mixed path's sum differs by 3e-9 (active site, kmax 16) and 1.3e-8 (large site, kmax 24) of the
+// largest MM gradient component, a tenth or less of the mixed path's error against FP64.  Level 0
 // is exact for any input while 4096 x 2 N_y N_z < 2^24 (kmax <= 20) and beyond that unless the
 // row-normalised coefficients, which decay as exp(-G^2/4 alpha^2), sum to more than 2^11 in
 // magnitude; levels 1 to 3 are sums of random-sign digit products, typically 2^17 or less.  The epilogue
@@ -37,7 +39,7 @@ namespace qmmm {
 namespace {
 using namespace tcd;
 constexpr int MM = 128;                 // charges per tile (MMA M)
-constexpr int NRMAX = 128;              // N rows (channel k, n_x, re/im) of one tile, a multiple of 16
+constexpr int NRMAX = 256;              // N rows (channel k, n_x, re/im) of one tile, a multiple of 16
 constexpr int KC = 16;                  // K entries per chunk: 8 (n_y, n_z) pairs x re/im
 constexpr int PCH = KC / 2;             // pairs per chunk
 constexpr int NSTGMAX = 3;              // pipeline depth (2 when three stages do not fit)
@@ -70,7 +72,7 @@ struct MmrArgs {
     int *err;
     int nmm, npad, NX, NY, NZ, npair, nchunk;
     int nr, cpt, nstg;         // N rows of a tile, channels per tile, stages
-    int nacc;                  // accumulators (4 or 5)
+    int nacc;                  // accumulators (3 or 5)
     double box0;
 };
 }  // namespace
@@ -403,8 +405,8 @@ __global__ void k_mmr_bplanes(EwaldDev e, const double2 *A, const double2 *Az, c
 // ---------------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------------
-// nacc = 5: levels 0..3 exact (channels split over N tiles so that 5 accumulators fit in 512
-// columns); nacc = 4: levels 0..2 exact and one tile where possible
+// nacc accumulators (levels 0 .. nacc-2 exact) of at most 512 / nacc columns each: the channels
+// take as few N tiles as fit (FP64 path: 5, 96 rows; mixed path: 3, 160 rows)
 void tc_mmr_shape(const EwaldDev &e, int nacc, int np, MmrShape &sh)
 {
     sh.np = np;

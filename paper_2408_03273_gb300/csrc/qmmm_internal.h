@@ -156,7 +156,7 @@ cudaError_t launch_structure_factor_tc(const EwaldDev &e, const TcShape &sh, con
 // Tensor-core MM-side reciprocal sum (mmrecip_tc.cu): tiling and scratch.
 // digit planes per operand of the MM-side tensor-core sum: 7 (48-bit fixed point) on the FP64
 // path, 5 (34-bit, 15 plane pairs instead of 28) on the mixed path, whose error is set by its FP32
-// region-I sweeps (about 1e-7) and not by the reciprocal sum (about 1e-10 of it with 5 planes)
+// region-I sweeps (about 1e-7 of the largest gradient; the 5-plane sum adds about 1e-8 at most)
 constexpr int MMR_NP_FP64 = 7, MMR_NP_MIXED = 5;
 struct MmrShape {
     int mtiles = 0, npad = 0, npair = 0, nchunk = 0;  // charge tiles (128), padded charges, (n_y, n_z) pairs, chunks of 8
@@ -200,7 +200,7 @@ struct EwaldBuf {
     TcShape tcs;
     TcBuf tcb;
     MmrShape mms[2];             // MM-side sum: [0] FP64 path (7 planes, 5 accumulators: levels 0-3
-                                 // exact), [1] mixed path (5 planes, 4: levels 0-2 exact, 3-4 merged)
+                                 // exact), [1] mixed path (5 planes, 3: levels 0-1 exact, 2-4 merged)
     MmrBuf mmb;
     int *err = nullptr;          // device error word of the handle
 };

@@ -121,7 +121,7 @@ def test_tensor_core_mm_side_matches_cuda_cores(name, precision, tol):
     # the two methods differ only in the reciprocal sums: dE/dq and dE/dR_MM agree to well below
     # the parity tolerance, measured against the size of the reciprocal part alone.  FP64: seven
     # digit planes, five accumulators (levels 0..3 exact); mixed path: five planes (34-bit
-    # operands), four accumulators (levels 3..4 merged in FP32)
+    # operands), three accumulators (levels 2..4 merged in FP32)
     s = _system(name)
     dq_lr, dR_lr = oracle.ewald_mm(s, oracle.multipoles(s), oracle.EW_LR)
     # same precision on both sides (the mixed region-I sweeps differ from FP64 by far more)
