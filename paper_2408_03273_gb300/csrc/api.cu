@@ -173,6 +173,10 @@ struct qmmm_handle {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t side[NCLASS] = {};   // one stream per angular class (concurrent class sweeps)
     cudaEvent_t fork = nullptr, join[NCLASS] = {};
+    // the moment kernels' class streams (fork_classes), apart from the sweeps' so that the two can
+    // run at the same time, and a stream that only records the end of a sweep for its timing
+    cudaStream_t mside[NCLASS] = {}, tstream = nullptr;
+    cudaEvent_t mfork = nullptr, mjoin[NCLASS] = {};
     // region-I sweep configuration per kernel kind (SweepKind) and angular class: SM-time weight
     // per primitive pair (flop model, or measured by qmmm_autotune), block variant, measured time
     double cls_cost[SW_NKIND][NCLASS] = {};
@@ -276,8 +280,12 @@ struct qmmm_handle {
         for (int c = 0; c < NCLASS; ++c) {
             if (side[c]) cudaStreamDestroy(side[c]);
             if (join[c]) cudaEventDestroy(join[c]);
+            if (mside[c]) cudaStreamDestroy(mside[c]);
+            if (mjoin[c]) cudaEventDestroy(mjoin[c]);
         }
         if (fork) cudaEventDestroy(fork);
+        if (mfork) cudaEventDestroy(mfork);
+        if (tstream) cudaStreamDestroy(tstream);
         qm.release(); Zd.release(); dexps.release(); dncoef.release(); mm_xyz.release(); mm_q.release();
         mm_beta.release(); user_xyz.release(); user_q.release(); dshell_atom.release(); dshell_off.release();
         dshell_ao.release(); dperm.release(); mm_cls.release(); blk.release(); cls_count.release();
@@ -321,9 +329,9 @@ int check_device_errors(qmmm_handle *h)
 cudaError_t mark(qmmm_handle *h, int k) { return h->quiet ? cudaSuccess : cudaEventRecord(h->ev[k], h->stream); }
 
 // End of a call: wait for the device, check its error flag and read the `nmarks` timing marks
-// (3: sweep = mark 0..1, rest = 1..2; 4: the same with mark 3..0 added to the rest; 2:
-// everything = 0..1).  Inside a batch capture nothing
-// waits: the batch checks every frame after the graph has run.
+// (3: sweep = mark 0..1, rest = 1..2; 4: sweep = mark 0..1 with mark 1 on the timing stream after
+// the class streams, rest = the span 3..2 less the sweep; 2: everything = 0..1).  Inside a batch
+// capture nothing waits: the batch checks every frame after the graph has run.
 int finish(qmmm_handle *h, int nmarks)
 {
     if (h->quiet) return QMMM_OK;
@@ -333,11 +341,10 @@ int finish(qmmm_handle *h, int nmarks)
         cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
     } else if (nmarks == 4) {
-        float before = 0.f;
+        float all = 0.f;
         cudaEventElapsedTime(&h->t_sweep, h->ev[0], h->ev[1]);
-        cudaEventElapsedTime(&before, h->ev[3], h->ev[0]);
-        cudaEventElapsedTime(&h->t_other, h->ev[1], h->ev[2]);
-        h->t_other += before;
+        cudaEventElapsedTime(&all, h->ev[3], h->ev[2]);
+        h->t_other = all - h->t_sweep;
     } else if (nmarks == 2) {
         h->t_sweep = 0.f;
         cudaEventElapsedTime(&h->t_other, h->ev[0], h->ev[1]);
@@ -660,7 +667,7 @@ bool split_sms(const qmmm_handle *h, int kind, const int *variant, int *share, i
 // picks its own charge slices (class_slices), and a class with fewer tiles than its share of the
 // SMs may take up to maxsl times its tile count in blocks.
 template <typename F>
-int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1, int nch = 0)
+int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 1, int nch = 0, bool join = true)
 {
     int share[NCLASS];
     if (!split_sms(h, kind, h->cls_variant[kind], share, nslice == 1 ? maxsl : 1)) return QMMM_OK;
@@ -684,26 +691,35 @@ int run_classes(qmmm_handle *h, int kind, F launch, int nslice = 1, int maxsl = 
         CUDA_TRY(launch(c, p0, p1, sh, h->cls_variant[kind][c], ns, h->side[c]));
         CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
     }
-    for (int c = 0; c < NCLASS; ++c)
-        if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join[c], 0));
+    if (join)
+        for (int c = 0; c < NCLASS; ++c)
+            if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join[c], 0));
     return QMMM_OK;
 }
 
-// One kernel per non-empty angular class, all classes concurrently on the class streams (forked
-// from and joined back into the handle's stream), each with its full grid.
+// Make `s` wait for every class sweep launched by run_classes(..., join = false).
+int join_classes(qmmm_handle *h, cudaStream_t s)
+{
+    for (int c = 0; c < NCLASS; ++c)
+        if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(s, h->join[c], 0));
+    return QMMM_OK;
+}
+
+// One kernel per non-empty angular class, all classes concurrently on the moment kernels' class
+// streams (forked from and joined back into the handle's stream), each with its full grid.
 template <typename F>
 int fork_classes(qmmm_handle *h, F launch)
 {
-    CUDA_TRY(cudaEventRecord(h->fork, h->stream));
+    CUDA_TRY(cudaEventRecord(h->mfork, h->stream));
     for (int c = 0; c < NCLASS; ++c) {
         const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
         if (p1 <= p0) continue;
-        CUDA_TRY(cudaStreamWaitEvent(h->side[c], h->fork, 0));
-        CUDA_TRY(launch(c, p0, p1, h->side[c]));
-        CUDA_TRY(cudaEventRecord(h->join[c], h->side[c]));
+        CUDA_TRY(cudaStreamWaitEvent(h->mside[c], h->mfork, 0));
+        CUDA_TRY(launch(c, p0, p1, h->mside[c]));
+        CUDA_TRY(cudaEventRecord(h->mjoin[c], h->mside[c]));
     }
     for (int c = 0; c < NCLASS; ++c)
-        if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join[c], 0));
+        if (h->class_off[c + 1] > h->class_off[c]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->mjoin[c], 0));
     return QMMM_OK;
 }
 
@@ -1187,9 +1203,13 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         CUDA_TRY(launch_gfac(e, h->gfac.p, nullptr));
         for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventCreate(&h->ev[k]));
         CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&h->mfork, cudaEventDisableTiming));
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->tstream, cudaStreamNonBlocking));
         for (int c = 0; c < NCLASS; ++c) {
             CUDA_TRY(cudaStreamCreateWithFlags(&h->side[c], cudaStreamNonBlocking));
             CUDA_TRY(cudaEventCreateWithFlags(&h->join[c], cudaEventDisableTiming));
+            CUDA_TRY(cudaStreamCreateWithFlags(&h->mside[c], cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->mjoin[c], cudaEventDisableTiming));
         }
     }
     for (int k = 0; k < SW_NKIND; ++k) reset_tuning(h, k);
@@ -1355,11 +1375,13 @@ int qmmm_energy(qmmm_handle *h, const double *dmat, double *E)
     return finish(h, 0);
 }
 
-// The forces in three parts, so that a batch can run the region-I adjoint sweeps of all its
-// frames together between the first and the last.  forces_begin: the density, cleared outputs,
-// multipoles with the Pulay term, the nuclear-MM region-I term and the multipolar Ewald sums
-// (everything but the sweep; all of them add into the same gradients as the sweep).
-static int forces_begin(qmmm_handle *h, const double *dmat, const double **ddm)
+// The forces in parts.  forces_prep: the density and the cleared outputs.  forces_sweep: the
+// region-I adjoint sweep (all classes on the class streams, left unjoined).  forces_rest:
+// multipoles with the Pulay term, the nuclear-MM region-I term and the multipolar Ewald sums.  The
+// sweep needs only the density and the cleared outputs, and every kernel adds to the gradients
+// atomically, so the sweep may run beside the rest (a batch runs the sweeps of all its frames
+// together).  forces_end: region-I charge gradients to the MM atoms, the user's order, copies out.
+static int forces_prep(qmmm_handle *h, const double *dmat, const double **ddm)
 {
     cudaStream_t st = h->stream;
     int rc;
@@ -1370,16 +1392,9 @@ static int forces_begin(qmmm_handle *h, const double *dmat, const double **ddm)
     CUDA_TRY(cudaMemsetAsync(h->gchg.p, 0, 4 * (size_t)std::max(h->nI, 1) * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(h->dq_int.p, 0, (size_t)std::max(h->nmm, 1) * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(h->dR_int.p, 0, 3 * (size_t)std::max(h->nmm, 1) * sizeof(double), st));
-    if ((rc = compute_multipoles(h, *ddm, nullptr, MOM_PULAY))) return rc;
-    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, h->gqm.p,
-                           h->gchg.p, 1, st));
-    const EwaldDev e = h->ewald();
-    CUDA_TRY(launch_ewald_mm(e, h->rI.p, h->nmm > 0 ? h->nI : 0, h->mult.p, h->phi.p, h->ew, h->dq_int.p,
-                             h->dR_int.p, h->gchg.p, h->gqm.p, h->precision == QMMM_MIXED, st));
     return QMMM_OK;
 }
 
-// The region-I adjoint sweep of one frame (all classes concurrently).
 static int forces_sweep(qmmm_handle *h, const double *ddm)
 {
     int rc;
@@ -1394,13 +1409,25 @@ static int forces_sweep(qmmm_handle *h, const double *ddm)
                 return launch_sweep(h, kind, cls, p0, p1, c0, c1, share, variant, nsl, 0, ddm, nullptr, h->gqm.p,
                                     h->gchg.p, cs);
             },
-            ns, std::max(1, std::min(8, (c1 - c0) / 128)), c1 - c0);
+            ns, std::max(1, std::min(8, (c1 - c0) / 128)), c1 - c0, false);
         if (rc) return rc;
     }
     return QMMM_OK;
 }
 
-// Region-I charge gradients to the MM atoms, the user's order, copies out.
+static int forces_rest(qmmm_handle *h, const double *ddm)
+{
+    cudaStream_t st = h->stream;
+    int rc;
+    if ((rc = compute_multipoles(h, ddm, nullptr, MOM_PULAY))) return rc;
+    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, h->gqm.p,
+                           h->gchg.p, 1, st));
+    const EwaldDev e = h->ewald();
+    CUDA_TRY(launch_ewald_mm(e, h->rI.p, h->nmm > 0 ? h->nI : 0, h->mult.p, h->phi.p, h->ew, h->dq_int.p,
+                             h->dR_int.p, h->gchg.p, h->gqm.p, h->precision == QMMM_MIXED, st));
+    return QMMM_OK;
+}
+
 static int forces_end(qmmm_handle *h, double *dE_dRqm, double *dE_dRmm, double *dE_dq)
 {
     cudaStream_t st = h->stream;
@@ -1422,10 +1449,18 @@ int qmmm_forces(qmmm_handle *h, const double *dmat, double *dE_dRqm, double *dE_
     if (!h || !dmat) return fail(QMMM_ERR_ARG, "null handle or density");
     int rc;
     const double *ddm;
-    if ((rc = forces_begin(h, dmat, &ddm))) return rc;
+    if ((rc = forces_prep(h, dmat, &ddm))) return rc;
     CUDA_TRY(mark(h, 0));
     if ((rc = forces_sweep(h, ddm))) return rc;
-    CUDA_TRY(mark(h, 1));
+    if (!h->quiet) {  // the sweep's own end, for its timing
+        if ((rc = join_classes(h, h->tstream))) return rc;
+        CUDA_TRY(cudaEventRecord(h->ev[1], h->tstream));
+    }
+    // The rest follows the sweep: run beside it, it delayed the FP64 classes, which hold their
+    // shares of the SMs for the whole sweep (large site: FP64 step 461 -> 496 ms), and on the mixed
+    // path it saved 2.6 of 49.6 ms but left the sweep's own duration unmeasurable
+    if ((rc = join_classes(h, h->stream))) return rc;
+    if ((rc = forces_rest(h, ddm))) return rc;
     if ((rc = forces_end(h, dE_dRqm, dE_dRmm, dE_dq))) return rc;
     CUDA_TRY(mark(h, 2));
     return finish(h, 4);
@@ -1784,8 +1819,9 @@ int batch_build_jobs(qmmm_batch *b, const double *const *dm)
     return QMMM_OK;
 }
 
-// The batched adjoint inside the capture: every class over the deferring frames once they have all
-// reached their sweep (one launch of each of the class's three kernels), highest class first.
+// The batched adjoint inside the capture: every class over the deferring frames once all of them
+// have cleared their gradients (one launch of each of the class's three kernels), highest class
+// first, beside the frames' other work.
 int batch_sweeps(qmmm_batch *b, const std::vector<int> &deferred)
 {
     for (int i : deferred) CUDA_TRY(cudaStreamWaitEvent(b->stream, b->adone[i], 0));
@@ -1914,14 +1950,18 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
             if ((e = cudaStreamWaitEvent(b->fst[i], b->fork, 0)) != cudaSuccess) break;
             h->quiet = true;
             if (defer[i]) {
+                // cleared gradients (the batched sweep waits for these of every frame), then V, the
+                // energy and the rest of the forces beside the sweeps
                 const double *ddm = nullptr;
-                rc = qmmm_vpot(h, at(V, i), nullptr);
-                if (!rc && at(E, i)) rc = qmmm_energy(h, dm[i], at(E, i));
-                if (!rc) rc = forces_begin(h, dm[i], &ddm);
+                rc = forces_prep(h, dm[i], &ddm);
+                if (!rc && (e = cudaEventRecord(b->adone[i], b->fst[i])) == cudaSuccess) {
+                    rc = qmmm_vpot(h, at(V, i), nullptr);
+                    if (!rc && at(E, i)) rc = qmmm_energy(h, dm[i], at(E, i));
+                    if (!rc) rc = forces_rest(h, ddm);
+                }
                 h->quiet = false;
                 if (rc) break;
-                e = cudaEventRecord(b->adone[i], b->fst[i]);
-                continue;
+                continue;  // the loop condition stops on a failed record
             }
             rc = batch_frame(h, dm[i], at(V, i), at(E, i), at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
             h->quiet = false;

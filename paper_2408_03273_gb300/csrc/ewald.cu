@@ -897,11 +897,11 @@ __global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_region1(EwaldDev e, co
     }
     double t[4];
     mmq_reduce(red, pot, fld, t);
-    if (warp == 0 && act) {
-        gchg[4 * (size_t)k + 0] += c.w * t[1];
-        gchg[4 * (size_t)k + 1] += c.w * t[2];
-        gchg[4 * (size_t)k + 2] += c.w * t[3];
-        gchg[4 * (size_t)k + 3] -= t[0];
+    if (warp == 0 && act) {  // atomics: the region-I adjoint sweep may add to gchg at the same time
+        atomicAdd(gchg + 4 * (size_t)k + 0, c.w * t[1]);
+        atomicAdd(gchg + 4 * (size_t)k + 1, c.w * t[2]);
+        atomicAdd(gchg + 4 * (size_t)k + 2, c.w * t[3]);
+        atomicAdd(gchg + 4 * (size_t)k + 3, -t[0]);
     }
 }
 
@@ -1210,9 +1210,9 @@ __global__ void k_qm_tensor_grad(int natm, const double *mult, const double *phi
     if (j >= natm) return;
     double p, fl[3];
     contract_pot_field(mult + 10 * j, phi + 20 * j, p, fl);
-    gqm[3 * j] += fl[0];
-    gqm[3 * j + 1] += fl[1];
-    gqm[3 * j + 2] += fl[2];
+    atomicAdd(gqm + 3 * j, fl[0]);  // atomics: the region-I adjoint sweep may run at the same time
+    atomicAdd(gqm + 3 * j + 1, fl[1]);
+    atomicAdd(gqm + 3 * j + 2, fl[2]);
 }
 
 cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, const double *mult, const double *phi,
@@ -1337,11 +1337,11 @@ k_enucmm(const double *qm_xyz, const double *Z, int natm, const double4_32a *rI,
         for (int w = 0; w < ENUC_WARPS; ++w)
 #pragma unroll
             for (int v = 0; v < 5; ++v) t[v] += red[v][w][lane];
-        if (want_grad && act) {
-            gchg[4 * (size_t)k + 0] += t[2];
-            gchg[4 * (size_t)k + 1] += t[3];
-            gchg[4 * (size_t)k + 2] += t[4];
-            gchg[4 * (size_t)k + 3] += t[1];
+        if (want_grad && act) {  // atomics: the region-I adjoint sweep may add at the same time
+            atomicAdd(gchg + 4 * (size_t)k + 0, t[2]);
+            atomicAdd(gchg + 4 * (size_t)k + 1, t[3]);
+            atomicAdd(gchg + 4 * (size_t)k + 2, t[4]);
+            atomicAdd(gchg + 4 * (size_t)k + 3, t[1]);
         }
         const double e = warp_sum(t[0]);
         if (lane == 0) Epart[blockIdx.x] = e;
