@@ -1259,27 +1259,42 @@ int qmmm_set_positions(qmmm_handle *h, const double *qm_xyz, const double *mm_xy
     return run_positions(h, qm_xyz, mm_xyz, mm_q);
 }
 
-int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
+// qmmm_vpot in parts (a batch runs the mixed V sweeps of all its frames together):
+// vpot_prep clears V, or the per-slice partial matrices when slices is set (then *Vdst points at
+// them and *nbuf is their count); vpot_sweep runs the class sweeps; vpot_end sums the slices, adds
+// the nuclear-MM energy and copies out.
+static int vpot_prep(qmmm_handle *h, bool slices, double **Vdst, int *nbuf)
 {
-    if (!h) return fail(QMMM_ERR_ARG, "null handle");
     cudaStream_t st = h->stream;
     int rc;
-    if ((rc = h->V.ensure((size_t)h->nao * h->nao))) return rc;
-    CUDA_TRY(cudaMemsetAsync(h->V.p, 0, (size_t)h->nao * h->nao * sizeof(double), st));
-    const int kind = sweep_kind(h, false), ch = chunk_for_kind(kind);
     const size_t n2 = (size_t)h->nao * h->nao;
+    if ((rc = h->V.ensure(n2))) return rc;
+    CUDA_TRY(cudaMemsetAsync(h->V.p, 0, n2 * sizeof(double), st));
+    *Vdst = h->V.p;
+    *nbuf = 1;
+    if (!slices) return QMMM_OK;
+    const int kind = sweep_kind(h, false), ch = chunk_for_kind(kind);
     const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
     // otherwise per-class charge slices (class_slices), as many as the per-slice partial
     // matrices' memory allows
     const int maxsl = ns > 1 ? 1 : vpot_max_slices(std::min(h->nI, ch), n2);
-    const int nbuf = std::max(ns, maxsl);
-    double *Vdst = h->V.p;
-    if (nbuf > 1) {  // per-slice partial V, summed in a fixed order afterwards
-        if ((rc = h->Vslices.ensure((size_t)nbuf * n2))) return rc;
-        CUDA_TRY(cudaMemsetAsync(h->Vslices.p, 0, (size_t)nbuf * n2 * sizeof(double), st));
-        Vdst = h->Vslices.p;
+    *nbuf = std::max(ns, maxsl);
+    if (*nbuf > 1) {  // per-slice partial V, summed in a fixed order afterwards
+        if ((rc = h->Vslices.ensure((size_t)*nbuf * n2))) return rc;
+        CUDA_TRY(cudaMemsetAsync(h->Vslices.p, 0, (size_t)*nbuf * n2 * sizeof(double), st));
+        *Vdst = h->Vslices.p;
     }
     CUDA_TRY(mark(h, 0));
+    return QMMM_OK;
+}
+
+static int vpot_sweep(qmmm_handle *h, double *Vdst, int nbuf)
+{
+    int rc;
+    const int kind = sweep_kind(h, false), ch = chunk_for_kind(kind);
+    const size_t n2 = (size_t)h->nao * h->nao;
+    const int ns = sweep_slices(h, kind, std::min(h->nI, ch));
+    const int maxsl = ns > 1 ? 1 : vpot_max_slices(std::min(h->nI, ch), n2);
     for (int c0 = 0; c0 < h->nI; c0 += ch) {
         const int c1 = std::min(h->nI, c0 + ch);
         rc = run_classes(
@@ -1291,17 +1306,35 @@ int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
             ns, maxsl, c1 - c0);
         if (rc) return rc;
     }
+    return QMMM_OK;
+}
+
+static int vpot_end(qmmm_handle *h, int nbuf, double *Vout, double *E_nuc_mm)
+{
+    cudaStream_t st = h->stream;
+    int rc;
+    const size_t n2 = (size_t)h->nao * h->nao;
     if (nbuf > 1) CUDA_TRY(launch_sum_slices_d(h->Vslices.p, nbuf, n2, h->V.p, st));
     CUDA_TRY(mark(h, 1));
     CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
                            nullptr, 0, st));
     CUDA_TRY(launch_sum(h->Epart.p, enucmm_nblk(h->nI), h->out4.p + 4, st));
-    if ((rc = copy_out(h, Vout, h->V.p, (size_t)h->nao * h->nao))) return rc;
+    if ((rc = copy_out(h, Vout, h->V.p, n2))) return rc;
     if ((rc = copy_out(h, E_nuc_mm, h->out4.p + 4, 1))) return rc;
     CUDA_TRY(mark(h, 2));
     if ((rc = finish(h, 3))) return rc;
     h->V_valid = true;
     return QMMM_OK;
+}
+
+int qmmm_vpot(qmmm_handle *h, double *Vout, double *E_nuc_mm)
+{
+    if (!h) return fail(QMMM_ERR_ARG, "null handle");
+    int rc, nbuf;
+    double *Vdst;
+    if ((rc = vpot_prep(h, true, &Vdst, &nbuf))) return rc;
+    if ((rc = vpot_sweep(h, Vdst, nbuf))) return rc;
+    return vpot_end(h, nbuf, Vout, E_nuc_mm);
 }
 
 static int compute_multipoles(qmmm_handle *h, const double *ddm, double *F, int extra_mode)
@@ -1682,6 +1715,11 @@ struct qmmm_batch {
     DBuf<ClJob> jobs;
     DBuf<int> counter;
     int job_off[NCLASS] = {}, njob[NCLASS] = {}, nthr[NCLASS] = {}, nitems[NCLASS] = {}, variant[NCLASS] = {};
+    // the batched mixed V sweep: per class a job table region (vjobs + vjob_off[c]), its blocks,
+    // the most charges of one block's slice and the block variant; V of every frame done (vdone)
+    DBuf<VJob> vjobs;
+    int vjob_off[NCLASS] = {}, nvjob[NCLASS] = {}, vblk[NCLASS] = {}, vmaxch[NCLASS] = {}, vvariant[NCLASS] = {};
+    cudaEvent_t vdone = nullptr, vjoin[NCLASS] = {};
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> key;  // what the graph was recorded for
     std::vector<int> planned_nI; // each frame's region-I size at the last plain pass (buffer sizes)
@@ -1702,12 +1740,15 @@ struct qmmm_batch {
             if (e) cudaEventDestroy(e);
         if (all_a) cudaEventDestroy(all_a);
         if (sweeps) cudaEventDestroy(sweeps);
+        if (vdone) cudaEventDestroy(vdone);
         for (int c = 0; c < NCLASS; ++c) {
             if (cjoin[c]) cudaEventDestroy(cjoin[c]);
+            if (vjoin[c]) cudaEventDestroy(vjoin[c]);
             if (cst[c]) cudaStreamDestroy(cst[c]);
         }
         jobs.release();
         counter.release();
+        vjobs.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -1816,6 +1857,51 @@ int batch_build_jobs(qmmm_batch *b, const double *const *dm)
     if ((rc = b->jobs.ensure(std::max<size_t>(all.size(), 1))) || (rc = b->counter.ensure(NCLASS))) return rc;
     if (!all.empty())
         CUDA_TRY(cudaMemcpy(b->jobs.p, all.data(), all.size() * sizeof(ClJob), cudaMemcpyHostToDevice));
+
+    // the V sweep: per class one job per deferring frame, each charge slice (at most CHUNK_F32
+    // charges) in blocks of one 32-pair tile per warp; the block variant of the frame with the
+    // most work in the class
+    std::vector<VJob> vall;
+    for (int c = 0; c < NCLASS; ++c) {
+        b->vjob_off[c] = (int)vall.size();
+        b->nvjob[c] = b->vblk[c] = b->vmaxch[c] = 0;
+        double best = -1.0;
+        b->vvariant[c] = 0;
+        for (qmmm_handle *h : b->f) {
+            if (!batch_defers(h)) continue;
+            const double w = (double)(h->class_off[c + 1] - h->class_off[c]) * h->nI;
+            if (w > best) {
+                best = w;
+                b->vvariant[c] = h->cls_variant[SW_VPOT_F32][c];
+            }
+        }
+        const int nwarp = variant_threads(SW_VPOT_F32, c, b->vvariant[c]) / 32;
+        int blk = 0;
+        for (size_t i = 0; i < b->f.size(); ++i) {
+            qmmm_handle *h = b->f[i];
+            const int p0 = h->class_off[c], p1 = h->class_off[c + 1];
+            if (!batch_defers(h) || p1 <= p0) continue;
+            VJob J{};
+            J.bd = h->basis();
+            J.rg = h->region();
+            J.V = h->V.p;
+            J.pp_begin = p0;
+            J.pp_end = p1;
+            J.ch_begin = 0;
+            J.ch_end = h->nI;
+            J.ns = (h->nI + CHUNK_F32 - 1) / CHUNK_F32;
+            J.gx = ((p1 - p0 + 31) / 32 + nwarp - 1) / nwarp;
+            J.blk0 = blk;
+            blk += J.gx * J.ns;
+            b->vmaxch[c] = std::max(b->vmaxch[c], (h->nI + J.ns - 1) / J.ns);
+            vall.push_back(J);
+            ++b->nvjob[c];
+        }
+        b->vblk[c] = blk;
+    }
+    if ((rc = b->vjobs.ensure(std::max<size_t>(vall.size(), 1)))) return rc;
+    if (!vall.empty())
+        CUDA_TRY(cudaMemcpy(b->vjobs.p, vall.data(), vall.size() * sizeof(VJob), cudaMemcpyHostToDevice));
     return QMMM_OK;
 }
 
@@ -1829,13 +1915,20 @@ int batch_sweeps(qmmm_batch *b, const std::vector<int> &deferred)
     const qmmm_handle *h0 = b->f[deferred[0]];
     for (int i = 0; i < NCLASS; ++i) {
         const int c = NCLASS - 1 - i;
-        if (!b->njob[c]) continue;
+        if (!b->njob[c] && !b->nvjob[c]) continue;
         CUDA_TRY(cudaStreamWaitEvent(b->cst[c], b->all_a, 0));
+        CUDA_TRY(launch_vpot_f32_jobs(c, b->vjobs.p + b->vjob_off[c], b->nvjob[c], b->vblk[c], b->vmaxch[c],
+                                      h0->boys32.p, h0->err.p, b->vvariant[c], b->cst[c]));
+        CUDA_TRY(cudaEventRecord(b->vjoin[c], b->cst[c]));
         CUDA_TRY(launch_vgrad_cl_jobs(c, b->jobs.p + b->job_off[c], b->njob[c], b->nthr[c], b->nitems[c],
                                       b->counter.p + c, h0->boys32.p, b->variant[c], h0->nsm, b->cst[c]));
         CUDA_TRY(cudaEventRecord(b->cjoin[c], b->cst[c]));
-        CUDA_TRY(cudaStreamWaitEvent(b->stream, b->cjoin[c], 0));
     }
+    for (int c = 0; c < NCLASS; ++c)
+        if (b->njob[c] || b->nvjob[c]) CUDA_TRY(cudaStreamWaitEvent(b->stream, b->vjoin[c], 0));
+    CUDA_TRY(cudaEventRecord(b->vdone, b->stream));
+    for (int c = 0; c < NCLASS; ++c)
+        if (b->njob[c] || b->nvjob[c]) CUDA_TRY(cudaStreamWaitEvent(b->stream, b->cjoin[c], 0));
     CUDA_TRY(cudaEventRecord(b->sweeps, b->stream));
     return QMMM_OK;
 }
@@ -1874,9 +1967,11 @@ int qmmm_batch_create(qmmm_handle *const *frames, int nframes, void *stream, qmm
     }
     CUDA_TRY(cudaEventCreateWithFlags(&b->all_a, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&b->sweeps, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->vdone, cudaEventDisableTiming));
     for (int c = 0; c < NCLASS; ++c) {
         CUDA_TRY(cudaStreamCreateWithFlags(&b->cst[c], cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreateWithFlags(&b->cjoin[c], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&b->vjoin[c], cudaEventDisableTiming));
     }
     b->ms.assign(nframes + 1, 0.0);
     *out = b.release();
@@ -1950,15 +2045,14 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
             if ((e = cudaStreamWaitEvent(b->fst[i], b->fork, 0)) != cudaSuccess) break;
             h->quiet = true;
             if (defer[i]) {
-                // cleared gradients (the batched sweep waits for these of every frame), then V, the
-                // energy and the rest of the forces beside the sweeps
+                // cleared V and gradients (the batched sweeps wait for these of every frame), then
+                // the forces' other parts beside the sweeps; V and the energy follow below
                 const double *ddm = nullptr;
-                rc = forces_prep(h, dm[i], &ddm);
-                if (!rc && (e = cudaEventRecord(b->adone[i], b->fst[i])) == cudaSuccess) {
-                    rc = qmmm_vpot(h, at(V, i), nullptr);
-                    if (!rc && at(E, i)) rc = qmmm_energy(h, dm[i], at(E, i));
-                    if (!rc) rc = forces_rest(h, ddm);
-                }
+                double *Vdst;
+                int nbuf;
+                rc = vpot_prep(h, false, &Vdst, &nbuf);
+                if (!rc) rc = forces_prep(h, dm[i], &ddm);
+                if (!rc && (e = cudaEventRecord(b->adone[i], b->fst[i])) == cudaSuccess) rc = forces_rest(h, ddm);
                 h->quiet = false;
                 if (rc) break;
                 continue;  // the loop condition stops on a failed record
@@ -1975,11 +2069,14 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
         for (size_t k = 0; k < deferred.size() && e == cudaSuccess && !rc; ++k) {
             const int i = deferred[k];
             qmmm_handle *h = b->f[i];
-            if ((e = cudaStreamWaitEvent(b->fst[i], b->sweeps, 0)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(b->fst[i], b->vdone, 0)) != cudaSuccess) break;
             h->quiet = true;
-            rc = forces_end(h, at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
+            rc = vpot_end(h, 1, at(V, i), nullptr);
+            if (!rc && at(E, i)) rc = qmmm_energy(h, dm[i], at(E, i));
+            if (!rc && (e = cudaStreamWaitEvent(b->fst[i], b->sweeps, 0)) == cudaSuccess)
+                rc = forces_end(h, at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
             h->quiet = false;
-            if (rc) break;
+            if (rc || e != cudaSuccess) break;
             if ((e = cudaEventRecordWithFlags(b->done[i], b->fst[i], cudaEventRecordExternal)) != cudaSuccess) break;
             if ((e = cudaEventRecord(b->join[i], b->fst[i])) != cudaSuccess) break;
             e = cudaStreamWaitEvent(b->stream, b->join[i], 0);

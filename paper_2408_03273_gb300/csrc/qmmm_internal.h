@@ -57,6 +57,20 @@ cudaError_t launch_vpot_f64(const BasisDev &b, const RegionDev &r, int cls, int 
 cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                             int ch_begin, int ch_end, const float *boys, double *V, int *err, int nsm, int variant,
                             int nslice, size_t vstride, cudaStream_t st);
+// One frame's share of a class's mixed V sweep: its basis, region I and V, the primitive pairs
+// [pp_begin, pp_end) and region-I charges [ch_begin, ch_end) in ns slices of gx blocks each, its
+// blocks [blk0, blk0 + gx ns) of a batched launch.
+struct VJob {
+    BasisDev bd;
+    RegionDev rg;
+    double *V;
+    int pp_begin, pp_end, ch_begin, ch_end;
+    int gx, ns, blk0;
+};
+// The mixed V sweep of class cls over njob frames in one launch of nblk blocks, every block adding
+// into its frame's V; maxch: the most charges of one slice (<= CHUNK_F32).
+cudaError_t launch_vpot_f32_jobs(int cls, const VJob *jobs, int njob, int nblk, int maxch, const float *boys,
+                                 int *err, int variant, cudaStream_t st);
 cudaError_t launch_vgrad_f64(const BasisDev &b, const RegionDev &r, int cls, int pp_begin, int pp_end,
                              int ch_begin, int ch_end, const double *boys, const double *dm, double *gqm,
                              double *gchg /* n*4: dC xyz, dq */, int *err, int nsm, int variant, int nslice,

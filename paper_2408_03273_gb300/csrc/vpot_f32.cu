@@ -19,26 +19,48 @@ struct VpotF32 {
                            int ch_end, const float *boys, double *V, int *err, int nsm, int variant, int nslice,
                            size_t vstride,
                            cudaStream_t st);
+    static cudaError_t run_jobs(const VJob *jobs, int njob, int nblk, int maxch, const float *boys, int *err,
+                                int variant, cudaStream_t st);
 };
 
 #ifdef QMMM_SPLIT_CLASS  // one angular class per compilation
 
 constexpr int FOLD = 16;
 
+// A block is (bx, slice) of a job: with jobs == nullptr the single job `one` over the grid
+// (gx, ns) = (gridDim.x, gridDim.y); otherwise block blockIdx.x of the flat range of all jobs,
+// job j owning blocks [blk0, blk0 + gx ns) (the batched form over many frames).
 template <int LA, int LB, int NT>
 __global__ void __launch_bounds__(NT, 1)
-k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, int ch_end,
-           const float *__restrict__ boys_g, unsigned boys_bytes, double *__restrict__ V, size_t vstride, int *err)
+k_vpot_f32(VJob one, const VJob *__restrict__ jobs, int njob, const float *__restrict__ boys_g, unsigned boys_bytes,
+           size_t vstride, int *err)
 {
-    V += (size_t)blockIdx.y * vstride;  // per-slice partial V when the charges are split
+    int bx = (int)blockIdx.x, by = (int)blockIdx.y;
+    if (jobs) {
+        int lo = 0, hi = njob - 1;  // the last job with blk0 <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&jobs[mid].blk0) <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        one = jobs[lo];
+        const int local = (int)blockIdx.x - one.blk0;
+        bx = local % one.gx;
+        by = local / one.gx;
+    }
+    const BasisDev &bd = one.bd;
+    const RegionDev &rg = one.rg;
+    const int pp_begin = one.pp_begin, pp_end = one.pp_end, gx = one.gx;
+    double *__restrict__ V = one.V + (size_t)by * vstride;  // per-slice partial V when the charges are split
     constexpr int L = LA + LB, NH = nherm(L), NA = ncart(LA), NB = ncart(LB);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    int ch_begin, ch_end;
     {
-        // this block row's slice of the charge chunk (gridDim.y > 1 spreads small systems over more SMs)
-        const int per = (ch_end - ch_begin + (int)gridDim.y - 1) / (int)gridDim.y;
-        ch_begin += (int)blockIdx.y * per;
-        ch_end = min(ch_end, ch_begin + per);
+        // this block row's slice of the charge chunk (several slices spread small systems over more SMs)
+        const int per = (one.ch_end - one.ch_begin + one.ns - 1) / one.ns;
+        ch_begin = one.ch_begin + by * per;
+        ch_end = min(one.ch_end, ch_begin + per);
     }
     if (ch_begin >= ch_end) return;
     const int nch = ch_end - ch_begin;
@@ -54,7 +76,7 @@ k_vpot_f32(BasisDev bd, RegionDev rg, int pp_begin, int pp_end, int ch_begin, in
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int ntile = (pp_end - pp_begin + 31) >> 5;
-    for (int tile = blockIdx.x * nwarp + warp; tile < ntile; tile += gridDim.x * nwarp) {
+    for (int tile = bx * nwarp + warp; tile < ntile; tile += gx * nwarp) {
         const PPLane pl = load_pp(bd, pp_begin + tile * 32 + lane, pp_end);
         float Ph[3], Plo[3];
 #pragma unroll
@@ -164,9 +186,39 @@ static cudaError_t launch_nt(const BasisDev &bd, const RegionDev &rg, int pp_beg
     int grid = (ntile + NT / 32 - 1) / (NT / 32);
     if (grid > nsm) grid = nsm;
     if (grid < 1) return cudaSuccess;
-    k_vpot_f32<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(bd, rg, pp_begin, pp_end, ch_begin, ch_end,
-                                                                 boys + (size_t)(LA + LB) * BOYS_TAB_F, tb, V,
-                                                                 vstride, err);
+    VJob one{};
+    one.bd = bd;
+    one.rg = rg;
+    one.V = V;
+    one.pp_begin = pp_begin;
+    one.pp_end = pp_end;
+    one.ch_begin = ch_begin;
+    one.ch_end = ch_end;
+    one.gx = grid;
+    one.ns = nslice;
+    k_vpot_f32<LA, LB, NT><<<dim3(grid, nslice), NT, smem, st>>>(one, nullptr, 0, boys + (size_t)(LA + LB) * BOYS_TAB_F,
+                                                                 tb, vstride, err);
+    return cudaGetLastError();
+}
+
+// every job's blocks in one launch; maxch: the most charges of one block's slice over the jobs
+template <int LA, int LB, int NT>
+static cudaError_t launch_nt_jobs(const VJob *jobs, int njob, int nblk, int maxch, const float *boys, int *err,
+                                  cudaStream_t st)
+{
+    const unsigned tb = boys32_bytes();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_vpot_f32<LA, LB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(CHUNK_F32 * 2 * sizeof(float4) + tb));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (maxch > CHUNK_F32) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)maxch * 2 * sizeof(float4) + tb;
+    const VJob none{};
+    k_vpot_f32<LA, LB, NT><<<nblk, NT, smem, st>>>(none, jobs, njob, boys + (size_t)(LA + LB) * BOYS_TAB_F, tb, 0,
+                                                   err);
     return cudaGetLastError();
 }
 
@@ -184,6 +236,16 @@ cudaError_t VpotF32<LA, LB>::run(const BasisDev &bd, const RegionDev &rg, int pp
     return launch_nt<LA, LB, 256>(bd, rg, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, nslice, vstride, st);
 }
 
+template <int LA, int LB>
+cudaError_t VpotF32<LA, LB>::run_jobs(const VJob *jobs, int njob, int nblk, int maxch, const float *boys, int *err,
+                                      int variant, cudaStream_t st)
+{
+    constexpr int W = sweep_wide_threads(SW_VPOT_F32, class_of(LA, LB));
+    if constexpr (W > 0)
+        if (variant == 1) return launch_nt_jobs<LA, LB, W>(jobs, njob, nblk, maxch, boys, err, st);
+    return launch_nt_jobs<LA, LB, 256>(jobs, njob, nblk, maxch, boys, err, st);
+}
+
 template struct VpotF32<la_of_class(QMMM_SPLIT_CLASS), lb_of_class(QMMM_SPLIT_CLASS)>;
 
 #else  // the dispatcher
@@ -196,6 +258,24 @@ cudaError_t launch_vpot_f32(const BasisDev &b, const RegionDev &r, int cls, int 
     if (pp_end <= pp_begin || ch_end <= ch_begin) return cudaSuccess;
     return dispatch_class<VpotF32>(cls, b, r, pp_begin, pp_end, ch_begin, ch_end, boys, V, err, nsm, variant,
                                    nslice, vstride, st);
+}
+
+namespace {
+template <int LA, int LB>
+struct VpotJobs {
+    static cudaError_t run(const VJob *jobs, int njob, int nblk, int maxch, const float *boys, int *err, int variant,
+                           cudaStream_t st)
+    {
+        return VpotF32<LA, LB>::run_jobs(jobs, njob, nblk, maxch, boys, err, variant, st);
+    }
+};
+}  // namespace
+
+cudaError_t launch_vpot_f32_jobs(int cls, const VJob *jobs, int njob, int nblk, int maxch, const float *boys,
+                                 int *err, int variant, cudaStream_t st)
+{
+    if (njob <= 0 || nblk <= 0) return cudaSuccess;
+    return dispatch_class<VpotJobs>(cls, jobs, njob, nblk, maxch, boys, err, variant, st);
 }
 
 #endif
