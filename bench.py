@@ -323,8 +323,12 @@ def run_batched(args, q, torch, dev, emit=True):
         b.run(dm, V, E, gq, gm, gc)
     runs, lat = [], []
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for _ in range(args.steps):
+        for k in range(args.steps):
+            if k == args.steps - 1:  # the last timed batch as an NVTX range ("replay/")
+                torch.cuda.nvtx.range_push("replay")
             b.run(dm, V, E, gq, gm, gc)
+            if k == args.steps - 1:
+                torch.cuda.nvtx.range_pop()
             tot, per = b.timing()
             runs.append(tot)
             lat += per
@@ -497,13 +501,17 @@ def main():
         torch.cuda.synchronize()
         rec = {"vpot": [], "grad": []}
         total = 0.0
-        for _ in range(K):
+        for k in range(K):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if k == K - 1:  # the last timed step as an NVTX range (for ncu --nvtx-include "step/")
+                torch.cuda.nvtx.range_push("step")
             e0.record(stream)
             step(hh, qm_d, mm_d, q_d, dm_d, V_d, En_d, EII_d, M_d, gq_d, gm_d, gc_d, rec)
             e1.record(stream)
             e1.synchronize()
+            if k == K - 1:
+                torch.cuda.nvtx.range_pop()
             total += e0.elapsed_time(e1)
         torch.cuda.synchronize()
         if dist:

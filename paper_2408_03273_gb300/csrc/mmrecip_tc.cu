@@ -71,7 +71,7 @@ struct MmrArgs {
     double *dq, *dR;
     int *err;
     int nmm, npad, NX, NY, NZ, npair, nchunk;
-    int nr, cpt, nstg;         // N rows of a tile, channels per tile, stages
+    int nr, nr_last, cpt, nstg;  // N rows of a tile and of the last tile, channels per tile, stages
     int nacc;                  // accumulators (3 or 5)
     double box0;
 };
@@ -84,7 +84,8 @@ template <int NP>
 __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int NSTG = a.nstg, NR = a.nr;
+    // the last N tile may hold fewer channels and rows; the smem layout follows its own NR
+    const int NSTG = a.nstg, NR = (int)blockIdx.y + 1 == (int)gridDim.y ? a.nr_last : a.nr;
     const uint32_t BPL = mmr_bpl(NR), STG = mmr_stage(NR, NP);
     unsigned char *pbuf0 = sm + NSTG * STG;
     uint64_t *bars = reinterpret_cast<uint64_t *>(pbuf0 + NSTG * PBUF);
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
     const int m0 = blockIdx.x * MM;
     // N tile blockIdx.y: channels [kfirst, kfirst + nk), its own B planes
     const int kfirst = blockIdx.y * a.cpt, nk = min(a.cpt, 3 - kfirst);
-    const uint32_t *bpl = a.bpl + (size_t)blockIdx.y * a.nchunk * (NP * BPL / 4);
+    const uint32_t *bpl = a.bpl + (size_t)blockIdx.y * a.nchunk * (NP * mmr_bpl(a.nr) / 4);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < NSTGMAX; ++k) {
@@ -422,10 +423,11 @@ void tc_mmr_shape(const EwaldDev &e, int nacc, int np, MmrShape &sh)
     sh.cpt = cpt;
     sh.ntiles = (3 + cpt - 1) / cpt;
     sh.nr = (2 * cpt * NX + 15) / 16 * 16;
+    sh.nr_last = (2 * (3 - (sh.ntiles - 1) * cpt) * NX + 15) / 16 * 16;
     sh.supported = sh.nr <= maxr && NZ >= PCH;  // a chunk of 8 pairs spans at most two n_y rows
     sh.nstg = mmr_smem(sh.nr, 3, np) <= SMEM_MAX ? 3 : 2;
     sh.phase_rows = (size_t)(NY + NZ) * sh.npad;
-    sh.bplane_words = (size_t)sh.ntiles * sh.nchunk * np * mmr_bpl(sh.nr) / 4;
+    sh.bplane_words = ((size_t)(sh.ntiles - 1) * mmr_bpl(sh.nr) + mmr_bpl(sh.nr_last)) * sh.nchunk * np / 4;
 }
 
 template <int NP>
@@ -468,8 +470,9 @@ static cudaError_t mm_recip_np(const EwaldDev &e, const MmrShape &sh, const MmrB
     const size_t tile_words = (size_t)sh.nchunk * NP * mmr_bpl(sh.nr) / 4;
     for (int tl = 0; tl < sh.ntiles; ++tl) {
         const int kfirst = tl * sh.cpt, nk = std::min(sh.cpt, 3 - kfirst);
-        const long long n = (long long)sh.nr * PCH * sh.nchunk;
-        k_mmr_bplanes<NP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, sh.nr,
+        const int nr = tl + 1 == sh.ntiles ? sh.nr_last : sh.nr;
+        const long long n = (long long)nr * PCH * sh.nchunk;
+        k_mmr_bplanes<NP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e, A, Az, b.cscale, kfirst, nk, nr,
                                                                         sh.nchunk, b.bpl + tl * tile_words);
         if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
     }
@@ -491,6 +494,7 @@ static cudaError_t mm_recip_np(const EwaldDev &e, const MmrShape &sh, const MmrB
     a.npair = sh.npair;
     a.nchunk = sh.nchunk;
     a.nr = sh.nr;
+    a.nr_last = sh.nr_last;
     a.cpt = sh.cpt;
     a.nstg = sh.nstg;
     a.nacc = sh.nacc;

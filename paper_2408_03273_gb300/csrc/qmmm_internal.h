@@ -175,6 +175,7 @@ constexpr int MMR_NP_FP64 = 7, MMR_NP_MIXED = 5;
 struct MmrShape {
     int mtiles = 0, npad = 0, npair = 0, nchunk = 0;  // charge tiles (128), padded charges, (n_y, n_z) pairs, chunks of 8
     int cpt = 3, ntiles = 1, nr = 0, nstg = 3;        // channels per N tile, N tiles, N rows, stages
+    int nr_last = 0;                                  // N rows of the last N tile (fewer channels)
     int nacc = 4;                                     // accumulators (exact levels + 1)
     int np = 7;                                       // digit planes per operand (5 or 7)
     bool supported = false;                           // kx small enough for one channel per tile

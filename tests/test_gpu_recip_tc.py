@@ -3,7 +3,7 @@ and the MM-side sum of the adjoint, as BF16 products of exact 7-bit digit planes
 accumulation of the leading levels.  The region-II potential, energies and gradients against the
 oracle, on shapes that exercise the tiling: ragged line tiles (128 lines), one and several blocks
 of 512 charges, one and two N tiles of the structure factor (2 (2 kz + 1) > 80 rows), ragged
-charge tiles of the MM-side sum, and its fallback for short n_z rows."""
+charge tiles of the MM-side sum, its N tiles of unequal size, and its fallback for short n_z rows."""
 import numpy as np
 import pytest
 
@@ -23,6 +23,9 @@ CASES = {
     "three_blocks": dict(seed=43, n_waters=400, box_A=24.0, kmax=(9, 9, 6)),
     # 2 (2 kz + 1) < 8: the MM-side sum stays on the CUDA cores (a chunk would span three n_y rows)
     "small_kz": dict(seed=44, n_waters=12, kmax=(5, 5, 3)),
+    # MM-side N tiles of unequal size: FP64 path 96 + 48 rows (kx 20), mixed path 128 + 64 (kx 30)
+    "uneven_ntiles_fp64": dict(seed=48, n_waters=12, kmax=(20, 6, 6)),
+    "uneven_ntiles_mixed": dict(seed=49, n_waters=12, kmax=(30, 5, 5)),
 }
 
 
