@@ -65,10 +65,11 @@ def flops_adjoint(L):
 
 CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la(la+1)/2 + lb
 
-# DRAM bytes (read + write) of one adjoint sweep (all angular-class kernels of one call), per
-# (workload, precision), from one ncu capture of the current kernels; a workload or precision
-# without a capture of the current kernels reports None.
-SWEEP_TRAFFIC = {}
+# DRAM bytes (read + write) of one adjoint sweep (all angular-class kernels of one call, the mixed
+# path's pair records and pair gradients included), per (workload, precision), from one ncu
+# capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum); a workload or
+# precision without a capture of the current kernels reports None.
+SWEEP_TRAFFIC = {("c4", "fp64"): 153_470_720, ("c4", "mixed"): 935_563_520}
 
 
 def sweep_flops(info, adjoint):
