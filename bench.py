@@ -445,9 +445,13 @@ def main():
 
     def recip_in_effect(precision):
         if RECIP != q.QMMM_RECIP_AUTO:
-            return RECIP_NAME[RECIP]
-        work = (s.kmax[0] + 1) * (2 * s.kmax[1] + 1) * (2 * s.kmax[2] + 1) * s.nmm
-        return RECIP_NAME[q.QMMM_RECIP_TENSOR if work >= 4e7 else q.QMMM_RECIP_CUDA_CORES]
+            name = RECIP_NAME[RECIP]
+        else:
+            work = (s.kmax[0] + 1) * (2 * s.kmax[1] + 1) * (2 * s.kmax[2] + 1) * s.nmm
+            name = RECIP_NAME[q.QMMM_RECIP_TENSOR if work >= 4e7 else q.QMMM_RECIP_CUDA_CORES]
+        if precision == q.QMMM_MIXED and name == RECIP_NAME[q.QMMM_RECIP_TENSOR]:
+            name = "tensor cores (BF16 products of exact 7-bit digit planes; structure factor FP64 class, MM side 34-bit)"
+        return name
 
     def positions_ms(hh, n=10):
         # set_positions alone (region I and the region-II potential, i.e. the structure factor)
@@ -563,7 +567,7 @@ def main():
         v_maxsl = min(8, min(nI, 4096) // 128, (512 << 20) // max(1, 8 * s.nao * s.nao))
         ch_f = math.ceil(nI / 4096) if nI else 0
         ch_g = math.ceil(nI / 2560) if nI else 0
-        tensor = recip_in_effect(precision) == RECIP_NAME[q.QMMM_RECIP_TENSOR]
+        tensor = recip_in_effect(precision).startswith("tensor cores")
         # MM-side tiling as the library plans it (N rows per tile <= 96 with the FP64 path's five
         # accumulators, <= 160 with the mixed path's three); the sum stays on the CUDA cores if
         # 2 kz + 1 < 8

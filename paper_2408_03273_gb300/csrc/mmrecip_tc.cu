@@ -77,6 +77,71 @@ struct MmrArgs {
 };
 }  // namespace
 
+// Mixed-path epilogue of one charge (row i of the tile) in double-float arithmetic on the FP32
+// pipes: the FP64 pipe (2 FMAs per clock and SM) took about a tenth of the kernel's time for the
+// level join, the row scales and the contraction with X_i(n_x), while the MMA pipeline of the SM
+// stood idle.  The exact levels and the merged one join by error-free two-sums (all terms are
+// FP32 values), the row scales are powers of two (exact), the phases X_i(n_x) come from an FP64
+// start and step and a double-float recurrence; about 44 significant bits throughout, against
+// the 34-bit operands of the sum.
+__device__ __forceinline__ void mmr_epilogue_df(const MmrArgs &a, uint32_t tl, int NR, int kfirst, int nk, bool act,
+                                                int i)
+{
+    double sn, cs;
+    sincospi(-2.0 * (act ? a.mm_xyz[3 * i] : 0.0) / a.box0, &sn, &cs);
+    const c2 step{f2_from(cs), f2_from(sn)};
+    c2 X{f2{1.0f, 0.0f}, f2{0.0f, 0.0f}};
+    const f2 g1 = f2_from(6.283185307179586476925 / a.box0);  // G_x per unit n_x
+    float ph = 0.0f, pl = 0.0f;                               // sum_nx Re(X T_0)
+    float fh[3] = {0.0f, 0.0f, 0.0f}, fl[3] = {0.0f, 0.0f, 0.0f};  // sum_nx Im(X T_k), tile channel kl
+    for (int nx = 0; nx < a.NX; ++nx) {
+#pragma unroll
+        for (int kl = 0; kl < 3; ++kl) {
+            if (kl >= nk) break;
+            const int k = kfirst + kl, col = 2 * (kl * a.NX + nx);
+            uint32_t v[NACCMAX][2];
+#pragma unroll
+            for (int acc = 0; acc < NACCMAX; ++acc) {
+                v[acc][0] = v[acc][1] = 0u;
+                if (acc < a.nacc)
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                                 : "=r"(v[acc][0]), "=r"(v[acc][1])
+                                 : "r"(tl + acc * NR + col)
+                                 : "memory");
+            }
+            tc::tmem_wait_ld();
+            const float sc = (float)(__ldg(a.cscale + k * a.NX + nx) * 0x1p-12);  // a power of two
+            f2 t[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float h = __uint_as_float(v[0][r]), l = 0.0f;
+#pragma unroll
+                for (int acc = 1; acc < NACCMAX; ++acc)
+                    if (acc < a.nacc) df_add(h, l, __uint_as_float(v[acc][r]));
+                t[r] = f2_fast2sum(h * sc, l * sc);
+            }
+            if (k == 0) {
+                f2_mac(ph, pl, X.re, t[0]);
+                f2_mac(ph, pl, f2_neg(X.im), t[1]);
+                const f2 u = f2_add(f2_mul(X.re, t[1]), f2_mul(X.im, t[0]));
+                f2_mac(fh[kl], fl[kl], f2_mul(g1, f2{(float)nx, 0.0f}), u);
+            } else {
+                f2_mac(fh[kl], fl[kl], X.re, t[1]);
+                f2_mac(fh[kl], fl[kl], X.im, t[0]);
+            }
+        }
+        X = c2_mul(X, step);
+    }
+    if (act) {
+        // each channel belongs to exactly one N tile: no two CTAs write the same output
+        const double q = a.mm_q[i];
+        if (kfirst == 0) a.dq[i] += f2_to(ph, pl);
+#pragma unroll
+        for (int kl = 0; kl < 3; ++kl)
+            if (kl < nk) a.dR[3 * i + kfirst + kl] += q * f2_to(fh[kl], fl[kl]);
+    }
+}
+
 // grid (mtiles, N tiles), NTHR threads, mmr_smem() dynamic shared memory; chunk ch uses buffer set
 // ch % nstg.  NP digit planes per operand: 7 (48-bit operands, FP64 class) on the FP64 path, 5
 // (34-bit) on the mixed path.
@@ -254,6 +319,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
             const int row = 32 * warp + lane, i = m0 + row;
             const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
             const bool act = i < a.nmm;
+            if constexpr (NP == MMR_NP_MIXED) {
+                mmr_epilogue_df(a, tl, NR, kfirst, nk, act, i);
+            } else {
             double sn, cs;
             sincospi(-2.0 * (act ? a.mm_xyz[3 * i] : 0.0) / a.box0, &sn, &cs);
             double xr = 1.0, xi = 0.0;
@@ -299,6 +367,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_mm_recip_tc(MmrArgs a)
                 const double q = a.mm_q[i];
                 if (kfirst == 0) a.dq[i] += pot;
                 for (int kl = 0; kl < nk; ++kl) a.dR[3 * i + kfirst + kl] += q * f[kfirst + kl];
+            }
             }
         }
     }
