@@ -36,6 +36,94 @@ struct VgradF32 {
 // by k_cl_pairs once every charge tile has added its sums.
 // ---------------------------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------------------------
+// Two charges of a lane at once: Blackwell's packed FP32 pair instructions (add, mul, fma on a
+// register pair; each component rounded exactly as the scalar instruction), so the contractions,
+// the Hermite recursion and most of the Boys function take half the instructions.
+// ---------------------------------------------------------------------------------------------
+struct f32x2 {
+    float2 v;
+    __device__ __forceinline__ f32x2() {}
+    __device__ __forceinline__ explicit f32x2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ f32x2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ f32x2 mk2(float2 x)
+{
+    f32x2 r;
+    r.v = x;
+    return r;
+}
+__device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b) { return mk2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f32x2 operator*(f32x2 a, f32x2 b) { return mk2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f32x2 fma(f32x2 a, f32x2 b, f32x2 c) { return mk2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ f32x2 operator-(f32x2 a) { return mk2(__fmul2_rn(a.v, make_float2(-1.0f, -1.0f))); }
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) { return fma(b, f32x2(-1.0f), a); }
+
+// boys_arg_f32 for two charges (same operations, componentwise)
+__device__ __forceinline__ void boys_arg_x2(f32x2 rho, f32x2 X, f32x2 Y, f32x2 Z, f32x2 &Th, f32x2 &Tl)
+{
+    const f32x2 x2 = X * X, y2 = Y * Y, z2 = Z * Z;
+    const f32x2 ex = fma(X, X, -x2), ey = fma(Y, Y, -y2), ez = fma(Z, Z, -z2);
+    const f32x2 s = x2 + y2;
+    f32x2 v = s - x2;
+    f32x2 e = (x2 - (s - v)) + (y2 - v);
+    const f32x2 s2 = s + z2;
+    v = s2 - s;
+    e = e + ((s - (s2 - v)) + (z2 - v));
+    const f32x2 lo = e + ((ex + ey) + ez);
+    Th = rho * s2;
+    Tl = fma(rho, s2, -Th) + rho * lo;
+}
+
+// boys_f32 for two charges: both in the table range or both in the asymptotic range take the
+// packed branch; a pair that straddles T = 20 takes the scalar function for each
+template <int M>
+__device__ __forceinline__ void boys_x2(f32x2 T, f32x2 Tlo, f32x2 (&F)[M + 1], const float *__restrict__ tab)
+{
+    const bool ta = T.v.x < BOYS_TMAX_F, tb = T.v.y < BOYS_TMAX_F;
+    if (ta && tb) {
+        const f32x2 kf = fma(T, f32x2(BOYS_INV_STEP_F), f32x2(12582912.0f));
+        const int ka = __float_as_int(kf.v.x) - 0x4B400000, kb = __float_as_int(kf.v.y) - 0x4B400000;
+        const f32x2 x = ((kf - f32x2(12582912.0f)) * f32x2((float)BOYS_STEP_F) - T) - Tlo;  // -(T + Tlo - T_k)
+        const float *ra = tab + ka * BOYS_ROW_F, *rb = tab + kb * BOYS_ROW_F;
+        f32x2 f = fma(f32x2(ra[4], rb[4]), x, f32x2(ra[3], rb[3]));
+        f = fma(f, x, f32x2(ra[2], rb[2]));
+        f = fma(f, x, f32x2(ra[1], rb[1]));
+        f = fma(f, x, f32x2(ra[0], rb[0]));
+        F[M] = f;
+        if (M > 0) {
+            f32x2 ex = fma(x, f32x2(1.0f / 24.0f), f32x2(1.0f / 6.0f));
+            ex = fma(ex, x, f32x2(0.5f));
+            ex = fma(ex, x, f32x2(1.0f));
+            ex = fma(ex, x, f32x2(1.0f));
+            const f32x2 e = f32x2(ra[BOYS_TAYLOR_F], rb[BOYS_TAYLOR_F]) * ex;
+            const f32x2 T2 = f32x2(2.0f) * T, T2l = f32x2(2.0f) * Tlo;
+#pragma unroll
+            for (int m = M; m > 0; --m) F[m - 1] = fma(T2, F[m], fma(T2l, F[m], e)) * f32x2(1.0f / (2 * m - 1));
+        }
+    } else if (!ta && !tb) {
+        f32x2 rs(rsqrtf(T.v.x), rsqrtf(T.v.y));
+        const f32x2 r2 = rs * rs;
+        const f32x2 h = fma(-T, r2, f32x2(1.0f)) - Tlo * r2;  // 1 - (T + Tlo) rs^2
+        rs = fma(f32x2(0.5f) * rs, h, rs);
+        F[0] = f32x2((float)HALF_SQRT_PI) * rs;
+        if (M > 0) {
+            const f32x2 e(__expf(-T.v.x), __expf(-T.v.y));
+            const f32x2 s2 = rs * rs, s2e = fma(rs, rs, -s2);
+            const f32x2 g = (fma(-T, s2, f32x2(1.0f)) - T * s2e) - Tlo * s2;
+            const f32x2 inv2T = f32x2(0.5f) * (s2 + fma(s2, g, s2e));
+#pragma unroll
+            for (int m = 0; m < M; ++m) F[m + 1] = fma(f32x2((float)(2 * m + 1)), F[m], -e) * inv2T;
+        }
+    } else {
+        float Fa[M + 1], Fb[M + 1];
+        boys_f32<M>(T.v.x, Fa, tab, Tlo.v.x);
+        boys_f32<M>(T.v.y, Fb, tab, Tlo.v.y);
+#pragma unroll
+        for (int m = 0; m <= M; ++m) F[m] = f32x2(Fa[m], Fb[m]);
+    }
+}
+
 // Every kernel below serves one class over one or many frames ("jobs"): with jobs == nullptr the
 // single job `one` (a kernel parameter), otherwise the device array jobs[njob], each job's share of
 // the flat thread / item range starting at its thr0 / item0.
@@ -89,9 +177,10 @@ k_cl_records(ClJob one, const ClJob *__restrict__ jobs, int njob, int nthr)
     for (int v = 0; v < 6; ++v) ps[v] = 0.0;
 }
 
-// CPL charges per lane (a block's tile holds CL_NT * CPL charges of one width class, each lane
-// CPL consecutive ones): the per-pair reduction is paid once per CPL charges and the lane has CPL
-// independent chains of Boys/R work; NB pairs per staged batch.  A work item is one (charge tile,
+// CPL charges per lane (a block's tile holds CL_NT * CPL charges of one width class, lane l the
+// entries l, l + CL_NT, ...): the per-pair reduction is paid once per CPL charges and the lane has
+// CPL independent chains of Boys/R work, in packed pairs when CPL is even; NB pairs per staged
+// batch.  A work item is one (charge tile,
 // range of pair batches) of a job.  With counter == nullptr each block does item blockIdx.x;
 // otherwise the grid is persistent and its blocks take items from *counter until nitems are done
 // (the batched form over many frames).
@@ -103,8 +192,14 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
     constexpr int L = LA + LB, NH1 = nherm(L + 1), R4 = cl_rec_floats(L) / 4, NB = cl_batch(L);
     constexpr int TILE = CL_NT * CPL;
     constexpr int PF = (NB * R4 + CL_NT - 1) / CL_NT;  // float4 per thread of a prefetched batch
+    // an even number of charges per lane goes in packed pairs; the coefficients of a record are
+    // then held twice in shared memory, (D0, D0, Dx, Dx) and (Dy, Dy, Dz, Dz), so that each
+    // operand pair of the packed contractions is one aligned register pair of a 16-byte load
+    constexpr bool PACK = CPL % 2 == 0;
+    constexpr int RS = PACK ? 2 + 2 * nherm(L) : R4;  // float4 per record in shared memory
+    constexpr int CP = PACK ? CPL / 2 : 1;
     __shared__ __align__(16) float tab[BOYS_TAB_F];
-    __shared__ __align__(16) float4 buf[2][NB * R4];
+    __shared__ __align__(16) float4 buf[2][NB * RS];
     __shared__ float2 rsq[2][NB];  // (rho, sqrt(kappa / (p + kappa))) per pair of a batch
     __shared__ float ps_h[2][NB * 8], ps_l[2][NB * 8];
     __shared__ int s_item;
@@ -148,11 +243,14 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
         const int bper = (nbatch + gx - 1) / gx;
         const int b0 = (local % gx) * bper, b1 = min(nbatch, b0 + bper);
         if (cbeg >= 0 && b0 < b1) {  // item-uniform
-            // this lane's charges: CPL consecutive region-I entries (inactive ones carry q = 0)
+            // this lane's charges: entries lane + i CL_NT of the tile (inactive ones carry q = 0).
+            // Consecutive region-I charges (the atoms of one water, whose terms cancel) sit in
+            // neighbouring lanes, which the pair-sum reduction combines first; a lane's own charges
+            // belong to different waters
             float4 ch[CPL], cl[CPL];
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                const int j = cbeg + CPL * (int)threadIdx.x + i;
+                const int j = cbeg + (int)threadIdx.x + i * CL_NT;
                 ch[i] = cl[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (j < cend) {
                     ch[i] = __ldg(rg.chg_hi + j);
@@ -163,14 +261,35 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
             // a batch's records: element idx of the batch into smem; the thread holding a record's
             // second float4 (with p) also forms (rho, sq) for the tile's width class, in FP64
             auto put = [&](int s, int idx, float4 v) {
-                buf[s][idx] = v;
-                if (idx % R4 == 1) {
+                const int pp = idx / R4, pos = idx - pp * R4;
+                if (!PACK || pos < 2) {
+                    buf[s][pp * RS + pos] = v;
+                } else {
+                    buf[s][pp * RS + 2 * pos - 2] = make_float4(v.x, v.x, v.y, v.y);
+                    buf[s][pp * RS + 2 * pos - 1] = make_float4(v.z, v.z, v.w, v.w);
+                }
+                if (pos == 1) {
                     const double p = __longlong_as_double(((long long)__float_as_int(v.w) << 32) |
                                                           (unsigned int)__float_as_int(v.z));
                     const double td = kap > 0.0 ? kap / (p + kap) : 1.0;
-                    rsq[s][idx / R4] = make_float2((float)(p * td), (float)sqrt(td));
+                    rsq[s][pp] = make_float2((float)(p * td), (float)sqrt(td));
                 }
             };
+            // packed charge pairs (2j, 2j + 1): negated coordinates, so that the packed additions
+            // form the same correctly rounded displacements as the scalar subtractions
+            f32x2 nh[CP][3], nl[CP][3], q2[CP];
+            if constexpr (PACK) {
+#pragma unroll
+                for (int j = 0; j < CP; ++j) {
+                    nh[j][0] = f32x2(-ch[2 * j].x, -ch[2 * j + 1].x);
+                    nh[j][1] = f32x2(-ch[2 * j].y, -ch[2 * j + 1].y);
+                    nh[j][2] = f32x2(-ch[2 * j].z, -ch[2 * j + 1].z);
+                    nl[j][0] = f32x2(-cl[2 * j].x, -cl[2 * j + 1].x);
+                    nl[j][1] = f32x2(-cl[2 * j].y, -cl[2 * j + 1].y);
+                    nl[j][2] = f32x2(-cl[2 * j].z, -cl[2 * j + 1].z);
+                    q2[j] = f32x2(ch[2 * j].w, ch[2 * j + 1].w);
+                }
+            }
             {
                 const int nb = min(NB, npair - b0 * NB);
                 for (int idx = threadIdx.x; idx < nb * R4; idx += CL_NT)
@@ -197,11 +316,74 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
                 float bp[CPL][4];
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) bp[i][0] = bp[i][1] = bp[i][2] = bp[i][3] = 0.0f;
+                f32x2 bp2[CP][4];
+#pragma unroll
+                for (int j = 0; j < CP; ++j) bp2[j][0] = bp2[j][1] = bp2[j][2] = bp2[j][3] = f32x2(0.0f);
                 for (int p = 0; p < nb; ++p) {
-                    const float4 *r = buf[s] + p * R4;
+                    const float4 *r = buf[s] + p * RS;
                     const float4 h0 = r[0], h1 = r[1];
                     const float2 rq = rsq[s][p];
                     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // this lane's pair sums
+                    if constexpr (PACK) {
+                        f32x2 vv[6];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) vv[c] = f32x2(0.0f);
+                        const f32x2 hx(h0.x), hy(h0.y), hz(h0.z), lx(h0.w), ly(h1.x), lz(h1.y);
+                        const f32x2 rho(rq.x), m2rho(-2.0f * rq.x);
+#pragma unroll
+                        for (int j = 0; j < CP; ++j) {
+                            const f32x2 X = (hx + nh[j][0]) + (lx + nl[j][0]);
+                            const f32x2 Y = (hy + nh[j][1]) + (ly + nl[j][1]);
+                            const f32x2 Z = (hz + nh[j][2]) + (lz + nl[j][2]);
+                            f32x2 T, Tl;
+                            boys_arg_x2(rho, X, Y, Z, T, Tl);
+                            f32x2 F[L + 2];
+                            boys_x2<L + 1>(T, Tl, F, tab);
+                            f32x2 Fn[L + 2];
+                            {
+                                f32x2 sc(rq.y);
+#pragma unroll
+                                for (int n = 0; n <= L + 1; ++n) {
+                                    Fn[n] = sc * F[n];
+                                    sc = sc * m2rho;
+                                }
+                            }
+                            f32x2 R[NH1];
+                            hermite_R_u<L + 1, f32x2>(R, Fn, X, Y, Z);
+                            f32x2 e0(0.0f), ex(0.0f), ey(0.0f), ez(0.0f), gx(0.0f), gy(0.0f), gz(0.0f);
+#pragma unroll
+                            for (int tt = 0; tt <= L; ++tt)
+#pragma unroll
+                                for (int uu = 0; uu <= L; ++uu)
+#pragma unroll
+                                    for (int ww = 0; ww <= L; ++ww) {
+                                        if (tt + uu + ww > L) continue;
+                                        const int k = hidx(tt, uu, ww);
+                                        const float4 da = r[2 + 2 * k], db = r[3 + 2 * k];
+                                        const f32x2 d0(da.x, da.y), dx(da.z, da.w), dy(db.x, db.y), dz(db.z, db.w);
+                                        e0 = fma(d0, R[k], e0);
+                                        ex = fma(d0, R[hidx(tt + 1, uu, ww)], ex);
+                                        ey = fma(d0, R[hidx(tt, uu + 1, ww)], ey);
+                                        ez = fma(d0, R[hidx(tt, uu, ww + 1)], ez);
+                                        gx = fma(dx, R[k], gx);
+                                        gy = fma(dy, R[k], gy);
+                                        gz = fma(dz, R[k], gz);
+                                    }
+                            const f32x2 q = q2[j];
+                            bp2[j][0] = fma(q, ex, bp2[j][0]);
+                            bp2[j][1] = fma(q, ey, bp2[j][1]);
+                            bp2[j][2] = fma(q, ez, bp2[j][2]);
+                            bp2[j][3] = bp2[j][3] - e0;
+                            vv[0] = fma(q, gx, vv[0]);
+                            vv[1] = fma(q, gy, vv[1]);
+                            vv[2] = fma(q, gz, vv[2]);
+                            vv[3] = fma(q, ex, vv[3]);
+                            vv[4] = fma(q, ey, vv[4]);
+                            vv[5] = fma(q, ez, vv[5]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) v[c] = vv[c].v.x + vv[c].v.y;
+                    } else {
 #pragma unroll
                     for (int i = 0; i < CPL; ++i) {
                         // correctly rounded displacement (grid-split hi parts subtract exactly)
@@ -254,6 +436,7 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
                         v[4] = fmaf(q, ey, v[4]);
                         v[5] = fmaf(q, ez, v[5]);
                     }
+                    }
                     // pair sums over the warp's 32 lanes: reduce-scatter of 8 values (6 used), combining
                     // neighbouring lanes first: consecutive region-I charges are the atoms of one water, so
                     // the partial sums cancel early and stay small (a 16-apart pairing first sums unrelated
@@ -290,10 +473,20 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
                         atomicAdd(&ps_l[s][p * 8 + vi], (old - (sum - bv)) + (w1 - bv));
                     }
                 }
+                if constexpr (PACK) {
 #pragma unroll
-                for (int i = 0; i < CPL; ++i)
+                    for (int j = 0; j < CP; ++j)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) df_add(ah[i][c], al[i][c], bp[i][c]);
+                        for (int c = 0; c < 4; ++c) {
+                            df_add(ah[2 * j][c], al[2 * j][c], bp2[j][c].v.x);
+                            df_add(ah[2 * j + 1][c], al[2 * j + 1][c], bp2[j][c].v.y);
+                        }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) df_add(ah[i][c], al[i][c], bp[i][c]);
+                }
                 __syncthreads();  // batch b read by all warps; its pair sums complete
                 if ((int)threadIdx.x < nb * 6) {
                     // each of these threads reads one sum and clears it for batch b + 2 (slots 6, 7 of a
@@ -311,7 +504,7 @@ k_vgrad_cl(ClJob one, const ClJob *__restrict__ jobs, int njob, int nitems, int 
             }
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                const int j = cbeg + CPL * (int)threadIdx.x + i;
+                const int j = cbeg + (int)threadIdx.x + i * CL_NT;
                 if (j < cend) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
