@@ -145,6 +145,40 @@ def test_batch_matches_plain_calls_and_replays(precision):
             h.close()
 
 
+def test_batch_mixes_precisions_and_an_empty_region1():
+    # FP64 frames keep their own sweeps inside the graph while the mixed frames' sweeps run
+    # batched; a mixed frame whose region I is empty has no sweep to batch.  Against each handle's
+    # plain calls, on the recording run and on a replay into cleared outputs.
+    torch = pytest.importorskip("torch")
+    import paper_2408_03273_gb300 as q
+    frames = _frames() + [workloads.small_system(seed=107, n_atoms=2, lmax=1, n_waters=6, cutoff_A=0.3)]
+    precs = [1, 0, 1, 1]
+    hs = [q.Handle(s, precision=p) for s, p in zip(frames, precs)]
+    try:
+        assert hs[3].info["n_region1"] == 0 and all(h.info["n_region1"] > 0 for h in hs[:3])
+        ref = [_plain(h, s, s.dm) for h, s in zip(hs, frames)]
+        dev = torch.device("cuda")
+        dm = [torch.as_tensor(s.dm, device=dev) for s in frames]
+        V, E, gq, gm, gc = _dev_outputs(torch, frames)
+        b = q.Batch(hs)
+        try:
+            for replay in (False, True):
+                if replay:
+                    for t in V + E + gq + gm + gc:
+                        t.zero_()
+                b.run(dm, V, E, gq, gm, gc)
+                for i, p in enumerate(precs):
+                    tol = 1e-12 if p == 0 else 1e-7
+                    for got, key in ((V, "V"), (E, "E"), (gq, "gq"), (gm, "gm"), (gc, "gc")):
+                        assert _close(got[i].cpu(), ref[i][key], tol), (replay, i, key)
+            assert b.captures() == 1
+        finally:
+            b.close()
+    finally:
+        for h in hs:
+            h.close()
+
+
 def test_batch_rejects_host_memory():
     torch = pytest.importorskip("torch")
     import paper_2408_03273_gb300 as q
