@@ -277,10 +277,12 @@ int qmmm_set_tuning(qmmm_handle *h, int kind, const int *threads, const double *
  * geometry, basis and charges) so that one call evaluates, for every frame, V (Eq. 9), the
  * energy E[4] as qmmm_energy, and the gradient as qmmm_forces, at that frame's density.
  *
- * qmmm_batch_run records the whole batch once into a CUDA graph -- every frame on its own stream,
- * its angular-class sweeps on that frame's class streams, so small frames fill the SMs that
- * large ones leave free -- and from then on launches the graph: one launch per call, no host
- * work per kernel.  Before recording it runs the batch once through the plain calls (which
+ * qmmm_batch_run records the whole batch once into a CUDA graph -- every frame on its own stream
+ * -- and from then on launches the graph: one launch per call, no host work per kernel.  The
+ * region-I sweeps of the mixed-precision frames are batched: per angular class one launch of the
+ * V sweep and one of each adjoint kernel over all those frames (job tables in device memory,
+ * written before the recording), beside the frames' multipole and Ewald work; FP64 frames run
+ * their own sweeps on their class streams.  Before recording it runs the batch once through the plain calls (which
  * sizes every buffer and sets every kernel attribute); the graph is recorded again when a frame's
  * region-I size, precision, sweep configuration or any array pointer differs from the recorded
  * one (see qmmm_batch_counts).  Positions change through qmmm_set_positions on the frame's
