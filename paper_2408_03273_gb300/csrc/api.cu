@@ -1309,16 +1309,22 @@ static int vpot_sweep(qmmm_handle *h, double *Vdst, int nbuf)
     return QMMM_OK;
 }
 
-static int vpot_end(qmmm_handle *h, int nbuf, double *Vout, double *E_nuc_mm)
+// enuc == false (a batch frame, whose forces have already formed the nuclear-MM partials): no
+// E_nuc_mm output
+static int vpot_end(qmmm_handle *h, int nbuf, double *Vout, double *E_nuc_mm, bool enuc = true)
 {
     cudaStream_t st = h->stream;
     int rc;
     const size_t n2 = (size_t)h->nao * h->nao;
     if (nbuf > 1) CUDA_TRY(launch_sum_slices_d(h->Vslices.p, nbuf, n2, h->V.p, st));
     CUDA_TRY(mark(h, 1));
-    CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p, nullptr,
-                           nullptr, 0, st));
-    CUDA_TRY(launch_sum(h->Epart.p, enucmm_nblk(h->nI), h->out4.p + 4, st));
+    if (enuc) {
+        CUDA_TRY(launch_enucmm(h->qm.p, h->Zd.p, h->natm, h->rI.p, h->rI_idx.p, h->nI, h->mm_beta.p, h->Epart.p,
+                               nullptr, nullptr, 0, st));
+        CUDA_TRY(launch_sum(h->Epart.p, enucmm_nblk(h->nI), h->out4.p + 4, st));
+    } else {
+        E_nuc_mm = nullptr;
+    }
     if ((rc = copy_out(h, Vout, h->V.p, n2))) return rc;
     if ((rc = copy_out(h, E_nuc_mm, h->out4.p + 4, 1))) return rc;
     CUDA_TRY(mark(h, 2));
@@ -1392,19 +1398,25 @@ int qmmm_density_gradient(qmmm_handle *h, const double *dmat, double *G)
     return finish(h, 0);
 }
 
+// E from V, the multipoles already in h->mult and the nuclear-MM partials (no multipole pass:
+// a batch frame's forces have just formed the same multipoles from the same density)
+static int energy_terms(qmmm_handle *h, const double *ddm, double *E)
+{
+    CUDA_TRY(launch_energy_terms(ddm, h->V.p, h->nao, 1, h->mult.p, h->phi.p, h->natm, h->Epart.p,
+                                 enucmm_nblk(h->nI), h->partials.p, NPART, h->out4.p, h->stream));
+    return copy_out(h, E, h->out4.p, 4);
+}
+
 int qmmm_energy(qmmm_handle *h, const double *dmat, double *E)
 {
     if (!h || !dmat || !E) return fail(QMMM_ERR_ARG, "null argument");
     if (!h->V_valid) return fail(QMMM_ERR_STATE, "qmmm_vpot must run at the current geometry first");
-    cudaStream_t st = h->stream;
     int rc;
     const double *ddm;
     const size_t n2 = (size_t)h->nao * h->nao;
     if ((rc = stage_input(h, dmat, n2, h->dm, &ddm))) return rc;
     if ((rc = compute_multipoles(h, ddm, nullptr, 0))) return rc;
-    CUDA_TRY(launch_energy_terms(ddm, h->V.p, h->nao, 1, h->mult.p, h->phi.p, h->natm, h->Epart.p,
-                                 enucmm_nblk(h->nI), h->partials.p, NPART, h->out4.p, st));
-    if ((rc = copy_out(h, E, h->out4.p, 4))) return rc;
+    if ((rc = energy_terms(h, ddm, E))) return rc;
     return finish(h, 0);
 }
 
@@ -2071,8 +2083,9 @@ int qmmm_batch_run(qmmm_batch *b, const double *const *dm, double *const *V, dou
             qmmm_handle *h = b->f[i];
             if ((e = cudaStreamWaitEvent(b->fst[i], b->vdone, 0)) != cudaSuccess) break;
             h->quiet = true;
-            rc = vpot_end(h, 1, at(V, i), nullptr);
-            if (!rc && at(E, i)) rc = qmmm_energy(h, dm[i], at(E, i));
+            rc = vpot_end(h, 1, at(V, i), nullptr, false);
+            // the energy from the multipoles and nuclear-MM partials the frame's forces formed
+            if (!rc && at(E, i)) rc = energy_terms(h, dm[i], at(E, i));
             if (!rc && (e = cudaStreamWaitEvent(b->fst[i], b->sweeps, 0)) == cudaSuccess)
                 rc = forces_end(h, at(dE_dRqm, i), at(dE_dRmm, i), at(dE_dq, i));
             h->quiet = false;
