@@ -549,11 +549,11 @@ def main():
     #   set_positions: gather, region-I count/scan/fill, real-space, region-I tensors, background
     #     sum, QM-site reciprocal, final = 9, plus the structure factor (tensor cores: max|q|,
     #     phases, B planes, MMA, reduction = 5; CUDA cores: kernel + slice sum = 2)
-    #   vpot: one kernel per class and charge chunk + nuclear-MM term
-    #   ewald: one moments kernel per class + 2 (sum, energy terms)
+    #   vpot: one kernel per class and charge chunk + nuclear-MM term and its sum
+    #   ewald: one moments kernel per class + the energy terms
     #   forces: two moments kernels per class (Pulay) + the adjoint sweep per class and chunk
-    #     (mixed path, classes with l_A + l_B >= 3: pair records, charge-lane sweep, pair
-    #     gradients = 3) + 8 fixed (nuclear-MM, sum, real space, region I, background, tensor
+    #     (mixed path: pair records, charge-lane sweep, pair gradients = 3 per class and chunk)
+    #     + 8 fixed (nuclear-MM, sum, real space, region I, background, tensor
     #     gradient, scatter, unpermute) + the MM-side reciprocal sum (tensor cores: atom phases,
     #     multipole structure factor, phases, scales, B planes per N tile, MMA = 5 + tiles; CUDA
     #     cores: 3)
@@ -562,7 +562,6 @@ def main():
     # whose classes ask for less than half the SMs, which have fewer charges than that here).
     def launches_per_step(precision):
         ncls = sum(1 for n in info["n_prim_pairs_class"] if n > 0)
-        ncl = sum(1 for c, n in enumerate(info["n_prim_pairs_class"]) if n > 0 and CLASS_L[c] >= 3)
         nI = info["n_region1"]
         v_maxsl = min(8, min(nI, 4096) // 128, (512 << 20) // max(1, 8 * s.nao * s.nao))
         ch_f = math.ceil(nI / 4096) if nI else 0
@@ -575,8 +574,8 @@ def main():
         cpt = next((c for c in (3, 2, 1) if 2 * c * kx <= lim), 1)
         mm_tc = tensor and (2 * cpt * kx + 15) // 16 * 16 <= lim and 2 * s.kmax[2] + 1 >= 8
         mm_tiles = -(-3 // cpt)
-        sweep_g = ncls * ch_g + (2 * ncl * ch_g if precision == q.QMMM_MIXED else 0)
-        return (9 + (5 if tensor else 2)) + (ncls * ch_f + 1 + (1 if v_maxsl > 1 else 0)) + (ncls + 2) + \
+        sweep_g = ncls * ch_g * (3 if precision == q.QMMM_MIXED else 1)
+        return (9 + (5 if tensor else 2)) + (ncls * ch_f + 2 + (1 if v_maxsl > 1 else 0)) + (ncls + 1) + \
             (2 * ncls + sweep_g + 8 + ((5 + mm_tiles) if mm_tc else 3))
 
     per_step = launches_per_step(prec)
