@@ -509,7 +509,7 @@ cudaError_t launch_mm_recip_tc(const EwaldDev &e, const MmrShape &sh, const MmrB
 {
     if (e.nmm == 0) return cudaSuccess;
     cudaError_t rc;
-    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
+    const int NX = e.kmax[0] + 1, NY = 2 * e.kmax[1] + 1;
     int4 *Yt = b.phase, *Zt = Yt + (size_t)NY * sh.npad;
     k_mmr_phases<<<(unsigned)((2ll * e.nmm + 255) / 256), 256, 0, st>>>(e, sh.npad, Yt, Zt);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
