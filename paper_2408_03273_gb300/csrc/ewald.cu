@@ -578,6 +578,86 @@ __global__ void __launch_bounds__(256) k_phi_recip(EwaldDev e, const double2 *S,
     block_reduce_store<20>(acc, part + ((size_t)j * ns + sl) * 20, scratch);
 }
 
+// Mixed path: the reciprocal factor times S(G) as double-float (re.h, re.l, im.h, im.l), once per
+// call for all QM atoms
+__global__ void k_gs_df(int n, const double2 *S, const double *gfac, float4 *gS)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double g = gfac[k];
+    const double2 v = S[k];
+    gS[k] = c2_pack(g * v.x, g * v.y);
+}
+
+// k_phi_recip in double-float arithmetic on the FP32 pipes (mixed path): the same terms, about 44
+// significant bits per operation (the region-II potential stays within 1e-10 of the FP64 one),
+// where the FP64 kernel spent about 60 FP64 instructions per (G, atom) on an FP64 pipe that
+// executes 2 of them per clock and SM.
+__global__ void __launch_bounds__(256) k_phi_recip_df(EwaldDev e, const float4 *gS, double *part)
+{
+    __shared__ double scratch[8 * 20];
+    __shared__ float4 ph[3][PHR_MAXN];
+    const int j = blockIdx.x, sl = blockIdx.y, ns = gridDim.y;
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
+    for (int t = threadIdx.x; t < (kx + 1) + NY + NZ; t += blockDim.x) {
+        const int d = t <= kx ? 0 : t <= kx + NY ? 1 : 2;
+        const int idx = d == 0 ? t : d == 1 ? t - (kx + 1) : t - (kx + 1) - NY;
+        const int nn = d == 0 ? idx : idx - e.kmax[d];
+        double sn, cs;
+        sincospi(2.0 * nn * (e.qm_xyz[3 * j + d] / e.box[d]), &sn, &cs);
+        ph[d][idx] = c2_pack(cs, sn);
+    }
+    __syncthreads();
+    const f2 g1[3] = {f2_from(TWO_PI / e.box[0]), f2_from(TWO_PI / e.box[1]), f2_from(TWO_PI / e.box[2])};
+    const f2 sixth = f2_from(1.0 / 6.0);
+    const int per = (n + ns - 1) / ns, k0 = sl * per, k1 = min(n, k0 + per);
+    float ah[20], al[20];
+#pragma unroll
+    for (int c = 0; c < 20; ++c) ah[c] = al[c] = 0.0f;
+    const f2 one{1.0f, 0.0f};
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const float4 w = gS[k];
+        if (w.x == 0.0f && w.z == 0.0f) continue;  // outside the half space (g = 0), or S = 0
+        const int nx = k / (NY * NZ), iy = (k / NZ) % NY, iz = k % NZ;
+        const c2 p = c2_mul(c2_mul(c2_from(ph[0][nx]), c2_from(ph[1][iy])), c2_from(ph[2][iz]));
+        const c2 q = c2_from(w);
+        // exp(i G.R_j) conj(g S): re = c Sr + s Si, im = s Sr - c Si
+        const f2 re = f2_add(f2_mul(p.re, q.re), f2_mul(p.im, q.im));
+        const f2 im = f2_add(f2_mul(p.im, q.re), f2_neg(f2_mul(p.re, q.im)));
+        const f2 G[3] = {f2_mul(g1[0], f2{(float)nx, 0.0f}), f2_mul(g1[1], f2{(float)(iy - ky), 0.0f}),
+                         f2_mul(g1[2], f2{(float)(iz - kz), 0.0f})};
+        f2_mac(ah[0], al[0], re, one);
+        const f2 mim = f2_neg(im), mhre{-0.5f * re.h, -0.5f * re.l};
+        f2 t6[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f2_mac(ah[1 + a], al[1 + a], G[a], mim);
+            t6[a] = f2_mul(f2_mul(G[a], im), sixth);
+        }
+        // u_ab = G_a G_b in the order xx xy xz yy yz zz
+        const f2 u[6] = {f2_mul(G[0], G[0]), f2_mul(G[0], G[1]), f2_mul(G[0], G[2]),
+                         f2_mul(G[1], G[1]), f2_mul(G[1], G[2]), f2_mul(G[2], G[2])};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f2_mac(ah[4 + c], al[4 + c], u[c], mhre);
+        // xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz = u_ab t_c / 6
+        f2_mac(ah[10], al[10], u[0], t6[0]);
+        f2_mac(ah[11], al[11], u[0], t6[1]);
+        f2_mac(ah[12], al[12], u[0], t6[2]);
+        f2_mac(ah[13], al[13], u[1], t6[1]);
+        f2_mac(ah[14], al[14], u[1], t6[2]);
+        f2_mac(ah[15], al[15], u[2], t6[2]);
+        f2_mac(ah[16], al[16], u[3], t6[1]);
+        f2_mac(ah[17], al[17], u[3], t6[2]);
+        f2_mac(ah[18], al[18], u[4], t6[2]);
+        f2_mac(ah[19], al[19], u[5], t6[2]);
+    }
+    double acc[20];
+#pragma unroll
+    for (int c = 0; c < 20; ++c) acc[c] = f2_to(ah[c], al[c]);
+    block_reduce_store<20>(acc, part + ((size_t)j * ns + sl) * 20, scratch);
+}
+
 // G slices per QM atom of the reciprocal part: two blocks per SM in all
 int ewald_recip_nslice(const EwaldDev &e, int nsm)
 {
@@ -720,7 +800,14 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     // reciprocal part at the QM sites (G slices), then the final combination in a fixed order
-    k_phi_recip<<<dim3(e.natm, w.recip_nslice), 256, 0, st>>>(e, w.S, w.gfac, w.precip);
+    if (df && w.gSdf) {
+        const int n = ewald_dense_size(e);
+        k_gs_df<<<(n + 255) / 256, 256, 0, st>>>(n, w.S, w.gfac, w.gSdf);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        k_phi_recip_df<<<dim3(e.natm, w.recip_nslice), 256, 0, st>>>(e, w.gSdf, w.precip);
+    } else {
+        k_phi_recip<<<dim3(e.natm, w.recip_nslice), 256, 0, st>>>(e, w.S, w.gfac, w.precip);
+    }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     k_phi_final<<<e.natm, 32, 0, st>>>(e, w.precip, w.recip_nslice, w.preal, w.real_nslice, w.pr1, w.sums, phi);
     return cudaGetLastError();

@@ -209,6 +209,7 @@ struct EwaldBuf {
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
     double2 *Az = nullptr;       // G_z times A
     float4 *Adf = nullptr;       // A and Az as double-float (re.h, re.l, im.h, im.l), mixed path
+    float4 *gSdf = nullptr;      // 2 g(G) S(G) as double-float, mixed path (region-II potential)
     float4 *Azdf = nullptr;
     double *sums = nullptr;      // [0] sum q_MM, [1] sum Q_QM
     int recip = 0;               // reciprocal sums: 0 CUDA cores (FP64 / double-float), 1 tensor cores
