@@ -149,7 +149,7 @@ __device__ __forceinline__ int cl_job_by_item(const ClJob *jobs, int njob, int i
 }
 
 // Pair records of one class (FP64 Hermite/density algebra, rounded to FP32), once per call; the
-// pair's charge sums are cleared here too.
+// pair's charge sums are cleared here too.  Classes with l_A + l_B <= 3: one thread per pair.
 template <int LA, int LB>
 __global__ void __launch_bounds__(128)
 k_cl_records(ClJob one, const ClJob *__restrict__ jobs, int njob, int nthr)
@@ -175,6 +175,197 @@ k_cl_records(ClJob one, const ClJob *__restrict__ jobs, int njob, int nthr)
     double *ps = J.psum + (size_t)(i - J.pp_begin) * 6;
 #pragma unroll
     for (int v = 0; v < 6; ++v) ps[v] = 0.0;
+}
+
+// The same records for l_A + l_B >= 4.  One thread per pair kept the four folds and the Hermite
+// coefficients in local memory (a 6.7 KB stack frame for (f, f)) and ran a few thousand threads on
+// part of the SMs (1.22 ms for the 8657 (f, f) pairs of the large site).  Here a block holds 32
+// pairs and four warps (eight when the folds are split): warps 0-2 write the coefficients
+// E^{ij}_t (i <= l_A + 1) of their lanes' pairs along x, y, z into shared memory, all warps the
+// pair densities, then warp w folds component w % 4 of every lane's record (D0, Dx, Dy, Dz: the
+// terms of fold_density_dA in the same order) with its Hermite sums in registers (0.45 ms).  For
+// the smaller classes the single thread per pair is faster.
+__host__ __device__ constexpr bool rec_tab(int L) { return L >= 4; }
+template <int LA, int LB>
+__host__ __device__ constexpr int rec_esz()
+{
+    return (LA + 2) * (LB + 1) * (LA + LB + 2);  // E[i][j][t] of one axis, i <= LA + 1
+}
+// Hermite-index halves of a record folded by separate warps (f shells with l >= 2 on the other
+// centre: 56 or 84 sums per fold do not fit in registers beside the operands)
+__host__ __device__ constexpr int rec_split(int L) { return L >= 5 ? 2 : 1; }
+template <int LA, int LB>
+inline size_t rec_smem()
+{
+    return ((size_t)3 * rec_esz<LA, LB>() + ncart(LA) * ncart(LB)) * 32 * sizeof(double);
+}
+
+// f(Ic<I>{}) for I = B .. E-1: every index a compile-time constant, so that the fold's Hermite sums
+// are named registers (pragma unroll left the large classes' loops rolled, the sums in local memory)
+template <int I>
+struct Ic {
+    static constexpr int value = I;
+};
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(Ic<B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+#define IC_VALUE(x) decltype(x)::value
+
+// es: the lane's column of the block's tables (E along x, y, z, then the pair densities g_ab)
+template <int LA, int LB, int C, int K0, int K1>
+__device__ __forceinline__ void rec_fold(const PPLane &pl, const double *es, double (&D)[nherm(LA + LB)])
+{
+    constexpr int L = LA + LB, NA = ncart(LA), NB = ncart(LB), EJ = LB + 1, ET = L + 2, ESZ = rec_esz<LA, LB>();
+    const double *ex = es, *ey = es + ESZ * 32, *ez = es + 2 * ESZ * 32, *gs = es + 3 * ESZ * 32;
+    // read at each use (volatile): the compiler otherwise keeps hundreds of coefficients of the
+    // (f, f) tables live in registers across the unrolled fold
+    auto E = [](const double *e, int i, int j, int t) {
+        return *reinterpret_cast<const volatile double *>(e + ((i * EJ + j) * ET + t) * 32);
+    };
+    const double aop = pl.a * pl.ip;
+    static_for<K0, K1>([&](auto k_) { D[IC_VALUE(k_)] = 0.0; });
+    static_for<0, NA>([&](auto ia_) {
+        static_for<0, NB>([&](auto ib_) {
+            constexpr int ia = IC_VALUE(ia_), ib = IC_VALUE(ib_);
+            constexpr int ax = cart_lx(LA, ia), ay = cart_ly(LA, ia), az = cart_lz(LA, ia);
+            constexpr int bx = cart_lx(LB, ib), by = cart_ly(LB, ib), bz = cart_lz(LB, ib);
+            const double g = gs[(ia * NB + ib) * 32];
+            // E' of the derivative's axis (g folded in along x)
+            double dE[L + 1];
+            (void)dE;
+            if constexpr (C == 1) {
+                static_for<0, ax + bx + 1>([&](auto t_) {
+                    constexpr int t = IC_VALUE(t_);
+                    double e = 2.0 * pl.a * E(ex, ax + 1, bx, t);
+                    if constexpr (ax > 0) e -= ax * E(ex, ax - 1, bx, t);
+                    if constexpr (t > 0) e -= aop * E(ex, ax, bx, t - 1);
+                    dE[t] = g * e;
+                });
+            } else if constexpr (C == 2) {
+                static_for<0, ay + by + 1>([&](auto u_) {
+                    constexpr int u = IC_VALUE(u_);
+                    double e = 2.0 * pl.a * E(ey, ay + 1, by, u);
+                    if constexpr (ay > 0) e -= ay * E(ey, ay - 1, by, u);
+                    if constexpr (u > 0) e -= aop * E(ey, ay, by, u - 1);
+                    dE[u] = e;
+                });
+            } else if constexpr (C == 3) {
+                static_for<0, az + bz + 1>([&](auto w_) {
+                    constexpr int w = IC_VALUE(w_);
+                    double e = 2.0 * pl.a * E(ez, az + 1, bz, w);
+                    if constexpr (az > 0) e -= az * E(ez, az - 1, bz, w);
+                    if constexpr (w > 0) e -= aop * E(ez, az, bz, w - 1);
+                    dE[w] = e;
+                });
+            }
+            static_for<0, ax + bx + 1>([&](auto t_) {
+                constexpr int t = IC_VALUE(t_);
+                const double gx = g * E(ex, ax, bx, t);
+                static_for<0, ay + by + 1>([&](auto u_) {
+                    constexpr int u = IC_VALUE(u_);
+                    const double ey_ = E(ey, ay, by, u);
+                    static_for<0, az + bz + 1>([&](auto w_) {
+                        constexpr int w = IC_VALUE(w_), k = hidx(t, u, w);
+                        if constexpr (k >= K0 && k < K1) {
+                            const double ez_ = E(ez, az, bz, w);
+                            if constexpr (C == 0) D[k] += gx * ey_ * ez_;
+                            else if constexpr (C == 1) D[k] += dE[t] * ey_ * ez_;
+                            else if constexpr (C == 2) D[k] += gx * dE[u] * ez_;
+                            else D[k] += gx * ey_ * dE[w];
+                        }
+                    });
+                });
+            });
+        });
+    });
+}
+#undef IC_VALUE
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(128 * rec_split(LA + LB), 1)
+k_cl_records_tab(ClJob one, const ClJob *__restrict__ jobs, int njob, int nthr)
+{
+    constexpr int L = LA + LB, NH = nherm(L), R4 = cl_rec_floats(L) / 4, ESZ = rec_esz<LA, LB>();
+    constexpr int NAB = ncart(LA) * ncart(LB), NW = 4 * rec_split(L), KH = (NH + 1) / 2;
+    extern __shared__ double es_raw[];  // [3 axes][ESZ][32 pairs], then g_ab [NAB][32 pairs]
+    // warp w folds component w % 4 (over Hermite half w / 4 when split)
+    const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5), comp = warp & 3, half = warp >> 2;
+    const int t = min((int)blockIdx.x * 32 + lane, nthr - 1);  // the grid covers nthr exactly
+    const ClJob &J = jobs ? jobs[cl_job_by_thread(jobs, njob, t)] : one;
+    const int i = J.pp_begin + (t - J.thr0);
+    const PPLane pl = load_pp(J.bd, i, J.pp_end);  // inactive past pp_end (its density is zero)
+    if (warp < 3) {
+        // the recursion of hermite_E<LA + 1, LB> (same terms, same order) on the lane's column
+        const double pa = comp == 0 ? pl.P[0] - pl.A[0] : comp == 1 ? pl.P[1] - pl.A[1] : pl.P[2] - pl.A[2];
+        const double pb = comp == 0 ? pl.P[0] - pl.B[0] : comp == 1 ? pl.P[1] - pl.B[1] : pl.P[2] - pl.B[2];
+        const double inv2p = 0.5 * pl.ip;
+        double *col = es_raw + warp * ESZ * 32 + lane;
+        auto at = [col](int a, int b, int h) -> double & { return col[((a * (LB + 1) + b) * (L + 2) + h) * 32]; };
+        for (int q = 0; q < ESZ; ++q) col[q * 32] = 0.0;
+        at(0, 0, 0) = 1.0;
+#pragma unroll 1
+        for (int a = 0; a <= LA + 1; ++a)
+#pragma unroll 1
+            for (int b = 0; b <= LB; ++b) {
+                if (a == 0 && b == 0) continue;
+                const bool up_a = a > 0;
+                const int pa_ = up_a ? a - 1 : a, pb_ = up_a ? b : b - 1;
+                const double X = up_a ? pa : pb;
+                for (int h = 0; h <= a + b; ++h) {
+                    double e = 0.0;
+                    if (h > 0) e += inv2p * at(pa_, pb_, h - 1);
+                    if (h <= pa_ + pb_) e += X * at(pa_, pb_, h);
+                    if (h + 1 <= pa_ + pb_) e += (double)(h + 1) * at(pa_, pb_, h + 1);
+                    at(a, b, h) = e;
+                }
+            }
+    }
+    // the pair densities, shared by the four folds (loaded inside the fold, the compiler hoisted
+    // them all ahead of the sums: 100 live doubles for (f, f))
+    for (int q = warp; q < NAB; q += NW)
+        es_raw[(3 * ESZ + q) * 32 + lane] = pair_density(pl, J.bd, J.dm, q / ncart(LB), q % ncart(LB));
+    __syncthreads();
+    const double *es = es_raw + lane;
+    double D[NH];
+    constexpr int K1A = rec_split(L) > 1 ? KH : NH;
+    if (half == 0) {
+        if (comp == 0) rec_fold<LA, LB, 0, 0, K1A>(pl, es, D);
+        else if (comp == 1) rec_fold<LA, LB, 1, 0, K1A>(pl, es, D);
+        else if (comp == 2) rec_fold<LA, LB, 2, 0, K1A>(pl, es, D);
+        else rec_fold<LA, LB, 3, 0, K1A>(pl, es, D);
+    } else if constexpr (rec_split(L) > 1) {
+        if (comp == 0) rec_fold<LA, LB, 0, KH, NH>(pl, es, D);
+        else if (comp == 1) rec_fold<LA, LB, 1, KH, NH>(pl, es, D);
+        else if (comp == 2) rec_fold<LA, LB, 2, KH, NH>(pl, es, D);
+        else rec_fold<LA, LB, 3, KH, NH>(pl, es, D);
+    }
+    if (!pl.active) return;
+    float4 *r = J.rec + (size_t)(i - J.pp_begin) * R4;
+    if (warp == 0) {
+        float ph[3], pl_[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) split_grid(pl.P[x] - J.rg.centre[x], ph[x], pl_[x]);
+        const long long pb = __double_as_longlong(pl.p);
+        r[0] = make_float4(ph[0], ph[1], ph[2], pl_[0]);
+        r[1] = make_float4(pl_[1], pl_[2], __int_as_float((int)(pb & 0xffffffffll)), __int_as_float((int)(pb >> 32)));
+        double *ps = J.psum + (size_t)(i - J.pp_begin) * 6;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) ps[v] = 0.0;
+    }
+    // record entry 2 + k = (D0, Dx, Dy, Dz) of Hermite index k
+    float *rf = reinterpret_cast<float *>(r + 2) + comp;
+    if (half == 0) {
+#pragma unroll
+        for (int k = 0; k < K1A; ++k) rf[4 * k] = (float)D[k];
+    } else {
+#pragma unroll
+        for (int k = KH; k < NH; ++k) rf[4 * k] = (float)D[k];
+    }
 }
 
 // CPL charges per lane (a block's tile holds CL_NT * CPL charges of one width class, lane l the
@@ -562,9 +753,22 @@ static cudaError_t launch_cl(const ClJob &one, const ClJob *jobs, int njob, int 
                              const float *boys, int nsm, cudaStream_t st)
 {
     if (nthr <= 0 || nitems <= 0) return cudaSuccess;
-    k_cl_records<LA, LB><<<(nthr + 127) / 128, 128, 0, st>>>(one, jobs, njob, nthr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if constexpr (rec_tab(LA + LB)) {
+        if (nthr % 32) return cudaErrorInvalidValue;  // every job's pairs are padded to 32
+        static bool attr = false;
+        if (!attr) {
+            if ((e = cudaFuncSetAttribute(k_cl_records_tab<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)rec_smem<LA, LB>())) != cudaSuccess)
+                return e;
+            attr = true;
+        }
+        k_cl_records_tab<LA, LB>
+            <<<nthr / 32, 128 * rec_split(LA + LB), rec_smem<LA, LB>(), st>>>(one, jobs, njob, nthr);
+    } else {
+        k_cl_records<LA, LB><<<(nthr + 127) / 128, 128, 0, st>>>(one, jobs, njob, nthr);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const float *tab = boys + (size_t)(LA + LB + 1) * BOYS_TAB_F;
     if (counter) {
         if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
