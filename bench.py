@@ -69,7 +69,7 @@ CLASS_L = [la + lb for la in range(4) for lb in range(la + 1)]  # class index la
 # path's pair records and pair gradients included), per (workload, precision), from one ncu
 # capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum); a workload or
 # precision without a capture of the current kernels reports None.
-SWEEP_TRAFFIC = {("c4", "fp64"): 153_470_720, ("c4", "mixed"): 935_563_520}
+SWEEP_TRAFFIC = {("c4", "fp64"): 153_470_720, ("c4", "mixed"): 364_729_600}
 
 
 def sweep_flops(info, adjoint):
