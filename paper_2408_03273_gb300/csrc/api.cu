@@ -202,7 +202,7 @@ struct qmmm_handle {
     DBuf<float> boys32;
     DBuf<double> centre_d;  // [3] QM centre for the kernels
     DBuf<double2> S, Spart, A, Az, atom_ph;
-    DBuf<float4> Adf, Azdf, gSdf;
+    DBuf<float4> Adf, Azdf, gSdf, atom_phdf;
     DBuf<int> err;
     DBuf<int4> tc_phase;  // tensor-core structure factor scratch (allocated on first use)
     DBuf<uint32_t> tc_bpl;
@@ -297,7 +297,7 @@ struct qmmm_handle {
         boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); atom_ph.release(); err.release();
         tc_phase.release(); tc_bpl.release(); tc_part.release(); tc_bmax.release();
         mmr_phase.release(); mmr_bpl.release(); mmr_cscale.release();
-        Adf.release(); Azdf.release(); gSdf.release();
+        Adf.release(); Azdf.release(); gSdf.release(); atom_phdf.release();
         tune_V.release(); tune_dm.release(); tune_gqm.release(); tune_gchg.release();
         oct.release(); oct_bins.release(); oct_err.release();
         qmq_P.release(); qmq_u.release(); qmq_g.release(); qmq_E.release(); qmq_F.release();
@@ -1182,7 +1182,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
             (rc = h->Spart.ensure((size_t)nd * std::max(h->ew.sf_nslice, h->ew.sf_nslice_df))) ||
             (rc = h->preal.ensure((size_t)natm * h->ew.real_nslice * 20)) ||
             (rc = h->precip.ensure((size_t)natm * h->ew.recip_nslice * 20)) || (rc = h->pr1.ensure(20 * (size_t)natm)) ||
-            (rc = h->atom_ph.ensure((size_t)natm * 3 * (2 * 56 + 1))))
+            (rc = h->atom_ph.ensure((size_t)natm * 3 * (2 * 56 + 1))) ||
+            (rc = h->atom_phdf.ensure((size_t)natm * 3 * (2 * 56 + 1))))
             return rc;
         h->ew.gfac = h->gfac.p;
         h->ew.S = h->S.p;
@@ -1190,6 +1191,7 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.preal = h->preal.p;
         h->ew.precip = h->precip.p;
         h->ew.atom_ph = h->atom_ph.p;
+        h->ew.atom_phdf = h->atom_phdf.p;
         h->ew.pr1 = h->pr1.p;
         h->ew.A = h->A.p;
         h->ew.Az = h->Az.p;

@@ -994,7 +994,7 @@ __global__ void __launch_bounds__(MMQ_CH *MMQ_WARPS) k_mm_region1(EwaldDev e, co
 
 // Phase rows of the QM atoms: ph[(j 3 + d) PHR_MAXN + idx] = exp(2 pi i n u_jd), idx = n for
 // d = 0 (n = 0..kx) and n + k_d for d = 1, 2 (n = -k_d..k_d); one sincospi per entry
-__global__ void k_atom_phases(EwaldDev e, double2 *ph)
+__global__ void k_atom_phases(EwaldDev e, double2 *ph, float4 *phdf)
 {
     const int j = blockIdx.x;
     const int kx = e.kmax[0], NY = 2 * e.kmax[1] + 1, NZ = 2 * e.kmax[2] + 1;
@@ -1005,6 +1005,7 @@ __global__ void k_atom_phases(EwaldDev e, double2 *ph)
         double sn, cs;
         sincospi(2.0 * nn * (e.qm_xyz[3 * j + d] / e.box[d]), &sn, &cs);
         ph[((size_t)j * 3 + d) * PHR_MAXN + idx] = make_double2(cs, sn);
+        if (phdf) phdf[((size_t)j * 3 + d) * PHR_MAXN + idx] = c2_pack(cs, sn);  // mixed path
     }
 }
 
@@ -1049,6 +1050,81 @@ __global__ void __launch_bounds__(256) k_multipole_sf(EwaldDev e, const double *
         Adf[k] = c2_pack(g * re, g * im);
         Azdf[k] = c2_pack(Gz * g * re, Gz * g * im);
     }
+}
+
+// Mixed path: A(G) and Az(G) as k_multipole_sf, the sum over the QM atoms in double-float
+// arithmetic on the FP32 pipes (about 44 significant bits; the mixed MM-side sum takes 34-bit
+// operands), where the FP64 kernel issues about 30 FP64 instructions per (G, atom).  The
+// multipoles of a chunk of atoms are staged in shared memory, pre-scaled by exact powers of two so
+// that Q - 1/2 G.theta.G = Q + sum_{a <= b} m_ab G_a G_b (m_aa = -theta_aa / 2, m_ab = -theta_ab).
+constexpr int MSF_CH = 64;
+__global__ void __launch_bounds__(256) k_multipole_sf_df(EwaldDev e, const double *gfac, const double *mult,
+                                                         const float4 *phdf, double2 *A, double2 *Az, float4 *Adf,
+                                                         float4 *Azdf)
+{
+    __shared__ float2 msh[MSF_CH][10];
+    const int kx = e.kmax[0], ky = e.kmax[1], kz = e.kmax[2];
+    const int NY = 2 * ky + 1, NZ = 2 * kz + 1, n = (kx + 1) * NY * NZ;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = k < n && gfac[k] != 0.0;
+    const int kk = min(k, n - 1);
+    const int nx = kk / (NY * NZ), iy = (kk / NZ) % NY, iz = kk % NZ;
+    const f2 G[3] = {f2_mul(f2_from(TWO_PI / e.box[0]), f2{(float)nx, 0.0f}),
+                     f2_mul(f2_from(TWO_PI / e.box[1]), f2{(float)(iy - ky), 0.0f}),
+                     f2_mul(f2_from(TWO_PI / e.box[2]), f2{(float)(iz - kz), 0.0f})};
+    const f2 u[6] = {f2_mul(G[0], G[0]), f2_mul(G[0], G[1]), f2_mul(G[0], G[2]),
+                     f2_mul(G[1], G[1]), f2_mul(G[1], G[2]), f2_mul(G[2], G[2])};
+    // normalised double-float from an accumulator (two-sum)
+    auto norm = [](float h, float l) {
+        const float s = h + l, v = s - h;
+        return f2{s, (h - (s - v)) + (l - v)};
+    };
+    float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
+    for (int j0 = 0; j0 < e.natm; j0 += MSF_CH) {
+        const int nj = min(MSF_CH, e.natm - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nj * 10; t += blockDim.x) {
+            const int jj = t / 10, c = t - jj * 10;
+            double v = mult[10 * (size_t)(j0 + jj) + c];
+            if (c >= 4) v *= (c == 4 || c == 7 || c == 9) ? -0.5 : -1.0;
+            const f2 f = f2_from(v);
+            msh[jj][c] = make_float2(f.h, f.l);
+        }
+        __syncthreads();
+        if (!act) continue;
+        for (int jj = 0; jj < nj; ++jj) {
+            const float2 *M = msh[jj];
+            float mh = M[0].x, ml = M[0].y;  // Q + sum m_ab G_a G_b
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f2_mac(mh, ml, f2{M[4 + c].x, M[4 + c].y}, u[c]);
+            float qh = 0.0f, ql = 0.0f;  // G.mu
+#pragma unroll
+            for (int a = 0; a < 3; ++a) f2_mac(qh, ql, f2{M[1 + a].x, M[1 + a].y}, G[a]);
+            const f2 mr = norm(mh, ml), mi = norm(qh, ql);
+            const float4 *pj = phdf + (size_t)(j0 + jj) * 3 * PHR_MAXN;
+            const c2 p = c2_mul(c2_mul(c2_from(__ldg(pj + nx)), c2_from(__ldg(pj + PHR_MAXN + iy))),
+                                c2_from(__ldg(pj + 2 * PHR_MAXN + iz)));
+            // re += c mr - s mi, im += s mr + c mi
+            f2_mac(rh, rl, p.re, mr);
+            f2_mac(rh, rl, f2_neg(p.im), mi);
+            f2_mac(ih, il, p.im, mr);
+            f2_mac(ih, il, p.re, mi);
+        }
+    }
+    if (k >= n) return;
+    if (!act) {
+        A[k] = make_double2(0.0, 0.0);
+        Az[k] = make_double2(0.0, 0.0);
+        Adf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        Azdf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const double g = gfac[k], re = f2_to(rh, rl), im = f2_to(ih, il);
+    const double Gz = TWO_PI * (iz - kz) / e.box[2];
+    A[k] = make_double2(g * re, g * im);
+    Az[k] = make_double2(Gz * g * re, Gz * g * im);
+    Adf[k] = c2_pack(g * re, g * im);
+    Azdf[k] = c2_pack(Gz * g * re, Gz * g * im);
 }
 
 // dq_i += sum_G Re[A(G) exp(-iG.R_i)],  dR_i += q_i sum_G G Im[A(G) exp(-iG.R_i)].
@@ -1318,10 +1394,15 @@ cudaError_t launch_ewald_mm(const EwaldDev &e, const double4_32a *rI, int nI, co
     }
     if (e.nmm > 0) {
         const int n = ewald_dense_size(e);
-        k_atom_phases<<<e.natm, 128, 0, st>>>(e, w.atom_ph);
+        const bool sfdf = df && w.atom_phdf && w.Adf && w.Azdf;
+        k_atom_phases<<<e.natm, 128, 0, st>>>(e, w.atom_ph, sfdf ? w.atom_phdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.atom_ph, w.A, w.Az,
-                                                         df ? w.Adf : nullptr, df ? w.Azdf : nullptr);
+        if (sfdf)
+            k_multipole_sf_df<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.atom_phdf, w.A, w.Az, w.Adf,
+                                                                w.Azdf);
+        else
+            k_multipole_sf<<<(n + 255) / 256, 256, 0, st>>>(e, w.gfac, mult, w.atom_ph, w.A, w.Az,
+                                                             df ? w.Adf : nullptr, df ? w.Azdf : nullptr);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         const MmrShape &ms = w.mms[df ? 1 : 0];
         if (w.recip == 1 && ms.supported) {

@@ -204,6 +204,7 @@ struct EwaldBuf {
     int real_nslice = 1;
     double *precip = nullptr;    // natm * recip_nslice * 20 (reciprocal part per G slice)
     double2 *atom_ph = nullptr;  // natm * 3 * (2 * 56 + 1) phase rows of the QM atoms
+    float4 *atom_phdf = nullptr; // the same rows as double-float (re.h, re.l, im.h, im.l), mixed path
     int recip_nslice = 1;
     double *pr1 = nullptr;       // natm * 20
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
