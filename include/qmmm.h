@@ -123,7 +123,10 @@ int qmmm_set_stream(qmmm_handle *h, void *stream);
  * moment integrals.  The two reciprocal Ewald sums are, on the tensor cores, exact products of
  * BF16 digit planes of fixed-point operands (QMMM_RECIP_TENSOR: 48-bit, except the mixed path's
  * MM-side sum, 34-bit, within about 1e-8 of the largest MM gradient) and on the CUDA cores FP64
- * (double-float on the mixed path, about 47 bits).  Measured error of the mixed path against
+ * (double-float on the mixed path, about 47 bits).  On the mixed path the two G sums around
+ * them, the region-II potential's reciprocal part at the QM atoms and the multipole structure
+ * factor A(G) of the MM-side sum, run in double-float arithmetic (about 44 bits; the region-II
+ * potential stays within 1e-12 of FP64).  Measured error of the mixed path against
  * FP64: 1e-7 to 8e-7 in V (relative Frobenius norm) and up to 8e-7 in the gradients
  * (max |error| / max |gradient|) on the benchmark workloads. */
 int qmmm_set_precision(qmmm_handle *h, int precision);
