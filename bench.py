@@ -546,8 +546,9 @@ def main():
 
     # launches of our kernels per step (a claim; the ncu launch list of this command confirms the
     # composition).  Per call:
-    #   set_positions: gather, region-I count/scan/fill, real-space, region-I tensors, background
-    #     sum, QM-site reciprocal, final = 9 (mixed path: + the double-float g(G) S(G) table),
+    #   set_positions: gather, region-I count/scan/fill, real-space pre-filter inputs, real-space,
+    #     region-I tensors, background sum, QM-site reciprocal, final = 10 (mixed path: + the
+    #     double-float g(G) S(G) table),
     #     plus the structure factor (tensor cores: max|q|, phases, B planes, MMA, reduction = 5;
     #     CUDA cores: kernel + slice sum = 2)
     #   vpot: one kernel per class and charge chunk + nuclear-MM term and its sum
@@ -577,7 +578,7 @@ def main():
         mm_tiles = -(-3 // cpt)
         sweep_g = ncls * ch_g * (3 if precision == q.QMMM_MIXED else 1)
         mixed = precision == q.QMMM_MIXED
-        return (9 + (1 if mixed else 0) + (5 if tensor else 2)) + (ncls * ch_f + 2 + (1 if v_maxsl > 1 else 0)) + (ncls + 1) + \
+        return (10 + (1 if mixed else 0) + (5 if tensor else 2)) + (ncls * ch_f + 2 + (1 if v_maxsl > 1 else 0)) + (ncls + 1) + \
             (2 * ncls + sweep_g + 8 + ((5 + mm_tiles) if mm_tc else 3))
 
     per_step = launches_per_step(prec)

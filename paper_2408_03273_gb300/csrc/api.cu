@@ -202,7 +202,7 @@ struct qmmm_handle {
     DBuf<float> boys32;
     DBuf<double> centre_d;  // [3] QM centre for the kernels
     DBuf<double2> S, Spart, A, Az, atom_ph;
-    DBuf<float4> Adf, Azdf, gSdf, atom_phdf;
+    DBuf<float4> Adf, Azdf, gSdf, atom_phdf, mm_filt, qm_filt;
     DBuf<int> err;
     DBuf<int4> tc_phase;  // tensor-core structure factor scratch (allocated on first use)
     DBuf<uint32_t> tc_bpl;
@@ -254,6 +254,8 @@ struct qmmm_handle {
         e.mm_q = mm_q.p;
         e.mm_beta = mm_beta.p;
         e.mm_cls = mm_cls.p;
+        e.mm_filt = mm_filt.p;
+        e.qm_filt = qm_filt.p;
         e.natm = natm;
         e.nmm = nmm;
         for (int x = 0; x < 3; ++x) {
@@ -297,7 +299,7 @@ struct qmmm_handle {
         boys32.release(); S.release(); Spart.release(); A.release(); Az.release(); atom_ph.release(); err.release();
         tc_phase.release(); tc_bpl.release(); tc_part.release(); tc_bmax.release();
         mmr_phase.release(); mmr_bpl.release(); mmr_cscale.release();
-        Adf.release(); Azdf.release(); gSdf.release(); atom_phdf.release();
+        Adf.release(); Azdf.release(); gSdf.release(); atom_phdf.release(); mm_filt.release(); qm_filt.release();
         tune_V.release(); tune_dm.release(); tune_gqm.release(); tune_gchg.release();
         oct.release(); oct_bins.release(); oct_err.release();
         qmq_P.release(); qmq_u.release(); qmq_g.release(); qmq_E.release(); qmq_F.release();
@@ -1120,7 +1122,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
             (rc = h->dR_out.ensure(3 * nm)) || (rc = h->partials.ensure(NPART)) || (rc = h->out4.ensure(8)) ||
             (rc = h->err.ensure(1)) || (rc = h->sums.ensure(2)) || (rc = h->Epart.ensure(1)) ||
             (rc = h->rI.ensure(1)) || (rc = h->rI_hi.ensure(1)) || (rc = h->rI_lo.ensure(1)) ||
-            (rc = h->rI_idx.ensure(1)) || (rc = h->gchg.ensure(4)))
+            (rc = h->rI_idx.ensure(1)) || (rc = h->gchg.ensure(4)) || (rc = h->mm_filt.ensure(nm)) ||
+            (rc = h->qm_filt.ensure((size_t)std::max(natm, 1))))
             return rc;
         CUDA_TRY(cudaMemset(h->err.p, 0, sizeof(int)));
         CUDA_TRY(cudaMemcpy(h->Zd.p, h->Z.data(), natm * sizeof(double), cudaMemcpyHostToDevice));
@@ -1192,6 +1195,8 @@ int qmmm_create(const qmmm_atom *atoms, int natm, const qmmm_shell *shells, int 
         h->ew.precip = h->precip.p;
         h->ew.atom_ph = h->atom_ph.p;
         h->ew.atom_phdf = h->atom_phdf.p;
+        h->ew.mm_filt = h->mm_filt.p;
+        h->ew.qm_filt = h->qm_filt.p;
         h->ew.pr1 = h->pr1.p;
         h->ew.A = h->A.p;
         h->ew.Az = h->Az.p;

@@ -197,22 +197,44 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double *out,
     __syncthreads();
 }
 
-// True when, with the minimum image only (no further images searched), the pair is certainly
-// farther apart than sqrt(lim2): an FP32 check in front of the FP64 evaluation.  lim2 carries a
-// margin (relative 1e-3 and 0.05 bohr) far above the FP32 rounding of the displacement, so no
-// pair the FP64 test accepts is dropped; with images beyond the minimum one it never filters.
-__device__ __forceinline__ bool far_min_image(const EwaldDev &e, double dx, double dy, double dz, float lim2)
-{
-    if (e.img[0] | e.img[1] | e.img[2]) return false;
-    const float bx = (float)e.box[0], by = (float)e.box[1], bz = (float)e.box[2];
-    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-    const float x = fx - rintf(fx / bx) * bx, y = fy - rintf(fy / by) * by, z = fz - rintf(fz / bz) * bz;
-    return x * x + y * y + z * z > lim2;
-}
+// The FP32 check in front of the FP64 evaluation of the real-space sums: with the minimum image
+// only (no further images searched), a pair farther apart than sqrt(lim2) is certainly outside
+// both ranges.  lim2 carries a margin (relative 1e-3 and 0.05 bohr) far above the FP32 rounding
+// of the positions and the displacement, so no pair the FP64 test accepts is dropped; with images
+// beyond the minimum one it never filters.
 __device__ __forceinline__ float filter_lim2(double rc, double rhat)
 {
     const double r = fmax(rc, rhat) * 1.001 + 0.05;
     return (float)(r * r);
+}
+// The same test from the FP32 positions of a QM atom (a) and a charge (c, with its squared filter
+// radius in c.w): rounding the positions to FP32 moves a displacement by a few 1e-5 bohr at most,
+// far inside the margin of filter_lim2
+__device__ __forceinline__ bool far_min_image_f(const EwaldDev &e, float4 a, float4 c)
+{
+    if (e.img[0] | e.img[1] | e.img[2]) return false;
+    const float bx = (float)e.box[0], by = (float)e.box[1], bz = (float)e.box[2];
+    const float fx = a.x - c.x, fy = a.y - c.y, fz = a.z - c.z;
+    const float x = fx - rintf(fx / bx) * bx, y = fy - rintf(fy / by) * by, z = fz - rintf(fz / bz) * bz;
+    return x * x + y * y + z * z > c.w;
+}
+
+// FP32 inputs of the real-space pre-filter, written with the positions: per MM charge its
+// position and squared filter radius (the Ewald cutoff or the Gaussian-hat range 9 sigma, with the
+// margin of filter_lim2), per QM atom its position.  The filter formed these in FP64 for every
+// (atom, charge) pair, an FP64 division among them, which made the real-space sums FP64-bound
+// over all pairs rather than over the few within the cutoff.
+__global__ void k_filter_prep(EwaldDev e, float4 *mmf, float4 *qmf)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < e.nmm) {
+        const double beta = e.mm_beta[t];
+        mmf[t] = make_float4((float)e.mm_xyz[3 * t], (float)e.mm_xyz[3 * t + 1], (float)e.mm_xyz[3 * t + 2],
+                             filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0));
+    } else if (t < e.nmm + e.natm) {
+        const int j = t - e.nmm;
+        qmf[j] = make_float4((float)e.qm_xyz[3 * j], (float)e.qm_xyz[3 * j + 1], (float)e.qm_xyz[3 * j + 2], 0.0f);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -232,6 +254,7 @@ __global__ void __launch_bounds__(256) k_phi_real(EwaldDev e, double *partial)
     const int j = blockIdx.y, nslice = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double Rx = e.qm_xyz[3 * j], Ry = e.qm_xyz[3 * j + 1], Rz = e.qm_xyz[3 * j + 2];
+    const float4 aj = e.qm_filt[j];
     const double rc2 = e.ewald_rc * e.ewald_rc;
     const int per = (e.nmm + nslice - 1) / nslice, i0 = blockIdx.x * per, i1 = min(e.nmm, i0 + per);
     double acc[20];
@@ -242,11 +265,7 @@ __global__ void __launch_bounds__(256) k_phi_real(EwaldDev e, double *partial)
     for (int base = i0; base < i1; base += 256) {
         const int i = base + threadIdx.x;
         bool cand = false;
-        if (i < i1) {
-            const double beta = e.mm_beta[i];
-            cand = !far_min_image(e, Rx - e.mm_xyz[3 * i], Ry - e.mm_xyz[3 * i + 1], Rz - e.mm_xyz[3 * i + 2],
-                                  filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0));
-        }
+        if (i < i1) cand = !far_min_image_f(e, aj, __ldg(e.mm_filt + i));
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (lane == 0) wcnt[warp] = __popc(bal);
         __syncthreads();
@@ -764,6 +783,11 @@ cudaError_t launch_ewald_phi(const EwaldDev &e, const double4_32a *rI, int nI, c
                              bool df, cudaStream_t st)
 {
     cudaError_t err;
+    // FP32 inputs of the real-space pre-filters (here and in the forces' MM-side sum)
+    if (e.nmm + e.natm > 0) {
+        k_filter_prep<<<(e.nmm + e.natm + 255) / 256, 256, 0, st>>>(e, w.mm_filt, w.qm_filt);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
     // sum of MM charges (background)
     if ((err = launch_sum(e.mm_q, e.nmm, w.sums, st)) != cudaSuccess) return err;
     // real space
@@ -881,12 +905,8 @@ __global__ void __launch_bounds__(256) k_mm_real(EwaldDev e, const double *mult,
         const int t = base + threadIdx.x;
         bool cand = false;
         if (t < npairs) {
-            const int il = t / natm, j = t - il * natm, i = c0 + il;
-            const double beta = e.mm_beta[i];
-            cand = !far_min_image(e, __ldg(e.qm_xyz + 3 * j) - e.mm_xyz[3 * i],
-                                  __ldg(e.qm_xyz + 3 * j + 1) - e.mm_xyz[3 * i + 1],
-                                  __ldg(e.qm_xyz + 3 * j + 2) - e.mm_xyz[3 * i + 2],
-                                  filter_lim2(e.ewald_rc, beta > 0.0 ? 9.0 / beta : 0.0));
+            const int il = t / natm, j = t - il * natm;
+            cand = !far_min_image_f(e, __ldg(e.qm_filt + j), __ldg(e.mm_filt + c0 + il));
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (lane == 0) wcnt[warp] = __popc(bal);

@@ -124,6 +124,8 @@ struct EwaldDev {
     const double *mm_q;         // nmm
     const double *mm_beta;      // nmm: 1/sigma (0: point charge)
     const int *mm_cls;          // nmm: sigma class
+    const float4 *mm_filt;      // nmm: FP32 position and squared pre-filter radius (real-space sums)
+    const float4 *qm_filt;      // natm: FP32 position
     int natm, nmm;
     double box[3];
     double centre[3];
@@ -205,6 +207,7 @@ struct EwaldBuf {
     double *precip = nullptr;    // natm * recip_nslice * 20 (reciprocal part per G slice)
     double2 *atom_ph = nullptr;  // natm * 3 * (2 * 56 + 1) phase rows of the QM atoms
     float4 *atom_phdf = nullptr; // the same rows as double-float (re.h, re.l, im.h, im.l), mixed path
+    float4 *mm_filt = nullptr, *qm_filt = nullptr;  // written with the positions (EwaldDev copies)
     int recip_nslice = 1;
     double *pr1 = nullptr;       // natm * 20
     double2 *A = nullptr;        // dense multipole structure factor times 2 g(G)
