@@ -278,11 +278,16 @@ def run_reference(args):
     value = float(np.mean([v["value"] for v in vals]))
     import oracle  # noqa: F401
     nI = len(__import__("oracle").region1(s)[0])
+    nsp = SCREENED_SHELL_PAIRS.get(args.config)
+    # the same workload description and config keys as the GPU arm's line
+    workload = (describe(s, {"n_shell_pairs": nsp, "n_region1": nI}) if nsp is not None else
+                f"{s.name} ({s.natm} QM atoms, {s.nao} AOs, {s.nmm} MM charges, {nI} region-I)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{s.name} ({s.natm} QM atoms, {s.nao} AOs, {s.nmm} MM charges, {nI} region-I)",
-                      "precision": "fp64", "parallelism": "replicas"},
+           "config": {"workload": workload, "precision": "fp64",
+                      "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+                      "units_per_step": (nsp * nI) if nsp is not None else None},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
