@@ -194,8 +194,9 @@ def cpu_baseline(s, seconds=12.0, seed=0, n_shell_pairs=None):
       * region-II potential at the QM sites (real-space + reciprocal Ewald, region-I and Gaussian
         corrections): a random subset of the MM charges;
       * the MM-side Ewald derivatives (dE/dq, dE/dR_MM): a random subset of the MM charges.
-    The Pulay and QM tensor-gradient terms (O(shell pairs) moment derivatives, O(natm)) are not
-    timed.  Same per-(shell pair, charge) unit as the GPU metric."""
+      * the Pulay term (moment derivatives): the same shell subset; the QM tensor gradient (O(natm)):
+        the whole system.
+    Same per-(shell pair, charge) unit as the GPU metric."""
     import oracle
     rng = np.random.default_rng(seed)
     cores = os.cpu_count()
@@ -230,6 +231,16 @@ def cpu_baseline(s, seconds=12.0, seed=0, n_shell_pairs=None):
     M_sub = oracle.multipoles(sub_s)
     t_mult_s = time.perf_counter() - t0
     t_mult = t_mult_s * npairs / (nsh * (nsh + 1) // 2)
+    # the Pulay term (moment derivatives, per shell pair) on the same subset, and the QM tensor
+    # gradient (per QM atom) on the whole system; their cost does not depend on the values
+    phi_r = rng.standard_normal((s.natm, 20))
+    t0 = time.perf_counter()
+    oracle.pulay_grad(sub_s, phi_r)
+    t_pul_s = time.perf_counter() - t0
+    t_pulay = t_pul_s * npairs / (nsh * (nsh + 1) // 2)
+    t0 = time.perf_counter()
+    oracle.tensor_grad_qm(s, M_sub, phi_r)
+    t_tg = time.perf_counter() - t0
     del M_sub
 
     # region-II potential at the QM sites, on a charge subset
@@ -249,18 +260,18 @@ def cpu_baseline(s, seconds=12.0, seed=0, n_shell_pairs=None):
     t_mm_s = time.perf_counter() - t0
     t_mm = t_mm_s * s.nmm / nmm_sub
 
-    t_step = t_region1 + t_mult + t_phi + t_mm
-    sampled = t_pairs + t_mult_s + t_phi_s + t_mm_s
+    t_step = t_region1 + t_mult + t_pulay + t_tg + t_phi + t_mm
+    sampled = t_pairs + t_mult_s + t_pul_s + t_tg + t_phi_s + t_mm_s
     return {"value": units / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"whole V+forces step estimated from bounded samples ({sampled:.1f} s of oracle time): "
                        f"V + adjoint on {n_pairs} random shell pairs x {nI} region-I charges ({t_region1:.0f} s "
                        f"scaled), moments/multipoles on {nsh} random shells ({t_mult:.1f} s scaled), region-II "
                        f"potential on {nsub} random MM charges ({t_phi:.1f} s scaled), MM-side Ewald derivatives "
-                       f"on {nmm_sub} MM charges ({t_mm:.1f} s scaled); Pulay and QM tensor-gradient terms not "
-                       f"timed; FP64, OpenMP"),
+                       f"on {nmm_sub} MM charges ({t_mm:.1f} s scaled), the Pulay term on the shell subset "
+                       f"({t_pulay:.1f} s scaled) and the QM tensor gradient ({t_tg:.3f} s); FP64, OpenMP"),
             "step_s": t_step,
-            "pieces_s": {"region1_v_adjoint": t_region1, "multipoles": t_mult, "region2_potential": t_phi,
-                         "mm_ewald_derivatives": t_mm}}
+            "pieces_s": {"region1_v_adjoint": t_region1, "multipoles": t_mult, "pulay": t_pulay,
+                         "qm_tensor_gradient": t_tg, "region2_potential": t_phi, "mm_ewald_derivatives": t_mm}}
 
 
 def run_reference(args):

@@ -311,6 +311,23 @@ def multipole_energy(M, phi) -> float:
 # composed energy and gradient
 # ----------------------------------------------------------------------------------------------
 
+def pulay_grad(s, phi, dm=None, ncomp: int = 20) -> np.ndarray:
+    """The multipoles' dependence on the basis-function centres (the Pulay term of Eq. 15):
+    dE/dR_QM of sum_j phi_j . (Q, mu, theta)_j at fixed density, phi[natm, ncomp] the potential
+    components the multipoles meet (20: the region-II potential; 10: the QM image potential)."""
+    dm = _d(s.dm if dm is None else dm)
+    g = np.zeros((s.natm, 3))
+    lib().oracle_pulay(*_Basis(s).args(), _dp(_d(s.atom_xyz)), _dp(_d(phi)), ncomp, s.nao, _dp(dm), _dp(g))
+    return g
+
+
+def tensor_grad_qm(s, M, phi) -> np.ndarray:
+    """dE/dR_QM from the tensors at fixed multipoles: sum_j (Q, mu, theta)_j . d phi_j / dR_j."""
+    g = np.zeros((s.natm, 3))
+    lib().oracle_tensor_grad_qm(s.natm, _dp(_d(M)), _dp(_d(phi)), _dp(g))
+    return g
+
+
 def energy(s, dm=None, mode: int = EW_ALL):
     """Energy terms of E_QM-MM at fixed density: region-I electronic and nuclear parts and the
     region-II multipole part (Eq. 6 QM-MM lines + Eq. 10)."""
@@ -357,8 +374,8 @@ def forces(s, dm=None, mode: int = EW_ALL, charge_subset=None, mm_subset=None):
     np.add.at(dq, idx, dqc)
     M = multipoles(s, dm)
     phi = ewald_phi(s, mode)
-    lib().oracle_tensor_grad_qm(s.natm, _dp(_d(M)), _dp(phi), _dp(dRqm))
-    lib().oracle_pulay(*b.args(), _dp(qm), _dp(phi), 20, s.nao, _dp(dm), _dp(dRqm))
+    dRqm += tensor_grad_qm(s, M, phi)
+    dRqm += pulay_grad(s, phi, dm)
     dq2, dR2 = ewald_mm(s, M, mode, mm_subset=mm_subset)
     return {"dE_dRqm": dRqm, "dE_dRmm": dRmm + dR2, "dE_dq": dq + dq2, "M": M, "phi": phi,
             "elec": {"dE_dRqm": elec_qm, "dE_dRmm": elec_mm, "dE_dq": elec_q}}
